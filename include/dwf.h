@@ -1,0 +1,207 @@
+/*
+ * dwf.h -- C ABI of the GB300 domain-wall fermion library.
+ *
+ * The library applies and inverts the 5D domain-wall fermion matrix of
+ * Sec. 2.2 (eq. domainwall_general, constant b and c: Shamir, Borici, Mobius)
+ * and Neff's modified matrix of Sec. 2.3 (eq. domainwall_neff), using the 4D
+ * even-odd preconditioning of eq. (even-odd_linear_equation) and CG on the
+ * normal equation (Sec. 2.3, last paragraphs).  The 4D Wilson kernel is
+ * eq. (Wilson_matrix) with mass -M0.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice     dims = {Lx, Ly, Lz, Lt}, each even and >= 2; V = Lx*Ly*Lz*Lt.
+ *             Lexicographic site index x + Lx*(y + Ly*(z + Lz*t)).
+ * Gamma basis chiral: gamma_k = [[0, -i sigma_k], [i sigma_k, 0]],
+ *             gamma_4 = [[0, 1], [1, 0]], gamma_5 = diag(1, 1, -1, -1),
+ *             P_+ = (1+gamma_5)/2 (spins 0,1), P_- = (1-gamma_5)/2 (spins 2,3).
+ * Boundaries  bc[mu] = +1 or -1 multiplies every fermion hop across the
+ *             boundary in direction mu (x, y, z, t); NULL means {1, 1, 1, -1}.
+ * Vectors     interleaved complex double (re, im), C order, x fastest:
+ *               4D field      [t][z][y][x][spin 4][colour 3]
+ *               5D field      [s][t][z][y][x][spin 4][colour 3]   (s = 1..Ls)
+ *               EO 5D field   [s][i_e][spin 4][colour 3], i_e = index of the
+ *                             even site among the even sites in lexicographic
+ *                             order ((x+y+z+t) even is "even", Sec. 2.3)
+ *               links         [mu][t][z][y][x][a][b]  (U_mu(x), 3x3 complex)
+ * Memory      unless an entry point says "host", every data pointer is a
+ *             device pointer that the caller owns, aligned to 16 bytes.  The
+ *             library never frees caller memory.  A handle owns its internal
+ *             copies (links in every precision, index tables, work vectors)
+ *             and frees them in dwf_destroy.
+ * Streams     stream is a cudaStream_t (NULL = legacy default stream).  All
+ *             device work is ordered on it; calls that return results to the
+ *             host (statistics, norms) synchronise it.  A handle must not be
+ *             used from two threads at once.
+ * Errors      every function returns a dwf_status; nothing aborts or exits.
+ *             dwf_strerror gives a static description; dwf_last_error gives
+ *             the last detailed message of the calling thread.
+ */
+#ifndef DWF_H
+#define DWF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dwf_ctx *dwf_handle;
+
+/* Sec. 2.2 (eq. domainwall_general) vs Sec. 2.3 (eq. domainwall_neff) */
+enum dwf_form { DWF_STANDARD = 0, DWF_NEFF = 1 };
+
+/* arithmetic of the device path: FP64; FP32; FP16 storage with one FP32
+ * scale per 5D site (12 complex numbers) and FP32 arithmetic */
+enum dwf_prec { DWF_F64 = 0, DWF_F32 = 1, DWF_F16 = 2 };
+
+/* DWF_OP_FULL5D: the whole 5D matrix on full-lattice 5D fields.
+ * DWF_OP_EO_PREC: D = 1 - D_ee^-1 D_eo D_oo^-1 D_oe on EO fields
+ *                 (eq. even-odd_linear_equation). */
+enum dwf_op { DWF_OP_FULL5D = 0, DWF_OP_EO_PREC = 1 };
+
+enum dwf_status {
+    DWF_OK = 0,
+    DWF_EINVAL = 1,      /* bad argument (size, pointer, alignment, enum)      */
+    DWF_ENOMEM = 2,      /* device allocation failed                           */
+    DWF_ECUDA = 3,       /* a CUDA call failed (message in dwf_last_error)      */
+    DWF_ENOTCONV = 4,    /* max_iter reached; x holds the best iterate          */
+    DWF_ENONFINITE = 5,  /* NaN or Inf met in the input or the iteration         */
+    DWF_ETIMEOUT = 6,    /* a bounded device-side wait gave up                  */
+    DWF_EBREAKDOWN = 7,  /* CG breakdown (p^dag A p <= 0)                        */
+    DWF_ENOGAUGE = 8     /* dwf_set_gauge has not been called                    */
+};
+
+/*
+ * Create a handle for one lattice and one operator.
+ *   dims   {Lx, Ly, Lz, Lt}, each even, >= 2
+ *   Ls     fifth-dimension extent, 2 <= Ls <= 32
+ *   M0     domain-wall height (D_W = D_W(-M0), Sec. 2.2)
+ *   mf     quark mass m of the corner blocks
+ *   b, c   D_+ = b D_W + 1, D_- = c D_W - 1 (the same for every s)
+ *   form   DWF_STANDARD or DWF_NEFF
+ *   alpha  Neff parameter (ignored for DWF_STANDARD), alpha != 0
+ *   bc     fermion boundary phases or NULL
+ * The handle selects the current CUDA device at creation and uses it.
+ * Fails with DWF_EINVAL when the 5D operator's site-local block
+ * (D_ee, Sec. 2.3) is singular.
+ */
+int dwf_create(const int dims[4], int Ls, double M0, double mf, double b, double c,
+               int form, double alpha, const int bc[4], dwf_handle *out);
+int dwf_destroy(dwf_handle h);
+const char *dwf_strerror(int status);
+const char *dwf_last_error(void);
+
+/* Copy the links (device, layout above) into the handle: the boundary phases
+ * are folded in and an internal copy in FP64, FP32 and FP16 is made for each
+ * output parity.  Must be called before any operator call. */
+int dwf_set_gauge(dwf_handle h, const void *U, void *stream);
+
+/*
+ * out = D in (dwf_apply) or out = D^dag in (dwf_apply_dag), D the handle's
+ * form, in precision prec.  op = DWF_OP_FULL5D: in/out are 5D fields (the
+ * whole matrix of Sec. 2.2 or 2.3).  op = DWF_OP_EO_PREC: in/out are EO 5D
+ * fields and D is the even-odd preconditioned matrix.  in and out must not
+ * overlap.  Input and output are always complex double; prec selects the
+ * device arithmetic.
+ */
+int dwf_apply(dwf_handle h, int op, int prec, const void *in, void *out, void *stream);
+int dwf_apply_dag(dwf_handle h, int op, int prec, const void *in, void *out, void *stream);
+
+/* b5 = (-D_-) P^dag (0, ..., 0, b4)^T  (Sec. 2.3, with D_- = diag_s(c D_W - 1)):
+ * b5(s=1) = (1 - c D_W) P_+ b4, b5(s=Ls) = (1 - c D_W) P_- b4, zero elsewhere.
+ * b4 is a 4D field, b5 a 5D field.  FP64. */
+int dwf_source_5d(dwf_handle h, const void *b4, void *b5, void *stream);
+
+/* x4 = [P^dag x5]_{s=1} = P_- x5(s=1) + P_+ x5(s=Ls)  (Sec. 2.3 and the 4D
+ * quark field of Sec. 2.2).  The same formula holds for both forms. */
+int dwf_project_4d(dwf_handle h, const void *x5, void *x4, void *stream);
+
+/* ---------------------------------------------------------------- solver */
+typedef struct {
+    double tol;         /* target ||b5 - D x5|| / ||b5|| of the full 5D system
+                           (checked in FP64 at the end); default 1e-10          */
+    int max_iter;       /* cap on inner CG iterations; default 20000            */
+    int inner_prec;     /* DWF_F64 (plain FP64 CG), DWF_F32 or DWF_F16; the
+                           outer residuals and corrections are always FP64     */
+    double delta;       /* reliable-update trigger: recompute the FP64 residual
+                           when the inner residual fell by this factor; 0.1    */
+    int check_every;    /* inner iterations between host convergence checks;
+                           they are captured as one CUDA graph; default 16     */
+    int use_graph;      /* 1: replay the inner iterations as a CUDA graph       */
+    int precond;        /* 0 none; 1 learned network (dwf_precond_*), FCG       */
+    int use_initial_guess; /* 1: x5 holds the initial guess on entry; 0: zero   */
+    int verbose;        /* 0 quiet                                              */
+} dwf_solve_params;
+
+typedef struct {
+    int status;               /* dwf_status of the solve                        */
+    int iterations;           /* inner CG iterations                            */
+    int reliable_updates;     /* FP64 residual recomputations                   */
+    int d_applications;       /* applications of D or D^dag (all precisions)    */
+    double true_residual;     /* ||b5 - D x5|| / ||b5||, FP64, full 5D system   */
+    double eo_residual;       /* ||b~ - D_pc x_e|| / ||b~||, FP64               */
+    double seconds;           /* wall time of the call (host clock)             */
+    double history[64];       /* eo residual at each reliable update            */
+    int n_history;
+} dwf_solve_stats;
+
+void dwf_solve_params_default(dwf_solve_params *p);
+
+/*
+ * Solve D x5 = b5 for the handle's form (5D fields, device).  Route:
+ * b~_e = D_ee^-1 (b_e - D_eo D_oo^-1 b_o); CG on D^dag D x_e = D^dag b~_e with
+ * D the even-odd matrix (inner precision as asked, FP64 reliable updates);
+ * x_o = D_oo^-1 (b_o - D_oe x_e); final FP64 residual of the full system
+ * (Sec. 2.3).  x5 is the initial guess when p->use_initial_guess is set,
+ * otherwise the initial guess is zero.  stats may be NULL.
+ * DWF_ENOTCONV: x5 holds the best iterate and stats are filled.
+ */
+int dwf_solve(dwf_handle h, const void *b5, void *x5, const dwf_solve_params *p,
+              dwf_solve_stats *stats, void *stream);
+
+/*
+ * The user-level propagator call with HOST buffers: x4 = [P^dag D^-1 b5(b4)]_{s=1}.
+ * b4_host and x4_host are host pointers to 4D fields (complex double); the
+ * call copies b4 to the device, builds b5, solves, projects and copies x4
+ * back, all on the given stream, and synchronises before returning.
+ */
+int dwf_propagator_host(dwf_handle h, const double *b4_host, double *x4_host,
+                        const dwf_solve_params *p, dwf_solve_stats *stats, void *stream);
+
+/*
+ * Solve n systems at once.  hs[i] are handles of the same lattice (they may
+ * differ in Ls, mf, b, c, form); b4[i] are 4D sources and x4[i] 4D solutions
+ * (device).  Every handle must have its gauge field set.  All systems' inner
+ * CG iterations run in shared launches: each kernel of an iteration is one
+ * launch over the (system, site-tile) work items of all systems still
+ * iterating, and the iterations are replayed as CUDA graphs.  The systems
+ * are processed in as few waves as device memory allows.  stats may be NULL or
+ * an array of n.  Returns the worst status of the systems.
+ */
+int dwf_solve_batch(dwf_handle const *hs, const void *const *b4, void *const *x4, int n,
+                    const dwf_solve_params *p, dwf_solve_stats *stats, void *stream);
+
+/* ----------------------------------------------------- introspection, tests */
+
+/* Host copy of one per-chirality fifth-direction matrix of the handle, FP64,
+ * row-major Ls x Ls.  which: 0 A5 = D_ee restricted to one chirality,
+ * 1 A5^-1, 2 B = b + c K, 3 R (Neff factor, identity for DWF_STANDARD).
+ * chirality: 0 for P_+ components, 1 for P_-. */
+int dwf_fifth_matrix(dwf_handle h, int which, int chirality, double *out_host);
+
+/* Number of device bytes the handle holds. */
+size_t dwf_device_bytes(dwf_handle h);
+
+/* Timing of one hop kernel launch in the given precision: runs the EO hop
+ * (the dominant kernel of every application of D) `reps` times on stream and
+ * writes the mean device time per launch in microseconds, measured with CUDA
+ * events on that stream, together with the kernel's algorithmic bytes per
+ * launch (inputs read once, outputs written once, links read once). */
+int dwf_time_hop(dwf_handle h, int prec, int reps, int flush_l2, double *us_per_launch,
+                 double *bytes_per_launch, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DWF_H */

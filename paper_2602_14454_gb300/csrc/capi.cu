@@ -1,0 +1,455 @@
+// C ABI: handle life cycle, link upload, operator application, 4D <-> 5D maps.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "dwf_internal.h"
+
+using namespace dwf;
+
+namespace {
+thread_local std::string g_last_error;
+
+int default_sb(int Ls)
+{
+    int sb = 128 / Ls;
+    if (Ls == 12) sb = 8;
+    if (sb < 1) sb = 1;
+    return sb;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+}  // namespace
+
+int dwf_set_error(int status, const std::string &msg)
+{
+    g_last_error = msg;
+    return status;
+}
+
+int dwf_cuda_error(cudaError_t e, const char *where)
+{
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? DWF_ENOMEM : DWF_ECUDA;
+}
+
+#define CK(call)                                                      \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return dwf_cuda_error(e_, #call);      \
+    } while (0)
+
+// ------------------------------------------------------------- dwf_ctx
+const void *dwf_ctx::mat(int prec, int id) const
+{
+    const size_t per = (size_t)2 * Ls * Ls;
+    if (prec == DWF_F64) return (const double *)mats_dev[0] + per * id;
+    return (const float *)mats_dev[1] + per * id;
+}
+
+const void *dwf_ctx::gauge_for(int prec, int out_par) const
+{
+    const size_t n = (size_t)Vh * 8 * 18 * out_par;
+    if (prec == DWF_F64) return (const double *)gauge[0] + n;
+    if (prec == DWF_F32) return (const float *)gauge[1] + n;
+    return (const __half *)gauge[2] + n;
+}
+
+void *dwf_ctx::ws(const std::string &name, size_t need, cudaError_t *err)
+{
+    auto it = work.find(name);
+    if (it != work.end() && it->second.second >= need) return it->second.first;
+    if (it != work.end()) {
+        cudaFree(it->second.first);
+        bytes -= it->second.second;
+        work.erase(it);
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (err) *err = e;
+    if (e != cudaSuccess) return nullptr;
+    work[name] = {p, need};
+    bytes += need;
+    return p;
+}
+
+FieldRef dwf_ctx::field(const std::string &name, int prec, cudaError_t *err)
+{
+    FieldRef f;
+    const size_t fb = field_bytes(prec, Vh, Ls);
+    const size_t sb = scale_bytes(prec, Vh, Ls);
+    const size_t off = (fb + 255) & ~(size_t)255;
+    char *p = (char *)ws(name + "#" + std::to_string(prec), off + sb, err);
+    if (!p) return f;
+    f.v = p;
+    f.scale = sb ? (float *)(p + off) : nullptr;
+    return f;
+}
+
+// --------------------------------------------------------------- helpers
+namespace dwf_detail {
+
+HopArgs hop_args(dwf_ctx *h, int prec, int out_par, FieldRef in, FieldRef out, int post)
+{
+    HopArgs a;
+    a.in = in;
+    a.out = out;
+    a.gauge = h->gauge_for(prec, out_par);
+    a.nbr = h->nbr_for(out_par);
+    a.Vh = h->Vh;
+    a.Ls = h->Ls;
+    a.post = h->mat(prec, post);
+    return a;
+}
+
+cudaError_t hop(dwf_ctx *h, int prec, bool dag, const HopArgs &a, cudaStream_t st)
+{
+    return launch_hop(prec, dag, a, default_sb(h->Ls), st);
+}
+
+cudaError_t mix(dwf_ctx *h, int prec, FieldRef in, FieldRef out, int id, cudaStream_t st)
+{
+    MixArgs m;
+    m.in = in;
+    m.out = out;
+    m.Vh = h->Vh;
+    m.Ls = h->Ls;
+    m.mat = h->mat(prec, id);
+    return launch_mix(prec, m, st);
+}
+
+RedArgs red(dwf_ctx *h, int op, CgScalars *scal)
+{
+    RedArgs r;
+    r.partials = h->partials;
+    r.counter = h->counter;
+    r.op = op;
+    r.scal = scal;
+    return r;
+}
+
+}  // namespace dwf_detail
+
+using namespace dwf_detail;
+
+void dwf_solver_release(dwf_ctx *h);
+
+// ------------------------------------------------------------------- ABI
+extern "C" {
+
+const char *dwf_strerror(int s)
+{
+    switch (s) {
+    case DWF_OK: return "ok";
+    case DWF_EINVAL: return "invalid argument";
+    case DWF_ENOMEM: return "out of device memory";
+    case DWF_ECUDA: return "CUDA error";
+    case DWF_ENOTCONV: return "solver did not converge";
+    case DWF_ENONFINITE: return "non-finite value";
+    case DWF_ETIMEOUT: return "bounded device wait timed out";
+    case DWF_EBREAKDOWN: return "CG breakdown";
+    case DWF_ENOGAUGE: return "gauge field not set";
+    default: return "unknown status";
+    }
+}
+
+const char *dwf_last_error(void) { return g_last_error.c_str(); }
+
+int dwf_create(const int dims[4], int Ls, double M0, double mf, double b, double c, int form, double alpha,
+               const int bc[4], dwf_handle *out)
+{
+    if (!dims || !out) return dwf_set_error(DWF_EINVAL, "dims/out is NULL");
+    *out = nullptr;
+    long long V = 1;
+    for (int k = 0; k < 4; ++k) {
+        if (dims[k] < 2 || (dims[k] & 1)) return dwf_set_error(DWF_EINVAL, "every lattice extent must be even and >= 2");
+        V *= dims[k];
+    }
+    if (V * (long long)Ls * 12 > (1LL << 40)) return dwf_set_error(DWF_EINVAL, "lattice too large");
+    if (V > (1LL << 30)) return dwf_set_error(DWF_EINVAL, "lattice too large for 32-bit site indices");
+    if (Ls < 2 || Ls > LS_MAX) return dwf_set_error(DWF_EINVAL, "Ls must be in [2, 32]");
+    if (form != DWF_STANDARD && form != DWF_NEFF) return dwf_set_error(DWF_EINVAL, "unknown form");
+    if (form == DWF_NEFF && !(alpha != 0.0 && std::isfinite(alpha)))
+        return dwf_set_error(DWF_EINVAL, "alpha must be finite and nonzero");
+    if (!std::isfinite(M0) || !std::isfinite(mf) || !std::isfinite(b) || !std::isfinite(c))
+        return dwf_set_error(DWF_EINVAL, "non-finite parameter");
+    int bcv[4] = {1, 1, 1, -1};
+    if (bc)
+        for (int k = 0; k < 4; ++k) {
+            if (bc[k] != 1 && bc[k] != -1) return dwf_set_error(DWF_EINVAL, "bc entries must be +1 or -1");
+            bcv[k] = bc[k];
+        }
+    dwf_ctx *h = new dwf_ctx();
+    for (int k = 0; k < 4; ++k) h->dims[k] = dims[k], h->bc[k] = bcv[k];
+    h->Ls = Ls;
+    h->M0 = M0;
+    h->mf = mf;
+    h->b = b;
+    h->c = c;
+    h->alpha = (form == DWF_NEFF) ? alpha : 1.0;
+    h->form = form;
+    h->V = (int)V;
+    h->Vh = (int)(V / 2);
+    std::string err;
+    if (!build_fifth_matrices(Ls, M0, mf, b, c, form, h->alpha, h->fm, err)) {
+        delete h;
+        return dwf_set_error(DWF_EINVAL, err);
+    }
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return dwf_cuda_error(e, "cudaGetDevice");
+    }
+    // matrices: [MAT_COUNT][2][Ls][Ls] transposed, FP64 and FP32
+    const size_t per = (size_t)2 * Ls * Ls;
+    std::vector<double> md(per * MAT_COUNT);
+    std::vector<float> mf32(per * MAT_COUNT);
+    for (int id = 0; id < MAT_COUNT; ++id)
+        for (int chi = 0; chi < 2; ++chi)
+            for (int s = 0; s < Ls; ++s)
+                for (int t = 0; t < Ls; ++t) {
+                    const double v = h->fm.mats[id][chi][(size_t)s * Ls + t];
+                    const size_t o = per * id + (size_t)chi * Ls * Ls + (size_t)t * Ls + s;
+                    md[o] = v;
+                    mf32[o] = (float)v;
+                }
+    auto fail = [&](cudaError_t ce, const char *w) {
+        int st = dwf_cuda_error(ce, w);
+        dwf_destroy(h);
+        return st;
+    };
+    if ((e = cudaMalloc(&h->mats_dev[0], md.size() * 8)) != cudaSuccess) return fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&h->mats_dev[1], mf32.size() * 4)) != cudaSuccess) return fail(e, "cudaMalloc");
+    if ((e = cudaMemcpy(h->mats_dev[0], md.data(), md.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e, "cudaMemcpy");
+    if ((e = cudaMemcpy(h->mats_dev[1], mf32.data(), mf32.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e, "cudaMemcpy");
+    if ((e = cudaMalloc(&h->nbr, (size_t)2 * h->Vh * 8 * sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&h->eo2lex, (size_t)2 * h->Vh * sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&h->partials, ((size_t)h->Vh + 8192) * sizeof(double))) != cudaSuccess)
+        return fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&h->counter, 64)) != cudaSuccess) return fail(e, "cudaMalloc");
+    if ((e = cudaMemset(h->counter, 0, 64)) != cudaSuccess) return fail(e, "cudaMemset");
+    if ((e = cudaMalloc(&h->scal, 8 * sizeof(CgScalars))) != cudaSuccess) return fail(e, "cudaMalloc");
+    if ((e = cudaMemset(h->scal, 0, 8 * sizeof(CgScalars))) != cudaSuccess) return fail(e, "cudaMemset");
+    if ((e = cudaMalloc(&h->one, 8)) != cudaSuccess) return fail(e, "cudaMalloc");
+    const double one = 1.0;
+    if ((e = cudaMemcpy(h->one, &one, 8, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "cudaMemcpy");
+    if ((e = launch_build_tables(h->dims, h->nbr, h->eo2lex, 0)) != cudaSuccess) return fail(e, "build_tables");
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "build_tables");
+    h->bytes = md.size() * 8 + mf32.size() * 4 + (size_t)2 * h->Vh * 9 * sizeof(int) + ((size_t)h->Vh + 8192) * 8;
+    *out = h;
+    return DWF_OK;
+}
+
+int dwf_destroy(dwf_handle h)
+{
+    if (!h) return DWF_OK;
+    dwf_solver_release(h);
+    for (auto &kv : h->work) cudaFree(kv.second.first);
+    h->work.clear();
+    for (int k = 0; k < 3; ++k) {
+        if (h->mats_dev[k]) cudaFree(h->mats_dev[k]);
+        if (h->gauge[k]) cudaFree(h->gauge[k]);
+    }
+    if (h->nbr) cudaFree(h->nbr);
+    if (h->eo2lex) cudaFree(h->eo2lex);
+    if (h->partials) cudaFree(h->partials);
+    if (h->counter) cudaFree(h->counter);
+    if (h->scal) cudaFree(h->scal);
+    if (h->one) cudaFree(h->one);
+    delete h;
+    return DWF_OK;
+}
+
+int dwf_set_gauge(dwf_handle h, const void *U, void *stream)
+{
+    if (!h || !U) return dwf_set_error(DWF_EINVAL, "NULL handle or links");
+    if (!aligned16(U)) return dwf_set_error(DWF_EINVAL, "links must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)2 * h->Vh * 8 * 18;
+    const size_t sz[3] = {n * 8, n * 4, n * 2};
+    for (int k = 0; k < 3; ++k)
+        if (!h->gauge[k]) {
+            CK(cudaMalloc(&h->gauge[k], sz[k]));
+            h->bytes += sz[k];
+        }
+    CK(launch_pack_gauge((const double *)U, h->dims, h->bc, h->eo2lex, h->nbr, h->gauge[0], h->gauge[1],
+                         h->gauge[2], st));
+    h->has_gauge = true;
+    return DWF_OK;
+}
+
+static int check_common(dwf_handle h, int prec, const void *in, const void *out)
+{
+    if (!h) return dwf_set_error(DWF_EINVAL, "NULL handle");
+    if (!h->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
+    if (prec != DWF_F64 && prec != DWF_F32 && prec != DWF_F16) return dwf_set_error(DWF_EINVAL, "bad precision");
+    if (!in || !out) return dwf_set_error(DWF_EINVAL, "NULL vector");
+    if (!aligned16(in) || !aligned16(out)) return dwf_set_error(DWF_EINVAL, "vectors must be 16-byte aligned");
+    return DWF_OK;
+}
+
+static int apply_impl(dwf_handle h, int op, int prec, const void *in, void *out, bool dag, cudaStream_t st)
+{
+    int rc = check_common(h, prec, in, out);
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    if (op == DWF_OP_FULL5D) {
+        FieldRef xe = h->field("ap_xe", prec, &e), xo = h->field("ap_xo", prec, &e);
+        FieldRef ye = h->field("ap_ye", prec, &e), yo = h->field("ap_yo", prec, &e);
+        FieldRef he = h->field("ap_he", prec, &e), ho = h->field("ap_ho", prec, &e);
+        if (!xe.v || !xo.v || !ye.v || !yo.v || !he.v || !ho.v) return dwf_cuda_error(e, "workspace");
+        CK(launch_pack_full(prec, (const double *)in, xe, xo, h->eo2lex, h->Vh, h->V, h->Ls, st));
+        if (!dag) {
+            CK(mix(h, prec, xe, he, MAT_P, st));
+            CK(mix(h, prec, xo, ho, MAT_P, st));
+            for (int par = 0; par < 2; ++par) {
+                HopArgs a = hop_args(h, prec, par, par ? he : ho, par ? yo : ye, MAT_NHALF);
+                a.y = par ? xo : xe;
+                a.ymode = 2;
+                a.ymat = h->mat(prec, MAT_A5R);
+                CK(hop(h, prec, false, a, st));
+            }
+        } else {
+            for (int par = 0; par < 2; ++par) {
+                HopArgs a = hop_args(h, prec, par, par ? xe : xo, par ? yo : ye, MAT_NHALF_RBT);
+                a.y = par ? xo : xe;
+                a.ymode = 2;
+                a.ymat = h->mat(prec, MAT_RA5T);
+                CK(hop(h, prec, true, a, st));
+            }
+        }
+        CK(launch_unpack_full(prec, ye, yo, (double *)out, h->eo2lex, h->Vh, h->V, h->Ls, st));
+        return DWF_OK;
+    }
+    if (op == DWF_OP_EO_PREC) {
+        FieldRef x = h->field("ap_xe", prec, &e), xh = h->field("ap_he", prec, &e);
+        FieldRef t = h->field("ap_ho", prec, &e), y = h->field("ap_ye", prec, &e);
+        if (!x.v || !xh.v || !t.v || !y.v) return dwf_cuda_error(e, "workspace");
+        CK(launch_pack_eo(prec, (const double *)in, x, h->Vh, h->Ls, st));
+        CK(mix(h, prec, x, xh, dag ? MAT_QT : MAT_P, st));
+        HopArgs a1 = hop_args(h, prec, 1, xh, t, dag ? MAT_MT : MAT_M);
+        CK(hop(h, prec, dag, a1, st));
+        HopArgs a2 = hop_args(h, prec, 0, t, y, dag ? MAT_NPT4 : MAT_NQ4);
+        a2.y = x;
+        a2.ymode = 1;
+        CK(hop(h, prec, dag, a2, st));
+        CK(launch_unpack_eo(prec, y, (double *)out, h->Vh, h->Ls, st));
+        return DWF_OK;
+    }
+    return dwf_set_error(DWF_EINVAL, "unknown operator");
+}
+
+int dwf_apply(dwf_handle h, int op, int prec, const void *in, void *out, void *stream)
+{
+    return apply_impl(h, op, prec, in, out, false, (cudaStream_t)stream);
+}
+
+int dwf_apply_dag(dwf_handle h, int op, int prec, const void *in, void *out, void *stream)
+{
+    return apply_impl(h, op, prec, in, out, true, (cudaStream_t)stream);
+}
+
+int dwf_source_5d(dwf_handle h, const void *b4, void *b5, void *stream)
+{
+    int rc = check_common(h, DWF_F64, b4, b5);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    double *v5 = (double *)h->ws("src_v5", (size_t)h->V * h->Ls * 24 * 8, &e);
+    FieldRef ve = h->field("ap_xe", DWF_F64, &e), vo = h->field("ap_xo", DWF_F64, &e);
+    FieldRef oe = h->field("ap_ye", DWF_F64, &e), oo = h->field("ap_yo", DWF_F64, &e);
+    if (!v5 || !ve.v || !vo.v || !oe.v || !oo.v) return dwf_cuda_error(e, "workspace");
+    CK(launch_chiral_embed((const double *)b4, v5, h->V, h->Ls, st));
+    CK(launch_pack_full(DWF_F64, v5, ve, vo, h->eo2lex, h->Vh, h->V, h->Ls, st));
+    for (int par = 0; par < 2; ++par) {
+        HopArgs a = hop_args(h, DWF_F64, par, par ? ve : vo, par ? oo : oe, MAT_SRC_POST);
+        a.y = par ? vo : ve;
+        a.ymode = 2;
+        a.ymat = h->mat(DWF_F64, MAT_SRC_Y);
+        CK(hop(h, DWF_F64, false, a, st));
+    }
+    CK(launch_unpack_full(DWF_F64, oe, oo, (double *)b5, h->eo2lex, h->Vh, h->V, h->Ls, st));
+    return DWF_OK;
+}
+
+int dwf_project_4d(dwf_handle h, const void *x5, void *x4, void *stream)
+{
+    if (!h || !x5 || !x4) return dwf_set_error(DWF_EINVAL, "NULL argument");
+    if (!aligned16(x5) || !aligned16(x4)) return dwf_set_error(DWF_EINVAL, "vectors must be 16-byte aligned");
+    CK(launch_project4d((const double *)x5, (double *)x4, h->V, h->Ls, (cudaStream_t)stream));
+    return DWF_OK;
+}
+
+int dwf_fifth_matrix(dwf_handle h, int which, int chi, double *out)
+{
+    if (!h || !out || chi < 0 || chi > 1) return dwf_set_error(DWF_EINVAL, "bad argument");
+    const std::vector<double> *m = nullptr;
+    switch (which) {
+    case 0: m = &h->fm.A5[chi]; break;
+    case 1: m = &h->fm.A5inv[chi]; break;
+    case 2: m = &h->fm.B[chi]; break;
+    case 3: m = &h->fm.R[chi]; break;
+    default: return dwf_set_error(DWF_EINVAL, "bad matrix id");
+    }
+    std::memcpy(out, m->data(), m->size() * sizeof(double));
+    return DWF_OK;
+}
+
+size_t dwf_device_bytes(dwf_handle h) { return h ? h->bytes : 0; }
+
+int dwf_time_hop(dwf_handle h, int prec, int reps, int flush_l2, double *us, double *bytes, void *stream)
+{
+    if (!h || reps < 1 || !us || !bytes) return dwf_set_error(DWF_EINVAL, "bad argument");
+    if (!h->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
+    if (prec != DWF_F64 && prec != DWF_F32 && prec != DWF_F16) return dwf_set_error(DWF_EINVAL, "bad precision");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    FieldRef in = h->field("th_in", prec, &e), out = h->field("th_out", prec, &e);
+    if (!in.v || !out.v) return dwf_cuda_error(e, "workspace");
+    CK(cudaMemsetAsync(in.v, 0x3c, field_bytes(prec, h->Vh, h->Ls), st));
+    if (in.scale) CK(cudaMemsetAsync(in.scale, 0x3f, scale_bytes(prec, h->Vh, h->Ls), st));
+    const size_t flush_bytes = (size_t)512 << 20;
+    void *flush = nullptr;
+    if (flush_l2) {
+        flush = h->ws("th_flush", flush_bytes, &e);
+        if (!flush) return dwf_cuda_error(e, "workspace");
+    }
+    HopArgs a = hop_args(h, prec, 1, in, out, MAT_M);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int w = 0; w < 3; ++w) CK(hop(h, prec, false, a, st));
+    double total_ms = 0;
+    if (flush_l2) {
+        for (int r = 0; r < reps; ++r) {
+            CK(cudaMemsetAsync(flush, r & 0xff, flush_bytes, st));
+            CK(cudaEventRecord(e0, st));
+            CK(hop(h, prec, false, a, st));
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            total_ms += ms;
+        }
+    } else {
+        CK(cudaEventRecord(e0, st));
+        for (int r = 0; r < reps; ++r) CK(hop(h, prec, false, a, st));
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        total_ms = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *us = 1000.0 * total_ms / reps;
+    const size_t link_sz = prec == DWF_F64 ? 8 : (prec == DWF_F32 ? 4 : 2);
+    *bytes = 2.0 * (double)(field_bytes(prec, h->Vh, h->Ls) + scale_bytes(prec, h->Vh, h->Ls)) +
+             (double)h->Vh * 8 * 18 * link_sz;
+    return DWF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,209 @@
+// Internal declarations of the GB300 domain-wall library (not part of the ABI).
+//
+// Data layout in device memory
+// ----------------------------
+// Every 5D field lives as two parity halves (Sec. 2.3: 4D even-odd split).
+// One half holds Vh = V/2 four-dimensional sites; each site carries Ls slices
+// of 24 reals (4 spins x 3 colours x re/im; spins 0,1 are the P_+ chirality,
+// spins 2,3 the P_- chirality).  The 24 reals of a (site, s) pair are cut into
+// G vectors of 16 bytes, and vector g of slice s of site i sits at
+//        ((i * G + g) * Ls + s)            (16-byte units)
+// so that the Ls slices of one site are adjacent: a warp that works on
+// consecutive (site, s) pairs reads 16-byte vectors that are consecutive in
+// memory (fully coalesced), and all Ls slices of a site share its links.
+//   FP64: G = 12 (double2),  FP32: G = 6 (float4),
+//   FP16: G = 3 (8 halves) plus one FP32 scale per (site, s) = max |real|.
+// Links: for each output parity p, a table [Vh][8][18 reals]: directions
+// 0..3 hold U_mu(x), directions 4..7 hold U_mu(x-mu)^dag, with the fermion
+// boundary phase folded in; FP64, FP32 and FP16 copies.
+// Neighbour table: [2][Vh][8] int32, the index (in the other parity) of x+mu
+// (d < 4) and x-mu (d >= 4).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "dwf.h"
+
+namespace dwf {
+
+constexpr int LS_MAX = 32;
+
+// Per-chirality Ls x Ls matrices of the fifth direction used by the kernels.
+// K_+ / K_- are the chirality blocks of the fifth-direction hop, B = b + cK,
+// A5 = alpha0 + beta0 K (site-local block), R = Neff factor (Sec. 2.3).
+enum MatId {
+    MAT_P = 0,       // B R                 (right factor of D_oe, D_eo)
+    MAT_PT,          // (B R)^T
+    MAT_Q,           // R^-1 A5^-1          (D_ee^-1)
+    MAT_QT,          // (R^-1 A5^-1)^T
+    MAT_M,           // B A5^-1             (= B R D_oo^-1)
+    MAT_MT,          // (B A5^-1)^T
+    MAT_A5R,         // A5 R                (D_ee)
+    MAT_RA5T,        // R A5^T              (D_ee^dag)
+    MAT_NHALF,       // -1/2
+    MAT_NHALF_RBT,   // -1/2 R B^T
+    MAT_NQ4,         // -1/4 R^-1 A5^-1
+    MAT_NPT4,        // -1/4 (B R)^T
+    MAT_ID,          // 1
+    MAT_HALF_Q,      // +1/2 R^-1 A5^-1
+    MAT_SRC_POST,    // c/2                 (hop part of 1 - c D_W, 5D source)
+    MAT_SRC_Y,       // 1 - c (4 - M0)      (diagonal part of 1 - c D_W)
+    MAT_COUNT
+};
+
+// CG scalars kept on the device (one set per system).
+struct CgScalars {
+    double gamma;   // |r|^2 of the normal-equation residual
+    double alpha;   // step length
+    double beta;    // direction update
+    double wn2;     // |D p|^2
+    double last;    // last reduction result (RED_STORE)
+    int flags;      // bit 0: breakdown, bit 1: non-finite
+    int pad;
+};
+
+enum RedOp { RED_NONE = 0, RED_STORE = 1, RED_CG_ALPHA = 2, RED_CG_BETA = 3, RED_GAMMA = 4 };
+
+// A field in internal layout; scale is non-null for FP16 fields only.
+struct FieldRef {
+    void *v = nullptr;
+    float *scale = nullptr;
+};
+
+struct RedArgs {
+    double *partials = nullptr;   // one slot per block
+    unsigned *counter = nullptr;  // zero between launches (the last block resets it)
+    int op = RED_NONE;
+    CgScalars *scal = nullptr;
+};
+
+// One launch of the even-odd hopping stencil with fused fifth-direction
+// mixing and epilogue:
+//   h      = H in                    (Wilson hop, eq. Wilson_matrix without the
+//                                     1/2 and the diagonal; DAG: gamma5 H gamma5)
+//   o      = Post h + Y y            (Post, Y per-chirality Ls x Ls; Y optional,
+//                                     ymode 1 = identity, 2 = dense)
+//   if rin: o = rin - (*ralpha) o    (residual form), and, if xacc, xacc += (*xalpha) xdir
+//   stored = zmat ? Z o : o          (the norm is taken of o)
+struct HopArgs {
+    FieldRef in, out, y, rin;
+    const void *gauge = nullptr;   // [Vh][8][18] for the output parity
+    const int *nbr = nullptr;      // [Vh][8] for the output parity
+    int Vh = 0, Ls = 0;
+    const void *post = nullptr;    // [2][Ls][Ls] transposed, compute precision
+    const void *ymat = nullptr;
+    int ymode = 0;
+    const void *zmat = nullptr;
+    const double *ralpha = nullptr;
+    void *xacc = nullptr;          // accumulator field (FP64 for FP64, else FP32)
+    FieldRef xdir;
+    const double *xalpha = nullptr;
+    RedArgs red;
+};
+
+struct MixArgs {
+    FieldRef in, out;
+    int Vh = 0, Ls = 0;
+    const void *mat = nullptr;     // [2][Ls][Ls] transposed
+};
+
+// p = r + beta p ; phat = P p   (or with init: p = r)
+struct CgUpdateArgs {
+    FieldRef r, p, phat;
+    int Vh = 0, Ls = 0;
+    const void *mat = nullptr;
+    const CgScalars *scal = nullptr;
+    int init = 0;
+};
+
+// ------------------------------------------------------------ launchers
+// prec: DWF_F64 / DWF_F32 / DWF_F16 (template dispatch inside)
+cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int sites_per_block, cudaStream_t st);
+cudaError_t launch_mix(int prec, const MixArgs &a, cudaStream_t st);
+cudaError_t launch_cg_update(int prec, const CgUpdateArgs &a, cudaStream_t st);
+
+// canonical complex-double field <-> internal halves
+// full: canon [s][lex][12 cplx]; eo: canon [s][i][12 cplx] of parity `par` only
+cudaError_t launch_pack_full(int prec, const double *canon, FieldRef even, FieldRef odd, const int *eo2lex,
+                             int Vh, int V, int Ls, cudaStream_t st);
+cudaError_t launch_unpack_full(int prec, FieldRef even, FieldRef odd, double *canon, const int *eo2lex,
+                               int Vh, int V, int Ls, cudaStream_t st);
+cudaError_t launch_pack_eo(int prec, const double *canon, FieldRef f, int Vh, int Ls, cudaStream_t st);
+cudaError_t launch_unpack_eo(int prec, FieldRef f, double *canon, int Vh, int Ls, cudaStream_t st);
+
+// precision conversion between internal fields of the same parity
+cudaError_t launch_convert(int prec_in, FieldRef in, int prec_out, FieldRef out, int Vh, int Ls, cudaStream_t st);
+// x64 += xs (xs: FP64 if xs_prec == DWF_F64 else FP32); then xs = 0
+cudaError_t launch_accum_x(double *x64, void *xs, int xs_prec, int Vh, int Ls, cudaStream_t st);
+// norm^2 of an internal field, reduced with op into scal (or partial sums)
+cudaError_t launch_norm2(int prec, FieldRef f, int Vh, int Ls, const RedArgs &red, cudaStream_t st);
+cudaError_t launch_zero(int prec, FieldRef f, int Vh, int Ls, cudaStream_t st);
+
+// gauge and index tables
+cudaError_t launch_build_tables(const int dims[4], int *nbr, int *eo2lex, cudaStream_t st);
+cudaError_t launch_pack_gauge(const double *U, const int dims[4], const int bc[4], const int *eo2lex,
+                              const int *nbr, void *g64, void *g32, void *g16, cudaStream_t st);
+
+// 4D source / projection on canonical 5D fields (FP64)
+cudaError_t launch_project4d(const double *x5, double *x4, int V, int Ls, cudaStream_t st);
+cudaError_t launch_chiral_embed(const double *b4, double *b5, int V, int Ls, cudaStream_t st);
+
+// bytes of one internal half field
+size_t field_bytes(int prec, int Vh, int Ls);
+size_t scale_bytes(int prec, int Vh, int Ls);
+
+// ------------------------------------------------------------ host side
+struct FifthMatrices {
+    int Ls;
+    // row-major Ls x Ls, per chirality (0: P_+, 1: P_-)
+    std::vector<double> A5[2], A5inv[2], B[2], R[2], Rinv[2];
+    std::vector<double> mats[MAT_COUNT][2];
+    double dee_norm2 = 0;   // spectral norm of D_ee (max over chiralities)
+};
+
+// Builds every matrix above; returns false when A5 is singular.
+bool build_fifth_matrices(int Ls, double M0, double mf, double b, double c, int form, double alpha,
+                          FifthMatrices &out, std::string &err);
+
+}  // namespace dwf
+
+// The handle.
+struct dwf_ctx {
+    int dims[4];
+    int bc[4];
+    int Ls;
+    double M0, mf, b, c, alpha;
+    int form;
+    int V, Vh;
+    int device;
+    dwf::FifthMatrices fm;
+    void *mats_dev[3] = {nullptr, nullptr, nullptr};   // double / float / float copies (F16 uses float)
+    int *nbr = nullptr;       // [2][Vh][8]
+    int *eo2lex = nullptr;    // [2][Vh]
+    void *gauge[3] = {nullptr, nullptr, nullptr};      // per precision, [2][Vh][8][18]
+    bool has_gauge = false;
+    double *partials = nullptr;
+    unsigned *counter = nullptr;
+    dwf::CgScalars *scal = nullptr;   // scratch scalars for apply/norm calls
+    double *one = nullptr;            // device constant 1.0
+    std::map<std::string, std::pair<void *, size_t>> work;
+    size_t bytes = 0;
+
+    const void *mat(int prec, int id) const;
+    const void *gauge_for(int prec, int out_par) const;
+    const int *nbr_for(int out_par) const { return nbr + (size_t)out_par * Vh * 8; }
+    // named workspace buffer (allocated on first use, grown if needed)
+    void *ws(const std::string &name, size_t bytes_needed, cudaError_t *err);
+    dwf::FieldRef field(const std::string &name, int prec, cudaError_t *err);
+};
+
+// error reporting helpers (capi.cu)
+int dwf_set_error(int status, const std::string &msg);
+int dwf_cuda_error(cudaError_t e, const char *where);

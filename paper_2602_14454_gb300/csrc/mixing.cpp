@@ -1,0 +1,179 @@
+// Host-side construction of the fifth-direction matrices (FP64).
+//
+// In the chiral basis the 5D matrix of Sec. 2.2 is
+//     D_DW = D_W (b + c K) + (1 - K),
+// where K acts on the fifth index and the chirality only (it is the operator
+// whose blocks are P_- above the diagonal, P_+ below it, and -m P_+, -m P_- in
+// the corners of eq. domainwall_general).  Per chirality K is a real Ls x Ls
+// matrix:
+//     P_+ components: (K x)_s = x_{s-1} (s > 1),  (K x)_1  = -m x_Ls
+//     P_- components: (K x)_s = x_{s+1} (s < Ls), (K x)_Ls = -m x_1
+// With D_W = (4 - M0) - H/2 (eq. Wilson_matrix, H = the hopping sum):
+//     site-local block  D_ee = D_oo = A5 = alpha0 + beta0 K,
+//                       alpha0 = b (4 - M0) + 1, beta0 = c (4 - M0) - 1,
+//     hopping blocks    D_eo = -1/2 H_eo (b + c K),  D_oe = -1/2 H_oe (b + c K).
+// Neff's matrix (eq. domainwall_neff) equals D_DW R with the site-local
+// R = P A P^dag = blockdiag_s(P_- + a P_+, a, ..., a, P_+ + a P_-)
+// (eq. relation_to_alpha=1), i.e. per chirality
+//     P_+: diag(a, ..., a, 1),   P_-: diag(1, a, ..., a).
+// Every mixing the kernels apply is a product of these small matrices.
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "dwf_internal.h"
+
+namespace dwf {
+namespace {
+
+using Mat = std::vector<double>;
+
+Mat zeros(int n) { return Mat((size_t)n * n, 0.0); }
+Mat eye(int n, double v = 1.0) {
+    Mat m = zeros(n);
+    for (int i = 0; i < n; ++i) m[(size_t)i * n + i] = v;
+    return m;
+}
+Mat mul(const Mat &a, const Mat &b, int n) {
+    Mat c = zeros(n);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            double aik = a[(size_t)i * n + k];
+            if (aik == 0.0) continue;
+            for (int j = 0; j < n; ++j) c[(size_t)i * n + j] += aik * b[(size_t)k * n + j];
+        }
+    return c;
+}
+Mat add(const Mat &a, double sa, const Mat &b, double sb) {
+    Mat c(a.size());
+    for (size_t i = 0; i < a.size(); ++i) c[i] = sa * a[i] + sb * b[i];
+    return c;
+}
+Mat scale(const Mat &a, double s) { return add(a, s, a, 0.0); }
+Mat transpose(const Mat &a, int n) {
+    Mat t = zeros(n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) t[(size_t)j * n + i] = a[(size_t)i * n + j];
+    return t;
+}
+// Gauss-Jordan with partial pivoting; false if singular.
+bool inverse(const Mat &a, int n, Mat &inv) {
+    Mat w = a;
+    inv = eye(n);
+    double amax = 0;
+    for (double v : a) amax = std::fmax(amax, std::fabs(v));
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (std::fabs(w[(size_t)r * n + col]) > std::fabs(w[(size_t)piv * n + col])) piv = r;
+        double p = w[(size_t)piv * n + col];
+        if (!(std::fabs(p) > 1e-14 * amax)) return false;
+        if (piv != col)
+            for (int j = 0; j < n; ++j) {
+                std::swap(w[(size_t)piv * n + j], w[(size_t)col * n + j]);
+                std::swap(inv[(size_t)piv * n + j], inv[(size_t)col * n + j]);
+            }
+        double ip = 1.0 / p;
+        for (int j = 0; j < n; ++j) {
+            w[(size_t)col * n + j] *= ip;
+            inv[(size_t)col * n + j] *= ip;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            double f = w[(size_t)r * n + col];
+            if (f == 0.0) continue;
+            for (int j = 0; j < n; ++j) {
+                w[(size_t)r * n + j] -= f * w[(size_t)col * n + j];
+                inv[(size_t)r * n + j] -= f * inv[(size_t)col * n + j];
+            }
+        }
+    }
+    return true;
+}
+// spectral norm by power iteration on A^T A
+double spectral_norm(const Mat &a, int n) {
+    Mat ata = mul(transpose(a, n), a, n);
+    std::vector<double> v(n, 1.0), w(n);
+    double lam = 0;
+    for (int it = 0; it < 500; ++it) {
+        double nn = 0;
+        for (int i = 0; i < n; ++i) {
+            double s = 0;
+            for (int j = 0; j < n; ++j) s += ata[(size_t)i * n + j] * v[j];
+            w[i] = s;
+            nn += s * s;
+        }
+        nn = std::sqrt(nn);
+        if (nn == 0) return 0;
+        for (int i = 0; i < n; ++i) v[i] = w[i] / nn;
+        lam = nn;
+    }
+    return std::sqrt(lam);
+}
+
+}  // namespace
+
+bool build_fifth_matrices(int Ls, double M0, double mf, double b, double c, int form, double alpha,
+                          FifthMatrices &out, std::string &err)
+{
+    const int n = Ls;
+    out.Ls = Ls;
+    const double alpha0 = b * (4.0 - M0) + 1.0;
+    const double beta0 = c * (4.0 - M0) - 1.0;
+    const double a = (form == DWF_NEFF) ? alpha : 1.0;
+    double dee = 0;
+    for (int chi = 0; chi < 2; ++chi) {
+        Mat K = zeros(n);
+        if (chi == 0) {
+            for (int s = 1; s < n; ++s) K[(size_t)s * n + (s - 1)] += 1.0;
+            K[(size_t)0 * n + (n - 1)] += -mf;
+        } else {
+            for (int s = 0; s + 1 < n; ++s) K[(size_t)s * n + (s + 1)] += 1.0;
+            K[(size_t)(n - 1) * n + 0] += -mf;
+        }
+        Mat I = eye(n);
+        Mat B = add(I, b, K, c);
+        Mat A5 = add(I, alpha0, K, beta0);
+        Mat R = eye(n, a);
+        if (chi == 0) R[(size_t)(n - 1) * n + (n - 1)] = 1.0;
+        else R[0] = 1.0;
+        Mat Rinv = zeros(n);
+        for (int i = 0; i < n; ++i) Rinv[(size_t)i * n + i] = 1.0 / R[(size_t)i * n + i];
+        Mat A5inv;
+        if (!inverse(A5, n, A5inv)) {
+            err = "fifth-direction block A5 = alpha0 + beta0 K is singular";
+            return false;
+        }
+        Mat P = mul(B, R, n);
+        Mat Q = mul(Rinv, A5inv, n);
+        Mat M = mul(B, A5inv, n);
+        Mat A5R = mul(A5, R, n);
+        out.A5[chi] = A5;
+        out.A5inv[chi] = A5inv;
+        out.B[chi] = B;
+        out.R[chi] = R;
+        out.Rinv[chi] = Rinv;
+        out.mats[MAT_P][chi] = P;
+        out.mats[MAT_PT][chi] = transpose(P, n);
+        out.mats[MAT_Q][chi] = Q;
+        out.mats[MAT_QT][chi] = transpose(Q, n);
+        out.mats[MAT_M][chi] = M;
+        out.mats[MAT_MT][chi] = transpose(M, n);
+        out.mats[MAT_A5R][chi] = A5R;
+        out.mats[MAT_RA5T][chi] = transpose(A5R, n);
+        out.mats[MAT_NHALF][chi] = eye(n, -0.5);
+        out.mats[MAT_NHALF_RBT][chi] = scale(mul(R, transpose(B, n), n), -0.5);
+        out.mats[MAT_NQ4][chi] = scale(Q, -0.25);
+        out.mats[MAT_NPT4][chi] = scale(transpose(P, n), -0.25);
+        out.mats[MAT_ID][chi] = I;
+        out.mats[MAT_HALF_Q][chi] = scale(Q, 0.5);
+        out.mats[MAT_SRC_POST][chi] = eye(n, 0.5 * c);
+        out.mats[MAT_SRC_Y][chi] = eye(n, 1.0 - c * (4.0 - M0));
+        dee = std::fmax(dee, spectral_norm(A5R, n));
+    }
+    out.dee_norm2 = dee;
+    return true;
+}
+
+}  // namespace dwf

@@ -1,0 +1,248 @@
+"""Thin ctypes binding of the C ABI in include/dwf.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``_lib/libdwf.so``; this module
+only turns torch tensors into device pointers and the current CUDA stream
+into a ``cudaStream_t``.  If the library is missing the calls fail loudly:
+there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "_lib", "libdwf.so")
+
+STANDARD, NEFF = 0, 1
+F64, F32, F16 = 0, 1, 2
+OP_FULL5D, OP_EO_PREC = 0, 1
+PREC = {"f64": F64, "f32": F32, "f16": F16, F64: F64, F32: F32, F16: F16}
+FORM = {"standard": STANDARD, "neff": NEFF, STANDARD: STANDARD, NEFF: NEFF}
+OPS = {"full": OP_FULL5D, "full5d": OP_FULL5D, "eo": OP_EO_PREC, "eo_prec": OP_EO_PREC,
+       OP_FULL5D: OP_FULL5D, OP_EO_PREC: OP_EO_PREC}
+
+STATUS = {0: "DWF_OK", 1: "DWF_EINVAL", 2: "DWF_ENOMEM", 3: "DWF_ECUDA", 4: "DWF_ENOTCONV",
+          5: "DWF_ENONFINITE", 6: "DWF_ETIMEOUT", 7: "DWF_EBREAKDOWN", 8: "DWF_ENOGAUGE"}
+
+EXPORTED = ["dwf_create", "dwf_destroy", "dwf_strerror", "dwf_last_error", "dwf_set_gauge",
+            "dwf_apply", "dwf_apply_dag", "dwf_source_5d", "dwf_project_4d",
+            "dwf_solve_params_default", "dwf_solve", "dwf_propagator_host", "dwf_solve_batch",
+            "dwf_fifth_matrix", "dwf_device_bytes", "dwf_time_hop"]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner_prec", ctypes.c_int),
+                ("delta", ctypes.c_double), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("precond", ctypes.c_int), ("use_initial_guess", ctypes.c_int), ("verbose", ctypes.c_int)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("d_applications", ctypes.c_int), ("true_residual", ctypes.c_double),
+                ("eo_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("history", ctypes.c_double * 64), ("n_history", ctypes.c_int)]
+
+    def as_dict(self):
+        return dict(status=STATUS.get(self.status, self.status), iterations=self.iterations,
+                    reliable_updates=self.reliable_updates, d_applications=self.d_applications,
+                    true_residual=self.true_residual, eo_residual=self.eo_residual, seconds=self.seconds,
+                    history=list(self.history[:self.n_history]))
+
+
+class DwfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (built by paper_2602_14454_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError("CUDA library %s is missing; build it with "
+                           "paper_2602_14454_gb300.build.build()" % _LIB_PATH)
+    L = ctypes.CDLL(_LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.dwf_create.argtypes = [ip, i, d, d, d, d, i, d, ip, ctypes.POINTER(vp)]
+    L.dwf_destroy.argtypes = [vp]
+    L.dwf_strerror.restype = ctypes.c_char_p
+    L.dwf_strerror.argtypes = [i]
+    L.dwf_last_error.restype = ctypes.c_char_p
+    L.dwf_last_error.argtypes = []
+    L.dwf_set_gauge.argtypes = [vp, vp, vp]
+    L.dwf_apply.argtypes = [vp, i, i, vp, vp, vp]
+    L.dwf_apply_dag.argtypes = [vp, i, i, vp, vp, vp]
+    L.dwf_source_5d.argtypes = [vp, vp, vp, vp]
+    L.dwf_project_4d.argtypes = [vp, vp, vp, vp]
+    L.dwf_solve_params_default.argtypes = [ctypes.POINTER(SolveParams)]
+    L.dwf_solve_params_default.restype = None
+    L.dwf_solve.argtypes = [vp, vp, vp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), vp]
+    L.dwf_propagator_host.argtypes = [vp, vp, vp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), vp]
+    L.dwf_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i,
+                                  ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), vp]
+    L.dwf_fifth_matrix.argtypes = [vp, i, i, ctypes.POINTER(ctypes.c_double)]
+    L.dwf_device_bytes.argtypes = [vp]
+    L.dwf_device_bytes.restype = ctypes.c_size_t
+    L.dwf_time_hop.argtypes = [vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]
+    _lib = L
+    return L
+
+
+def check(rc):
+    if rc != 0:
+        raise DwfError(rc, lib().dwf_last_error().decode())
+    return rc
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, dtype=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if t.dtype != torch.complex128:
+        raise TypeError("fields and links are complex128")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def default_params(**kw) -> SolveParams:
+    p = SolveParams()
+    lib().dwf_solve_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "inner_prec":
+            v = PREC[v]
+        setattr(p, k, v)
+    return p
+
+
+class Operator:
+    """One lattice, one 5D operator (standard or Neff form), one gauge field."""
+
+    def __init__(self, dims, Ls, M0, mf, b, c, form="standard", alpha=1.0, bc=None):
+        self.dims = tuple(int(x) for x in dims)
+        self.Ls = int(Ls)
+        h = ctypes.c_void_p()
+        d = (ctypes.c_int * 4)(*self.dims)
+        bcp = (ctypes.c_int * 4)(*bc) if bc is not None else None
+        check(lib().dwf_create(d, self.Ls, float(M0), float(mf), float(b), float(c), FORM[form],
+                               float(alpha), bcp, ctypes.byref(h)))
+        self._h = h
+        Lx, Ly, Lz, Lt = self.dims
+        self.site_shape = (Lt, Lz, Ly, Lx)
+        self.V = Lx * Ly * Lz * Lt
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().dwf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_gauge(self, U):
+        self._U = U
+        check(lib().dwf_set_gauge(self._h, _ptr(U), _stream()))
+
+    def _new(self, shape):
+        import torch
+        return torch.empty(shape, dtype=torch.complex128, device="cuda")
+
+    def shape5(self):
+        return (self.Ls,) + self.site_shape + (4, 3)
+
+    def shape_eo(self):
+        return (self.Ls, self.V // 2, 4, 3)
+
+    def apply(self, x, op="full", prec="f64", dag=False, out=None):
+        o = OPS[op]
+        if out is None:
+            out = self._new(x.shape)
+        fn = lib().dwf_apply_dag if dag else lib().dwf_apply
+        check(fn(self._h, o, PREC[prec], _ptr(x), _ptr(out), _stream()))
+        return out
+
+    def source_5d(self, b4, out=None):
+        if out is None:
+            out = self._new(self.shape5())
+        check(lib().dwf_source_5d(self._h, _ptr(b4), _ptr(out), _stream()))
+        return out
+
+    def project_4d(self, x5, out=None):
+        if out is None:
+            out = self._new(self.site_shape + (4, 3))
+        check(lib().dwf_project_4d(self._h, _ptr(x5), _ptr(out), _stream()))
+        return out
+
+    def solve(self, b5, x5=None, allow_notconv=False, **kw):
+        if x5 is None:
+            x5 = self._new(self.shape5())
+        p = default_params(**kw)
+        st = SolveStats()
+        rc = lib().dwf_solve(self._h, _ptr(b5), _ptr(x5), ctypes.byref(p), ctypes.byref(st), _stream())
+        if rc != 0 and not (allow_notconv and rc == 4):
+            check(rc)
+        return x5, st.as_dict()
+
+    def propagator_host(self, b4: np.ndarray, **kw):
+        b4 = np.ascontiguousarray(b4, dtype=np.complex128)
+        x4 = np.empty_like(b4)
+        p = default_params(**kw)
+        st = SolveStats()
+        rc = lib().dwf_propagator_host(self._h, b4.ctypes.data_as(ctypes.c_void_p),
+                                       x4.ctypes.data_as(ctypes.c_void_p), ctypes.byref(p),
+                                       ctypes.byref(st), _stream())
+        check(rc)
+        return x4, st.as_dict()
+
+    def fifth_matrix(self, which, chirality):
+        out = (ctypes.c_double * (self.Ls * self.Ls))()
+        check(lib().dwf_fifth_matrix(self._h, int(which), int(chirality), out))
+        return np.array(out, dtype=np.float64).reshape(self.Ls, self.Ls)
+
+    def device_bytes(self):
+        return int(lib().dwf_device_bytes(self._h))
+
+    def time_hop(self, prec="f32", reps=20, flush_l2=True):
+        us = ctypes.c_double()
+        by = ctypes.c_double()
+        check(lib().dwf_time_hop(self._h, PREC[prec], int(reps), int(bool(flush_l2)), ctypes.byref(us),
+                                 ctypes.byref(by), _stream()))
+        return us.value, by.value
+
+
+def solve_batch(ops, b4s, x4s=None, allow_notconv=False, **kw):
+    """Solve len(ops) systems (4D sources -> 4D solutions) in shared launches."""
+    import torch
+    n = len(ops)
+    if x4s is None:
+        x4s = [torch.empty_like(b) for b in b4s]
+    H = (ctypes.c_void_p * n)(*[o.handle for o in ops])
+    B = (ctypes.c_void_p * n)(*[_ptr(b).value for b in b4s])
+    X = (ctypes.c_void_p * n)(*[_ptr(x).value for x in x4s])
+    p = default_params(**kw)
+    st = (SolveStats * n)()
+    rc = lib().dwf_solve_batch(H, B, X, n, ctypes.byref(p), st, _stream())
+    if rc != 0 and not (allow_notconv and rc == 4):
+        check(rc)
+    return x4s, [s.as_dict() for s in st]

@@ -1,0 +1,149 @@
+"""Parity of the CUDA operators with the FP64 oracle, through the C ABI.
+
+FULL5D: the whole 5D matrix (eq. domainwall_general / domainwall_neff) and its
+adjoint; EO_PREC: the even-odd matrix of eq. even-odd_linear_equation and its
+adjoint; the 5D source and the 4D projection of Sec. 2.3.  Element-wise
+comparison on the same seeded inputs, in FP64 (1e-12), FP32 (1e-5) and
+FP16-with-scales (3e-3).
+"""
+
+import numpy as np
+import pytest
+
+from _util import TOL, make_pair, maxrel, rel, to_gpu, to_np
+from paper_2602_14454_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built(cuda_ok):
+    from paper_2602_14454_gb300 import build
+    build.build()
+
+
+CASES = [
+    # dims, Ls, M0, mf, b, c, form, alpha
+    ((4, 4, 4, 4), 8, 1.8, 0.04, 1.0, 0.0, "standard", 1.0),
+    ((4, 4, 4, 4), 8, 1.8, 0.04, 1.0, 0.0, "neff", 0.5),
+    ((4, 2, 6, 4), 12, 1.8, 0.01, 1.5, 0.5, "neff", 0.4),
+    ((6, 2, 2, 4), 16, 1.8, 0.01, 1.5, 0.5, "standard", 1.0),
+    ((2, 4, 4, 6), 4, 1.0, 0.1, 1.0, 1.0, "neff", 0.7),
+    ((4, 4, 2, 2), 2, 1.8, 0.2, 1.5, 0.5, "neff", 0.6),
+    ((2, 2, 2, 4), 32, 1.8, 0.005, 1.5, 0.5, "neff", 0.5),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "L%s_Ls%d_%s" % ("x".join(map(str, c[0])), c[1], c[6]))
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_full5d_apply_and_dag(case, prec):
+    dims, Ls, M0, mf, b, c, form, alpha = case
+    op, ref = make_pair(dims, Ls, M0, mf, b, c, form, alpha, seed=11)
+    x = inputs.gaussian_5d(dims, Ls, 12)
+    for dag in (False, True):
+        want = ref.apply(x, dag=dag)
+        got = to_np(op.apply(to_gpu(x), op="full", prec=prec, dag=dag))
+        assert rel(got, want) < TOL[prec], (dag, rel(got, want))
+        assert maxrel(got, want) < 10 * TOL[prec]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "L%s_Ls%d_%s" % ("x".join(map(str, c[0])), c[1], c[6]))
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_eo_prec_apply_and_dag(case, prec):
+    dims, Ls, M0, mf, b, c, form, alpha = case
+    op, ref = make_pair(dims, Ls, M0, mf, b, c, form, alpha, seed=21)
+    x = ref.to_eo(inputs.gaussian_5d(dims, Ls, 22), 0)
+    for dag in (False, True):
+        want = ref.d_pc(x, dag=dag)
+        got = to_np(op.apply(to_gpu(x), op="eo", prec=prec, dag=dag))
+        assert rel(got, want) < TOL[prec], (dag, rel(got, want))
+
+
+@pytest.mark.parametrize("bc", [(1, 1, 1, -1), (1, 1, 1, 1), (-1, 1, -1, 1)])
+def test_boundary_phases(bc):
+    dims = (4, 2, 2, 4)
+    op, ref = make_pair(dims, 6, 1.8, 0.03, 1.5, 0.5, "neff", 0.5, seed=31, bc=bc)
+    x = inputs.gaussian_5d(dims, 6, 32)
+    assert rel(to_np(op.apply(to_gpu(x), op="full", prec="f64")), ref.apply(x)) < 1e-12
+
+
+@pytest.mark.parametrize("form", ["standard", "neff"])
+def test_source_and_projection(form):
+    dims = (4, 4, 2, 4)
+    op, ref = make_pair(dims, 8, 1.8, 0.02, 1.5, 0.5, form, 0.5, seed=41)
+    b4 = inputs.gaussian_4d(dims, 42)
+    b5 = op.source_5d(to_gpu(b4))
+    assert rel(to_np(b5), ref.source_5d(b4)) < 1e-13
+    x5 = inputs.gaussian_5d(dims, 8, 43)
+    assert rel(to_np(op.project_4d(to_gpu(x5))), ref.project_4d(x5)) == 0.0
+
+
+def test_fifth_matrices_against_closed_form():
+    """A5^-1 per chirality equals the closed form of the bidiagonal-plus-corner inverse:
+    with kappa = -beta0/alpha0, on P_+ components
+    x_Ls = (sum_t kappa^(Ls-t) z_t / alpha0) / (1 + m kappa^Ls),
+    x_s = sum_{t<=s} kappa^(s-t) z_t / alpha0 - m kappa^s x_Ls."""
+    from paper_2602_14454_gb300 import dwf
+    for (Ls, M0, m, b, c) in [(8, 1.8, 0.04, 1.0, 0.0), (16, 1.8, 0.01, 1.5, 0.5), (12, 1.0, 0.1, 1.0, 1.0)]:
+        op = dwf.Operator((2, 2, 2, 2), Ls, M0, m, b, c)
+        a0, b0 = b * (4 - M0) + 1, c * (4 - M0) - 1
+        k = -b0 / a0
+        Ainv = op.fifth_matrix(1, 0)
+        for t in range(Ls):
+            z = np.zeros(Ls)
+            z[t] = 1.0
+            xl = sum(k ** (Ls - 1 - u) * z[u] / a0 for u in range(Ls)) / (1 + m * k ** Ls)
+            x = np.array([sum(k ** (s - u) * z[u] / a0 for u in range(s + 1)) - m * k ** (s + 1) * xl
+                          for s in range(Ls)])
+            assert np.abs(Ainv[:, t] - x).max() < 1e-13
+        A = op.fifth_matrix(0, 0)
+        assert np.abs(A @ Ainv - np.eye(Ls)).max() < 1e-13
+        Am = op.fifth_matrix(0, 1)
+        assert np.abs(Am @ op.fifth_matrix(1, 1) - np.eye(Ls)).max() < 1e-13
+        op.close()
+
+
+def test_adjoint_identity_full_size_f32():
+    """<y, D x> = <D^dag y, x> on the 16^3x32, Ls=16 workload (no oracle needed)."""
+    dims = (16, 16, 16, 32)
+    U = inputs.random_links(dims, 0.3, 1002)
+    op, _ = make_pair(dims, 16, 1.8, 0.01, 1.5, 0.5, "neff", 0.5, U=U)
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(5)
+    shp = (16, 65536, 4, 3)
+    x = torch.randn(shp, dtype=torch.complex128, device="cuda", generator=g)
+    y = torch.randn(shp, dtype=torch.complex128, device="cuda", generator=g)
+    for prec, tol in (("f64", 1e-13), ("f32", 1e-6)):
+        lhs = torch.vdot(y.flatten(), op.apply(x, op="eo", prec=prec).flatten())
+        rhs = torch.vdot(op.apply(y, op="eo", prec=prec, dag=True).flatten(), x.flatten())
+        assert abs((lhs - rhs) / lhs) < tol
+
+
+def test_full_size_eo_parity():
+    """EO_PREC at the full 16^3x32, Ls=16 size against the oracle (FP64 and FP32)."""
+    from oracle import dwf as orc
+    dims = (16, 16, 16, 32)
+    U = inputs.random_links(dims, 0.3, 1002)
+    op, ref = make_pair(dims, 16, 1.8, 0.01, 1.5, 0.5, "neff", 0.5, U=U)
+    x = ref.to_eo(inputs.gaussian_5d(dims, 16, 7), 0)
+    want = ref.d_pc(x)
+    for prec in ("f64", "f32"):
+        got = to_np(op.apply(to_gpu(x), op="eo", prec=prec))
+        assert rel(got, want) < TOL[prec]
+
+
+def test_errors():
+    import torch
+    from paper_2602_14454_gb300 import dwf
+    with pytest.raises(dwf.DwfError) as e:
+        dwf.Operator((3, 4, 4, 4), 8, 1.8, 0.1, 1, 0)
+    assert e.value.status == 1
+    with pytest.raises(dwf.DwfError):
+        dwf.Operator((4, 4, 4, 4), 33, 1.8, 0.1, 1, 0)
+    with pytest.raises(dwf.DwfError):
+        dwf.Operator((4, 4, 4, 4), 8, 1.8, 0.1, 1, 0, form="neff", alpha=0.0)
+    op = dwf.Operator((4, 4, 4, 4), 8, 1.8, 0.1, 1, 0)
+    x = torch.zeros((8, 4, 4, 4, 4, 4, 3), dtype=torch.complex128, device="cuda")
+    with pytest.raises(dwf.DwfError) as e:
+        op.apply(x)
+    assert e.value.status == 8

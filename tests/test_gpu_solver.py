@@ -1,0 +1,116 @@
+"""Solver parity: CUDA CG (FP64, FP32 and FP16 inner, FP64 reliable updates)
+against the FP64 oracle, through the C ABI.
+
+Checks: the full 5D true residual ||b5 - D x5|| / ||b5|| <= 1e-10 recomputed by
+the oracle; the 5D solution against the oracle's solve; the 4D solution of
+the standard and Neff forms within 1e-9 of each other and of the oracle
+(Sec. 2.3: the 4D solution does not depend on alpha); edge cases.
+"""
+
+import numpy as np
+import pytest
+
+from _util import make_pair, rel, to_gpu, to_np
+from paper_2602_14454_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+C1 = dict(dims=(4, 4, 4, 4), Ls=8, M0=1.8, mf=0.04, b=1.0, c=0.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built(cuda_ok):
+    from paper_2602_14454_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def c1_reference():
+    """Oracle solution of the 4^4 Ls=8 Shamir workload (links eps 0.5, seed 1001; source seed 2001)."""
+    U = inputs.random_links(C1["dims"], 0.5, 1001)
+    b4 = inputs.gaussian_4d(C1["dims"], 2001)
+    from oracle import dwf as orc
+    ref = orc.DWF(U, C1["dims"], C1["Ls"], C1["M0"], C1["mf"], C1["b"], C1["c"])
+    b5 = ref.source_5d(b4)
+    x5, info = ref.solve(b5, tol=1e-13)
+    return U, b4, b5, x5, ref.project_4d(x5)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("form,alpha", [("standard", 1.0), ("neff", 0.5)])
+def test_c1_solve(c1_reference, prec, form, alpha):
+    U, b4, b5, x5_ref, x4_ref = c1_reference
+    op, ref = make_pair(C1["dims"], C1["Ls"], C1["M0"], C1["mf"], C1["b"], C1["c"], form, alpha, U=U)
+    x5, st = op.solve(to_gpu(b5), inner_prec=prec, tol=1e-10)
+    x5 = to_np(x5)
+    # the oracle recomputes the residual of the full 5D system of this form
+    assert rel(ref.apply(x5), b5) <= 1e-10
+    assert st["true_residual"] <= 1e-10
+    x4 = ref.project_4d(x5)
+    assert rel(x4, x4_ref) < 1e-9
+    if form == "standard":
+        assert rel(x5, x5_ref) < 1e-8
+
+
+def test_c1_fp64_residual_history_matches_oracle(c1_reference):
+    """Plain FP64 CG on the GPU and the oracle's CGNR are the same iteration: after K
+    iterations from a zero guess both have the same eo residual ||b~ - D x_K|| / ||b~||."""
+    U, b4, b5, x5_ref, x4_ref = c1_reference
+    from oracle import dwf as orc
+    op, ref = make_pair(C1["dims"], C1["Ls"], C1["M0"], C1["mf"], C1["b"], C1["c"], "standard", 1.0, U=U)
+    bt = ref.b_tilde(b5)
+    K = 40
+    _, info = orc.cgnr(ref.d_pc, lambda v: ref.d_pc(v, dag=True), bt, tol=0.0, maxiter=K)
+    _, st = op.solve(to_gpu(b5), inner_prec="f64", max_iter=K, check_every=K, delta=1e-30,
+                     allow_notconv=True)
+    assert st["iterations"] == K
+    assert abs(st["history"][-1] / info["history"][K] - 1) < 1e-6
+
+
+def test_propagator_host_matches_device_path(c1_reference):
+    U, b4, b5, x5_ref, x4_ref = c1_reference
+    op, ref = make_pair(C1["dims"], C1["Ls"], C1["M0"], C1["mf"], C1["b"], C1["c"], "neff", 0.5, U=U)
+    x4, st = op.propagator_host(b4, inner_prec="f32")
+    assert rel(x4, x4_ref) < 1e-9
+    assert st["true_residual"] <= 1e-10
+
+
+def test_zero_source_and_nan():
+    import torch
+    from paper_2602_14454_gb300 import dwf
+    op, ref = make_pair((4, 4, 2, 2), 4, 1.8, 0.1, 1.0, 0.0, "standard", 1.0)
+    z = torch.zeros((4, 2, 2, 4, 4, 4, 3), dtype=torch.complex128, device="cuda")
+    x, st = op.solve(z)
+    assert float(x.abs().max()) == 0.0
+    z[0, 0, 0, 0, 0, 0, 0] = float("nan")
+    with pytest.raises(dwf.DwfError) as e:
+        op.solve(z)
+    assert e.value.status == 5
+
+
+def test_max_iter_returns_best_iterate():
+    from paper_2602_14454_gb300 import dwf
+    op, ref = make_pair((4, 4, 4, 4), 8, 1.8, 0.01, 1.5, 0.5, "standard", 1.0)
+    b5 = inputs.gaussian_5d((4, 4, 4, 4), 8, 3)
+    with pytest.raises(dwf.DwfError) as e:
+        op.solve(to_gpu(b5), max_iter=8, check_every=4)
+    assert e.value.status == 4
+    x5, st = op.solve(to_gpu(b5), max_iter=8, check_every=4, allow_notconv=True)
+    assert st["status"] == "DWF_ENOTCONV"
+    r = rel(ref.apply(to_np(x5)), b5)
+    assert r < 1.0 and st["iterations"] >= 8
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_c2_mixed_precision_full_size(prec):
+    """16^3x32, Ls=16 Mobius (b,c)=(1.5,0.5), M0=1.8, m=0.01, smeared links:
+    mixed-precision solve to 1e-10 true residual, checked by the oracle."""
+    w = inputs.WORKLOADS["c2_16^3x32_ls16_mobius"]
+    U = inputs.workload_links(w)
+    op, ref = make_pair(w["dims"], w["Ls"], w["M0"], w["mf"], w["b"], w["c"], "standard", 1.0, U=U)
+    b4 = inputs.gaussian_4d(w["dims"], w["src_seed"])
+    b5 = op.source_5d(to_gpu(b4))
+    x5, st = op.solve(b5, inner_prec=prec, tol=1e-10)
+    assert st["true_residual"] <= 1e-10
+    b5n = to_np(b5)
+    assert rel(ref.apply(to_np(x5)), b5n) <= 1e-10
