@@ -144,6 +144,7 @@ typedef struct {
     double seconds;           /* wall time of the call (host clock)             */
     double history[64];       /* eo residual at each reliable update            */
     int n_history;
+    long long kernel_launches; /* device kernels launched by the call           */
 } dwf_solve_stats;
 
 void dwf_solve_params_default(dwf_solve_params *p);
@@ -192,6 +193,31 @@ int dwf_fifth_matrix(dwf_handle h, int which, int chirality, double *out_host);
 
 /* Number of device bytes the handle holds. */
 size_t dwf_device_bytes(dwf_handle h);
+
+/* Number of device kernels launched through the handle since its creation
+ * (every entry point counts the kernels it launches, graph replays included). */
+long long dwf_launch_count(dwf_handle h);
+
+/* Configuration of the hop kernel in precision prec: variant 0 loads the
+ * neighbour spinors directly from global memory, variant 1 stages the
+ * neighbour sites in shared memory with TMA bulk copies; ns fifth-direction
+ * slices per thread (1, or 2 when Ls is even); sb four-dimensional sites per
+ * CTA.  -1 / 0 select the built-in defaults.  No numerical effect. */
+int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb);
+int dwf_get_hop_config(dwf_handle h, int prec, int *variant, int *ns, int *sb);
+
+/* Autotuner: times every hop configuration (both variants, ns in {1, 2},
+ * CTAs of 64 to 256 threads) on this handle's lattice with CUDA events on
+ * `stream` and keeps the fastest.  cache_path (host string, may be NULL)
+ * names a text file of earlier results keyed by device name, lattice, Ls and
+ * precision: a hit skips the timing, a miss appends the new result.  Needs
+ * the gauge field. */
+int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream);
+
+/* Synchronise `stream` and report device-side failures of earlier calls on
+ * the handle: DWF_ETIMEOUT if a bounded wait inside a kernel gave up (the
+ * flag is cleared by this call), else DWF_OK. */
+int dwf_device_status(dwf_handle h, void *stream);
 
 /* Timing of one hop kernel launch in the given precision: runs the EO hop
  * (the dominant kernel of every application of D) `reps` times on stream and

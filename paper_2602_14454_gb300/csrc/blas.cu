@@ -9,99 +9,95 @@ namespace {
 constexpr int kThreads = 256;
 
 inline int blocks_for(size_t n, int t = kThreads) { return (int)((n + t - 1) / t); }
+inline int grid_cap(size_t n) { int b = blocks_for(n); return b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b); }
 
-template <typename real>
-__device__ __forceinline__ void mix_tile2(const real *M, const real *tile, int s, int Ls, real *o)
+// Tiled kernels over (site, s) with one slice per thread: blockDim = (Ls, SB).
+inline int tile_sb(int Ls) { int sb = 128 / Ls; return sb < 1 ? 1 : sb; }
+
+// copy the [chi][t][s] matrix into shared memory as [chi][t][s] (NS = 1 layout)
+template <typename R>
+__device__ __forceinline__ void load_mat(R *dst, const void *src, int Ls)
 {
-    for (int t = 0; t < Ls; ++t) {
-        const real mu = M[t * Ls + s];
-        const real ml = M[Ls * Ls + t * Ls + s];
-        const real *h = tile + t * 24;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) o[k] += mu * h[k];
-#pragma unroll
-        for (int k = 12; k < 24; ++k) o[k] += ml * h[k];
-    }
+    const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int k = tid; k < 2 * Ls * Ls; k += nt) dst[k] = reinterpret_cast<const R *>(src)[k];
 }
-
-inline int mix_sb(int Ls) { int sb = 128 / Ls; return sb < 1 ? 1 : sb; }
 
 // out(site, s) = sum_t M[chi][s][t] in(site, t)
 template <int P>
 __global__ void __launch_bounds__(256) mix_kernel(const MixArgs a)
 {
-    typedef typename Tr<P>::real real;
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ls = a.Ls, s = threadIdx.x, j = threadIdx.y, SB = blockDim.y;
     const int site = blockIdx.x * SB + j;
     const bool active = site < a.Vh;
-    const int tstride = Ls * 24 + (sizeof(real) == 8 ? 2 : 4);
-    real *tile = reinterpret_cast<real *>(smem_raw);
-    real *mtx = tile + SB * tstride;
-    const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
-    for (int k = tid; k < 2 * Ls * Ls; k += nt) mtx[k] = reinterpret_cast<const real *>(a.mat)[k];
+    const int tstride = Ls * 12 + 2;
+    T2 *tile = reinterpret_cast<T2 *>(smem_raw);
+    R *mtx = reinterpret_cast<R *>(tile + SB * tstride);
+    load_mat<R>(mtx, a.mat, Ls);
     if (active) {
-        real v[24];
-        ld_field<P, true>(a.in, (size_t)site, s, Ls, v);
-        real *dst = tile + j * tstride + s * 24;
+        T2 v[12];
+        ld_pairs<P, true>(a.in, (size_t)site, s, Ls, v);
+        T2 *dst = tile + j * tstride + s * 12;
 #pragma unroll
-        for (int k = 0; k < 24; ++k) dst[k] = v[k];
+        for (int k = 0; k < 12; ++k) dst[k] = v[k];
     }
     __syncthreads();
     if (!active) return;
-    real o[24];
+    T2 o[1][12];
 #pragma unroll
-    for (int k = 0; k < 24; ++k) o[k] = 0;
-    mix_tile2(mtx, tile + j * tstride, s, Ls, o);
-    st_field<P>(a.out, (size_t)site, s, Ls, o);
+    for (int k = 0; k < 12; ++k) o[0][k] = p_splat((R)0);
+    mix_pairs<1>(mtx, tile + j * tstride, s, Ls, o);
+    st_pairs<P>(a.out, (size_t)site, s, Ls, o[0]);
 }
 
 // p = r + beta p (or p = r), phat = M p
 template <int P>
 __global__ void __launch_bounds__(256) cg_update_kernel(const CgUpdateArgs a)
 {
-    typedef typename Tr<P>::real real;
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ls = a.Ls, s = threadIdx.x, j = threadIdx.y, SB = blockDim.y;
     const int site = blockIdx.x * SB + j;
     const bool active = site < a.Vh;
-    const int tstride = Ls * 24 + (sizeof(real) == 8 ? 2 : 4);
-    real *tile = reinterpret_cast<real *>(smem_raw);
-    real *mtx = tile + SB * tstride;
-    const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
-    for (int k = tid; k < 2 * Ls * Ls; k += nt) mtx[k] = reinterpret_cast<const real *>(a.mat)[k];
+    const int tstride = Ls * 12 + 2;
+    T2 *tile = reinterpret_cast<T2 *>(smem_raw);
+    R *mtx = reinterpret_cast<R *>(tile + SB * tstride);
+    load_mat<R>(mtx, a.mat, Ls);
     if (active) {
-        real r[24], p[24];
-        ld_field<P, false>(a.r, (size_t)site, s, Ls, r);
+        T2 r[12], p[12];
+        ld_pairs<P, false>(a.r, (size_t)site, s, Ls, r);
         if (a.init) {
 #pragma unroll
-            for (int k = 0; k < 24; ++k) p[k] = r[k];
+            for (int k = 0; k < 12; ++k) p[k] = r[k];
         } else {
-            ld_field<P, false>(a.p, (size_t)site, s, Ls, p);
-            const real be = (real)a.scal->beta;
+            ld_pairs<P, false>(a.p, (size_t)site, s, Ls, p);
+            const T2 be = p_splat((R)a.scal->beta);
 #pragma unroll
-            for (int k = 0; k < 24; ++k) p[k] = r[k] + be * p[k];
+            for (int k = 0; k < 12; ++k) p[k] = p_fma(be, p[k], r[k]);
         }
-        st_field<P>(a.p, (size_t)site, s, Ls, p);
-        real *dst = tile + j * tstride + s * 24;
+        st_pairs<P>(a.p, (size_t)site, s, Ls, p);
+        T2 *dst = tile + j * tstride + s * 12;
 #pragma unroll
-        for (int k = 0; k < 24; ++k) dst[k] = p[k];
+        for (int k = 0; k < 12; ++k) dst[k] = p[k];
     }
     __syncthreads();
     if (!active) return;
-    real o[24];
+    T2 o[1][12];
 #pragma unroll
-    for (int k = 0; k < 24; ++k) o[k] = 0;
-    mix_tile2(mtx, tile + j * tstride, s, Ls, o);
-    st_field<P>(a.phat, (size_t)site, s, Ls, o);
+    for (int k = 0; k < 12; ++k) o[0][k] = p_splat((R)0);
+    mix_pairs<1>(mtx, tile + j * tstride, s, Ls, o);
+    st_pairs<P>(a.phat, (size_t)site, s, Ls, o[0]);
 }
 
 template <int P>
 size_t tile_smem(int Ls, int SB)
 {
-    typedef typename Tr<P>::real real;
-    const int tstride = Ls * 24 + (sizeof(real) == 8 ? 2 : 4);
-    return (size_t)(SB * tstride + 2 * Ls * Ls) * sizeof(real);
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
+    return (size_t)SB * (Ls * 12 + 2) * sizeof(T2) + (size_t)2 * Ls * Ls * sizeof(R);
 }
 
 template <int P>
@@ -109,11 +105,11 @@ cudaError_t launch_mix_t(const MixArgs &a, cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(mix_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(mix_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int SB = mix_sb(a.Ls);
+    const int SB = tile_sb(a.Ls);
     mix_kernel<P><<<(a.Vh + SB - 1) / SB, dim3(a.Ls, SB), tile_smem<P>(a.Ls, SB), st>>>(a);
     return cudaGetLastError();
 }
@@ -124,16 +120,42 @@ cudaError_t launch_cg_update_t(const CgUpdateArgs &a, cudaStream_t st)
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(cg_update_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             160 * 1024);
+                                             200 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int SB = mix_sb(a.Ls);
+    const int SB = tile_sb(a.Ls);
     cg_update_kernel<P><<<(a.Vh + SB - 1) / SB, dim3(a.Ls, SB), tile_smem<P>(a.Ls, SB), st>>>(a);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ packing
+// canonical 24 reals (spin*3 + a)*2 + c  <->  internal pairs (4g + spin, g = 2a + c)
+__device__ __forceinline__ void canon_to_pairs(const double *c, double2 *v)
+{
+    double r[24];
+#pragma unroll
+    for (int k = 0; k < 24; k += 2) {
+        const double2 q = *reinterpret_cast<const double2 *>(c + k);
+        r[k] = q.x;
+        r[k + 1] = q.y;
+    }
+#pragma unroll
+    for (int p = 0; p < 12; ++p)
+        v[p] = make_double2(r[canon_of_internal(2 * p)], r[canon_of_internal(2 * p + 1)]);
+}
+__device__ __forceinline__ void pairs_to_canon(const double2 *v, double *c)
+{
+    double r[24];
+#pragma unroll
+    for (int p = 0; p < 12; ++p) {
+        r[canon_of_internal(2 * p)] = v[p].x;
+        r[canon_of_internal(2 * p + 1)] = v[p].y;
+    }
+#pragma unroll
+    for (int k = 0; k < 24; k += 2) *reinterpret_cast<double2 *>(c + k) = make_double2(r[k], r[k + 1]);
+}
+
 // thread per (parity, eo site, s); canonical full field [s][lex][24 reals]
 template <int P>
 __global__ void pack_full_kernel(const double *canon, FieldRef even, FieldRef odd, const int *eo2lex, int Vh,
@@ -148,19 +170,13 @@ __global__ void pack_full_kernel(const double *canon, FieldRef even, FieldRef od
         const int lex = eo2lex[(size_t)par * Vh + site];
         const FieldRef &f = par ? odd : even;
         double *c = const_cast<double *>(canon) + ((size_t)s * V + lex) * 24;
-        double r[24];
+        double2 v[12];
         if (!unpack) {
-#pragma unroll
-            for (int k = 0; k < 24; k += 2) {
-                double2 q = *reinterpret_cast<const double2 *>(c + k);
-                r[k] = q.x;
-                r[k + 1] = q.y;
-            }
-            st_field<P>(f, (size_t)site, s, Ls, r);
+            canon_to_pairs(c, v);
+            st_pairs<P>(f, (size_t)site, s, Ls, v);
         } else {
-            ld_field<P, false>(f, (size_t)site, s, Ls, r);
-#pragma unroll
-            for (int k = 0; k < 24; k += 2) *reinterpret_cast<double2 *>(c + k) = make_double2(r[k], r[k + 1]);
+            ld_pairs<P, false>(f, (size_t)site, s, Ls, v);
+            pairs_to_canon(v, c);
         }
     }
 }
@@ -174,19 +190,13 @@ __global__ void pack_eo_kernel(const double *canon, FieldRef f, int Vh, int Ls, 
         const int s = (int)(idx % Ls);
         const int site = (int)(idx / Ls);
         double *c = const_cast<double *>(canon) + ((size_t)s * Vh + site) * 24;
-        double r[24];
+        double2 v[12];
         if (!unpack) {
-#pragma unroll
-            for (int k = 0; k < 24; k += 2) {
-                double2 q = *reinterpret_cast<const double2 *>(c + k);
-                r[k] = q.x;
-                r[k + 1] = q.y;
-            }
-            st_field<P>(f, (size_t)site, s, Ls, r);
+            canon_to_pairs(c, v);
+            st_pairs<P>(f, (size_t)site, s, Ls, v);
         } else {
-            ld_field<P, false>(f, (size_t)site, s, Ls, r);
-#pragma unroll
-            for (int k = 0; k < 24; k += 2) *reinterpret_cast<double2 *>(c + k) = make_double2(r[k], r[k + 1]);
+            ld_pairs<P, false>(f, (size_t)site, s, Ls, v);
+            pairs_to_canon(v, c);
         }
     }
 }
@@ -198,9 +208,9 @@ __global__ void convert_kernel(FieldRef in, FieldRef out, int Vh, int Ls)
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
         const int s = (int)(idx % Ls);
         const size_t site = idx / Ls;
-        double r[24];
-        ld_field<PI, true>(in, site, s, Ls, r);
-        st_field<PO>(out, site, s, Ls, r);
+        double2 v[12];
+        ld_pairs<PI, true>(in, site, s, Ls, v);
+        st_pairs<PO>(out, site, s, Ls, v);
     }
 }
 
@@ -215,16 +225,16 @@ __global__ void accum_x_kernel(double *x64, void *xs, int Vh, int Ls)
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
         const int s = (int)(idx % Ls);
         const size_t site = idx / Ls;
-        double x[24], d[24];
-        ld_field<DWF_F64, false>(fx, site, s, Ls, x);
-        ld_field<XP, false>(fs, site, s, Ls, d);
+        double2 x[12], d[12];
+        ld_pairs<DWF_F64, false>(fx, site, s, Ls, x);
+        ld_pairs<XP, false>(fs, site, s, Ls, d);
 #pragma unroll
-        for (int k = 0; k < 24; ++k) {
-            x[k] += d[k];
-            d[k] = 0.0;
+        for (int k = 0; k < 12; ++k) {
+            x[k] = p_add(x[k], d[k]);
+            d[k] = make_double2(0.0, 0.0);
         }
-        st_field<DWF_F64>(fx, site, s, Ls, x);
-        st_field<XP>(fs, site, s, Ls, d);
+        st_pairs<DWF_F64>(fx, site, s, Ls, x);
+        st_pairs<XP>(fs, site, s, Ls, d);
     }
 }
 
@@ -236,10 +246,10 @@ __global__ void __launch_bounds__(256) norm2_kernel(FieldRef f, int Vh, int Ls, 
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
         const int s = (int)(idx % Ls);
         const size_t site = idx / Ls;
-        double r[24];
-        ld_field<P, true>(f, site, s, Ls, r);
+        double2 v[12];
+        ld_pairs<P, true>(f, site, s, Ls, v);
 #pragma unroll
-        for (int k = 0; k < 24; ++k) acc += r[k] * r[k];
+        for (int k = 0; k < 12; ++k) acc += v[k].x * v[k].x + v[k].y * v[k].y;
     }
     grid_reduce(acc, red);
 }
@@ -354,8 +364,6 @@ __global__ void chiral_embed_kernel(const double *b4, double *v5, int V, int Ls)
     }
 }
 
-inline int grid_cap(size_t n) { int b = blocks_for(n); return b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b); }
-
 }  // namespace
 
 size_t field_bytes(int prec, int Vh, int Ls)
@@ -363,7 +371,8 @@ size_t field_bytes(int prec, int Vh, int Ls)
     const size_t n = (size_t)Vh * Ls * 24;
     return prec == DWF_F64 ? n * 8 : (prec == DWF_F32 ? n * 4 : n * 2);
 }
-size_t scale_bytes(int prec, int Vh, int Ls) { return prec == DWF_F16 ? (size_t)Vh * Ls * 4 : 0; }
+// FP16 scales: [site][Ls rounded up to 4] floats, so that one site's scales are a 16-byte multiple
+size_t scale_bytes(int prec, int Vh, int Ls) { return prec == DWF_F16 ? (size_t)Vh * ((Ls + 3) & ~3) * 4 : 0; }
 
 cudaError_t launch_mix(int prec, const MixArgs &a, cudaStream_t st)
 {
@@ -384,14 +393,6 @@ cudaError_t launch_cg_update(int prec, const CgUpdateArgs &a, cudaStream_t st)
     }
     return cudaErrorInvalidValue;
 }
-
-#define DWF_PREC_DISPATCH(prec, KER, ...)                                     \
-    switch (prec) {                                                           \
-    case DWF_F64: KER<DWF_F64><<<__VA_ARGS__>>>; break;                       \
-    case DWF_F32: KER<DWF_F32><<<__VA_ARGS__>>>; break;                       \
-    case DWF_F16: KER<DWF_F16><<<__VA_ARGS__>>>; break;                       \
-    default: return cudaErrorInvalidValue;                                    \
-    }
 
 cudaError_t launch_pack_full(int prec, const double *canon, FieldRef even, FieldRef odd, const int *eo2lex, int Vh,
                              int V, int Ls, cudaStream_t st)

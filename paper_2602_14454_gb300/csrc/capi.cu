@@ -11,14 +11,6 @@ using namespace dwf;
 namespace {
 thread_local std::string g_last_error;
 
-int default_sb(int Ls)
-{
-    int sb = 128 / Ls;
-    if (Ls == 12) sb = 8;
-    if (sb < 1) sb = 1;
-    return sb;
-}
-
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 }  // namespace
 
@@ -100,12 +92,14 @@ HopArgs hop_args(dwf_ctx *h, int prec, int out_par, FieldRef in, FieldRef out, i
     a.Vh = h->Vh;
     a.Ls = h->Ls;
     a.post = h->mat(prec, post);
+    a.err = h->errflag();
     return a;
 }
 
 cudaError_t hop(dwf_ctx *h, int prec, bool dag, const HopArgs &a, cudaStream_t st)
 {
-    return launch_hop(prec, dag, a, default_sb(h->Ls), st);
+    h->launches += 1;
+    return launch_hop(prec, dag, a, h->hop_var[prec], h->hop_ns[prec], h->hop_sb[prec], st);
 }
 
 cudaError_t mix(dwf_ctx *h, int prec, FieldRef in, FieldRef out, int id, cudaStream_t st)
@@ -116,6 +110,7 @@ cudaError_t mix(dwf_ctx *h, int prec, FieldRef in, FieldRef out, int id, cudaStr
     m.Vh = h->Vh;
     m.Ls = h->Ls;
     m.mat = h->mat(prec, id);
+    h->launches += 1;
     return launch_mix(prec, m, st);
 }
 
@@ -277,6 +272,7 @@ int dwf_set_gauge(dwf_handle h, const void *U, void *stream)
         }
     CK(launch_pack_gauge((const double *)U, h->dims, h->bc, h->eo2lex, h->nbr, h->gauge[0], h->gauge[1],
                          h->gauge[2], st));
+    h->launches += 1;
     h->has_gauge = true;
     return DWF_OK;
 }
@@ -302,6 +298,7 @@ static int apply_impl(dwf_handle h, int op, int prec, const void *in, void *out,
         FieldRef he = h->field("ap_he", prec, &e), ho = h->field("ap_ho", prec, &e);
         if (!xe.v || !xo.v || !ye.v || !yo.v || !he.v || !ho.v) return dwf_cuda_error(e, "workspace");
         CK(launch_pack_full(prec, (const double *)in, xe, xo, h->eo2lex, h->Vh, h->V, h->Ls, st));
+        h->launches += 2;   // pack + unpack below
         if (!dag) {
             CK(mix(h, prec, xe, he, MAT_P, st));
             CK(mix(h, prec, xo, ho, MAT_P, st));
@@ -329,6 +326,7 @@ static int apply_impl(dwf_handle h, int op, int prec, const void *in, void *out,
         FieldRef t = h->field("ap_ho", prec, &e), y = h->field("ap_ye", prec, &e);
         if (!x.v || !xh.v || !t.v || !y.v) return dwf_cuda_error(e, "workspace");
         CK(launch_pack_eo(prec, (const double *)in, x, h->Vh, h->Ls, st));
+        h->launches += 2;   // pack + unpack below
         CK(mix(h, prec, x, xh, dag ? MAT_QT : MAT_P, st));
         HopArgs a1 = hop_args(h, prec, 1, xh, t, dag ? MAT_MT : MAT_M);
         CK(hop(h, prec, dag, a1, st));
@@ -363,6 +361,7 @@ int dwf_source_5d(dwf_handle h, const void *b4, void *b5, void *stream)
     FieldRef oe = h->field("ap_ye", DWF_F64, &e), oo = h->field("ap_yo", DWF_F64, &e);
     if (!v5 || !ve.v || !vo.v || !oe.v || !oo.v) return dwf_cuda_error(e, "workspace");
     CK(launch_chiral_embed((const double *)b4, v5, h->V, h->Ls, st));
+    h->launches += 3;   // embed, pack, unpack
     CK(launch_pack_full(DWF_F64, v5, ve, vo, h->eo2lex, h->Vh, h->V, h->Ls, st));
     for (int par = 0; par < 2; ++par) {
         HopArgs a = hop_args(h, DWF_F64, par, par ? ve : vo, par ? oo : oe, MAT_SRC_POST);
@@ -380,6 +379,7 @@ int dwf_project_4d(dwf_handle h, const void *x5, void *x4, void *stream)
     if (!h || !x5 || !x4) return dwf_set_error(DWF_EINVAL, "NULL argument");
     if (!aligned16(x5) || !aligned16(x4)) return dwf_set_error(DWF_EINVAL, "vectors must be 16-byte aligned");
     CK(launch_project4d((const double *)x5, (double *)x4, h->V, h->Ls, (cudaStream_t)stream));
+    h->launches += 1;
     return DWF_OK;
 }
 
@@ -399,6 +399,112 @@ int dwf_fifth_matrix(dwf_handle h, int which, int chi, double *out)
 }
 
 size_t dwf_device_bytes(dwf_handle h) { return h ? h->bytes : 0; }
+
+int dwf_device_status(dwf_handle h, void *stream)
+{
+    if (!h) return dwf_set_error(DWF_EINVAL, "NULL handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, h->errflag(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (flag) {
+        CK(cudaMemsetAsync(h->errflag(), 0, sizeof(int), st));
+        CK(cudaStreamSynchronize(st));
+        return dwf_set_error(DWF_ETIMEOUT, "a bounded wait inside a hop kernel gave up");
+    }
+    return DWF_OK;
+}
+
+long long dwf_launch_count(dwf_handle h) { return h ? h->launches : 0; }
+
+int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb)
+{
+    if (!h || prec < 0 || prec > 2) return dwf_set_error(DWF_EINVAL, "bad handle or precision");
+    if (variant < -1 || variant > 1) return dwf_set_error(DWF_EINVAL, "variant must be -1, 0 or 1");
+    if (ns < 0 || ns > 2 || (ns == 2 && h->Ls % 2)) return dwf_set_error(DWF_EINVAL, "ns must be 0, 1 or 2 (2 needs even Ls)");
+    const int nsv = ns ? ns : hop_default_ns(prec, h->Ls);
+    if (sb < 0 || (sb && (h->Ls / nsv) * sb > 256)) return dwf_set_error(DWF_EINVAL, "sb out of range (CTA > 256 threads)");
+    h->hop_var[prec] = variant;
+    h->hop_ns[prec] = ns;
+    h->hop_sb[prec] = sb;
+    return DWF_OK;
+}
+
+int dwf_get_hop_config(dwf_handle h, int prec, int *variant, int *ns, int *sb)
+{
+    if (!h || prec < 0 || prec > 2 || !variant || !ns || !sb) return dwf_set_error(DWF_EINVAL, "bad argument");
+    *variant = h->hop_var[prec] >= 0 ? h->hop_var[prec] : hop_default_variant(prec);
+    *ns = h->hop_ns[prec] ? h->hop_ns[prec] : hop_default_ns(prec, h->Ls);
+    *sb = h->hop_sb[prec] ? h->hop_sb[prec] : hop_default_sb(prec, h->Ls, *ns);
+    return DWF_OK;
+}
+
+int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
+{
+    if (!h || prec < 0 || prec > 2) return dwf_set_error(DWF_EINVAL, "bad handle or precision");
+    if (!h->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, h->device));
+    char key[256];
+    std::snprintf(key, sizeof key, "%s|%dx%dx%dx%d|Ls=%d|prec=%d", prop.name, h->dims[0], h->dims[1], h->dims[2],
+                  h->dims[3], h->Ls, prec);
+    for (char *c = key; *c; ++c)
+        if (*c == ' ') *c = '_';
+    if (cache_path) {
+        FILE *f = std::fopen(cache_path, "r");
+        if (f) {
+            char k[256];
+            int var, ns, sb;
+            double us;
+            bool hit = false;
+            while (std::fscanf(f, "%255s %d %d %d %lf", k, &var, &ns, &sb, &us) == 5) {
+                if (std::strcmp(k, key) == 0) {
+                    h->hop_var[prec] = var;
+                    h->hop_ns[prec] = ns;
+                    h->hop_sb[prec] = sb;
+                    hit = true;
+                }
+            }
+            std::fclose(f);
+            if (hit) return DWF_OK;
+        }
+    }
+    double best = 1e30;
+    int bvar = -1, bns = 0, bsb = 0;
+    for (int var = 0; var <= 1; ++var)
+        for (int ns = 1; ns <= 2; ++ns) {
+            if (h->Ls % ns) continue;
+            const int LsN = h->Ls / ns;
+            for (int threads = 64; threads <= 256; threads += 64) {
+                const int sb = threads / LsN;
+                if (sb < 1 || LsN * sb > 256) continue;
+                if (var == 1 && hop_staged_smem_bytes(prec, h->Ls, sb) > 220 * 1024) continue;
+                h->hop_var[prec] = var;
+                h->hop_ns[prec] = ns;
+                h->hop_sb[prec] = sb;
+                double us = 0, by = 0;
+                int rc = dwf_time_hop(h, prec, 10, 0, &us, &by, stream);
+                if (rc) return rc;
+                if (us < best) {
+                    best = us;
+                    bvar = var;
+                    bns = ns;
+                    bsb = sb;
+                }
+            }
+        }
+    h->hop_var[prec] = bvar;
+    h->hop_ns[prec] = bns;
+    h->hop_sb[prec] = bsb;
+    if (cache_path) {
+        FILE *f = std::fopen(cache_path, "a");
+        if (f) {
+            std::fprintf(f, "%s %d %d %d %.3f\n", key, bvar, bns, bsb, best);
+            std::fclose(f);
+        }
+    }
+    return DWF_OK;
+}
 
 int dwf_time_hop(dwf_handle h, int prec, int reps, int flush_l2, double *us, double *bytes, void *stream)
 {
@@ -447,7 +553,7 @@ int dwf_time_hop(dwf_handle h, int prec, int reps, int flush_l2, double *us, dou
     cudaEventDestroy(e1);
     *us = 1000.0 * total_ms / reps;
     const size_t link_sz = prec == DWF_F64 ? 8 : (prec == DWF_F32 ? 4 : 2);
-    *bytes = 2.0 * (double)(field_bytes(prec, h->Vh, h->Ls) + scale_bytes(prec, h->Vh, h->Ls)) +
+    *bytes = 2.0 * (double)(field_bytes(prec, h->Vh, h->Ls) + (prec == DWF_F16 ? (size_t)h->Vh * h->Ls * 4 : 0)) +
              (double)h->Vh * 8 * 18 * link_sz;
     return DWF_OK;
 }

@@ -12,7 +12,8 @@
 // consecutive (site, s) pairs reads 16-byte vectors that are consecutive in
 // memory (fully coalesced), and all Ls slices of a site share its links.
 //   FP64: G = 12 (double2),  FP32: G = 6 (float4),
-//   FP16: G = 3 (8 halves) plus one FP32 scale per (site, s) = max |real|.
+//   FP16: G = 3 (8 halves) plus one FP32 scale per (site, s) = max |real|,
+//         stored [site][Ls rounded up to a multiple of 4].
 // Links: for each output parity p, a table [Vh][8][18 reals]: directions
 // 0..3 hold U_mu(x), directions 4..7 hold U_mu(x-mu)^dag, with the fermion
 // boundary phase folded in; FP64, FP32 and FP16 copies.
@@ -106,6 +107,7 @@ struct HopArgs {
     FieldRef xdir;
     const double *xalpha = nullptr;
     RedArgs red;
+    int *err = nullptr;            // bit 0 set when a bounded device wait gave up
 };
 
 struct MixArgs {
@@ -125,7 +127,14 @@ struct CgUpdateArgs {
 
 // ------------------------------------------------------------ launchers
 // prec: DWF_F64 / DWF_F32 / DWF_F16 (template dispatch inside)
-cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int sites_per_block, cudaStream_t st);
+// var: 0 direct neighbour loads, 1 TMA-staged neighbour sites; ns: fifth-direction
+// slices per thread (1, or 2 when Ls is even); sb: sites per CTA.
+// var < 0 / ns <= 0 / sb <= 0 pick the defaults.
+cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int var, int ns, int sb, cudaStream_t st);
+int hop_default_variant(int prec);
+int hop_default_ns(int prec, int Ls);
+int hop_default_sb(int prec, int Ls, int ns);
+size_t hop_staged_smem_bytes(int prec, int Ls, int sb);
 cudaError_t launch_mix(int prec, const MixArgs &a, cudaStream_t st);
 cudaError_t launch_cg_update(int prec, const CgUpdateArgs &a, cudaStream_t st);
 
@@ -195,6 +204,11 @@ struct dwf_ctx {
     double *one = nullptr;            // device constant 1.0
     std::map<std::string, std::pair<void *, size_t>> work;
     size_t bytes = 0;
+    long long launches = 0;           // device kernels launched through this handle
+    int hop_var[3] = {-1, -1, -1};    // hop variant per precision (-1 = default), set by the autotuner
+    int hop_ns[3] = {0, 0, 0};        // hop tiling per precision (0 = default)
+    int hop_sb[3] = {0, 0, 0};
+    int *errflag() const { return &scal[7].flags; }
 
     const void *mat(int prec, int id) const;
     const void *gauge_for(int prec, int out_par) const;

@@ -1,5 +1,14 @@
-// Device helpers shared by the kernels: precision traits, field loads and
-// stores in the internal layout (see dwf_internal.h), block reductions.
+// Device helpers shared by the kernels: precision traits, spin-paired complex
+// arithmetic, field loads and stores in the internal layout (dwf_internal.h),
+// block reductions.
+//
+// Internal order of the 24 reals of one (site, s): group g = 2a + c
+// (colour a, c = 0 re / 1 im) holds the four spins contiguously, so real k of
+// the internal order is k = 4g + spin.  Registers hold a field as 12 pairs
+// v[2g] = (spin 0, spin 1) and v[2g+1] = (spin 2, spin 3) of group g: even
+// pairs are the P_+ chirality, odd pairs the P_- chirality.  Every spin
+// projection, SU(3) product and fifth-direction mixing then works on pairs,
+// which maps onto the packed FP32x2 instructions (FFMA2, FADD2, FMUL2).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -12,95 +21,125 @@ namespace dwf {
 template <int P> struct Tr;
 template <> struct Tr<DWF_F64> {
     typedef double real;
+    typedef double2 pair;
     typedef double link_t;
-    typedef double xs_t;
     static constexpr int G = 12;
 };
 template <> struct Tr<DWF_F32> {
     typedef float real;
+    typedef float2 pair;
     typedef float link_t;
-    typedef float xs_t;
     static constexpr int G = 6;
 };
 template <> struct Tr<DWF_F16> {
     typedef float real;
+    typedef float2 pair;
     typedef __half link_t;
-    typedef float xs_t;
     static constexpr int G = 3;
 };
 
-// ---------------------------------------------------------------- loads
-// r[24] <- field(site, s).  RO = true uses the read-only data path.
-template <int P, bool RO, typename T>
-__device__ __forceinline__ void ld_field(const FieldRef &f, size_t site, int s, int Ls, T *r)
+template <typename T2> struct PairReal;
+template <> struct PairReal<float2> { typedef float R; };
+template <> struct PairReal<double2> { typedef double R; };
+
+// ------------------------------------------------------- pair arithmetic
+__device__ __forceinline__ float2 p_make(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 p_make(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 p_splat(float a) { return make_float2(a, a); }
+__device__ __forceinline__ double2 p_splat(double a) { return make_double2(a, a); }
+__device__ __forceinline__ float2 p_zero(float2) { return make_float2(0.f, 0.f); }
+__device__ __forceinline__ double2 p_zero(double2) { return make_double2(0.0, 0.0); }
+
+// a * b + c
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 p_fma(double2 a, double2 b, double2 c)
 {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 p_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ double2 p_sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 p_mul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+
+// ---------------------------------------------------------------- loads
+// v[12] <- field(site, s) (FP16: scaled back to real values)
+template <int P, bool RO, typename T2>
+__device__ __forceinline__ void ld_pairs(const FieldRef &f, size_t site, int s, int Ls, T2 *v)
+{
+    typedef typename PairReal<T2>::R R;
     if constexpr (P == DWF_F64) {
-        const double2 *v = reinterpret_cast<const double2 *>(f.v) + (site * 12) * Ls + s;
+        const double2 *p = reinterpret_cast<const double2 *>(f.v) + (site * 12) * Ls + s;
 #pragma unroll
-        for (int g = 0; g < 12; ++g) {
-            double2 q = RO ? __ldg(v + (size_t)g * Ls) : v[(size_t)g * Ls];
-            r[2 * g] = (T)q.x;
-            r[2 * g + 1] = (T)q.y;
+        for (int k = 0; k < 12; ++k) {
+            double2 q = RO ? __ldg(p + (size_t)k * Ls) : p[(size_t)k * Ls];
+            v[k] = p_make((R)q.x, (R)q.y);
         }
     } else if constexpr (P == DWF_F32) {
-        const float4 *v = reinterpret_cast<const float4 *>(f.v) + (site * 6) * Ls + s;
+        const float4 *p = reinterpret_cast<const float4 *>(f.v) + (site * 6) * Ls + s;
 #pragma unroll
         for (int g = 0; g < 6; ++g) {
-            float4 q = RO ? __ldg(v + (size_t)g * Ls) : v[(size_t)g * Ls];
-            r[4 * g] = (T)q.x;
-            r[4 * g + 1] = (T)q.y;
-            r[4 * g + 2] = (T)q.z;
-            r[4 * g + 3] = (T)q.w;
+            float4 q = RO ? __ldg(p + (size_t)g * Ls) : p[(size_t)g * Ls];
+            v[2 * g] = p_make((R)q.x, (R)q.y);
+            v[2 * g + 1] = p_make((R)q.z, (R)q.w);
         }
     } else {
-        const uint4 *v = reinterpret_cast<const uint4 *>(f.v) + (site * 3) * Ls + s;
-        const float sc = RO ? __ldg(f.scale + site * Ls + s) : f.scale[site * Ls + s];
+        const uint4 *p = reinterpret_cast<const uint4 *>(f.v) + (site * 3) * Ls + s;
+        const size_t si = site * (size_t)((Ls + 3) & ~3) + s;
+        const float sc = RO ? __ldg(f.scale + si) : f.scale[si];
 #pragma unroll
         for (int g = 0; g < 3; ++g) {
-            uint4 q = RO ? __ldg(v + (size_t)g * Ls) : v[(size_t)g * Ls];
+            uint4 q = RO ? __ldg(p + (size_t)g * Ls) : p[(size_t)g * Ls];
             const unsigned w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                __half2 h2 = *reinterpret_cast<const __half2 *>(&w[k]);
-                float2 f2 = __half22float2(h2);
-                r[8 * g + 2 * k] = (T)(f2.x * sc);
-                r[8 * g + 2 * k + 1] = (T)(f2.y * sc);
+                float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
+                v[4 * g + k] = p_make((R)(f2.x * sc), (R)(f2.y * sc));
             }
         }
     }
 }
 
-// field(site, s) <- r[24]
-template <int P, typename T>
-__device__ __forceinline__ void st_field(const FieldRef &f, size_t site, int s, int Ls, const T *r)
+// field(site, s) <- v[12]
+template <int P, typename T2>
+__device__ __forceinline__ void st_pairs(const FieldRef &f, size_t site, int s, int Ls, const T2 *v)
 {
     if constexpr (P == DWF_F64) {
-        double2 *v = reinterpret_cast<double2 *>(f.v) + (site * 12) * Ls + s;
+        double2 *p = reinterpret_cast<double2 *>(f.v) + (site * 12) * Ls + s;
 #pragma unroll
-        for (int g = 0; g < 12; ++g) v[(size_t)g * Ls] = make_double2((double)r[2 * g], (double)r[2 * g + 1]);
+        for (int k = 0; k < 12; ++k) p[(size_t)k * Ls] = make_double2((double)v[k].x, (double)v[k].y);
     } else if constexpr (P == DWF_F32) {
-        float4 *v = reinterpret_cast<float4 *>(f.v) + (site * 6) * Ls + s;
+        float4 *p = reinterpret_cast<float4 *>(f.v) + (site * 6) * Ls + s;
 #pragma unroll
         for (int g = 0; g < 6; ++g)
-            v[(size_t)g * Ls] = make_float4((float)r[4 * g], (float)r[4 * g + 1], (float)r[4 * g + 2], (float)r[4 * g + 3]);
+            p[(size_t)g * Ls] = make_float4((float)v[2 * g].x, (float)v[2 * g].y, (float)v[2 * g + 1].x,
+                                            (float)v[2 * g + 1].y);
     } else {
         float mx = 0.f;
 #pragma unroll
-        for (int k = 0; k < 24; ++k) mx = fmaxf(mx, fabsf((float)r[k]));
+        for (int k = 0; k < 12; ++k) mx = fmaxf(mx, fmaxf(fabsf((float)v[k].x), fabsf((float)v[k].y)));
         const float inv = mx > 0.f ? 1.0f / mx : 0.f;
-        uint4 *v = reinterpret_cast<uint4 *>(f.v) + (site * 3) * Ls + s;
+        uint4 *p = reinterpret_cast<uint4 *>(f.v) + (site * 3) * Ls + s;
 #pragma unroll
         for (int g = 0; g < 3; ++g) {
             unsigned w[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                __half2 h2 = __floats2half2_rn((float)r[8 * g + 2 * k] * inv, (float)r[8 * g + 2 * k + 1] * inv);
+                __half2 h2 = __floats2half2_rn((float)v[4 * g + k].x * inv, (float)v[4 * g + k].y * inv);
                 w[k] = *reinterpret_cast<unsigned *>(&h2);
             }
-            v[(size_t)g * Ls] = make_uint4(w[0], w[1], w[2], w[3]);
+            p[(size_t)g * Ls] = make_uint4(w[0], w[1], w[2], w[3]);
         }
-        f.scale[site * Ls + s] = mx;
+        f.scale[site * (size_t)((Ls + 3) & ~3) + s] = mx;
     }
+}
+
+// internal real index (4g + spin, g = 2a + c) <-> canonical (spin*3 + a)*2 + c
+__host__ __device__ __forceinline__ int canon_of_internal(int k)
+{
+    const int spin = k & 3, g = k >> 2, a = g >> 1, c = g & 1;
+    return (spin * 3 + a) * 2 + c;
 }
 
 // ------------------------------------------------------------ reductions
@@ -191,6 +230,48 @@ __device__ __forceinline__ void grid_reduce(double v, const RedArgs &r)
         if (tid == 0) {
             finish_reduction(tot, r);
             *r.counter = 0u;
+        }
+    }
+}
+
+// ------------------------------------------------- fifth-direction mixing
+// Tile of one site in shared memory: Ls rows of 12 pairs.  o[n] += sum_t
+// M[chi][s_n][t] tile[t], chi = pair parity; the coefficients are stored as
+// mt[chi][t][x * NS + n] (x = thread's slice index, s_n = x + n Ls/NS).
+__device__ __forceinline__ void ld_tile_row(const float2 *row, float2 *h)
+{
+    const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const float4 v = r4[q];
+        h[2 * q] = make_float2(v.x, v.y);
+        h[2 * q + 1] = make_float2(v.z, v.w);
+    }
+}
+__device__ __forceinline__ void ld_tile_row(const double2 *row, double2 *h)
+{
+#pragma unroll
+    for (int q = 0; q < 12; ++q) h[q] = row[q];
+}
+
+// The tile rows must be 16-byte aligned (row stride 12 pairs, site stride a
+// multiple of 2 pairs).
+template <int NS, typename T2, typename R>
+__device__ __forceinline__ void mix_pairs(const R *mt, const T2 *tile, int x, int Ls, T2 (*o)[12])
+{
+    const int LL = Ls * Ls;
+    for (int t = 0; t < Ls; ++t) {
+        T2 h[12];
+        ld_tile_row(tile + t * 12, h);
+#pragma unroll
+        for (int n = 0; n < NS; ++n) {
+            const T2 cu = p_splat(mt[t * Ls + x * NS + n]);
+            const T2 cl = p_splat(mt[LL + t * Ls + x * NS + n]);
+#pragma unroll
+            for (int p = 0; p < 12; p += 2) {
+                o[n][p] = p_fma(cu, h[p], o[n][p]);
+                o[n][p + 1] = p_fma(cl, h[p + 1], o[n][p + 1]);
+            }
         }
     }
 }

@@ -4,313 +4,678 @@
 //
 // H psi(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ]
 // is the hopping sum of eq. (Wilson_matrix) (D_W = (4 - M0) - H/2); it is the
-// same for every fifth-direction slice s, so one CTA handles SB sites x all
-// Ls slices and every link it loads serves Ls slices.  The adjoint hop is
-// gamma5 H gamma5 (signs of the projectors flipped).
+// same for every fifth-direction slice s.  A CTA handles SB sites x all Ls
+// slices; each thread owns NS slices of one site (s = x + n Ls/NS), so every
+// link it loads serves NS slices.  The adjoint hop is gamma5 H gamma5
+// (projector signs flipped).
 //
-// In the chiral basis gamma_mu = [[0, e_mu], [e_mu^dag, 0]] with
-// e_k = -i sigma_k, e_4 = 1, so (1 - sig gamma_mu) psi = [h ; -sig e_mu^dag h]
-// with the half spinor h = psi_u - sig e_mu psi_l: only h (6 complex) is
-// multiplied by the link.
+// Chiral basis: gamma_mu = [[0, e_mu], [e_mu^dag, 0]], e_k = -i sigma_k,
+// e_4 = 1, so (1 - sig gamma_mu) psi = [h ; -sig e_mu^dag h] with the half
+// spinor h = psi_u - sig e_mu psi_l: only h is multiplied by the link.  h is
+// held as spin pairs Hx[a] = (h0.re, h1.re), Hy[a] = (h0.im, h1.im), so the
+// SU(3) product is 4 packed FMAs per (a, b) for both spins at once.
 //
-// After the hop, each thread owns h(site, s); the CTA writes its Ls x 24 tile
-// to shared memory and each thread forms (Post h)(site, s) = sum_t Post[s][t]
-// h(site, t) per chirality; the optional epilogue adds a mixed second input,
-// forms a residual, updates a solution accumulator, applies a final mixing
-// and reduces |o|^2 deterministically.
+// Two variants load the neighbours:
+//   0 (direct): every thread reads its 8 neighbour spinors from global memory;
+//   1 (staged): the neighbour sites' whole 5D spinors (all Ls slices are
+//     contiguous in the internal layout) and the CTA's links are brought into
+//     shared memory by 1D TMA bulk copies, two directions per stage, double
+//     buffered on mbarriers, so that every load of a stage is in flight at
+//     once while the previous stage is computed.  Every mbarrier wait is
+//     bounded by wall time; a wait that runs out sets an error flag and the
+//     kernel finishes without waiting further.
+// After the hop each thread writes h(site, s) to the CTA's shared tile and
+// forms (Post h)(site, s) = sum_t Post[s][t] h(site, t) per chirality; the
+// epilogue adds a mixed second input, forms a residual, updates a solution
+// accumulator, applies a final mixing and reduces |o|^2 deterministically.
+#include <cstdint>
+
 #include "fields.cuh"
 
 namespace dwf {
 namespace {
 
-template <typename real, int MU, int SIG>
-__device__ __forceinline__ void project(const real *p, real *h)
+// h = P^{(mu, sig)} psi, spin-paired (see fields.cuh for the pair layout)
+template <int MU, int SIG, typename T2>
+__device__ __forceinline__ void project(const T2 *v, T2 *Hx, T2 *Hy)
 {
+    typedef typename PairReal<T2>::R R;
+    constexpr R s = (R)SIG;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const real p0r = p[(0 * 3 + a) * 2], p0i = p[(0 * 3 + a) * 2 + 1];
-        const real p1r = p[(1 * 3 + a) * 2], p1i = p[(1 * 3 + a) * 2 + 1];
-        const real p2r = p[(2 * 3 + a) * 2], p2i = p[(2 * 3 + a) * 2 + 1];
-        const real p3r = p[(3 * 3 + a) * 2], p3i = p[(3 * 3 + a) * 2 + 1];
-        real h0r, h0i, h1r, h1i;
-        if constexpr (MU == 0) {        // e_1 psi_l = (-i psi3, -i psi2)
-            h0r = p0r - SIG * p3i; h0i = p0i + SIG * p3r;
-            h1r = p1r - SIG * p2i; h1i = p1i + SIG * p2r;
-        } else if constexpr (MU == 1) { // e_2 psi_l = (-psi3, psi2)
-            h0r = p0r + SIG * p3r; h0i = p0i + SIG * p3i;
-            h1r = p1r - SIG * p2r; h1i = p1i - SIG * p2i;
-        } else if constexpr (MU == 2) { // e_3 psi_l = (-i psi2, i psi3)
-            h0r = p0r - SIG * p2i; h0i = p0i + SIG * p2r;
-            h1r = p1r + SIG * p3i; h1i = p1i - SIG * p3r;
-        } else {                        // e_4 psi_l = (psi2, psi3)
-            h0r = p0r - SIG * p2r; h0i = p0i - SIG * p2i;
-            h1r = p1r - SIG * p3r; h1i = p1i - SIG * p3i;
-        }
-        h[(0 * 3 + a) * 2] = h0r; h[(0 * 3 + a) * 2 + 1] = h0i;
-        h[(1 * 3 + a) * 2] = h1r; h[(1 * 3 + a) * 2 + 1] = h1i;
-    }
-}
-
-template <typename real, int MU, int SIG>
-__device__ __forceinline__ void reconstruct(real *acc, const real *q)
-{
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const real q0r = q[(0 * 3 + a) * 2], q0i = q[(0 * 3 + a) * 2 + 1];
-        const real q1r = q[(1 * 3 + a) * 2], q1i = q[(1 * 3 + a) * 2 + 1];
-        real *a0 = acc + (0 * 3 + a) * 2, *a1 = acc + (1 * 3 + a) * 2;
-        real *a2 = acc + (2 * 3 + a) * 2, *a3 = acc + (3 * 3 + a) * 2;
-        a0[0] += q0r; a0[1] += q0i;
-        a1[0] += q1r; a1[1] += q1i;
-        // lower = -SIG e_mu^dag q
-        if constexpr (MU == 0) {        // e_1^dag q = (i q1, i q0)
-            a2[0] += SIG * q1i; a2[1] -= SIG * q1r;
-            a3[0] += SIG * q0i; a3[1] -= SIG * q0r;
-        } else if constexpr (MU == 1) { // e_2^dag q = (q1, -q0)
-            a2[0] -= SIG * q1r; a2[1] -= SIG * q1i;
-            a3[0] += SIG * q0r; a3[1] += SIG * q0i;
-        } else if constexpr (MU == 2) { // e_3^dag q = (i q0, -i q1)
-            a2[0] += SIG * q0i; a2[1] -= SIG * q0r;
-            a3[0] -= SIG * q1i; a3[1] += SIG * q1r;
-        } else {                        // e_4^dag q = (q0, q1)
-            a2[0] -= SIG * q0r; a2[1] -= SIG * q0i;
-            a3[0] -= SIG * q1r; a3[1] -= SIG * q1i;
+        const T2 XU = v[4 * a], XL = v[4 * a + 1], YU = v[4 * a + 2], YL = v[4 * a + 3];
+        if constexpr (MU == 3) {        // h0 = p0 - s p2, h1 = p1 - s p3
+            Hx[a] = p_fma(p_splat(-s), XL, XU);
+            Hy[a] = p_fma(p_splat(-s), YL, YU);
+        } else if constexpr (MU == 2) { // h0 = p0 + s i p2, h1 = p1 - s i p3
+            Hx[a] = p_fma(p_make(-s, s), YL, XU);
+            Hy[a] = p_fma(p_make(s, -s), XL, YU);
+        } else if constexpr (MU == 1) { // h0 = p0 + s p3, h1 = p1 - s p2
+            Hx[a] = p_make(XU.x + s * XL.y, XU.y - s * XL.x);
+            Hy[a] = p_make(YU.x + s * YL.y, YU.y - s * YL.x);
+        } else {                        // h0 = p0 + s i p3, h1 = p1 + s i p2
+            Hx[a] = p_make(XU.x - s * YL.y, XU.y - s * YL.x);
+            Hy[a] = p_make(YU.x + s * XL.y, YU.y + s * XL.x);
         }
     }
 }
 
-template <int P>
-__device__ __forceinline__ void load_link(const typename Tr<P>::link_t *U, typename Tr<P>::real *u)
+// acc += [q ; -sig e_mu^dag q]
+template <int MU, int SIG, typename T2>
+__device__ __forceinline__ void reconstruct(T2 *acc, const T2 *Qx, const T2 *Qy)
+{
+    typedef typename PairReal<T2>::R R;
+    constexpr R s = (R)SIG;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T2 &XU = acc[4 * a], &XL = acc[4 * a + 1], &YU = acc[4 * a + 2], &YL = acc[4 * a + 3];
+        XU = p_add(XU, Qx[a]);
+        YU = p_add(YU, Qy[a]);
+        if constexpr (MU == 3) {        // lower = -s (q0, q1)
+            XL = p_fma(p_splat(-s), Qx[a], XL);
+            YL = p_fma(p_splat(-s), Qy[a], YL);
+        } else if constexpr (MU == 2) { // p2 += -s i q0, p3 += s i q1
+            XL = p_fma(p_make(s, -s), Qy[a], XL);
+            YL = p_fma(p_make(-s, s), Qx[a], YL);
+        } else if constexpr (MU == 1) { // p2 += -s q1, p3 += s q0
+            XL = p_make(XL.x - s * Qx[a].y, XL.y + s * Qx[a].x);
+            YL = p_make(YL.x - s * Qy[a].y, YL.y + s * Qy[a].x);
+        } else {                        // p2 += -s i q1, p3 += -s i q0
+            XL = p_make(XL.x + s * Qy[a].y, XL.y + s * Qy[a].x);
+            YL = p_make(YL.x - s * Qx[a].y, YL.y - s * Qx[a].x);
+        }
+    }
+}
+
+// link (row-major 3x3 complex) -> u[9] complex pairs (re, im); global (RO) or shared
+template <int P, bool GLOBAL, typename T2>
+__device__ __forceinline__ void load_link(const typename Tr<P>::link_t *U, T2 *u)
 {
     if constexpr (P == DWF_F64) {
         const double2 *v = reinterpret_cast<const double2 *>(U);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            double2 q = __ldg(v + k);
-            u[2 * k] = q.x;
-            u[2 * k + 1] = q.y;
-        }
+        for (int k = 0; k < 9; ++k) u[k] = GLOBAL ? __ldg(v + k) : v[k];
     } else if constexpr (P == DWF_F32) {
         const float2 *v = reinterpret_cast<const float2 *>(U);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            float2 q = __ldg(v + k);
-            u[2 * k] = q.x;
-            u[2 * k + 1] = q.y;
-        }
+        for (int k = 0; k < 9; ++k) u[k] = GLOBAL ? __ldg(v + k) : v[k];
     } else {
         const __half2 *v = reinterpret_cast<const __half2 *>(U);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            float2 q = __half22float2(__ldg(v + k));
-            u[2 * k] = q.x;
-            u[2 * k + 1] = q.y;
-        }
+        for (int k = 0; k < 9; ++k) u[k] = __half22float2(GLOBAL ? __ldg(v + k) : v[k]);
     }
 }
 
-// q[sp][a] = sum_b U[a][b] h[sp][b]
-template <typename real>
-__device__ __forceinline__ void su3_mul(const real *u, const real *h, real *q)
+// Q = U H for both spins: Qx[a] = sum_b ur Hx[b] - ui Hy[b], Qy[a] = sum_b ur Hy[b] + ui Hx[b]
+template <typename T2>
+__device__ __forceinline__ void su3_pairs(const T2 *u, const T2 *Hx, const T2 *Hy, T2 *Qx, T2 *Qy)
 {
 #pragma unroll
-    for (int sp = 0; sp < 2; ++sp)
+    for (int a = 0; a < 3; ++a) {
+        T2 qx = p_zero(Hx[0]), qy = p_zero(Hx[0]);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            real re = 0, im = 0;
+        for (int b = 0; b < 3; ++b) {
+            const T2 ur = p_splat(u[a * 3 + b].x), ui = p_splat(u[a * 3 + b].y);
+            const T2 nui = p_splat(-u[a * 3 + b].y);
+            qx = p_fma(ur, Hx[b], qx);
+            qx = p_fma(nui, Hy[b], qx);
+            qy = p_fma(ur, Hy[b], qy);
+            qy = p_fma(ui, Hx[b], qy);
+        }
+        Qx[a] = qx;
+        Qy[a] = qy;
+    }
+}
+
+template <int MU, int SIG, typename T2>
+__device__ __forceinline__ void hop_one(T2 *acc, const T2 *u, const T2 *v)
+{
+    T2 Hx[3], Hy[3], Qx[3], Qy[3];
+    project<MU, SIG>(v, Hx, Hy);
+    su3_pairs(u, Hx, Hy, Qx, Qy);
+    reconstruct<MU, SIG>(acc, Qx, Qy);
+}
+
+// one (site, s) of a neighbour site copied to shared memory: the Ls x G block
+// of 16-byte vectors in the global layout, followed (FP16) by its scales
+template <int P, typename T2>
+__device__ __forceinline__ void ld_pairs_smem(const unsigned char *slot, int s, int Ls, T2 *v)
+{
+    typedef typename PairReal<T2>::R R;
+    if constexpr (P == DWF_F64) {
+        const double2 *p = reinterpret_cast<const double2 *>(slot) + s;
 #pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const real ur = u[(a * 3 + b) * 2], ui = u[(a * 3 + b) * 2 + 1];
-                const real hr = h[(sp * 3 + b) * 2], hi = h[(sp * 3 + b) * 2 + 1];
-                re += ur * hr - ui * hi;
-                im += ur * hi + ui * hr;
+        for (int k = 0; k < 12; ++k) {
+            const double2 q = p[k * Ls];
+            v[k] = p_make((R)q.x, (R)q.y);
+        }
+    } else if constexpr (P == DWF_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>(slot) + s;
+#pragma unroll
+        for (int g = 0; g < 6; ++g) {
+            const float4 q = p[g * Ls];
+            v[2 * g] = p_make((R)q.x, (R)q.y);
+            v[2 * g + 1] = p_make((R)q.z, (R)q.w);
+        }
+    } else {
+        const uint4 *p = reinterpret_cast<const uint4 *>(slot) + s;
+        const float sc = reinterpret_cast<const float *>(slot + (size_t)Ls * 48)[s];
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            const uint4 q = p[g * Ls];
+            const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
+                v[4 * g + k] = p_make((R)(f2.x * sc), (R)(f2.y * sc));
             }
-            q[(sp * 3 + a) * 2] = re;
-            q[(sp * 3 + a) * 2 + 1] = im;
         }
-}
-
-template <int P, bool DAG, int D>
-__device__ __forceinline__ void hop_dir(typename Tr<P>::real *acc, const FieldRef &in, int nb, int s, int Ls,
-                                        const typename Tr<P>::link_t *U)
-{
-    typedef typename Tr<P>::real real;
-    constexpr int MU = D & 3;
-    constexpr int SIG = (D < 4 ? 1 : -1) * (DAG ? -1 : 1);
-    real psi[24], h[12], q[12], u[18];
-    ld_field<P, true>(in, (size_t)nb, s, Ls, psi);
-    load_link<P>(U + D * 18, u);
-    project<real, MU, SIG>(psi, h);
-    su3_mul<real>(u, h, q);
-    reconstruct<real, MU, SIG>(acc, q);
-}
-
-// o[k] += sum_t M[chi(k)][s][t] tile[t][k], M stored transposed [chi][t][s]
-template <typename real>
-__device__ __forceinline__ void mix_tile(const real *M, const real *tile, int s, int Ls, real *o)
-{
-    for (int t = 0; t < Ls; ++t) {
-        const real mu = M[t * Ls + s];
-        const real ml = M[Ls * Ls + t * Ls + s];
-        const real *h = tile + t * 24;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) o[k] += mu * h[k];
-#pragma unroll
-        for (int k = 12; k < 24; ++k) o[k] += ml * h[k];
     }
 }
 
-template <typename real>
-__device__ __forceinline__ void put_tile(real *tile, int s, const real *v)
+template <typename T2>
+__device__ __forceinline__ void put_tile(T2 *tile, int s, const T2 *v)
 {
-    real *dst = tile + s * 24;
+    T2 *dst = tile + s * 12;
 #pragma unroll
-    for (int k = 0; k < 24; ++k) dst[k] = v[k];
+    for (int k = 0; k < 12; ++k) dst[k] = v[k];
 }
 
-template <int P, bool DAG>
-__global__ void __launch_bounds__(256) hop_kernel(const HopArgs a)
+// ------------------------------------------------------------ the epilogue
+// acc: hop result of this thread's NS slices.  Must be called by every thread.
+template <int P, int NS, typename T2, typename R>
+__device__ __forceinline__ void hop_epilogue(const HopArgs &a, T2 (*acc)[12], T2 *mytile, const R *mtx, int site,
+                                             int x, int LsN, bool active)
 {
-    typedef typename Tr<P>::real real;
-    typedef typename Tr<P>::link_t link_t;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ls = a.Ls;
-    const int s = threadIdx.x;
-    const int j = threadIdx.y;
-    const int SB = blockDim.y;
-    const int site = blockIdx.x * SB + j;
-    const bool active = site < a.Vh;
-    const int tstride = Ls * 24 + (sizeof(real) == 8 ? 2 : 4);
-    real *tile = reinterpret_cast<real *>(smem_raw);
-    real *mtx = tile + SB * tstride;
     const int msz = 2 * Ls * Ls;
-    const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
-    for (int k = tid; k < msz; k += nt) {
-        mtx[k] = reinterpret_cast<const real *>(a.post)[k];
-        if (a.ymode == 2) mtx[msz + k] = reinterpret_cast<const real *>(a.ymat)[k];
-        if (a.zmat) mtx[2 * msz + k] = reinterpret_cast<const real *>(a.zmat)[k];
-    }
-
-    real acc[24];
-#pragma unroll
-    for (int k = 0; k < 24; ++k) acc[k] = 0;
     if (active) {
-        const int *nb = a.nbr + (size_t)site * 8;
-        const link_t *U = reinterpret_cast<const link_t *>(a.gauge) + (size_t)site * 8 * 18;
-        int n[8];
 #pragma unroll
-        for (int d = 0; d < 8; ++d) n[d] = __ldg(nb + d);
-        hop_dir<P, DAG, 0>(acc, a.in, n[0], s, Ls, U);
-        hop_dir<P, DAG, 1>(acc, a.in, n[1], s, Ls, U);
-        hop_dir<P, DAG, 2>(acc, a.in, n[2], s, Ls, U);
-        hop_dir<P, DAG, 3>(acc, a.in, n[3], s, Ls, U);
-        hop_dir<P, DAG, 4>(acc, a.in, n[4], s, Ls, U);
-        hop_dir<P, DAG, 5>(acc, a.in, n[5], s, Ls, U);
-        hop_dir<P, DAG, 6>(acc, a.in, n[6], s, Ls, U);
-        hop_dir<P, DAG, 7>(acc, a.in, n[7], s, Ls, U);
-        put_tile(tile + j * tstride, s, acc);
+        for (int n = 0; n < NS; ++n) put_tile(mytile, x + n * LsN, acc[n]);
     }
     __syncthreads();
 
-    real o[24];
+    T2 o[NS][12];
 #pragma unroll
-    for (int k = 0; k < 24; ++k) o[k] = 0;
-    if (active) mix_tile(mtx, tile + j * tstride, s, Ls, o);
+    for (int n = 0; n < NS; ++n)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o[n][k] = p_splat((R)0);
+    if (active) mix_pairs<NS>(mtx, mytile, x, Ls, o);
 
-    if (a.ymode == 1 && active) {
-        real y[24];
-        ld_field<P, false>(a.y, (size_t)site, s, Ls, y);
+    if (a.ymode == 1) {
+        if (active) {
 #pragma unroll
-        for (int k = 0; k < 24; ++k) o[k] += y[k];
+            for (int n = 0; n < NS; ++n) {
+                T2 y[12];
+                ld_pairs<P, false>(a.y, (size_t)site, x + n * LsN, Ls, y);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) o[n][k] = p_add(o[n][k], y[k]);
+            }
+        }
     } else if (a.ymode == 2) {
         __syncthreads();
         if (active) {
-            real y[24];
-            ld_field<P, false>(a.y, (size_t)site, s, Ls, y);
-            put_tile(tile + j * tstride, s, y);
+#pragma unroll
+            for (int n = 0; n < NS; ++n) {
+                T2 y[12];
+                ld_pairs<P, false>(a.y, (size_t)site, x + n * LsN, Ls, y);
+                put_tile(mytile, x + n * LsN, y);
+            }
         }
         __syncthreads();
-        if (active) mix_tile(mtx + msz, tile + j * tstride, s, Ls, o);
+        if (active) mix_pairs<NS>(mtx + msz, mytile, x, Ls, o);
     }
 
     if (a.rin.v && active) {
-        real r[24];
-        ld_field<P, false>(a.rin, (size_t)site, s, Ls, r);
-        const real al = (real)(*a.ralpha);
+        const R al = (R)(*a.ralpha);
+        const T2 nal = p_splat(-al);
 #pragma unroll
-        for (int k = 0; k < 24; ++k) o[k] = r[k] - al * o[k];
+        for (int n = 0; n < NS; ++n) {
+            T2 r[12];
+            ld_pairs<P, false>(a.rin, (size_t)site, x + n * LsN, Ls, r);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) o[n][k] = p_fma(nal, o[n][k], r[k]);
+        }
         if (a.xacc) {
-            typedef typename Tr<P>::xs_t xs_t;
             constexpr int XP = (P == DWF_F64) ? DWF_F64 : DWF_F32;
             FieldRef xf;
             xf.v = a.xacc;
-            real x[24], dx[24];
-            ld_field<XP, false>(xf, (size_t)site, s, Ls, x);
-            ld_field<P, false>(a.xdir, (size_t)site, s, Ls, dx);
-            const real xa = (real)(*a.xalpha);
+            const T2 xa = p_splat((R)(*a.xalpha));
 #pragma unroll
-            for (int k = 0; k < 24; ++k) x[k] += xa * dx[k];
-            st_field<XP>(xf, (size_t)site, s, Ls, x);
-            (void)sizeof(xs_t);
+            for (int n = 0; n < NS; ++n) {
+                T2 xv[12], dx[12];
+                ld_pairs<XP, false>(xf, (size_t)site, x + n * LsN, Ls, xv);
+                ld_pairs<P, false>(a.xdir, (size_t)site, x + n * LsN, Ls, dx);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) xv[k] = p_fma(xa, dx[k], xv[k]);
+                st_pairs<XP>(xf, (size_t)site, x + n * LsN, Ls, xv);
+            }
         }
     }
 
     double nrm = 0;
     if (active && a.red.op != RED_NONE) {
 #pragma unroll
-        for (int k = 0; k < 24; ++k) nrm += (double)o[k] * (double)o[k];
+        for (int n = 0; n < NS; ++n)
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                nrm += (double)o[n][k].x * (double)o[n][k].x + (double)o[n][k].y * (double)o[n][k].y;
     }
 
     if (a.zmat) {
         __syncthreads();
-        if (active) put_tile(tile + j * tstride, s, o);
-        __syncthreads();
-        real z[24];
+        if (active) {
 #pragma unroll
-        for (int k = 0; k < 24; ++k) z[k] = 0;
-        if (active) mix_tile(mtx + 2 * msz, tile + j * tstride, s, Ls, z);
-        if (active) st_field<P>(a.out, (size_t)site, s, Ls, z);
+            for (int n = 0; n < NS; ++n) put_tile(mytile, x + n * LsN, o[n]);
+        }
+        __syncthreads();
+        T2 z[NS][12];
+#pragma unroll
+        for (int n = 0; n < NS; ++n)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) z[n][k] = p_splat((R)0);
+        if (active) {
+            mix_pairs<NS>(mtx + 2 * msz, mytile, x, Ls, z);
+#pragma unroll
+            for (int n = 0; n < NS; ++n) st_pairs<P>(a.out, (size_t)site, x + n * LsN, Ls, z[n]);
+        }
     } else if (active) {
-        st_field<P>(a.out, (size_t)site, s, Ls, o);
+#pragma unroll
+        for (int n = 0; n < NS; ++n) st_pairs<P>(a.out, (size_t)site, x + n * LsN, Ls, o[n]);
     }
 
     if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
 }
 
-template <int P>
-size_t hop_smem(int Ls, int SB)
+// matrices arrive as [chi][t][s]; store them as [chi][t][x*NS + n] with s = x + n*LsN
+template <int NS, typename R>
+__device__ __forceinline__ void load_matrices(const HopArgs &a, R *mtx)
 {
-    typedef typename Tr<P>::real real;
-    const int tstride = Ls * 24 + (sizeof(real) == 8 ? 2 : 4);
-    return (size_t)(SB * tstride + 3 * 2 * Ls * Ls) * sizeof(real);
+    const int Ls = a.Ls, LsN = Ls / NS, msz = 2 * Ls * Ls;
+    const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int k = tid; k < msz; k += nt) {
+        const int chi_t = k / Ls, s = k % Ls;
+        const int dst = chi_t * Ls + (s % LsN) * NS + s / LsN;
+        mtx[dst] = reinterpret_cast<const R *>(a.post)[k];
+        if (a.ymode == 2) mtx[msz + dst] = reinterpret_cast<const R *>(a.ymat)[k];
+        if (a.zmat) mtx[2 * msz + dst] = reinterpret_cast<const R *>(a.zmat)[k];
+    }
 }
 
-template <int P, bool DAG>
-cudaError_t launch_hop_t(const HopArgs &a, int SB, cudaStream_t st)
+// ------------------------------------------------------ variant 0: direct
+template <int P, bool DAG, int D, int NS, typename T2>
+__device__ __forceinline__ void hop_dir(T2 (*acc)[12], const FieldRef &in, int nb, int x, int LsN, int Ls,
+                                        const typename Tr<P>::link_t *U)
+{
+    constexpr int MU = D & 3;
+    constexpr int SIG = (D < 4 ? 1 : -1) * (DAG ? -1 : 1);
+    T2 u[9];
+    load_link<P, true>(U + D * 18, u);
+#pragma unroll
+    for (int n = 0; n < NS; ++n) {
+        T2 v[12];
+        ld_pairs<P, true>(in, (size_t)nb, x + n * LsN, Ls, v);
+        hop_one<MU, SIG>(acc[n], u, v);
+    }
+}
+
+template <int P, bool DAG, int NS>
+__global__ void __launch_bounds__(256) hop_kernel(const HopArgs a)
+{
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
+    typedef typename Tr<P>::link_t link_t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ls = a.Ls;
+    const int LsN = Ls / NS;
+    const int x = threadIdx.x;
+    const int j = threadIdx.y;
+    const int SB = blockDim.y;
+    const int site = blockIdx.x * SB + j;
+    const bool active = site < a.Vh;
+    const int tstride = Ls * 12 + 2;
+    T2 *tile = reinterpret_cast<T2 *>(smem_raw);
+    R *mtx = reinterpret_cast<R *>(tile + SB * tstride);
+    load_matrices<NS>(a, mtx);
+
+    T2 acc[NS][12];
+#pragma unroll
+    for (int n = 0; n < NS; ++n)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[n][k] = p_splat((R)0);
+    if (active) {
+        const int *nb = a.nbr + (size_t)site * 8;
+        const link_t *U = reinterpret_cast<const link_t *>(a.gauge) + (size_t)site * 8 * 18;
+        int n8[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) n8[d] = __ldg(nb + d);
+        hop_dir<P, DAG, 0, NS>(acc, a.in, n8[0], x, LsN, Ls, U);
+        hop_dir<P, DAG, 1, NS>(acc, a.in, n8[1], x, LsN, Ls, U);
+        hop_dir<P, DAG, 2, NS>(acc, a.in, n8[2], x, LsN, Ls, U);
+        hop_dir<P, DAG, 3, NS>(acc, a.in, n8[3], x, LsN, Ls, U);
+        hop_dir<P, DAG, 4, NS>(acc, a.in, n8[4], x, LsN, Ls, U);
+        hop_dir<P, DAG, 5, NS>(acc, a.in, n8[5], x, LsN, Ls, U);
+        hop_dir<P, DAG, 6, NS>(acc, a.in, n8[6], x, LsN, Ls, U);
+        hop_dir<P, DAG, 7, NS>(acc, a.in, n8[7], x, LsN, Ls, U);
+    }
+    hop_epilogue<P, NS>(a, acc, tile + j * tstride, mtx, site, x, LsN, active);
+}
+
+// ------------------------------------------------------ variant 1: staged
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: gives up after one second of wall time; returns false then.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > 1000000000ull) return false;
+    }
+}
+
+template <int P>
+struct StageGeom {
+    uint32_t site_bytes;   // one neighbour site: Ls x 24 stored reals
+    uint32_t slot_bytes;   // + its scales (FP16)
+    uint32_t link_bytes;   // 8 links of one site
+};
+
+template <int P>
+__host__ __device__ __forceinline__ StageGeom<P> stage_geom(int Ls)
+{
+    StageGeom<P> g;
+    const uint32_t w = (P == DWF_F64) ? 8 : (P == DWF_F32 ? 4 : 2);
+    g.site_bytes = (uint32_t)Ls * 24 * w;
+    g.slot_bytes = g.site_bytes + ((P == DWF_F16) ? (uint32_t)((Ls + 3) & ~3) * 4 : 0);
+    g.link_bytes = 8 * 18 * w;
+    return g;
+}
+
+// Issue the copies of stage st (directions 2st, 2st+1) for the CTA's nsite sites.
+// Called by the CTA's first 32 threads (one warp).
+template <int P>
+__device__ __forceinline__ void issue_stage(const HopArgs &a, int st, unsigned char *buf, uint32_t bar, int site0,
+                                            int nsite, int SB, const StageGeom<P> &g, int lane)
+{
+    if (lane == 0) mbar_arrive_expect_tx(bar, 2u * nsite * g.slot_bytes);
+    __syncwarp(__activemask());
+    for (int it = lane; it < 2 * nsite; it += 32) {
+        const int k = it / nsite, j = it % nsite;
+        const int d = 2 * st + k;
+        const int nb = __ldg(a.nbr + (size_t)(site0 + j) * 8 + d);
+        unsigned char *slot = buf + (size_t)(k * SB + j) * g.slot_bytes;
+        bulk_g2s(smem_u32(slot), (const unsigned char *)a.in.v + (size_t)nb * g.site_bytes, g.site_bytes, bar);
+        if (P == DWF_F16) {
+            const uint32_t sb = g.slot_bytes - g.site_bytes;
+            bulk_g2s(smem_u32(slot + g.site_bytes), (const unsigned char *)a.in.scale + (size_t)nb * sb, sb, bar);
+        }
+    }
+}
+
+template <int P, bool DAG, int D, int NS, typename T2>
+__device__ __forceinline__ void compute_dir_smem(T2 (*acc)[12], const unsigned char *slot, const unsigned char *links,
+                                                 int j, int x, int LsN, int Ls, const StageGeom<P> &g)
+{
+    typedef typename Tr<P>::link_t link_t;
+    constexpr int MU = D & 3;
+    constexpr int SIG = (D < 4 ? 1 : -1) * (DAG ? -1 : 1);
+    T2 u[9];
+    load_link<P, false>(reinterpret_cast<const link_t *>(links + (size_t)j * g.link_bytes) + D * 18, u);
+#pragma unroll
+    for (int n = 0; n < NS; ++n) {
+        T2 v[12];
+        ld_pairs_smem<P>(slot, x + n * LsN, Ls, v);
+        hop_one<MU, SIG>(acc[n], u, v);
+    }
+}
+
+template <int P, bool DAG, int ST, int NS, typename T2>
+__device__ __forceinline__ void compute_stage(T2 (*acc)[12], const unsigned char *buf, const unsigned char *links,
+                                              int j, int x, int LsN, int Ls, int SB, const StageGeom<P> &g)
+{
+    compute_dir_smem<P, DAG, 2 * ST, NS>(acc, buf + (size_t)(0 * SB + j) * g.slot_bytes, links, j, x, LsN, Ls, g);
+    compute_dir_smem<P, DAG, 2 * ST + 1, NS>(acc, buf + (size_t)(1 * SB + j) * g.slot_bytes, links, j, x, LsN, Ls, g);
+}
+
+template <int P>
+__host__ __device__ __forceinline__ size_t staged_smem(int Ls, int SB, size_t *off_links, size_t *off_b0,
+                                                       size_t *off_b1, size_t *off_mtx)
+{
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
+    const StageGeom<P> g = stage_geom<P>(Ls);
+    size_t o = 64;   // mbarriers
+    *off_links = o;
+    o += (size_t)SB * g.link_bytes;
+    o = (o + 15) & ~(size_t)15;
+    size_t bufsz = (size_t)2 * SB * g.slot_bytes;
+    const size_t tilesz = (size_t)SB * (Ls * 12 + 2) * sizeof(T2);
+    if (tilesz > bufsz) bufsz = tilesz;
+    bufsz = (bufsz + 15) & ~(size_t)15;
+    *off_b0 = o;
+    o += bufsz;
+    *off_b1 = o;
+    o += bufsz;
+    *off_mtx = o;
+    o += (size_t)3 * 2 * Ls * Ls * sizeof(R);
+    return o;
+}
+
+template <int P, bool DAG, int NS>
+__global__ void __launch_bounds__(256) hop_staged_kernel(const HopArgs a)
+{
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int aborted;
+    const int Ls = a.Ls;
+    const int LsN = Ls / NS;
+    const int x = threadIdx.x;
+    const int j = threadIdx.y;
+    const int SB = blockDim.y;
+    const int site0 = blockIdx.x * SB;
+    const int site = site0 + j;
+    const int nsite = min(SB, a.Vh - site0);
+    const bool active = j < nsite;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const StageGeom<P> g = stage_geom<P>(Ls);
+    size_t off_links, off_b0, off_b1, off_mtx;
+    staged_smem<P>(Ls, SB, &off_links, &off_b0, &off_b1, &off_mtx);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
+    unsigned char *links = smem_raw + off_links;
+    unsigned char *b0 = smem_raw + off_b0;
+    unsigned char *b1 = smem_raw + off_b1;
+    R *mtx = reinterpret_cast<R *>(smem_raw + off_mtx);
+    const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]), barl = smem_u32(&bars[2]);
+
+    if (tid == 0) {
+        aborted = 0;
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        mbar_init(barl, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid < 32) {
+        if (tid == 0) mbar_arrive_expect_tx(barl, (uint32_t)nsite * g.link_bytes);
+        __syncwarp(__activemask());
+        for (int jj = tid; jj < nsite; jj += 32)
+            bulk_g2s(smem_u32(links + (size_t)jj * g.link_bytes),
+                     (const unsigned char *)a.gauge + (size_t)(site0 + jj) * g.link_bytes, g.link_bytes, barl);
+        issue_stage<P>(a, 0, b0, bar0, site0, nsite, SB, g, tid);
+        issue_stage<P>(a, 1, b1, bar1, site0, nsite, SB, g, tid);
+    }
+    load_matrices<NS>(a, mtx);
+
+    T2 acc[NS][12];
+#pragma unroll
+    for (int n = 0; n < NS; ++n)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[n][k] = p_splat((R)0);
+
+    // stage 0: directions 0,1 in b0 (phase 0)
+    bool ok = mbar_wait_bounded(barl, 0) && mbar_wait_bounded(bar0, 0);
+    if (ok && active) compute_stage<P, DAG, 0, NS>(acc, b0, links, j, x, LsN, Ls, SB, g);
+    if (!ok) atomicOr(&aborted, 1);
+    __syncthreads();
+    if (tid < 32 && !aborted) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue_stage<P>(a, 2, b0, bar0, site0, nsite, SB, g, tid);
+    }
+    // stage 1: directions 2,3 in b1 (phase 0)
+    ok = !aborted && mbar_wait_bounded(bar1, 0);
+    if (ok && active) compute_stage<P, DAG, 1, NS>(acc, b1, links, j, x, LsN, Ls, SB, g);
+    if (!ok) atomicOr(&aborted, 1);
+    __syncthreads();
+    if (tid < 32 && !aborted) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue_stage<P>(a, 3, b1, bar1, site0, nsite, SB, g, tid);
+    }
+    // stage 2: directions 4,5 in b0 (phase 1)
+    ok = !aborted && mbar_wait_bounded(bar0, 1);
+    if (ok && active) compute_stage<P, DAG, 2, NS>(acc, b0, links, j, x, LsN, Ls, SB, g);
+    if (!ok) atomicOr(&aborted, 1);
+    // stage 3: directions 6,7 in b1 (phase 1)
+    ok = !aborted && mbar_wait_bounded(bar1, 1);
+    if (ok && active) compute_stage<P, DAG, 3, NS>(acc, b1, links, j, x, LsN, Ls, SB, g);
+    if (!ok) atomicOr(&aborted, 1);
+    __syncthreads();   // every read of b0 is done before it becomes the tile
+    if (aborted && tid == 0 && a.err) atomicOr(a.err, 1);
+
+    const int tstride = Ls * 12 + 2;
+    T2 *tile = reinterpret_cast<T2 *>(b0);
+    hop_epilogue<P, NS>(a, acc, tile + j * tstride, mtx, site, x, LsN, active);
+}
+
+// ---------------------------------------------------------------- launch
+template <int P>
+size_t direct_smem(int Ls, int SB)
+{
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
+    return (size_t)SB * (Ls * 12 + 2) * sizeof(T2) + (size_t)3 * 2 * Ls * Ls * sizeof(R);
+}
+
+template <int P, bool DAG, int NS>
+cudaError_t launch_direct(const HopArgs &a, int SB, cudaStream_t st)
 {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(hop_kernel<P, DAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             160 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(hop_kernel<P, DAG, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (a.Ls * SB > 256) SB = 256 / a.Ls;
-    if (SB < 1) SB = 1;
-    dim3 block(a.Ls, SB);
-    dim3 grid((a.Vh + SB - 1) / SB);
-    hop_kernel<P, DAG><<<grid, block, hop_smem<P>(a.Ls, SB), st>>>(a);
+    const int LsN = a.Ls / NS;
+    hop_kernel<P, DAG, NS><<<(a.Vh + SB - 1) / SB, dim3(LsN, SB), direct_smem<P>(a.Ls, SB), st>>>(a);
     return cudaGetLastError();
+}
+
+template <int P, bool DAG, int NS>
+cudaError_t launch_staged(const HopArgs &a, int SB, cudaStream_t st)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(hop_staged_kernel<P, DAG, NS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    size_t o1, o2, o3, o4;
+    const size_t smem = staged_smem<P>(a.Ls, SB, &o1, &o2, &o3, &o4);
+    if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
+    const int LsN = a.Ls / NS;
+    hop_staged_kernel<P, DAG, NS><<<(a.Vh + SB - 1) / SB, dim3(LsN, SB), smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int P, bool DAG>
+cudaError_t launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
+{
+    if (var == 1) {
+        if (NS == 2) return launch_staged<P, DAG, 2>(a, SB, st);
+        return launch_staged<P, DAG, 1>(a, SB, st);
+    }
+    if (NS == 2) return launch_direct<P, DAG, 2>(a, SB, st);
+    return launch_direct<P, DAG, 1>(a, SB, st);
 }
 
 }  // namespace
 
-cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int SB, cudaStream_t st)
+int hop_default_variant(int prec) { return prec == DWF_F64 ? 0 : 1; }
+
+int hop_default_ns(int prec, int Ls)
 {
+    (void)prec;
+    (void)Ls;
+    return 1;
+}
+
+int hop_default_sb(int prec, int Ls, int NS)
+{
+    (void)prec;
+    const int LsN = Ls / NS;
+    int sb = 128 / LsN;
+    if (sb < 1) sb = 1;
+    return sb;
+}
+
+size_t hop_staged_smem_bytes(int prec, int Ls, int SB)
+{
+    size_t o1, o2, o3, o4;
     switch (prec) {
-    case DWF_F64: return dag ? launch_hop_t<DWF_F64, true>(a, SB, st) : launch_hop_t<DWF_F64, false>(a, SB, st);
-    case DWF_F32: return dag ? launch_hop_t<DWF_F32, true>(a, SB, st) : launch_hop_t<DWF_F32, false>(a, SB, st);
-    case DWF_F16: return dag ? launch_hop_t<DWF_F16, true>(a, SB, st) : launch_hop_t<DWF_F16, false>(a, SB, st);
+    case DWF_F64: return staged_smem<DWF_F64>(Ls, SB, &o1, &o2, &o3, &o4);
+    case DWF_F32: return staged_smem<DWF_F32>(Ls, SB, &o1, &o2, &o3, &o4);
+    default: return staged_smem<DWF_F16>(Ls, SB, &o1, &o2, &o3, &o4);
+    }
+}
+
+cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
+{
+    if (var < 0 || var > 1) var = hop_default_variant(prec);
+    if (NS <= 0 || NS > 2 || (a.Ls % NS) != 0) NS = hop_default_ns(prec, a.Ls);
+    if (SB <= 0) SB = hop_default_sb(prec, a.Ls, NS);
+    if ((a.Ls / NS) * SB > 256) SB = 256 / (a.Ls / NS);
+    if (SB < 1) SB = 1;
+    while (var == 1 && SB > 1 && hop_staged_smem_bytes(prec, a.Ls, SB) > 220 * 1024) SB /= 2;
+    if (var == 1 && hop_staged_smem_bytes(prec, a.Ls, SB) > 220 * 1024) var = 0;
+    switch (prec) {
+    case DWF_F64: return dag ? launch_pd<DWF_F64, true>(a, var, NS, SB, st) : launch_pd<DWF_F64, false>(a, var, NS, SB, st);
+    case DWF_F32: return dag ? launch_pd<DWF_F32, true>(a, var, NS, SB, st) : launch_pd<DWF_F32, false>(a, var, NS, SB, st);
+    case DWF_F16: return dag ? launch_pd<DWF_F16, true>(a, var, NS, SB, st) : launch_pd<DWF_F16, false>(a, var, NS, SB, st);
     default: return cudaErrorInvalidValue;
     }
 }

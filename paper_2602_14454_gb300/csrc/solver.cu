@@ -106,6 +106,7 @@ cudaError_t inner_iteration(dwf_ctx *h, const Bufs &B, cudaStream_t st)
     ue.Ls = h->Ls;
     ue.mat = h->mat(P, MAT_P);
     ue.scal = B.cg;
+    h->launches += 1;
     if ((e = launch_cg_update(P, ue, st)) != cudaSuccess) return e;
 
     HopArgs ka = hop_args(h, P, 1, B.ph, B.t, MAT_M);
@@ -155,6 +156,7 @@ cudaError_t normal_residual(dwf_ctx *h, const Bufs &B, cudaStream_t st)
 {
     const int P = B.ps;
     cudaError_t e;
+    h->launches += 1;
     if ((e = launch_convert(DWF_F64, B.r64, P, B.rs, h->Vh, h->Ls, st)) != cudaSuccess) return e;
     if ((e = mix(h, P, B.rs, B.ph, MAT_QT, st)) != cudaSuccess) return e;
     HopArgs a1 = hop_args(h, P, 1, B.ph, B.u, MAT_MT);
@@ -202,6 +204,7 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
                       cudaStream_t st)
 {
     auto t0 = std::chrono::steady_clock::now();
+    const long long launches0 = h->launches;
     dwf_solve_stats S;
     std::memset(&S, 0, sizeof(S));
     S.status = DWF_OK;
@@ -221,6 +224,7 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
     CK(launch_pack_full(DWF_F64, (const double *)b5, B.be, B.bo, h->eo2lex, h->Vh, h->V, h->Ls, st));
     CK(launch_norm2(DWF_F64, B.be, h->Vh, h->Ls, red(h, RED_STORE, B.n64), st));
     CK(launch_norm2(DWF_F64, B.bo, h->Vh, h->Ls, red(h, RED_STORE, B.aux), st));
+    h->launches += 3;
     if ((rc = read_scalars(B, hs, 3, st))) return rc;
     const double b5n = std::sqrt(hs[1].last + hs[2].last);
     if (!std::isfinite(b5n)) return dwf_set_error(DWF_ENONFINITE, "source contains NaN or Inf");
@@ -246,6 +250,7 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
     if (p->use_initial_guess) {
         FieldRef dummy = B.xo64;
         CK(launch_pack_full(DWF_F64, (const double *)x5, B.x64, dummy, h->eo2lex, h->Vh, h->V, h->Ls, st));
+        h->launches += 1;
     } else {
         CK(launch_zero(DWF_F64, B.x64, h->Vh, h->Ls, st));
     }
@@ -268,6 +273,7 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
         if (G.exec) cudaGraphExecDestroy(G.exec);
         G.exec = nullptr;
         cudaGraph_t g;
+        const long long saved = h->launches;
         CK(cudaStreamBeginCapture(X.cap, cudaStreamCaptureModeThreadLocal));
         for (int k = 0; k < N; ++k) {
             cudaError_t e = inner_iteration(h, B, X.cap);
@@ -277,13 +283,17 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
             }
         }
         CK(cudaStreamEndCapture(X.cap, &g));
+        h->launches = saved;
         CK(cudaGraphInstantiate(&G.exec, g, 0));
         cudaGraphDestroy(g);
         G.key = keybuf;
     }
 
     auto reliable = [&](bool first) -> int {
-        if (!first) CK(launch_accum_x((double *)B.x64.v, B.xs.v, B.xp, h->Vh, h->Ls, st));
+        if (!first) {
+            CK(launch_accum_x((double *)B.x64.v, B.xs.v, B.xp, h->Vh, h->Ls, st));
+            h->launches += 1;
+        }
         CK(true_residual(h, B, st));
         CgScalars n64;
         CK(cudaMemcpyAsync(&hs[1], B.n64, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
@@ -300,6 +310,7 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
         CK(normal_residual(h, B, st));
         reliable_fix_kernel<<<1, 1, 0, st>>>(B.cg, B.n64, first ? 1 : 0);
         CK(cudaGetLastError());
+        h->launches += 1;
         dapp += 1;
         CK(cudaMemcpyAsync(hs, B.cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -320,6 +331,7 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
             }
             if (p->use_graph) {
                 CK(cudaGraphLaunch(G.exec, st));
+                h->launches += 5LL * N;
             } else {
                 for (int k = 0; k < N; ++k) CK(inner_iteration(h, B, st));
             }
@@ -375,12 +387,14 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
         target *= 0.1;
     }
     CK(launch_unpack_full(DWF_F64, B.x64, B.xo64, (double *)x5, h->eo2lex, h->Vh, h->V, h->Ls, st));
+    h->launches += 1;
     CK(cudaStreamSynchronize(st));
     if (status == DWF_OK && S.true_residual > p->tol) status = DWF_ENOTCONV;
     S.status = status;
     S.iterations = iters;
     S.reliable_updates = nru;
     S.d_applications = dapp;
+    S.kernel_launches = h->launches - launches0;
     S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = S;
     if (status != DWF_OK) dwf_set_error(status, "solver did not reach the tolerance");

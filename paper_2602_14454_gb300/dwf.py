@@ -30,7 +30,8 @@ STATUS = {0: "DWF_OK", 1: "DWF_EINVAL", 2: "DWF_ENOMEM", 3: "DWF_ECUDA", 4: "DWF
 EXPORTED = ["dwf_create", "dwf_destroy", "dwf_strerror", "dwf_last_error", "dwf_set_gauge",
             "dwf_apply", "dwf_apply_dag", "dwf_source_5d", "dwf_project_4d",
             "dwf_solve_params_default", "dwf_solve", "dwf_propagator_host", "dwf_solve_batch",
-            "dwf_fifth_matrix", "dwf_device_bytes", "dwf_time_hop"]
+            "dwf_fifth_matrix", "dwf_device_bytes", "dwf_time_hop", "dwf_launch_count",
+            "dwf_set_hop_config", "dwf_get_hop_config", "dwf_autotune", "dwf_device_status"]
 
 
 class SolveParams(ctypes.Structure):
@@ -43,13 +44,14 @@ class SolveStats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int),
                 ("d_applications", ctypes.c_int), ("true_residual", ctypes.c_double),
                 ("eo_residual", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("history", ctypes.c_double * 64), ("n_history", ctypes.c_int)]
+                ("history", ctypes.c_double * 64), ("n_history", ctypes.c_int),
+                ("kernel_launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return dict(status=STATUS.get(self.status, self.status), iterations=self.iterations,
                     reliable_updates=self.reliable_updates, d_applications=self.d_applications,
                     true_residual=self.true_residual, eo_residual=self.eo_residual, seconds=self.seconds,
-                    history=list(self.history[:self.n_history]))
+                    history=list(self.history[:self.n_history]), kernel_launches=self.kernel_launches)
 
 
 class DwfError(RuntimeError):
@@ -93,6 +95,12 @@ def lib():
     L.dwf_device_bytes.argtypes = [vp]
     L.dwf_device_bytes.restype = ctypes.c_size_t
     L.dwf_time_hop.argtypes = [vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]
+    L.dwf_set_hop_config.argtypes = [vp, i, i, i, i]
+    L.dwf_get_hop_config.argtypes = [vp, i, ip, ip, ip]
+    L.dwf_device_status.argtypes = [vp, vp]
+    L.dwf_autotune.argtypes = [vp, i, ctypes.c_char_p, vp]
+    L.dwf_launch_count.argtypes = [vp]
+    L.dwf_launch_count.restype = ctypes.c_longlong
     _lib = L
     return L
 
@@ -219,6 +227,27 @@ class Operator:
         out = (ctypes.c_double * (self.Ls * self.Ls))()
         check(lib().dwf_fifth_matrix(self._h, int(which), int(chirality), out))
         return np.array(out, dtype=np.float64).reshape(self.Ls, self.Ls)
+
+    def set_hop_config(self, prec, variant, ns, sb):
+        check(lib().dwf_set_hop_config(self._h, PREC[prec], int(variant), int(ns), int(sb)))
+
+    def hop_config(self, prec):
+        var, ns, sb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(lib().dwf_get_hop_config(self._h, PREC[prec], ctypes.byref(var), ctypes.byref(ns),
+                                       ctypes.byref(sb)))
+        return var.value, ns.value, sb.value
+
+    def device_status(self):
+        """DWF_OK, or raises DwfError(DWF_ETIMEOUT) if a bounded device wait gave up."""
+        return check(lib().dwf_device_status(self._h, _stream()))
+
+    def autotune(self, prec, cache_path=None):
+        cp = cache_path.encode() if cache_path else None
+        check(lib().dwf_autotune(self._h, PREC[prec], cp, _stream()))
+        return self.hop_config(prec)
+
+    def launch_count(self):
+        return int(lib().dwf_launch_count(self._h))
 
     def device_bytes(self):
         return int(lib().dwf_device_bytes(self._h))

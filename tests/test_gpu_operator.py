@@ -132,6 +132,43 @@ def test_full_size_eo_parity():
         assert rel(got, want) < TOL[prec]
 
 
+HOP_CONFIGS = [(0, 1, 3), (0, 2, 5), (1, 1, 3), (1, 2, 7), (1, 1, 16), (1, 2, 1)]
+
+
+@pytest.mark.parametrize("cfg", HOP_CONFIGS, ids=lambda c: "var%d_ns%d_sb%d" % c)
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("Ls", [8, 12])
+def test_hop_configurations_ragged_tiles(cfg, prec, Ls):
+    """Every hop variant and tiling gives the same operator; the lattice has
+    Vh = 48 sites so most CTA sizes leave a ragged last tile."""
+    var, ns, sb = cfg
+    dims = (6, 2, 2, 4)
+    op, ref = make_pair(dims, Ls, 1.8, 0.02, 1.5, 0.5, "neff", 0.6, seed=51)
+    op.set_hop_config(prec, var, ns, sb)
+    assert op.hop_config(prec) == (var, ns, sb)
+    x = ref.to_eo(inputs.gaussian_5d(dims, Ls, 52), 0)
+    for dag in (False, True):
+        got = to_np(op.apply(to_gpu(x), op="eo", prec=prec, dag=dag))
+        assert rel(got, ref.d_pc(x, dag=dag)) < TOL[prec]
+    xf = inputs.gaussian_5d(dims, Ls, 53)
+    got = to_np(op.apply(to_gpu(xf), op="full", prec=prec))
+    assert rel(got, ref.apply(xf)) < TOL[prec]
+    op.device_status()
+
+
+def test_autotuner_picks_a_valid_configuration(tmp_path):
+    from paper_2602_14454_gb300 import dwf
+    dims = (8, 8, 4, 4)
+    op, ref = make_pair(dims, 16, 1.8, 0.01, 1.5, 0.5, "standard", 1.0, seed=61)
+    cache = str(tmp_path / "tune.txt")
+    cfg = op.autotune("f32", cache)
+    assert cfg[0] in (0, 1) and cfg[1] in (1, 2) and cfg[2] >= 1
+    op2, _ = make_pair(dims, 16, 1.8, 0.01, 1.5, 0.5, "standard", 1.0, seed=61)
+    assert op2.autotune("f32", cache) == cfg          # cache hit
+    x = ref.to_eo(inputs.gaussian_5d(dims, 16, 62), 0)
+    assert rel(to_np(op.apply(to_gpu(x), op="eo", prec="f32")), ref.d_pc(x)) < TOL["f32"]
+
+
 def test_errors():
     import torch
     from paper_2602_14454_gb300 import dwf
