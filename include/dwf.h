@@ -200,19 +200,31 @@ long long dwf_launch_count(dwf_handle h);
 
 /* Configuration of the hop kernel in precision prec: variant 0 loads the
  * neighbour spinors directly from global memory, variant 1 stages the
- * neighbour sites in shared memory with TMA bulk copies; ns fifth-direction
+ * neighbour sites in shared memory with TMA bulk copies, variant 2 is a
+ * persistent kernel whose producer warp streams the neighbour sites through a
+ * ring of shared-memory stages for the consumer warps; ns fifth-direction
  * slices per thread (1, or 2 when Ls is even); sb four-dimensional sites per
  * CTA.  -1 / 0 select the built-in defaults.  No numerical effect. */
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb);
 int dwf_get_hop_config(dwf_handle h, int prec, int *variant, int *ns, int *sb);
 
-/* Autotuner: times every hop configuration (both variants, ns in {1, 2},
+/* Autotuner: times every hop configuration (all variants, ns in {1, 2},
  * CTAs of 64 to 256 threads) on this handle's lattice with CUDA events on
  * `stream` and keeps the fastest.  cache_path (host string, may be NULL)
  * names a text file of earlier results keyed by device name, lattice, Ls and
  * precision: a hit skips the timing, a miss appends the new result.  Needs
  * the gauge field. */
 int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream);
+
+/* Fifth-direction mixing in precision prec: 0 applies the dense per-chirality
+ * Ls x Ls matrices, 1 their structured form (diagonal, bidiagonal-plus-corner
+ * and closed-form inverse factors, about 6 flops per element instead of
+ * 2 Ls; compiled for the direct hop variant, which it then selects).
+ * -1 restores the default (dense).  mode 1 is
+ * refused when the handle's parameters make the structured form unavailable
+ * (|kappa| = |beta0/alpha0| >= 0.95). */
+int dwf_set_mix_mode(dwf_handle h, int prec, int mode);
+int dwf_get_mix_mode(dwf_handle h, int prec, int *mode);
 
 /* Synchronise `stream` and report device-side failures of earlier calls on
  * the handle: DWF_ETIMEOUT if a bounded wait inside a kernel gave up (the

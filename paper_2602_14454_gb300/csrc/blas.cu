@@ -22,8 +22,30 @@ __device__ __forceinline__ void load_mat(R *dst, const void *src, int Ls)
     for (int k = tid; k < 2 * Ls * Ls; k += nt) dst[k] = reinterpret_cast<const R *>(src)[k];
 }
 
+// o = (mixing of row s of site j's tile): dense matrix or structured program
+// (the structured form transforms the CTA's whole tile in place first).  The
+// tile must be complete and visible; every thread of the CTA must call it.
+template <int MIX, typename T2, typename R>
+__device__ __forceinline__ void mix_tile_any(const void *prog, const R *mtx, T2 *tile, int tstride, int j,
+                                             int s, int Ls, bool active, T2 (*o)[12])
+{
+    if constexpr (MIX == 1) {
+        chain_mix<R>(reinterpret_cast<const MixProg<R> *>(prog), tile, tstride, blockDim.y, Ls,
+                     threadIdx.y * blockDim.x + threadIdx.x, blockDim.x * blockDim.y);
+        __syncthreads();
+        if (active) {
+            T2 h[12];
+            ld_tile_row(tile + j * tstride + s * 12, h);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) o[0][k] = p_add(o[0][k], h[k]);
+        }
+    } else if (active) {
+        mix_pairs<1>(mtx, tile + j * tstride, s, Ls, o);
+    }
+}
+
 // out(site, s) = sum_t M[chi][s][t] in(site, t)
-template <int P>
+template <int P, int MIX>
 __global__ void __launch_bounds__(256) mix_kernel(const MixArgs a)
 {
     typedef typename Tr<P>::real R;
@@ -44,16 +66,15 @@ __global__ void __launch_bounds__(256) mix_kernel(const MixArgs a)
         for (int k = 0; k < 12; ++k) dst[k] = v[k];
     }
     __syncthreads();
-    if (!active) return;
     T2 o[1][12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) o[0][k] = p_splat((R)0);
-    mix_pairs<1>(mtx, tile + j * tstride, s, Ls, o);
-    st_pairs<P>(a.out, (size_t)site, s, Ls, o[0]);
+    mix_tile_any<MIX>(a.prog, mtx, tile, tstride, j, s, Ls, active, o);
+    if (active) st_pairs<P>(a.out, (size_t)site, s, Ls, o[0]);
 }
 
 // p = r + beta p (or p = r), phat = M p
-template <int P>
+template <int P, int MIX>
 __global__ void __launch_bounds__(256) cg_update_kernel(const CgUpdateArgs a)
 {
     typedef typename Tr<P>::real R;
@@ -84,12 +105,11 @@ __global__ void __launch_bounds__(256) cg_update_kernel(const CgUpdateArgs a)
         for (int k = 0; k < 12; ++k) dst[k] = p[k];
     }
     __syncthreads();
-    if (!active) return;
     T2 o[1][12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) o[0][k] = p_splat((R)0);
-    mix_pairs<1>(mtx, tile + j * tstride, s, Ls, o);
-    st_pairs<P>(a.phat, (size_t)site, s, Ls, o[0]);
+    mix_tile_any<MIX>(a.prog, mtx, tile, tstride, j, s, Ls, active, o);
+    if (active) st_pairs<P>(a.phat, (size_t)site, s, Ls, o[0]);
 }
 
 template <int P>
@@ -100,33 +120,46 @@ size_t tile_smem(int Ls, int SB)
     return (size_t)SB * (Ls * 12 + 2) * sizeof(T2) + (size_t)2 * Ls * Ls * sizeof(R);
 }
 
-template <int P>
-cudaError_t launch_mix_t(const MixArgs &a, cudaStream_t st)
+template <int P, int MIX>
+cudaError_t launch_mix_m(const MixArgs &a, cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(mix_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaError_t e =
+            cudaFuncSetAttribute(mix_kernel<P, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int SB = tile_sb(a.Ls);
-    mix_kernel<P><<<(a.Vh + SB - 1) / SB, dim3(a.Ls, SB), tile_smem<P>(a.Ls, SB), st>>>(a);
+    mix_kernel<P, MIX><<<(a.Vh + SB - 1) / SB, dim3(a.Ls, SB), tile_smem<P>(a.Ls, SB), st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_mix_t(const MixArgs &a, cudaStream_t st)
+{
+    return a.mixmode == 1 ? launch_mix_m<P, 1>(a, st) : launch_mix_m<P, 0>(a, st);
+}
+
+template <int P, int MIX>
+cudaError_t launch_cg_update_m(const CgUpdateArgs &a, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(cg_update_kernel<P, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int SB = tile_sb(a.Ls);
+    cg_update_kernel<P, MIX><<<(a.Vh + SB - 1) / SB, dim3(a.Ls, SB), tile_smem<P>(a.Ls, SB), st>>>(a);
     return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t launch_cg_update_t(const CgUpdateArgs &a, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(cg_update_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    const int SB = tile_sb(a.Ls);
-    cg_update_kernel<P><<<(a.Vh + SB - 1) / SB, dim3(a.Ls, SB), tile_smem<P>(a.Ls, SB), st>>>(a);
-    return cudaGetLastError();
+    return a.mixmode == 1 ? launch_cg_update_m<P, 1>(a, st) : launch_cg_update_m<P, 0>(a, st);
 }
 
 // ------------------------------------------------------------------ packing

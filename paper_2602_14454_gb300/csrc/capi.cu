@@ -40,6 +40,31 @@ const void *dwf_ctx::mat(int prec, int id) const
     return (const float *)mats_dev[1] + per * id;
 }
 
+int dwf_ctx::mix_mode(int prec) const
+{
+    if (!fm.structured) return 0;
+    if (mixmode[prec] >= 0) return mixmode[prec];
+    return 0;
+}
+
+const void *dwf_ctx::prog(int prec, int id) const
+{
+    if (prec == DWF_F64) return (const MixProg<double> *)progs_dev[0] + id;
+    return (const MixProg<float> *)progs_dev[1] + id;
+}
+
+// MatId of a matrix pointer handed out by mat(); -1 if it is not one
+static int mat_id_of(const dwf_ctx *h, int prec, const void *p)
+{
+    if (!p) return -1;
+    const size_t per = (size_t)2 * h->Ls * h->Ls * (prec == DWF_F64 ? 8 : 4);
+    const char *base = (const char *)h->mats_dev[prec == DWF_F64 ? 0 : 1];
+    const ptrdiff_t off = (const char *)p - base;
+    if (off < 0 || off % (ptrdiff_t)per) return -1;
+    const int id = (int)(off / (ptrdiff_t)per);
+    return id < MAT_COUNT ? id : -1;
+}
+
 const void *dwf_ctx::gauge_for(int prec, int out_par) const
 {
     const size_t n = (size_t)Vh * 8 * 18 * out_par;
@@ -93,13 +118,35 @@ HopArgs hop_args(dwf_ctx *h, int prec, int out_par, FieldRef in, FieldRef out, i
     a.Ls = h->Ls;
     a.post = h->mat(prec, post);
     a.err = h->errflag();
+    a.ext[0] = h->dims[0] / 2;
+    a.ext[1] = h->dims[1];
+    a.ext[2] = h->dims[2];
+    a.ext[3] = h->dims[3];
+    return a;
+}
+
+// Fills in the structured programs that match the dense matrices of `a`.
+HopArgs with_programs(dwf_ctx *h, int prec, const HopArgs &a0)
+{
+    HopArgs a = a0;
+    a.mixmode = h->mix_mode(prec);
+    if (a.mixmode == 1) {
+        const int ip = mat_id_of(h, prec, a.post), iy = mat_id_of(h, prec, a.ymat), iz = mat_id_of(h, prec, a.zmat);
+        if (ip < 0 || (a.ymat && iy < 0) || (a.zmat && iz < 0)) {
+            a.mixmode = 0;
+        } else {
+            a.post_prog = h->prog(prec, ip);
+            a.y_prog = a.ymat ? h->prog(prec, iy) : nullptr;
+            a.z_prog = a.zmat ? h->prog(prec, iz) : nullptr;
+        }
+    }
     return a;
 }
 
 cudaError_t hop(dwf_ctx *h, int prec, bool dag, const HopArgs &a, cudaStream_t st)
 {
     h->launches += 1;
-    return launch_hop(prec, dag, a, h->hop_var[prec], h->hop_ns[prec], h->hop_sb[prec], st);
+    return launch_hop(prec, dag, with_programs(h, prec, a), h->hop_var[prec], h->hop_ns[prec], h->hop_sb[prec], st);
 }
 
 cudaError_t mix(dwf_ctx *h, int prec, FieldRef in, FieldRef out, int id, cudaStream_t st)
@@ -110,6 +157,8 @@ cudaError_t mix(dwf_ctx *h, int prec, FieldRef in, FieldRef out, int id, cudaStr
     m.Vh = h->Vh;
     m.Ls = h->Ls;
     m.mat = h->mat(prec, id);
+    m.mixmode = h->mix_mode(prec);
+    m.prog = h->prog(prec, id);
     h->launches += 1;
     return launch_mix(prec, m, st);
 }
@@ -220,6 +269,40 @@ int dwf_create(const int dims[4], int Ls, double M0, double mf, double b, double
         return fail(e, "cudaMemcpy");
     if ((e = cudaMemcpy(h->mats_dev[1], mf32.data(), mf32.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e, "cudaMemcpy");
+    {
+        // structured programs, FP64 and FP32 copies
+        std::vector<MixProg<double>> pd(MAT_COUNT);
+        std::vector<MixProg<float>> pf(MAT_COUNT);
+        for (int id = 0; id < MAT_COUNT; ++id) {
+            const FifthMatrices::Prog &s = h->fm.prog[id];
+            MixProg<double> &d = pd[id];
+            MixProg<float> &f = pf[id];
+            std::memset(&d, 0, sizeof(d));
+            std::memset(&f, 0, sizeof(f));
+            d.inv = f.inv = s.inv;
+            d.shift = f.shift = s.shift;
+            for (int chi = 0; chi < 2; ++chi) {
+                d.up[chi] = f.up[chi] = s.up[chi];
+                for (int k = 0; k < LS_MAX; ++k) {
+                    d.d1[chi][k] = s.d1[chi][k];
+                    d.d2[chi][k] = s.d2[chi][k];
+                    f.d1[chi][k] = (float)s.d1[chi][k];
+                    f.d2[chi][k] = (float)s.d2[chi][k];
+                }
+            }
+            d.s0 = s.s0, d.s1 = s.s1, d.a0inv = s.a0inv, d.kappa = s.kappa, d.mneg = s.mneg, d.corner = s.corner;
+            f.s0 = (float)s.s0, f.s1 = (float)s.s1, f.a0inv = (float)s.a0inv, f.kappa = (float)s.kappa;
+            f.mneg = (float)s.mneg, f.corner = (float)s.corner;
+        }
+        if ((e = cudaMalloc(&h->progs_dev[0], pd.size() * sizeof(pd[0]))) != cudaSuccess) return fail(e, "cudaMalloc");
+        if ((e = cudaMalloc(&h->progs_dev[1], pf.size() * sizeof(pf[0]))) != cudaSuccess) return fail(e, "cudaMalloc");
+        if ((e = cudaMemcpy(h->progs_dev[0], pd.data(), pd.size() * sizeof(pd[0]), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return fail(e, "cudaMemcpy");
+        if ((e = cudaMemcpy(h->progs_dev[1], pf.data(), pf.size() * sizeof(pf[0]), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return fail(e, "cudaMemcpy");
+    }
     if ((e = cudaMalloc(&h->nbr, (size_t)2 * h->Vh * 8 * sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&h->eo2lex, (size_t)2 * h->Vh * sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&h->partials, ((size_t)h->Vh + 8192) * sizeof(double))) != cudaSuccess)
@@ -248,6 +331,8 @@ int dwf_destroy(dwf_handle h)
         if (h->mats_dev[k]) cudaFree(h->mats_dev[k]);
         if (h->gauge[k]) cudaFree(h->gauge[k]);
     }
+    for (int k = 0; k < 2; ++k)
+        if (h->progs_dev[k]) cudaFree(h->progs_dev[k]);
     if (h->nbr) cudaFree(h->nbr);
     if (h->eo2lex) cudaFree(h->eo2lex);
     if (h->partials) cudaFree(h->partials);
@@ -420,13 +505,29 @@ long long dwf_launch_count(dwf_handle h) { return h ? h->launches : 0; }
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb)
 {
     if (!h || prec < 0 || prec > 2) return dwf_set_error(DWF_EINVAL, "bad handle or precision");
-    if (variant < -1 || variant > 1) return dwf_set_error(DWF_EINVAL, "variant must be -1, 0 or 1");
+    if (variant < -1 || variant > 4) return dwf_set_error(DWF_EINVAL, "variant must be -1 or 0..4");
     if (ns < 0 || ns > 2 || (ns == 2 && h->Ls % 2)) return dwf_set_error(DWF_EINVAL, "ns must be 0, 1 or 2 (2 needs even Ls)");
     const int nsv = ns ? ns : hop_default_ns(prec, h->Ls);
     if (sb < 0 || (sb && (h->Ls / nsv) * sb > 256)) return dwf_set_error(DWF_EINVAL, "sb out of range (CTA > 256 threads)");
     h->hop_var[prec] = variant;
     h->hop_ns[prec] = ns;
     h->hop_sb[prec] = sb;
+    return DWF_OK;
+}
+
+int dwf_set_mix_mode(dwf_handle h, int prec, int mode)
+{
+    if (!h || prec < 0 || prec > 2 || mode < -1 || mode > 1) return dwf_set_error(DWF_EINVAL, "bad argument");
+    if (mode == 1 && !h->fm.structured)
+        return dwf_set_error(DWF_EINVAL, "the structured mixing is not available for these parameters");
+    h->mixmode[prec] = mode;
+    return DWF_OK;
+}
+
+int dwf_get_mix_mode(dwf_handle h, int prec, int *mode)
+{
+    if (!h || prec < 0 || prec > 2 || !mode) return dwf_set_error(DWF_EINVAL, "bad argument");
+    *mode = h->mix_mode(prec);
     return DWF_OK;
 }
 
@@ -454,14 +555,15 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
         FILE *f = std::fopen(cache_path, "r");
         if (f) {
             char k[256];
-            int var, ns, sb;
+            int var, ns, sb, mix;
             double us;
             bool hit = false;
-            while (std::fscanf(f, "%255s %d %d %d %lf", k, &var, &ns, &sb, &us) == 5) {
+            while (std::fscanf(f, "%255s %d %d %d %d %lf", k, &var, &ns, &sb, &mix, &us) == 6) {
                 if (std::strcmp(k, key) == 0) {
                     h->hop_var[prec] = var;
                     h->hop_ns[prec] = ns;
                     h->hop_sb[prec] = sb;
+                    h->mixmode[prec] = (mix == 1 && !h->fm.structured) ? 0 : mix;
                     hit = true;
                 }
             }
@@ -470,36 +572,41 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
         }
     }
     double best = 1e30;
-    int bvar = -1, bns = 0, bsb = 0;
-    for (int var = 0; var <= 1; ++var)
-        for (int ns = 1; ns <= 2; ++ns) {
-            if (h->Ls % ns) continue;
-            const int LsN = h->Ls / ns;
-            for (int threads = 64; threads <= 256; threads += 64) {
-                const int sb = threads / LsN;
-                if (sb < 1 || LsN * sb > 256) continue;
-                if (var == 1 && hop_staged_smem_bytes(prec, h->Ls, sb) > 220 * 1024) continue;
-                h->hop_var[prec] = var;
-                h->hop_ns[prec] = ns;
-                h->hop_sb[prec] = sb;
-                double us = 0, by = 0;
-                int rc = dwf_time_hop(h, prec, 10, 0, &us, &by, stream);
-                if (rc) return rc;
-                if (us < best) {
-                    best = us;
-                    bvar = var;
-                    bns = ns;
-                    bsb = sb;
+    int bvar = -1, bns = 0, bsb = 0, bmix = 0;
+    for (int mix = 0; mix <= (h->fm.structured ? 1 : 0); ++mix)
+        for (int var = 0; var <= 4; ++var)
+            for (int ns = 1; ns <= 2; ++ns) {
+                if (h->Ls % ns) continue;
+                const int LsN = h->Ls / ns;
+                for (int threads = 64; threads <= 256; threads += 64) {
+                    const int sb = threads / LsN;
+                    if (sb < 1 || LsN * sb > 256) continue;
+                    if (var == 1 && hop_staged_smem_bytes(prec, h->Ls, sb) > 220 * 1024) continue;
+                    if (var == 2 && hop_pipe_smem_bytes(prec, h->Ls, sb) > 220 * 1024) continue;
+                    h->mixmode[prec] = mix;
+                    h->hop_var[prec] = var;
+                    h->hop_ns[prec] = ns;
+                    h->hop_sb[prec] = sb;
+                    double us = 0, by = 0;
+                    int rc = dwf_time_hop(h, prec, 10, 0, &us, &by, stream);
+                    if (rc) return rc;
+                    if (us < best) {
+                        best = us;
+                        bvar = var;
+                        bns = ns;
+                        bsb = sb;
+                        bmix = mix;
+                    }
                 }
             }
-        }
     h->hop_var[prec] = bvar;
     h->hop_ns[prec] = bns;
     h->hop_sb[prec] = bsb;
+    h->mixmode[prec] = bmix;
     if (cache_path) {
         FILE *f = std::fopen(cache_path, "a");
         if (f) {
-            std::fprintf(f, "%s %d %d %d %.3f\n", key, bvar, bns, bsb, best);
+            std::fprintf(f, "%s %d %d %d %d %.3f\n", key, bvar, bns, bsb, bmix, best);
             std::fclose(f);
         }
     }

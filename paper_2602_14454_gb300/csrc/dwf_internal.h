@@ -108,12 +108,17 @@ struct HopArgs {
     const double *xalpha = nullptr;
     RedArgs red;
     int *err = nullptr;            // bit 0 set when a bounded device wait gave up
+    int ext[4] = {0, 0, 0, 0};     // half-lattice extents (Lx/2, Ly, Lz, Lt): blocked hop variant
+    int mixmode = 0;               // 0 dense matrices, 1 structured programs (MixProg)
+    const void *post_prog = nullptr, *y_prog = nullptr, *z_prog = nullptr;
 };
 
 struct MixArgs {
     FieldRef in, out;
     int Vh = 0, Ls = 0;
     const void *mat = nullptr;     // [2][Ls][Ls] transposed
+    int mixmode = 0;
+    const void *prog = nullptr;
 };
 
 // p = r + beta p ; phat = P p   (or with init: p = r)
@@ -123,11 +128,14 @@ struct CgUpdateArgs {
     const void *mat = nullptr;
     const CgScalars *scal = nullptr;
     int init = 0;
+    int mixmode = 0;
+    const void *prog = nullptr;
 };
 
 // ------------------------------------------------------------ launchers
 // prec: DWF_F64 / DWF_F32 / DWF_F16 (template dispatch inside)
-// var: 0 direct neighbour loads, 1 TMA-staged neighbour sites; ns: fifth-direction
+// var: 0 direct neighbour loads, 1 TMA-staged neighbour sites, 2 persistent warp-specialised
+// TMA pipeline; ns: fifth-direction
 // slices per thread (1, or 2 when Ls is even); sb: sites per CTA.
 // var < 0 / ns <= 0 / sb <= 0 pick the defaults.
 cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int var, int ns, int sb, cudaStream_t st);
@@ -135,6 +143,7 @@ int hop_default_variant(int prec);
 int hop_default_ns(int prec, int Ls);
 int hop_default_sb(int prec, int Ls, int ns);
 size_t hop_staged_smem_bytes(int prec, int Ls, int sb);
+size_t hop_pipe_smem_bytes(int prec, int Ls, int sb);
 cudaError_t launch_mix(int prec, const MixArgs &a, cudaStream_t st);
 cudaError_t launch_cg_update(int prec, const CgUpdateArgs &a, cudaStream_t st);
 
@@ -175,6 +184,30 @@ struct FifthMatrices {
     std::vector<double> A5[2], A5inv[2], B[2], R[2], Rinv[2];
     std::vector<double> mats[MAT_COUNT][2];
     double dee_norm2 = 0;   // spectral norm of D_ee (max over chiralities)
+    // structured form of every matrix (see MixProg); valid when `structured`
+    bool structured = false;
+    struct Prog {
+        int inv, shift, up[2];
+        double s0, s1, a0inv, kappa, mneg, corner;
+        double d1[2][LS_MAX], d2[2][LS_MAX];
+    } prog[MAT_COUNT];
+};
+
+// Structured fifth-direction mixing, applied along one chain x_0..x_{Ls-1}
+// (one real component of one site, all slices) of chirality chi:
+//   x <- d1 * x ;  if inv: x <- A5^-1 x ;  if shift: x <- (s0 + s1 K) x ;  x <- d2 * x
+// where K is the chirality's fifth-direction hop and "up[chi]" tells whether
+// it reads x_{s+1} (with the corner -m x_0 at s = Ls-1) or x_{s-1} (corner
+// -m x_{Ls-1} at s = 0); transposed matrices flip the direction.  A5^-1 uses
+// the closed form of the bidiagonal-plus-corner inverse: with
+// kappa = -beta0/alpha0, x_last = (sum_t kappa^(Ls-1-t) v_t / alpha0) / (1 + m kappa^Ls),
+// then the forward recurrence x_s = v_s / alpha0 + kappa x_{s-1} from
+// x_{-1} = -m x_last.  Stable for |kappa| < 1.
+template <typename R>
+struct MixProg {
+    int inv, shift, up[2];
+    R s0, s1, a0inv, kappa, mneg, corner;
+    R d1[2][LS_MAX], d2[2][LS_MAX];
 };
 
 // Builds every matrix above; returns false when A5 is singular.
@@ -194,6 +227,10 @@ struct dwf_ctx {
     int device;
     dwf::FifthMatrices fm;
     void *mats_dev[3] = {nullptr, nullptr, nullptr};   // double / float / float copies (F16 uses float)
+    void *progs_dev[2] = {nullptr, nullptr};           // MixProg<double>[MAT_COUNT], MixProg<float>[MAT_COUNT]
+    int mixmode[3] = {-1, -1, -1};    // fifth-direction mixing per precision: 0 dense, 1 structured, -1 default
+    int mix_mode(int prec) const;
+    const void *prog(int prec, int id) const;
     int *nbr = nullptr;       // [2][Vh][8]
     int *eo2lex = nullptr;    // [2][Vh]
     void *gauge[3] = {nullptr, nullptr, nullptr};      // per precision, [2][Vh][8][18]

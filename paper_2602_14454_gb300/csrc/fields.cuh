@@ -254,6 +254,66 @@ __device__ __forceinline__ void ld_tile_row(const double2 *row, double2 *h)
     for (int q = 0; q < 12; ++q) h[q] = row[q];
 }
 
+// Structured mixing (see MixProg in dwf_internal.h) applied in place to the
+// tiles of `nsites` sites (site stride tstride pairs, row stride 12 pairs):
+// one chain = one real component of one site over all Ls rows.  The caller's
+// `nthr` threads (index tid) share the chains; no barrier inside.
+template <typename R, typename T2>
+__device__ __forceinline__ void chain_mix(const MixProg<R> *pg, T2 *tile, int tstride, int nsites, int Ls, int tid,
+                                          int nthr)
+{
+    R *t = reinterpret_cast<R *>(tile);
+    const R kappa = pg->kappa, a0inv = pg->a0inv, mneg = pg->mneg;
+    for (int c = tid; c < nsites * 24; c += nthr) {
+        const int jj = c / 24, k = c % 24;
+        const int chi = (k >> 1) & 1;
+        R *base = t + (size_t)jj * tstride * 2 + k;
+        const bool up = pg->up[chi] != 0;
+        const R *d1 = pg->d1[chi], *d2 = pg->d2[chi];
+        R v[LS_MAX];
+        R last = 0;
+#pragma unroll
+        for (int u = 0; u < LS_MAX; ++u)
+            if (u < Ls) {
+                const int s = up ? Ls - 1 - u : u;
+                v[u] = base[s * 24] * d1[s];
+            }
+        if (pg->inv) {
+            R acc = 0;
+#pragma unroll
+            for (int u = 0; u < LS_MAX; ++u)
+                if (u < Ls) acc = kappa * acc + v[u];
+            R prev = mneg * (acc * a0inv * pg->corner);
+#pragma unroll
+            for (int u = 0; u < LS_MAX; ++u)
+                if (u < Ls) {
+                    v[u] = v[u] * a0inv + kappa * prev;
+                    prev = v[u];
+                }
+        }
+        if (pg->shift) {
+#pragma unroll
+            for (int u = 0; u < LS_MAX; ++u)
+                if (u == Ls - 1) last = v[u];
+            const R s0 = pg->s0, s1 = pg->s1;
+            R prev = mneg * last;
+#pragma unroll
+            for (int u = 0; u < LS_MAX; ++u)
+                if (u < Ls) {
+                    const R tt = v[u];
+                    v[u] = s0 * tt + s1 * prev;
+                    prev = tt;
+                }
+        }
+#pragma unroll
+        for (int u = 0; u < LS_MAX; ++u)
+            if (u < Ls) {
+                const int s = up ? Ls - 1 - u : u;
+                base[s * 24] = v[u] * d2[s];
+            }
+    }
+}
+
 // The tile rows must be 16-byte aligned (row stride 12 pairs, site stride a
 // multiple of 2 pairs).
 template <int NS, typename T2, typename R>

@@ -182,10 +182,55 @@ __device__ __forceinline__ void put_tile(T2 *tile, int s, const T2 *v)
 }
 
 // ------------------------------------------------------------ the epilogue
-// acc: hop result of this thread's NS slices.  Must be called by every thread.
-template <int P, int NS, typename T2, typename R>
-__device__ __forceinline__ void hop_epilogue(const HopArgs &a, T2 (*acc)[12], T2 *mytile, const R *mtx, int site,
-                                             int x, int LsN, bool active)
+struct CtaBarrier {
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+// named barrier 1 over the n consumer threads of a warp-specialised CTA
+struct ConsumerBarrier {
+    int n;
+    __device__ __forceinline__ void sync() const { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
+};
+
+// Where the CTA's tile lives and which threads share the structured mixing.
+template <typename T2>
+struct TileCtx {
+    T2 *tile0;     // tile of the CTA's first site
+    int tstride;   // pairs between consecutive sites
+    int nsites;    // sites in the tile
+    int tid, nthr; // this thread among the threads that share the work
+};
+
+// o[n] += (mixing of this thread's rows of the tile).  Dense: Ls x Ls matrix M
+// from shared memory.  Structured: the CTA first transforms the whole tile in
+// place along its chains, then every thread reads its rows back.  The tile
+// must hold the input and be visible to all threads on entry.
+template <int MIX, int NS, typename T2, typename R, typename Bar>
+__device__ __forceinline__ void mix_into(const void *prog, const R *M, const TileCtx<T2> &tc, T2 *mytile,
+                                         int x, int LsN, int Ls, bool active, T2 (*o)[12], const Bar &bar)
+{
+    if constexpr (MIX == 1) {
+        chain_mix<R>(reinterpret_cast<const MixProg<R> *>(prog), tc.tile0, tc.tstride, tc.nsites, Ls, tc.tid, tc.nthr);
+        bar.sync();
+        if (active) {
+#pragma unroll
+            for (int n = 0; n < NS; ++n) {
+                T2 h[12];
+                ld_tile_row(mytile + (x + n * LsN) * 12, h);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) o[n][k] = p_add(o[n][k], h[k]);
+            }
+        }
+    } else if (active) {
+        mix_pairs<NS>(M, mytile, x, Ls, o);
+    }
+}
+
+// acc: hop result of this thread's NS slices.  Every thread taking part in
+// `bar` must call it.  Returns this thread's contribution to |o|^2.
+template <int P, int NS, int MIX = 0, typename T2, typename R, typename Bar>
+__device__ __forceinline__ double hop_epilogue_core(const HopArgs &a, T2 (*acc)[12], const TileCtx<T2> &tc,
+                                                    T2 *mytile, const R *mtx, int site, int x, int LsN, bool active,
+                                                    const Bar &bar)
 {
     const int Ls = a.Ls;
     const int msz = 2 * Ls * Ls;
@@ -193,14 +238,14 @@ __device__ __forceinline__ void hop_epilogue(const HopArgs &a, T2 (*acc)[12], T2
 #pragma unroll
         for (int n = 0; n < NS; ++n) put_tile(mytile, x + n * LsN, acc[n]);
     }
-    __syncthreads();
+    bar.sync();
 
     T2 o[NS][12];
 #pragma unroll
     for (int n = 0; n < NS; ++n)
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[n][k] = p_splat((R)0);
-    if (active) mix_pairs<NS>(mtx, mytile, x, Ls, o);
+    mix_into<MIX, NS>(a.post_prog, mtx, tc, mytile, x, LsN, Ls, active, o, bar);
 
     if (a.ymode == 1) {
         if (active) {
@@ -213,7 +258,7 @@ __device__ __forceinline__ void hop_epilogue(const HopArgs &a, T2 (*acc)[12], T2
             }
         }
     } else if (a.ymode == 2) {
-        __syncthreads();
+        bar.sync();
         if (active) {
 #pragma unroll
             for (int n = 0; n < NS; ++n) {
@@ -222,8 +267,8 @@ __device__ __forceinline__ void hop_epilogue(const HopArgs &a, T2 (*acc)[12], T2
                 put_tile(mytile, x + n * LsN, y);
             }
         }
-        __syncthreads();
-        if (active) mix_pairs<NS>(mtx + msz, mytile, x, Ls, o);
+        bar.sync();
+        mix_into<MIX, NS>(a.y_prog, mtx + msz, tc, mytile, x, LsN, Ls, active, o, bar);
     }
 
     if (a.rin.v && active) {
@@ -263,19 +308,19 @@ __device__ __forceinline__ void hop_epilogue(const HopArgs &a, T2 (*acc)[12], T2
     }
 
     if (a.zmat) {
-        __syncthreads();
+        bar.sync();
         if (active) {
 #pragma unroll
             for (int n = 0; n < NS; ++n) put_tile(mytile, x + n * LsN, o[n]);
         }
-        __syncthreads();
+        bar.sync();
         T2 z[NS][12];
 #pragma unroll
         for (int n = 0; n < NS; ++n)
 #pragma unroll
             for (int k = 0; k < 12; ++k) z[n][k] = p_splat((R)0);
+        mix_into<MIX, NS>(a.z_prog, mtx + 2 * msz, tc, mytile, x, LsN, Ls, active, z, bar);
         if (active) {
-            mix_pairs<NS>(mtx + 2 * msz, mytile, x, Ls, z);
 #pragma unroll
             for (int n = 0; n < NS; ++n) st_pairs<P>(a.out, (size_t)site, x + n * LsN, Ls, z[n]);
         }
@@ -284,6 +329,29 @@ __device__ __forceinline__ void hop_epilogue(const HopArgs &a, T2 (*acc)[12], T2
         for (int n = 0; n < NS; ++n) st_pairs<P>(a.out, (size_t)site, x + n * LsN, Ls, o[n]);
     }
 
+    return nrm;
+}
+
+// Epilogue of the kernels whose whole CTA forms one tile (blockDim = (Ls/NS, SB)).
+template <typename T2>
+__device__ __forceinline__ TileCtx<T2> cta_tile(T2 *tile0, int Ls)
+{
+    TileCtx<T2> tc;
+    tc.tile0 = tile0;
+    tc.tstride = Ls * 12 + 2;
+    tc.nsites = blockDim.y;
+    tc.tid = threadIdx.y * blockDim.x + threadIdx.x;
+    tc.nthr = blockDim.x * blockDim.y;
+    return tc;
+}
+
+template <int P, int NS, int MIX = 0, typename T2, typename R>
+__device__ __forceinline__ void hop_epilogue(const HopArgs &a, T2 (*acc)[12], T2 *tile0, int j, const R *mtx,
+                                             int site, int x, int LsN, bool active)
+{
+    const TileCtx<T2> tc = cta_tile(tile0, a.Ls);
+    const double nrm = hop_epilogue_core<P, NS, MIX>(a, acc, tc, tile0 + j * tc.tstride, mtx, site, x, LsN, active,
+                                                CtaBarrier());
     if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
 }
 
@@ -319,7 +387,7 @@ __device__ __forceinline__ void hop_dir(T2 (*acc)[12], const FieldRef &in, int n
     }
 }
 
-template <int P, bool DAG, int NS>
+template <int P, bool DAG, int NS, int MIX>
 __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a)
 {
     typedef typename Tr<P>::real R;
@@ -358,7 +426,124 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a)
         hop_dir<P, DAG, 6, NS>(acc, a.in, n8[6], x, LsN, Ls, U);
         hop_dir<P, DAG, 7, NS>(acc, a.in, n8[7], x, LsN, Ls, U);
     }
-    hop_epilogue<P, NS>(a, acc, tile + j * tstride, mtx, site, x, LsN, active);
+    hop_epilogue<P, NS, MIX>(a, acc, tile, j, mtx, site, x, LsN, active);
+}
+
+// ------------------------------------------------- variant 4: blocked tiles
+// The direct kernel with each CTA's SB sites taken as a 4D block
+// tb[0] x tb[1] x tb[2] x tb[3] of the half lattice (coordinates xh = x/2, y,
+// z, t; the even-odd index is lexicographic in them), so that the neighbour
+// sites the CTA reads overlap and are served from L1.  The block extents
+// divide the half-lattice extents.
+struct Tile4 {
+    int tb[4];
+};
+
+template <int P, bool DAG, int NS>
+__global__ void __launch_bounds__(256) hop_block_kernel(const HopArgs a, Tile4 T)
+{
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
+    typedef typename Tr<P>::link_t link_t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ls = a.Ls;
+    const int LsN = Ls / NS;
+    const int x = threadIdx.x;
+    const int j = threadIdx.y;
+    const int SB = blockDim.y;
+    // block coordinates (lexicographic over the tiled half lattice) and local offsets
+    int b = blockIdx.x, l = j, c[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const int nb = a.ext[d] / T.tb[d];
+        const int bd = b % nb, ld = l % T.tb[d];
+        b /= nb;
+        l /= T.tb[d];
+        c[d] = bd * T.tb[d] + ld;
+    }
+    const int site = c[0] + a.ext[0] * (c[1] + a.ext[1] * (c[2] + a.ext[2] * c[3]));
+    const bool active = true;
+    const int tstride = Ls * 12 + 2;
+    T2 *tile = reinterpret_cast<T2 *>(smem_raw);
+    R *mtx = reinterpret_cast<R *>(tile + SB * tstride);
+    load_matrices<NS>(a, mtx);
+
+    T2 acc[NS][12];
+#pragma unroll
+    for (int n = 0; n < NS; ++n)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[n][k] = p_splat((R)0);
+    {
+        const int *nb = a.nbr + (size_t)site * 8;
+        const link_t *U = reinterpret_cast<const link_t *>(a.gauge) + (size_t)site * 8 * 18;
+        int n8[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) n8[d] = __ldg(nb + d);
+        hop_dir<P, DAG, 0, NS>(acc, a.in, n8[0], x, LsN, Ls, U);
+        hop_dir<P, DAG, 1, NS>(acc, a.in, n8[1], x, LsN, Ls, U);
+        hop_dir<P, DAG, 2, NS>(acc, a.in, n8[2], x, LsN, Ls, U);
+        hop_dir<P, DAG, 3, NS>(acc, a.in, n8[3], x, LsN, Ls, U);
+        hop_dir<P, DAG, 4, NS>(acc, a.in, n8[4], x, LsN, Ls, U);
+        hop_dir<P, DAG, 5, NS>(acc, a.in, n8[5], x, LsN, Ls, U);
+        hop_dir<P, DAG, 6, NS>(acc, a.in, n8[6], x, LsN, Ls, U);
+        hop_dir<P, DAG, 7, NS>(acc, a.in, n8[7], x, LsN, Ls, U);
+    }
+    hop_epilogue<P, NS>(a, acc, tile, j, mtx, site, x, LsN, active);
+}
+
+// ------------------------------------------ variant 3: persistent direct sweep
+// The direct kernel, persistent: CTA b handles the consecutive tiles
+// [b*tpc, (b+1)*tpc).  Consecutive tiles are consecutive x-rows, so an input
+// row fetched as the +y neighbour of one tile is fetched again (from L1) as
+// the x neighbour and the -y neighbour of the next two tiles.
+template <int P, bool DAG, int NS>
+__global__ void __launch_bounds__(256) hop_sweep_kernel(const HopArgs a, int tpc)
+{
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
+    typedef typename Tr<P>::link_t link_t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ls = a.Ls;
+    const int LsN = Ls / NS;
+    const int x = threadIdx.x;
+    const int j = threadIdx.y;
+    const int SB = blockDim.y;
+    const int tstride = Ls * 12 + 2;
+    T2 *tile = reinterpret_cast<T2 *>(smem_raw);
+    R *mtx = reinterpret_cast<R *>(tile + SB * tstride);
+    load_matrices<NS>(a, mtx);
+    const int ntiles = (a.Vh + SB - 1) / SB;
+    const int u0 = blockIdx.x * tpc;
+    const int u1 = min(u0 + tpc, ntiles);
+    double nrm = 0;
+    for (int u = u0; u < u1; ++u) {
+        const int site = u * SB + j;
+        const bool active = site < a.Vh;
+        T2 acc[NS][12];
+#pragma unroll
+        for (int n = 0; n < NS; ++n)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[n][k] = p_splat((R)0);
+        if (active) {
+            const int *nb = a.nbr + (size_t)site * 8;
+            const link_t *U = reinterpret_cast<const link_t *>(a.gauge) + (size_t)site * 8 * 18;
+            int n8[8];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) n8[d] = __ldg(nb + d);
+            hop_dir<P, DAG, 0, NS>(acc, a.in, n8[0], x, LsN, Ls, U);
+            hop_dir<P, DAG, 1, NS>(acc, a.in, n8[1], x, LsN, Ls, U);
+            hop_dir<P, DAG, 2, NS>(acc, a.in, n8[2], x, LsN, Ls, U);
+            hop_dir<P, DAG, 3, NS>(acc, a.in, n8[3], x, LsN, Ls, U);
+            hop_dir<P, DAG, 4, NS>(acc, a.in, n8[4], x, LsN, Ls, U);
+            hop_dir<P, DAG, 5, NS>(acc, a.in, n8[5], x, LsN, Ls, U);
+            hop_dir<P, DAG, 6, NS>(acc, a.in, n8[6], x, LsN, Ls, U);
+            hop_dir<P, DAG, 7, NS>(acc, a.in, n8[7], x, LsN, Ls, U);
+        }
+        __syncthreads();   // the previous tile's epilogue is done with `tile`
+        nrm += hop_epilogue_core<P, NS>(a, acc, cta_tile(tile, Ls), tile + j * tstride, mtx, site, x, LsN, active,
+                                        CtaBarrier());
+    }
+    if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
 }
 
 // ------------------------------------------------------ variant 1: staged
@@ -577,7 +762,191 @@ __global__ void __launch_bounds__(256) hop_staged_kernel(const HopArgs a)
 
     const int tstride = Ls * 12 + 2;
     T2 *tile = reinterpret_cast<T2 *>(b0);
-    hop_epilogue<P, NS>(a, acc, tile + j * tstride, mtx, site, x, LsN, active);
+    hop_epilogue<P, NS>(a, acc, tile, j, mtx, site, x, LsN, active);
+}
+
+// ---------------------------------------- variant 2: persistent, warp-specialised
+// Warp 0 streams the work of the CTA's tiles (SB sites each, tiles taken in a
+// grid-stride loop) through a ring of NST shared-memory stages: one stage =
+// the neighbour sites of two directions for the tile; links come through a
+// two-slot ring.  Every slot has a "full" mbarrier (TMA transaction count) and
+// an "empty" mbarrier (one arrival per consumer warp).  Warps 1..NCW compute:
+// each consumer thread owns NS slices of one site of the tile.  All waits are
+// bounded and stop as soon as any warp of the CTA has given up.
+template <int P>
+__host__ __device__ __forceinline__ size_t pipe_smem(int Ls, int SB, int NST, size_t *off_links, size_t *off_stage,
+                                                     size_t *off_tile, size_t *off_mtx)
+{
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
+    const StageGeom<P> g = stage_geom<P>(Ls);
+    size_t o = ((size_t)(2 * NST + 4) * 8 + 15) & ~(size_t)15;   // mbarriers
+    *off_links = o;
+    o += (size_t)2 * SB * g.link_bytes;
+    o = (o + 15) & ~(size_t)15;
+    *off_stage = o;
+    o += (size_t)NST * 2 * SB * g.slot_bytes;
+    o = (o + 15) & ~(size_t)15;
+    *off_tile = o;
+    o += (size_t)SB * (Ls * 12 + 2) * sizeof(T2);
+    *off_mtx = o;
+    o += (size_t)3 * 2 * Ls * Ls * sizeof(R);
+    return o;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Bounded wait that also stops when another warp of the CTA has aborted.
+__device__ __forceinline__ bool mbar_wait_abortable(uint32_t bar, uint32_t parity, volatile int *aborted)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*aborted) return false;
+        if (globaltimer_ns() - t0 > 1000000000ull) {
+            *aborted = 1;
+            return false;
+        }
+    }
+}
+
+template <int P, bool DAG, int NS, typename T2>
+__device__ __forceinline__ void compute_stage_rt(int st, T2 (*acc)[12], const unsigned char *buf,
+                                                 const unsigned char *links, int j, int x, int LsN, int Ls, int SB,
+                                                 const StageGeom<P> &g)
+{
+    switch (st) {
+    case 0: compute_stage<P, DAG, 0, NS>(acc, buf, links, j, x, LsN, Ls, SB, g); break;
+    case 1: compute_stage<P, DAG, 1, NS>(acc, buf, links, j, x, LsN, Ls, SB, g); break;
+    case 2: compute_stage<P, DAG, 2, NS>(acc, buf, links, j, x, LsN, Ls, SB, g); break;
+    default: compute_stage<P, DAG, 3, NS>(acc, buf, links, j, x, LsN, Ls, SB, g); break;
+    }
+}
+
+template <int P, bool DAG, int NS>
+__global__ void __launch_bounds__(288) hop_pipe_kernel(const HopArgs a, int SB, int NST)
+{
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int aborted;
+    __shared__ int decide;
+    const int Ls = a.Ls;
+    const int LsN = Ls / NS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NCW = (blockDim.x >> 5) - 1;
+    const int CT = 32 * NCW;
+    const int c = threadIdx.x - 32;
+    const int j = c / LsN, x = c % LsN;
+    const bool consumer = warp >= 1;
+    const bool slot_ok = consumer && j < SB;
+    const StageGeom<P> g = stage_geom<P>(Ls);
+    size_t off_links, off_stage, off_tile, off_mtx;
+    pipe_smem<P>(Ls, SB, NST, &off_links, &off_stage, &off_tile, &off_mtx);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
+    unsigned char *links = smem_raw + off_links;
+    unsigned char *stages = smem_raw + off_stage;
+    T2 *tile = reinterpret_cast<T2 *>(smem_raw + off_tile);
+    R *mtx = reinterpret_cast<R *>(smem_raw + off_mtx);
+    auto full = [&](int b) { return smem_u32(&bars[b]); };
+    auto empty = [&](int b) { return smem_u32(&bars[NST + b]); };
+    auto lfull = [&](int b) { return smem_u32(&bars[2 * NST + b]); };
+    auto lempty = [&](int b) { return smem_u32(&bars[2 * NST + 2 + b]); };
+    const size_t stage_sz = (size_t)2 * SB * g.slot_bytes;
+    const int ntiles = (a.Vh + SB - 1) / SB;
+
+    if (threadIdx.x == 0) {
+        aborted = 0;
+        for (int b = 0; b < NST; ++b) {
+            mbar_init(full(b), 1);
+            mbar_init(empty(b), NCW);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(lfull(b), 1);
+            mbar_init(lempty(b), NCW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    load_matrices<NS>(a, mtx);
+    __syncthreads();
+
+    double nrm = 0;
+    if (!consumer) {
+        // ---------------- producer warp
+        int k = 0, ui = 0;
+        for (int u = blockIdx.x; u < ntiles; u += gridDim.x, ++ui) {
+            const int site0 = u * SB;
+            const int nsite = min(SB, a.Vh - site0);
+            const int lb = ui & 1;
+            if (!mbar_wait_abortable(lempty(lb), ((ui >> 1) & 1) ^ 1, &aborted)) break;
+            if (lane == 0) {
+                mbar_arrive_expect_tx(lfull(lb), (uint32_t)nsite * g.link_bytes);
+                bulk_g2s(smem_u32(links + (size_t)lb * SB * g.link_bytes),
+                         (const unsigned char *)a.gauge + (size_t)site0 * g.link_bytes, (uint32_t)nsite * g.link_bytes,
+                         lfull(lb));
+            }
+            bool ok = true;
+            for (int st = 0; st < 4; ++st, ++k) {
+                const int b = k % NST;
+                if (!mbar_wait_abortable(empty(b), ((k / NST) & 1) ^ 1, &aborted)) {
+                    ok = false;
+                    break;
+                }
+                issue_stage<P>(a, st, stages + (size_t)b * stage_sz, full(b), site0, nsite, SB, g, lane);
+            }
+            if (!ok) break;
+        }
+    } else {
+        // ---------------- consumer warps
+        const ConsumerBarrier cbar{CT};
+        int k = 0, ui = 0;
+        for (int u = blockIdx.x; u < ntiles; u += gridDim.x, ++ui) {
+            const int site0 = u * SB;
+            const int nsite = min(SB, a.Vh - site0);
+            const bool active = slot_ok && j < nsite;
+            const int lb = ui & 1;
+            T2 acc[NS][12];
+#pragma unroll
+            for (int n = 0; n < NS; ++n)
+#pragma unroll
+                for (int q = 0; q < 12; ++q) acc[n][q] = p_splat((R)0);
+            bool ok = mbar_wait_abortable(lfull(lb), (ui >> 1) & 1, &aborted);
+            const unsigned char *lk = links + (size_t)lb * SB * g.link_bytes;
+            for (int st = 0; st < 4 && ok; ++st, ++k) {
+                const int b = k % NST;
+                ok = mbar_wait_abortable(full(b), (k / NST) & 1, &aborted);
+                if (!ok) break;
+                if (active) compute_stage_rt<P, DAG, NS>(st, acc, stages + (size_t)b * stage_sz, lk, j, x, LsN, Ls, SB, g);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty(b));
+            }
+            if (ok) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(lempty(lb));
+            }
+            // all consumer warps take the same decision: one thread samples the
+            // sticky abort flag between two consumer barriers (this also orders
+            // the previous tile's epilogue reads of `tile` before the next writes)
+            cbar.sync();
+            if (c == 0) decide = aborted;
+            cbar.sync();
+            if (decide) break;
+            TileCtx<T2> tc;
+            tc.tile0 = tile;
+            tc.tstride = Ls * 12 + 2;
+            tc.nsites = SB;
+            tc.tid = c;
+            tc.nthr = CT;
+            nrm += hop_epilogue_core<P, NS>(a, acc, tc, tile + (slot_ok ? j : 0) * tc.tstride, mtx, site0 + j, x,
+                                            LsN, active, cbar);
+        }
+    }
+    __syncthreads();
+    if (aborted && threadIdx.x == 0 && a.err) atomicOr(a.err, 1);
+    if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
 }
 
 // ---------------------------------------------------------------- launch
@@ -589,18 +958,18 @@ size_t direct_smem(int Ls, int SB)
     return (size_t)SB * (Ls * 12 + 2) * sizeof(T2) + (size_t)3 * 2 * Ls * Ls * sizeof(R);
 }
 
-template <int P, bool DAG, int NS>
+template <int P, bool DAG, int NS, int MIX = 0>
 cudaError_t launch_direct(const HopArgs &a, int SB, cudaStream_t st)
 {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(hop_kernel<P, DAG, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(hop_kernel<P, DAG, NS, MIX>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int LsN = a.Ls / NS;
-    hop_kernel<P, DAG, NS><<<(a.Vh + SB - 1) / SB, dim3(LsN, SB), direct_smem<P>(a.Ls, SB), st>>>(a);
+    hop_kernel<P, DAG, NS, MIX><<<(a.Vh + SB - 1) / SB, dim3(LsN, SB), direct_smem<P>(a.Ls, SB), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -622,9 +991,146 @@ cudaError_t launch_staged(const HopArgs &a, int SB, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Ring depth: as many stages as fit in about half of an SM's shared memory
+// (two CTAs per SM), at least 2, at most 8.
+template <int P>
+int pipe_stages(int Ls, int SB)
+{
+    size_t o1, o2, o3, o4;
+    const size_t fixed = pipe_smem<P>(Ls, SB, 0, &o1, &o2, &o3, &o4);
+    const size_t stage = (size_t)2 * SB * stage_geom<P>(Ls).slot_bytes;
+    long n = (long)((110 * 1024 - (long)fixed) / (long)stage);
+    if (n < 2) n = 2;
+    if (n > 8) n = 8;
+    return (int)n;
+}
+
+template <int P, bool DAG, int NS>
+cudaError_t launch_pipe(const HopArgs &a, int SB, cudaStream_t st)
+{
+    static int attr_dev = -1, nsm = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (attr_dev != dev) {
+        e = cudaFuncSetAttribute(hop_pipe_kernel<P, DAG, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    const int LsN = a.Ls / NS;
+    const int ncw = (SB * LsN + 31) / 32;
+    const int threads = 32 * (1 + ncw);
+    const int NST = pipe_stages<P>(a.Ls, SB);
+    size_t o1, o2, o3, o4;
+    const size_t smem = pipe_smem<P>(a.Ls, SB, NST, &o1, &o2, &o3, &o4);
+    if (smem > 220 * 1024 || threads > 288) return cudaErrorInvalidConfiguration;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_pipe_kernel<P, DAG, NS>, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int ntiles = (a.Vh + SB - 1) / SB;
+    int grid = nsm * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    hop_pipe_kernel<P, DAG, NS><<<grid, threads, smem, st>>>(a, SB, NST);
+    return cudaGetLastError();
+}
+
+// The 4D block of SB sites with the smallest faces whose extents divide the
+// half-lattice extents; false if SB has no such factorisation.
+bool choose_tile4(const int ext[4], int SB, Tile4 &best)
+{
+    long bestcost = -1;
+    for (int t0 = 1; t0 <= ext[0] && t0 <= SB; ++t0) {
+        if (ext[0] % t0 || SB % t0) continue;
+        for (int t1 = 1; t1 <= ext[1] && t0 * t1 <= SB; ++t1) {
+            if (ext[1] % t1 || (SB / t0) % t1) continue;
+            for (int t2 = 1; t2 <= ext[2] && t0 * t1 * t2 <= SB; ++t2) {
+                if (ext[2] % t2 || (SB / (t0 * t1)) % t2) continue;
+                const int t3 = SB / (t0 * t1 * t2);
+                if (t3 < 1 || t3 > ext[3] || ext[3] % t3) continue;
+                // halo sites fetched besides the block's own: one face per direction
+                const long cost = 2L * SB / t0 + 2L * SB / t1 + 2L * SB / t2 + 2L * SB / t3;
+                if (bestcost < 0 || cost < bestcost) {
+                    bestcost = cost;
+                    best.tb[0] = t0;
+                    best.tb[1] = t1;
+                    best.tb[2] = t2;
+                    best.tb[3] = t3;
+                }
+            }
+        }
+    }
+    return bestcost >= 0;
+}
+
+template <int P, bool DAG, int NS>
+cudaError_t launch_block(const HopArgs &a, int SB, cudaStream_t st)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(hop_block_kernel<P, DAG, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    Tile4 T;
+    if (!choose_tile4(a.ext, SB, T)) return launch_direct<P, DAG, NS>(a, SB, st);
+    const int LsN = a.Ls / NS;
+    hop_block_kernel<P, DAG, NS><<<a.Vh / SB, dim3(LsN, SB), direct_smem<P>(a.Ls, SB), st>>>(a, T);
+    return cudaGetLastError();
+}
+
+template <int P, bool DAG, int NS>
+cudaError_t launch_sweep(const HopArgs &a, int SB, cudaStream_t st)
+{
+    static int attr_dev = -1, nsm = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (attr_dev != dev) {
+        e = cudaFuncSetAttribute(hop_sweep_kernel<P, DAG, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    const int LsN = a.Ls / NS;
+    const size_t smem = direct_smem<P>(a.Ls, SB);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_sweep_kernel<P, DAG, NS>, LsN * SB, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int ntiles = (a.Vh + SB - 1) / SB;
+    int grid = nsm * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    const int tpc = (ntiles + grid - 1) / grid;
+    grid = (ntiles + tpc - 1) / tpc;
+    hop_sweep_kernel<P, DAG, NS><<<grid, dim3(LsN, SB), smem, st>>>(a, tpc);
+    return cudaGetLastError();
+}
+
 template <int P, bool DAG>
 cudaError_t launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
 {
+    // the structured fifth-direction mixing is compiled for the direct variant only
+    if (a.mixmode == 1) {
+        if (NS == 2) return launch_direct<P, DAG, 2, 1>(a, SB, st);
+        return launch_direct<P, DAG, 1, 1>(a, SB, st);
+    }
+    if (var == 4) {
+        if (NS == 2) return launch_block<P, DAG, 2>(a, SB, st);
+        return launch_block<P, DAG, 1>(a, SB, st);
+    }
+    if (var == 3) {
+        if (NS == 2) return launch_sweep<P, DAG, 2>(a, SB, st);
+        return launch_sweep<P, DAG, 1>(a, SB, st);
+    }
+    if (var == 2) {
+        if (NS == 2) return launch_pipe<P, DAG, 2>(a, SB, st);
+        return launch_pipe<P, DAG, 1>(a, SB, st);
+    }
     if (var == 1) {
         if (NS == 2) return launch_staged<P, DAG, 2>(a, SB, st);
         return launch_staged<P, DAG, 1>(a, SB, st);
@@ -663,15 +1169,27 @@ size_t hop_staged_smem_bytes(int prec, int Ls, int SB)
     }
 }
 
+size_t hop_pipe_smem_bytes(int prec, int Ls, int SB)
+{
+    size_t o1, o2, o3, o4;
+    switch (prec) {
+    case DWF_F64: return pipe_smem<DWF_F64>(Ls, SB, pipe_stages<DWF_F64>(Ls, SB), &o1, &o2, &o3, &o4);
+    case DWF_F32: return pipe_smem<DWF_F32>(Ls, SB, pipe_stages<DWF_F32>(Ls, SB), &o1, &o2, &o3, &o4);
+    default: return pipe_smem<DWF_F16>(Ls, SB, pipe_stages<DWF_F16>(Ls, SB), &o1, &o2, &o3, &o4);
+    }
+}
+
 cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
 {
-    if (var < 0 || var > 1) var = hop_default_variant(prec);
+    if (var < 0 || var > 4) var = hop_default_variant(prec);
     if (NS <= 0 || NS > 2 || (a.Ls % NS) != 0) NS = hop_default_ns(prec, a.Ls);
     if (SB <= 0) SB = hop_default_sb(prec, a.Ls, NS);
     if ((a.Ls / NS) * SB > 256) SB = 256 / (a.Ls / NS);
     if (SB < 1) SB = 1;
     while (var == 1 && SB > 1 && hop_staged_smem_bytes(prec, a.Ls, SB) > 220 * 1024) SB /= 2;
     if (var == 1 && hop_staged_smem_bytes(prec, a.Ls, SB) > 220 * 1024) var = 0;
+    while (var == 2 && SB > 1 && hop_pipe_smem_bytes(prec, a.Ls, SB) > 220 * 1024) SB /= 2;
+    if (var == 2 && hop_pipe_smem_bytes(prec, a.Ls, SB) > 220 * 1024) var = 0;
     switch (prec) {
     case DWF_F64: return dag ? launch_pd<DWF_F64, true>(a, var, NS, SB, st) : launch_pd<DWF_F64, false>(a, var, NS, SB, st);
     case DWF_F32: return dag ? launch_pd<DWF_F32, true>(a, var, NS, SB, st) : launch_pd<DWF_F32, false>(a, var, NS, SB, st);

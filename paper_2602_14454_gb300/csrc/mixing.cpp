@@ -19,6 +19,7 @@
 // Every mixing the kernels apply is a product of these small matrices.
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -114,6 +115,9 @@ double spectral_norm(const Mat &a, int n) {
 
 }  // namespace
 
+void build_programs(int L, double alpha0, double beta0, double b, double c, double mf, double M0, double a,
+                    FifthMatrices &out);
+
 bool build_fifth_matrices(int Ls, double M0, double mf, double b, double c, int form, double alpha,
                           FifthMatrices &out, std::string &err)
 {
@@ -173,7 +177,96 @@ bool build_fifth_matrices(int Ls, double M0, double mf, double b, double c, int 
         dee = std::fmax(dee, spectral_norm(A5R, n));
     }
     out.dee_norm2 = dee;
+    build_programs(n, alpha0, beta0, b, c, mf, M0, a, out);
     return true;
+}
+
+// Host copy of the device chain routine (FP64): used to check every program
+// against its dense matrix before the structured path is enabled.
+static void apply_prog(const FifthMatrices::Prog &p, int chi, int L, double *x)
+{
+    double v[LS_MAX];
+    auto idx = [&](int s) { return p.up[chi] ? (L - 1 - s) : s; };
+    for (int s = 0; s < L; ++s) v[s] = x[idx(s)] * p.d1[chi][idx(s)];
+    if (p.inv) {
+        double acc = 0;
+        for (int s = 0; s < L; ++s) acc = p.kappa * acc + v[s];
+        double prev = p.mneg * (acc * p.a0inv * p.corner);
+        for (int s = 0; s < L; ++s) {
+            v[s] = v[s] * p.a0inv + p.kappa * prev;
+            prev = v[s];
+        }
+    }
+    if (p.shift) {
+        double prev = p.mneg * v[L - 1];
+        for (int s = 0; s < L; ++s) {
+            const double t = v[s];
+            v[s] = p.s0 * t + p.s1 * prev;
+            prev = t;
+        }
+    }
+    for (int s = 0; s < L; ++s) x[idx(s)] = v[s] * p.d2[chi][idx(s)];
+}
+
+void build_programs(int L, double alpha0, double beta0, double b, double c, double mf, double M0, double a,
+                    FifthMatrices &out)
+{
+    const double kappa = -beta0 / alpha0;
+    out.structured = std::fabs(kappa) < 0.95;
+    if (!out.structured) return;
+    const double corner = 1.0 / (1.0 + mf * std::pow(kappa, L));
+    auto R = [&](int chi, int s) { return chi == 0 ? (s == L - 1 ? 1.0 : a) : (s == 0 ? 1.0 : a); };
+    enum { ONE, RD, RINV };
+    struct Spec {
+        int id, d1, inv, shift_kind, transposed, d2;
+        double d2scale;
+    };
+    // shift_kind: 0 none, 1 B = b + cK, 2 A5 = alpha0 + beta0 K
+    const Spec specs[] = {
+        {MAT_P, RD, 0, 1, 0, ONE, 1.0},         {MAT_PT, ONE, 0, 1, 1, RD, 1.0},
+        {MAT_Q, ONE, 1, 0, 0, RINV, 1.0},       {MAT_QT, RINV, 1, 0, 1, ONE, 1.0},
+        {MAT_M, ONE, 1, 1, 0, ONE, 1.0},        {MAT_MT, ONE, 1, 1, 1, ONE, 1.0},
+        {MAT_A5R, RD, 0, 2, 0, ONE, 1.0},       {MAT_RA5T, ONE, 0, 2, 1, RD, 1.0},
+        {MAT_NHALF, ONE, 0, 0, 0, ONE, -0.5},   {MAT_NHALF_RBT, ONE, 0, 1, 1, RD, -0.5},
+        {MAT_NQ4, ONE, 1, 0, 0, RINV, -0.25},   {MAT_NPT4, ONE, 0, 1, 1, RD, -0.25},
+        {MAT_ID, ONE, 0, 0, 0, ONE, 1.0},       {MAT_HALF_Q, ONE, 1, 0, 0, RINV, 0.5},
+        {MAT_SRC_POST, ONE, 0, 0, 0, ONE, 0.5 * c},
+        {MAT_SRC_Y, ONE, 0, 0, 0, ONE, 1.0 - c * (4.0 - M0)},
+    };
+    for (const Spec &sp : specs) {
+        FifthMatrices::Prog &p = out.prog[sp.id];
+        std::memset(&p, 0, sizeof(p));
+        p.inv = sp.inv;
+        p.shift = sp.shift_kind != 0;
+        p.s0 = sp.shift_kind == 1 ? b : alpha0;
+        p.s1 = sp.shift_kind == 1 ? c : beta0;
+        p.a0inv = 1.0 / alpha0;
+        p.kappa = kappa;
+        p.mneg = -mf;
+        p.corner = corner;
+        for (int chi = 0; chi < 2; ++chi) {
+            p.up[chi] = (chi == 1) != (sp.transposed != 0);
+            for (int s = 0; s < L; ++s) {
+                auto val = [&](int kind) { return kind == ONE ? 1.0 : (kind == RD ? R(chi, s) : 1.0 / R(chi, s)); };
+                p.d1[chi][s] = val(sp.d1);
+                p.d2[chi][s] = val(sp.d2) * sp.d2scale;
+            }
+        }
+        // the program must reproduce the dense matrix column by column
+        double amax = 0, emax = 0;
+        for (int chi = 0; chi < 2; ++chi)
+            for (int t = 0; t < L; ++t) {
+                double x[LS_MAX] = {0};
+                x[t] = 1.0;
+                apply_prog(p, chi, L, x);
+                for (int s = 0; s < L; ++s) {
+                    const double want = out.mats[sp.id][chi][(size_t)s * L + t];
+                    amax = std::fmax(amax, std::fabs(want));
+                    emax = std::fmax(emax, std::fabs(x[s] - want));
+                }
+            }
+        if (!(emax <= 1e-12 * std::fmax(amax, 1e-300))) out.structured = false;
+    }
 }
 
 }  // namespace dwf

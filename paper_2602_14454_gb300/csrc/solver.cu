@@ -105,6 +105,8 @@ cudaError_t inner_iteration(dwf_ctx *h, const Bufs &B, cudaStream_t st)
     ue.Vh = h->Vh;
     ue.Ls = h->Ls;
     ue.mat = h->mat(P, MAT_P);
+    ue.mixmode = h->mix_mode(P);
+    ue.prog = h->prog(P, MAT_P);
     ue.scal = B.cg;
     h->launches += 1;
     if ((e = launch_cg_update(P, ue, st)) != cudaSuccess) return e;

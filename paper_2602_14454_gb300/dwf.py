@@ -31,7 +31,8 @@ EXPORTED = ["dwf_create", "dwf_destroy", "dwf_strerror", "dwf_last_error", "dwf_
             "dwf_apply", "dwf_apply_dag", "dwf_source_5d", "dwf_project_4d",
             "dwf_solve_params_default", "dwf_solve", "dwf_propagator_host", "dwf_solve_batch",
             "dwf_fifth_matrix", "dwf_device_bytes", "dwf_time_hop", "dwf_launch_count",
-            "dwf_set_hop_config", "dwf_get_hop_config", "dwf_autotune", "dwf_device_status"]
+            "dwf_set_hop_config", "dwf_get_hop_config", "dwf_autotune", "dwf_device_status",
+            "dwf_set_mix_mode", "dwf_get_mix_mode"]
 
 
 class SolveParams(ctypes.Structure):
@@ -98,6 +99,8 @@ def lib():
     L.dwf_set_hop_config.argtypes = [vp, i, i, i, i]
     L.dwf_get_hop_config.argtypes = [vp, i, ip, ip, ip]
     L.dwf_device_status.argtypes = [vp, vp]
+    L.dwf_set_mix_mode.argtypes = [vp, i, i]
+    L.dwf_get_mix_mode.argtypes = [vp, i, ip]
     L.dwf_autotune.argtypes = [vp, i, ctypes.c_char_p, vp]
     L.dwf_launch_count.argtypes = [vp]
     L.dwf_launch_count.restype = ctypes.c_longlong
@@ -236,6 +239,14 @@ class Operator:
         check(lib().dwf_get_hop_config(self._h, PREC[prec], ctypes.byref(var), ctypes.byref(ns),
                                        ctypes.byref(sb)))
         return var.value, ns.value, sb.value
+
+    def set_mix_mode(self, prec, mode):
+        check(lib().dwf_set_mix_mode(self._h, PREC[prec], int(mode)))
+
+    def mix_mode(self, prec):
+        m = ctypes.c_int()
+        check(lib().dwf_get_mix_mode(self._h, PREC[prec], ctypes.byref(m)))
+        return m.value
 
     def device_status(self):
         """DWF_OK, or raises DwfError(DWF_ETIMEOUT) if a bounded device wait gave up."""

@@ -132,7 +132,8 @@ def test_full_size_eo_parity():
         assert rel(got, want) < TOL[prec]
 
 
-HOP_CONFIGS = [(0, 1, 3), (0, 2, 5), (1, 1, 3), (1, 2, 7), (1, 1, 16), (1, 2, 1)]
+HOP_CONFIGS = [(4, 1, 4), (4, 2, 6), (4, 1, 12), (4, 2, 16), (4, 1, 5), (3, 1, 3), (3, 2, 8), (3, 1, 8), (0, 1, 3), (0, 2, 5), (1, 1, 3), (1, 2, 7), (1, 1, 16), (1, 2, 1),
+               (2, 1, 8), (2, 2, 5), (2, 1, 3), (2, 2, 1), (2, 1, 16)]
 
 
 @pytest.mark.parametrize("cfg", HOP_CONFIGS, ids=lambda c: "var%d_ns%d_sb%d" % c)
@@ -156,13 +157,50 @@ def test_hop_configurations_ragged_tiles(cfg, prec, Ls):
     op.device_status()
 
 
+MIX_CASES = [
+    ((4, 2, 6, 4), 12, 1.8, 0.01, 1.5, 0.5, "neff", 0.4),    # Mobius, kappa = -0.023
+    ((4, 4, 2, 4), 8, 1.8, 0.04, 1.0, 0.0, "standard", 1.0),  # Shamir, kappa = 0.3125
+    ((4, 4, 2, 4), 16, 1.8, 0.02, 1.0, 1.0, "neff", 0.6),     # Borici, kappa = -0.375
+    ((2, 2, 4, 4), 32, 1.0, 0.1, 1.0, 1.0, "neff", 0.5),      # Borici M0 = 1, kappa = -0.5, Ls = 32
+    ((2, 2, 2, 4), 3, 1.8, 0.3, 1.5, 0.5, "neff", 1.7),       # odd Ls, alpha > 1
+]
+
+
+@pytest.mark.parametrize("case", MIX_CASES, ids=lambda c: "Ls%d_b%g_c%g_%s" % (c[1], c[4], c[5], c[6]))
+@pytest.mark.parametrize("mix", [0, 1])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_dense_and_structured_mixing(case, mix, prec):
+    """The dense Ls x Ls mixing and its structured (recurrence) form give the same operators."""
+    dims, Ls, M0, mf, b, c, form, alpha = case
+    op, ref = make_pair(dims, Ls, M0, mf, b, c, form, alpha, seed=71)
+    op.set_mix_mode(prec, mix)
+    assert op.mix_mode(prec) == mix
+    x = ref.to_eo(inputs.gaussian_5d(dims, Ls, 72), 0)
+    for dag in (False, True):
+        assert rel(to_np(op.apply(to_gpu(x), op="eo", prec=prec, dag=dag)), ref.d_pc(x, dag=dag)) < TOL[prec]
+    xf = inputs.gaussian_5d(dims, Ls, 73)
+    for dag in (False, True):
+        assert rel(to_np(op.apply(to_gpu(xf), op="full", prec=prec, dag=dag)), ref.apply(xf, dag=dag)) < TOL[prec]
+
+
+def test_structured_mixing_refused_when_unstable():
+    from paper_2602_14454_gb300 import dwf
+    # b = 0.1, c = 1: alpha0 = 0.1*2.2 + 1 = 1.22, beta0 = 1.2 -> |kappa| = 0.98
+    op, ref = make_pair((2, 2, 2, 4), 8, 1.8, 0.05, 0.1, 1.0, "standard", 1.0, seed=81)
+    assert op.mix_mode("f64") == 0   # dense is the default; the structured form is refused
+    with pytest.raises(dwf.DwfError):
+        op.set_mix_mode("f64", 1)
+    x = ref.to_eo(inputs.gaussian_5d((2, 2, 2, 4), 8, 82), 0)
+    assert rel(to_np(op.apply(to_gpu(x), op="eo", prec="f64")), ref.d_pc(x)) < 1e-12
+
+
 def test_autotuner_picks_a_valid_configuration(tmp_path):
     from paper_2602_14454_gb300 import dwf
     dims = (8, 8, 4, 4)
     op, ref = make_pair(dims, 16, 1.8, 0.01, 1.5, 0.5, "standard", 1.0, seed=61)
     cache = str(tmp_path / "tune.txt")
     cfg = op.autotune("f32", cache)
-    assert cfg[0] in (0, 1) and cfg[1] in (1, 2) and cfg[2] >= 1
+    assert cfg[0] in range(5) and cfg[1] in (1, 2) and cfg[2] >= 1
     op2, _ = make_pair(dims, 16, 1.8, 0.01, 1.5, 0.5, "standard", 1.0, seed=61)
     assert op2.autotune("f32", cache) == cfg          # cache hit
     x = ref.to_eo(inputs.gaussian_5d(dims, 16, 62), 0)
