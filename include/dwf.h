@@ -226,6 +226,26 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream);
 int dwf_set_mix_mode(dwf_handle h, int prec, int mode);
 int dwf_get_mix_mode(dwf_handle h, int prec, int *mode);
 
+/*
+ * Allocation-free variant of dwf_apply / dwf_apply_dag with DWF_OP_EO_PREC
+ * (the paper has no counterpart: this is a service of the library).  It
+ * computes the same out = D in (dag = 0) or out = D^dag in (dag != 0) on EO
+ * fields, for callers that cannot let a library allocate device memory
+ * during a call (an application that has handed all device memory to its own
+ * pool, or a path where an allocation would synchronise the device): its
+ * four work fields live in one fixed, file-scope device array of 64 MiB that
+ * exists on every GPU that loads the library until the process exits.  The
+ * call performs no cudaMalloc or cudaFree; the handle itself, created and
+ * given its links beforehand, is reused.  Lattices whose work fields exceed
+ * the array are rejected with DWF_EINVAL (4 internal half fields in
+ * precision prec; FP64 on 8^4 x Ls=16 uses 25 MB).  The array's device
+ * address is looked up once per device, on the first call made with that
+ * device current.  Every call shares the array and it keeps the last call's
+ * contents; calls whose GPU work overlaps (other streams, other handles of
+ * the same device) race.  in/out: device EO fields as for dwf_apply.
+ */
+int dwf_apply_eo_noalloc(dwf_handle h, int prec, int dag, const void *in, void *out, void *stream);
+
 /* Synchronise `stream` and report device-side failures of earlier calls on
  * the handle: DWF_ETIMEOUT if a bounded wait inside a kernel gave up (the
  * flag is cleared by this call), else DWF_OK. */

@@ -32,7 +32,7 @@ EXPORTED = ["dwf_create", "dwf_destroy", "dwf_strerror", "dwf_last_error", "dwf_
             "dwf_solve_params_default", "dwf_solve", "dwf_propagator_host", "dwf_solve_batch",
             "dwf_fifth_matrix", "dwf_device_bytes", "dwf_time_hop", "dwf_launch_count",
             "dwf_set_hop_config", "dwf_get_hop_config", "dwf_autotune", "dwf_device_status",
-            "dwf_set_mix_mode", "dwf_get_mix_mode"]
+            "dwf_set_mix_mode", "dwf_get_mix_mode", "dwf_apply_eo_noalloc"]
 
 
 class SolveParams(ctypes.Structure):
@@ -101,6 +101,7 @@ def lib():
     L.dwf_device_status.argtypes = [vp, vp]
     L.dwf_set_mix_mode.argtypes = [vp, i, i]
     L.dwf_get_mix_mode.argtypes = [vp, i, ip]
+    L.dwf_apply_eo_noalloc.argtypes = [vp, i, i, vp, vp, vp]
     L.dwf_autotune.argtypes = [vp, i, ctypes.c_char_p, vp]
     L.dwf_launch_count.argtypes = [vp]
     L.dwf_launch_count.restype = ctypes.c_longlong
