@@ -54,6 +54,24 @@ def dist_env():
     return rank, world, local
 
 
+def source_seed(w, rank):
+    """Each rank solves its own source (independent systems, weak scaling)."""
+    return w["src_seed"] + rank
+
+
+def max_over_ranks(x):
+    """The largest x over the ranks of the process group (x itself without one);
+    the only collective of the benchmark (timing, not data)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -217,7 +235,7 @@ def main():
     U = inputs.workload_links(w)
     op = dwf.Operator(w["dims"], w["Ls"], w["M0"], w["mf"], w["b"], w["c"], form=args.form, alpha=args.alpha)
     op.set_gauge(torch.from_numpy(U).cuda())
-    b4_host = inputs.gaussian_4d(w["dims"], w["src_seed"] + rank)
+    b4_host = inputs.gaussian_4d(w["dims"], source_seed(w, rank))
     b4 = torch.from_numpy(b4_host).cuda()
     st = torch.cuda.current_stream()
     kw = dict(inner_prec=args.inner, tol=args.tol)
@@ -251,9 +269,7 @@ def main():
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms)
     worst_res = max(s["true_residual"] for s in stats)
     iters = stats[-1]["iterations"]
 

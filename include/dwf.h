@@ -129,9 +129,13 @@ typedef struct {
     int check_every;    /* inner iterations between host convergence checks;
                            they are captured as one CUDA graph; default 16     */
     int use_graph;      /* 1: replay the inner iterations as a CUDA graph       */
-    int precond;        /* 0 none; 1 learned network (dwf_precond_*), FCG       */
+    int precond;        /* 0: CG with reliable updates; 1: flexible CG with the
+                           handle's learned network as preconditioner (FP32
+                           inner, FP64 defect correction; dwf_precond_*)       */
     int use_initial_guess; /* 1: x5 holds the initial guess on entry; 0: zero   */
     int verbose;        /* 0 quiet                                              */
+    int batch_wave;     /* dwf_solve_batch: at most this many systems per wave;
+                           0 (default): as many as device memory allows        */
 } dwf_solve_params;
 
 typedef struct {
@@ -145,6 +149,9 @@ typedef struct {
     double history[64];       /* eo residual at each reliable update            */
     int n_history;
     long long kernel_launches; /* device kernels launched by the call           */
+    int waves;                /* memory waves of the call (1 for dwf_solve)     */
+    int precond_applications; /* applications of the learned preconditioner     */
+    int fallbacks;            /* FCG cycles that fell back to plain CG          */
 } dwf_solve_stats;
 
 void dwf_solve_params_default(dwf_solve_params *p);
@@ -171,14 +178,24 @@ int dwf_propagator_host(dwf_handle h, const double *b4_host, double *x4_host,
                         const dwf_solve_params *p, dwf_solve_stats *stats, void *stream);
 
 /*
- * Solve n systems at once.  hs[i] are handles of the same lattice (they may
- * differ in Ls, mf, b, c, form); b4[i] are 4D sources and x4[i] 4D solutions
- * (device).  Every handle must have its gauge field set.  All systems' inner
- * CG iterations run in shared launches: each kernel of an iteration is one
- * launch over the (system, site-tile) work items of all systems still
- * iterating, and the iterations are replayed as CUDA graphs.  The systems
- * are processed in as few waves as device memory allows.  stats may be NULL or
- * an array of n.  Returns the worst status of the systems.
+ * Solve n systems at once (no counterpart in the paper, which solves one
+ * system at a time; the systems are independent).  hs[i] are handles of the
+ * same lattice dimensions (they may differ in Ls, mf, b, c, form, alpha; a
+ * handle may serve several systems); b4[i] are 4D sources and x4[i] the 4D
+ * solutions x4 = P_- x5(1) + P_+ x5(Ls) (device, complex double, 16-byte
+ * aligned; caller-owned).  Every handle must have its gauge field set.
+ * The systems run in lock step in waves that fit in device memory (systems
+ * ordered round robin over the handles, so that a wave mixes Ls and mf;
+ * p->batch_wave caps the wave size).  Within a wave every kernel of the
+ * inner iteration is one launch per distinct Ls over the (site tile, system)
+ * work items of all its systems, the links of a tile being read once from
+ * DRAM for all of them; the iterations are replayed as CUDA graphs, and
+ * converged systems are skipped by their flag.  Reliable updates, the source
+ * and the final FP64 check run per system between replays, as in dwf_solve.
+ * The initial guess is always zero.  stats may be NULL or an array of n
+ * (stats[i].waves: number of waves; seconds, kernel_launches: of the whole
+ * call).  Returns the worst status of the systems; DWF_ENOMEM when one system
+ * alone does not fit.
  */
 int dwf_solve_batch(dwf_handle const *hs, const void *const *b4, void *const *x4, int n,
                     const dwf_solve_params *p, dwf_solve_stats *stats, void *stream);
@@ -202,14 +219,16 @@ long long dwf_launch_count(dwf_handle h);
  * neighbour spinors directly from global memory, variant 1 stages the
  * neighbour sites in shared memory with TMA bulk copies, variant 2 is a
  * persistent kernel whose producer warp streams the neighbour sites through a
- * ring of shared-memory stages for the consumer warps; ns fifth-direction
+ * ring of shared-memory stages for the consumer warps, variant 3 is a
+ * persistent kernel sweeping consecutive tiles, variant 4 takes each CTA's
+ * sites as a 4D block of the half lattice (neighbour reuse in L1); ns fifth-direction
  * slices per thread (1, or 2 when Ls is even); sb four-dimensional sites per
  * CTA.  -1 / 0 select the built-in defaults.  No numerical effect. */
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb);
 int dwf_get_hop_config(dwf_handle h, int prec, int *variant, int *ns, int *sb);
 
 /* Autotuner: times every hop configuration (all variants, ns in {1, 2},
- * CTAs of 64 to 256 threads) on this handle's lattice with CUDA events on
+ * CTAs of 64 to 256 threads, every available mixing mode) on this handle's lattice with CUDA events on
  * `stream` and keeps the fastest.  cache_path (host string, may be NULL)
  * names a text file of earlier results keyed by device name, lattice, Ls and
  * precision: a hit skips the timing, a miss appends the new result.  Needs
@@ -219,10 +238,15 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream);
 /* Fifth-direction mixing in precision prec: 0 applies the dense per-chirality
  * Ls x Ls matrices, 1 their structured form (diagonal, bidiagonal-plus-corner
  * and closed-form inverse factors, about 6 flops per element instead of
- * 2 Ls; compiled for the direct hop variant, which it then selects).
- * -1 restores the default (dense).  mode 1 is
- * refused when the handle's parameters make the structured form unavailable
- * (|kappa| = |beta0/alpha0| >= 0.95). */
+ * 2 Ls), 2 the dense matrices as one [Ls x Ls] x [Ls x 12 sites] product per
+ * chirality and CTA on the tensor cores (TF32 MMAs with the matrix split in
+ * two TF32 terms; FP32 fields also split the field, FP16 fields do not; FP32
+ * and FP16 only).  Modes 1 and 2 are compiled for the direct hop variant,
+ * which they then select (mode 2 needs CTAs of at least 32 threads, else the
+ * dense form runs); the vector kernels outside the hop keep the dense form in
+ * mode 2.  -1 restores the default (dense).  mode 1 is refused when the
+ * handle's parameters make the structured form unavailable
+ * (|kappa| = |beta0/alpha0| >= 0.95), mode 2 for prec = DWF_F64. */
 int dwf_set_mix_mode(dwf_handle h, int prec, int mode);
 int dwf_get_mix_mode(dwf_handle h, int prec, int *mode);
 
@@ -258,6 +282,73 @@ int dwf_device_status(dwf_handle h, void *stream);
  * launch (inputs read once, outputs written once, links read once). */
 int dwf_time_hop(dwf_handle h, int prec, int reps, int flush_l2, double *us_per_launch,
                  double *bytes_per_launch, void *stream);
+
+/* ------------------------------------------------ learned preconditioner
+ * No counterpart in the paper (it solves with plain CG).  A gauge-covariant
+ * linear stencil network N approximates D^-1 for the even-odd matrix D;
+ * M = N N^dag (Hermitian, positive semi-definite) preconditions flexible CG on
+ * D^dag D (dwf_solve with params.precond = 1).
+ * Channels are the Ls fifth-direction slices (Ls <= 16).  Layer l maps a
+ * field psi of Ls channels to
+ *   out(x, c) = sum_p sum_c' W[l][p][chi][c][c'] T_p(x, c'),
+ *   T_0 = psi(x), T_{1+2mu} = (1 - gamma_mu) U_mu(x) psi(x+mu),
+ *   T_{2+2mu} = (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu)   (mu = 0..3: x, y, z, t),
+ * chi = 0 for output spins 0, 1 (P_+), 1 for spins 2, 3 (P_-), with the
+ * handle's boundary phases on hops across the boundary.  N(r) places an EO
+ * field r on the even sites (zero on odd sites), applies the layers and keeps
+ * the even sites; N^dag applies the adjoint layers in reverse order.  Weights: complex, host layout [layer][9][2][Ls][Ls]
+ * interleaved (re, im); FP64 master copy (Adam), BF16-rounded copy used by
+ * the FP32 kernels.
+ *
+ * Training: loss L = (1/K) sum_k |N(b_k) - x_k|^2 / |x_k|^2 over pairs
+ * D x_k = b_k, x_k = even part of the solution of D5 x5 = b5(b4_k) (dwf_solve)
+ * and b_k = D x_k; Adam (beta 0.9, 0.999, eps 1e-8) over minibatches.  The
+ * output layer starts scaled by the least-squares factor
+ * s = sum Re<b,x>/|x|^2 / sum |b|^2/|x|^2.
+ */
+typedef struct {
+    int layers;              /* network depth; default 3                          */
+    int epochs;              /* passes over the pairs; default 20                 */
+    int batch;               /* pairs per Adam step; default 16                   */
+    double lr;               /* Adam step size; default 2e-3                      */
+    int solve_inner_prec;    /* precision of the solves that make the pairs       */
+    double solve_tol;        /* their tolerance; default 1e-8                     */
+    unsigned long long seed; /* initial weights and pair order                    */
+    double noise;            /* scale of the random part of the initial weights   */
+    int verbose;
+} dwf_train_params;
+
+typedef struct {
+    int status;
+    int pairs, epochs, steps;
+    double loss_first, loss_last;  /* mean loss over the first and last epoch     */
+    double loss_history[64];       /* per epoch                                   */
+    int n_history;
+    double seconds;                /* whole call (host clock)                     */
+    double solve_seconds;          /* of which: making the pairs                  */
+} dwf_train_stats;
+
+void dwf_train_params_default(dwf_train_params *p);
+
+/* Identity network (self weights 1 on every channel and chirality) plus
+ * seeded normal noise of the given scale. */
+int dwf_precond_init(dwf_handle h, int layers, unsigned long long seed, double noise);
+/* Host weights in, FP64 (layout above); the Adam state is reset. */
+int dwf_precond_set_weights(dwf_handle h, int layers, const double *w);
+/* Host weights out: the FP64 master copy, or (compute_copy != 0) the
+ * BF16-rounded values the kernels use. */
+int dwf_precond_get_weights(dwf_handle h, int layers, int compute_copy, double *w);
+/* out = N in (which = 0), N^dag in (1) or M in = N N^dag in (2) on EO fields
+ * (device, complex double, layout of DWF_OP_EO_PREC); FP32 kernels. */
+int dwf_precond_apply(dwf_handle h, int which, const void *in, void *out, void *stream);
+/* Loss over npairs pairs (EO fields b[k], x[k], device) and its gradient with
+ * respect to the weights (host, layout above, may be NULL); FP32 kernels
+ * with the BF16-rounded weights, FP64 accumulation across thread blocks. */
+int dwf_precond_loss_grad(dwf_handle h, int npairs, const void *const *b, const void *const *x,
+                          double *loss, double *grad, void *stream);
+/* Make the pairs from nsrc 4D sources b4[k] (device) and train (above). */
+int dwf_precond_train(dwf_handle h, int nsrc, const void *const *b4, const dwf_train_params *p,
+                      dwf_train_stats *stats, void *stream);
 
 #ifdef __cplusplus
 }

@@ -23,13 +23,15 @@ C = 1, W_0 = 4 - M0, W_{+-mu} = -1/2 is D_W(-M0) itself (pinned by a test
 against the C oracle of D_W).  Gauge transformations act on colour only and
 W on channels and chirality only, so every layer is gauge covariant.
 
-The preconditioner M acts on even-site 5D fields r (Ls, Vh, 4, 3) of the
-even-odd system: the Ls slices are the C = Ls channels, the field is put on
-the even sites of the full lattice (zero on odd sites), three layers are
-applied, and the even sites of the result are M(r).  M is linear in r.
+The network N acts on even-site 5D fields r (Ls, Vh, 4, 3) of the even-odd
+system: the Ls slices are the C = Ls channels, the field is put on the even
+sites of the full lattice (zero on odd sites), the layers are applied, and
+the even sites of the result are N(r).  N is linear in r and is trained to
+approximate D^-1, D the even-odd matrix; the preconditioner of CG on the
+normal equation D^dag D is M = N N^dag (Hermitian, positive semi-definite).
 
-Training loss over pairs (b_k, x_k) of the normal equation A x = b
-(A = D^dag D, D the even-odd matrix):  L = (1/K) sum_k |M(b_k) - x_k|^2 / |x_k|^2.
+Training loss over pairs (b_k, x_k) with D x_k = b_k:
+L = (1/K) sum_k |N(b_k) - x_k|^2 / |x_k|^2.
 Gradients use the convention grad(z) = dL/dRe z + i dL/dIm z, under which
 y = w t gives grad(w) = sum grad(y) conj(t) and grad(t) = sum grad(y) conj(w).
 """
@@ -107,16 +109,23 @@ def layer_backward(U: np.ndarray, W: np.ndarray, psi: np.ndarray, G: np.ndarray,
     """Given grad of the layer output G, return (grad W, grad psi).
 
     grad W[p, chi, c, c'] = sum_{x, alpha in chi, a} G(c, x)_alpha,a conj(T_p(c', x)_alpha,a);
-    grad T_p = W^H G per chirality; grad psi is the adjoint of each transport
-    applied to grad T_p, written out hop by hop (not derived from the forward).
+    grad psi = layer_adjoint(G).
     """
     T = transports(U, psi, bc)
     C = psi.shape[0]
     gW = np.zeros((NHOP, 2, C, C), dtype=np.complex128)
-    gpsi = np.zeros_like(psi)
     for p in range(NHOP):
         for chi, sp in ((0, slice(0, 2)), (1, slice(2, 4))):
             gW[p, chi] = np.einsum("ctzyxsa,dtzyxsa->cd", G[..., sp, :], T[p][..., sp, :].conj())
+    return gW, layer_adjoint(U, W, G, bc)
+
+
+def layer_adjoint(U: np.ndarray, W: np.ndarray, G: np.ndarray, bc) -> np.ndarray:
+    """The adjoint of the layer (as a linear map of its input) applied to G:
+    grad T_p = W^H G per chirality, then the adjoint of each transport, written
+    out hop by hop (not derived from the forward)."""
+    gpsi = np.zeros_like(G)
+    for p in range(NHOP):
         # grad T_p(c') = sum_c conj(W[p, chi, c, c']) G(c)
         gT = np.empty_like(G)
         gT[..., 0:2, :] = np.einsum("ij,itzyxsa->jtzyxsa", W[p, 0].conj(), G[..., 0:2, :])
@@ -133,12 +142,12 @@ def layer_backward(U: np.ndarray, W: np.ndarray, psi: np.ndarray, G: np.ndarray,
             # T(x) = S U_mu(x-mu)^dag psi(x-mu)  =>  grad psi(y) += U_mu(y) S^dag gT(y+mu)
             h = shift(spinm((ONE4 + GAMMA[mu]).conj().T, gT), mu, +1, bc)
             gpsi += colour(link(U, mu), h)
-    return gW, gpsi
+    return gpsi
 
 
 class Net:
-    """The preconditioner M: weights (L, 9, 2, C, C) complex, on the even-odd
-    system of a lattice with the parity split of the oracle (even: x+y+z+t even)."""
+    """The network N: weights (L, 9, 2, C, C) complex, on the even-odd system of
+    a lattice with the parity split of the oracle (even: x+y+z+t even)."""
 
     def __init__(self, U, dims, bc, weights: np.ndarray):
         self.U = np.asarray(U)
@@ -170,6 +179,19 @@ class Net:
             acts.append(layer(self.U, self.W[l], acts[-1], self.bc))
         out = self.restrict(acts[-1])
         return (out, acts) if keep else out
+
+    def adjoint(self, r: np.ndarray) -> np.ndarray:
+        """N^dag r: the adjoint layers in reverse order between the same embedding
+        and restriction (their adjoints are each other)."""
+        G = self.embed(r)
+        for l in range(self.W.shape[0] - 1, -1, -1):
+            G = layer_adjoint(self.U, self.W[l], G, self.bc)
+        return self.restrict(G)
+
+    def precondition(self, r: np.ndarray) -> np.ndarray:
+        """M r = N N^dag r: Hermitian positive semi-definite by construction, the
+        preconditioner of CG on D^dag D when N approximates D^-1."""
+        return self.forward(self.adjoint(r))
 
     def loss_and_grad(self, pairs):
         """L = (1/K) sum |M b - x|^2/|x|^2 and its gradient with respect to W."""

@@ -73,15 +73,15 @@ __global__ void __launch_bounds__(256) mix_kernel(const MixArgs a)
     if (active) st_pairs<P>(a.out, (size_t)site, s, Ls, o[0]);
 }
 
-// p = r + beta p (or p = r), phat = M p
+// p = r + beta p (or p = r), phat = M p, on tile u (sites u SB .. u SB + SB - 1)
 template <int P, int MIX>
-__global__ void __launch_bounds__(256) cg_update_kernel(const CgUpdateArgs a)
+__device__ __forceinline__ void cg_update_tile(const CgUpdateArgs &a, int u)
 {
     typedef typename Tr<P>::real R;
     typedef typename Tr<P>::pair T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ls = a.Ls, s = threadIdx.x, j = threadIdx.y, SB = blockDim.y;
-    const int site = blockIdx.x * SB + j;
+    const int site = u * SB + j;
     const bool active = site < a.Vh;
     const int tstride = Ls * 12 + 2;
     T2 *tile = reinterpret_cast<T2 *>(smem_raw);
@@ -110,6 +110,28 @@ __global__ void __launch_bounds__(256) cg_update_kernel(const CgUpdateArgs a)
     for (int k = 0; k < 12; ++k) o[0][k] = p_splat((R)0);
     mix_tile_any<MIX>(a.prog, mtx, tile, tstride, j, s, Ls, active, o);
     if (active) st_pairs<P>(a.phat, (size_t)site, s, Ls, o[0]);
+}
+
+template <int P, int MIX>
+__global__ void __launch_bounds__(256) cg_update_kernel(const CgUpdateArgs a)
+{
+    cg_update_tile<P, MIX>(a, blockIdx.x);
+}
+
+// Batched form over nsys systems of equal Ls: CTA b updates tile b / nsys of
+// system b % nsys; systems whose skip flag is set are left untouched.
+template <int P, int MIX>
+__global__ void __launch_bounds__(256) cg_update_batch_kernel(const CgUpdateArgs *__restrict__ tab, int nsys)
+{
+    __shared__ __align__(16) unsigned char abuf[sizeof(CgUpdateArgs)];
+    const int sys = blockIdx.x % nsys, u = blockIdx.x / nsys;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    const unsigned *src = reinterpret_cast<const unsigned *>(tab + sys);
+    for (int k = tid; k < (int)(sizeof(CgUpdateArgs) / 4); k += nt) reinterpret_cast<unsigned *>(abuf)[k] = src[k];
+    __syncthreads();
+    const CgUpdateArgs &a = *reinterpret_cast<const CgUpdateArgs *>(abuf);
+    if (a.skip && *a.skip) return;
+    cg_update_tile<P, MIX>(a, u);
 }
 
 template <int P>
@@ -160,6 +182,30 @@ template <int P>
 cudaError_t launch_cg_update_t(const CgUpdateArgs &a, cudaStream_t st)
 {
     return a.mixmode == 1 ? launch_cg_update_m<P, 1>(a, st) : launch_cg_update_m<P, 0>(a, st);
+}
+
+template <int P, int MIX>
+cudaError_t launch_cg_update_batch_m(const CgUpdateArgs *tab, int nsys, const CgUpdateArgs &a0, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(cg_update_batch_kernel<P, MIX>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int SB = tile_sb(a0.Ls);
+    const long long grid = (long long)((a0.Vh + SB - 1) / SB) * nsys;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    cg_update_batch_kernel<P, MIX><<<(unsigned)grid, dim3(a0.Ls, SB), tile_smem<P>(a0.Ls, SB), st>>>(tab, nsys);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_cg_update_batch_t(const CgUpdateArgs *tab, int nsys, const CgUpdateArgs &a0, cudaStream_t st)
+{
+    return a0.mixmode == 1 ? launch_cg_update_batch_m<P, 1>(tab, nsys, a0, st)
+                           : launch_cg_update_batch_m<P, 0>(tab, nsys, a0, st);
 }
 
 // ------------------------------------------------------------------ packing
@@ -423,6 +469,18 @@ cudaError_t launch_cg_update(int prec, const CgUpdateArgs &a, cudaStream_t st)
     case DWF_F64: return launch_cg_update_t<DWF_F64>(a, st);
     case DWF_F32: return launch_cg_update_t<DWF_F32>(a, st);
     case DWF_F16: return launch_cg_update_t<DWF_F16>(a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cg_update_batch(int prec, const CgUpdateArgs *tab, int nsys, const CgUpdateArgs &a0,
+                                   cudaStream_t st)
+{
+    if (nsys < 1) return cudaSuccess;
+    switch (prec) {
+    case DWF_F64: return launch_cg_update_batch_t<DWF_F64>(tab, nsys, a0, st);
+    case DWF_F32: return launch_cg_update_batch_t<DWF_F32>(tab, nsys, a0, st);
+    case DWF_F16: return launch_cg_update_batch_t<DWF_F16>(tab, nsys, a0, st);
     }
     return cudaErrorInvalidValue;
 }

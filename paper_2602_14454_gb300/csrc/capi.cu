@@ -42,8 +42,9 @@ const void *dwf_ctx::mat(int prec, int id) const
 
 int dwf_ctx::mix_mode(int prec) const
 {
-    if (!fm.structured) return 0;
-    if (mixmode[prec] >= 0) return mixmode[prec];
+    const int m = mixmode[prec];
+    if (m == 1) return fm.structured ? 1 : 0;
+    if (m == 2) return prec == DWF_F64 ? 0 : 2;
     return 0;
 }
 
@@ -325,6 +326,7 @@ int dwf_destroy(dwf_handle h)
 {
     if (!h) return DWF_OK;
     dwf_solver_release(h);
+    dwf_precond_release(h);
     for (auto &kv : h->work) cudaFree(kv.second.first);
     h->work.clear();
     for (int k = 0; k < 3; ++k) {
@@ -517,9 +519,11 @@ int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb)
 
 int dwf_set_mix_mode(dwf_handle h, int prec, int mode)
 {
-    if (!h || prec < 0 || prec > 2 || mode < -1 || mode > 1) return dwf_set_error(DWF_EINVAL, "bad argument");
+    if (!h || prec < 0 || prec > 2 || mode < -1 || mode > 2) return dwf_set_error(DWF_EINVAL, "bad argument");
     if (mode == 1 && !h->fm.structured)
         return dwf_set_error(DWF_EINVAL, "the structured mixing is not available for these parameters");
+    if (mode == 2 && prec == DWF_F64)
+        return dwf_set_error(DWF_EINVAL, "the tensor-core mixing has no FP64 form");
     h->mixmode[prec] = mode;
     return DWF_OK;
 }
@@ -563,7 +567,8 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
                     h->hop_var[prec] = var;
                     h->hop_ns[prec] = ns;
                     h->hop_sb[prec] = sb;
-                    h->mixmode[prec] = (mix == 1 && !h->fm.structured) ? 0 : mix;
+                    h->mixmode[prec] = mix;
+                    h->mixmode[prec] = h->mix_mode(prec);
                     hit = true;
                 }
             }
@@ -573,9 +578,12 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
     }
     double best = 1e30;
     int bvar = -1, bns = 0, bsb = 0, bmix = 0;
-    for (int mix = 0; mix <= (h->fm.structured ? 1 : 0); ++mix)
+    for (int mix = 0; mix <= 2; ++mix)
         for (int var = 0; var <= 4; ++var)
             for (int ns = 1; ns <= 2; ++ns) {
+                if (mix == 1 && !h->fm.structured) continue;
+                if (mix == 2 && prec == DWF_F64) continue;
+                if (mix != 0 && var != 0) continue;   // those mixings exist in the direct variant only
                 if (h->Ls % ns) continue;
                 const int LsN = h->Ls / ns;
                 for (int threads = 64; threads <= 256; threads += 64) {

@@ -109,8 +109,9 @@ struct HopArgs {
     RedArgs red;
     int *err = nullptr;            // bit 0 set when a bounded device wait gave up
     int ext[4] = {0, 0, 0, 0};     // half-lattice extents (Lx/2, Ly, Lz, Lt): blocked hop variant
-    int mixmode = 0;               // 0 dense matrices, 1 structured programs (MixProg)
+    int mixmode = 0;               // 0 dense matrices, 1 structured programs (MixProg), 2 tensor-core product
     const void *post_prog = nullptr, *y_prog = nullptr, *z_prog = nullptr;
+    const int *skip = nullptr;     // batched launches: the system is left untouched while *skip != 0
 };
 
 struct MixArgs {
@@ -130,6 +131,7 @@ struct CgUpdateArgs {
     int init = 0;
     int mixmode = 0;
     const void *prog = nullptr;
+    const int *skip = nullptr;     // batched launches: the system is left untouched while *skip != 0
 };
 
 // ------------------------------------------------------------ launchers
@@ -146,6 +148,13 @@ size_t hop_staged_smem_bytes(int prec, int Ls, int sb);
 size_t hop_pipe_smem_bytes(int prec, int Ls, int sb);
 cudaError_t launch_mix(int prec, const MixArgs &a, cudaStream_t st);
 cudaError_t launch_cg_update(int prec, const CgUpdateArgs &a, cudaStream_t st);
+// Batched launches over nsys systems with equal Ls (tables in device memory;
+// a0: host copy of one entry, for Ls, Vh and the mixing mode): the direct hop
+// with (ns, sb) tiling, and the CG update.
+cudaError_t launch_hop_batch(int prec, bool dag, const HopArgs *tab, int nsys, const HopArgs &a0, int ns, int sb,
+                             cudaStream_t st);
+cudaError_t launch_cg_update_batch(int prec, const CgUpdateArgs *tab, int nsys, const CgUpdateArgs &a0,
+                                   cudaStream_t st);
 
 // canonical complex-double field <-> internal halves
 // full: canon [s][lex][12 cplx]; eo: canon [s][i][12 cplx] of parity `par` only
@@ -210,6 +219,12 @@ struct MixProg {
     R d1[2][LS_MAX], d2[2][LS_MAX];
 };
 
+struct NetState;   // learned preconditioner of a handle (precond.cu)
+
+// Flexible-CG helpers (precond.cu, solver.cu): FP32 even fields.
+cudaError_t launch_vdot(FieldRef x, FieldRef y, int Vh, int Ls, const RedArgs &red, cudaStream_t st);   // Re <x, y>
+cudaError_t launch_vaxpby(float a, FieldRef x, float b, FieldRef y, int Vh, int Ls, cudaStream_t st);  // y = a x + b y
+
 // Builds every matrix above; returns false when A5 is singular.
 bool build_fifth_matrices(int Ls, double M0, double mf, double b, double c, int form, double alpha,
                           FifthMatrices &out, std::string &err);
@@ -228,7 +243,7 @@ struct dwf_ctx {
     dwf::FifthMatrices fm;
     void *mats_dev[3] = {nullptr, nullptr, nullptr};   // double / float / float copies (F16 uses float)
     void *progs_dev[2] = {nullptr, nullptr};           // MixProg<double>[MAT_COUNT], MixProg<float>[MAT_COUNT]
-    int mixmode[3] = {-1, -1, -1};    // fifth-direction mixing per precision: 0 dense, 1 structured, -1 default
+    int mixmode[3] = {-1, -1, -1};    // fifth-direction mixing per precision: 0 dense, 1 structured, 2 tensor cores, -1 default
     int mix_mode(int prec) const;
     const void *prog(int prec, int id) const;
     int *nbr = nullptr;       // [2][Vh][8]
@@ -245,6 +260,7 @@ struct dwf_ctx {
     int hop_var[3] = {-1, -1, -1};    // hop variant per precision (-1 = default), set by the autotuner
     int hop_ns[3] = {0, 0, 0};        // hop tiling per precision (0 = default)
     int hop_sb[3] = {0, 0, 0};
+    dwf::NetState *net = nullptr;     // learned preconditioner (dwf_precond_*)
     int *errflag() const { return &scal[7].flags; }
 
     const void *mat(int prec, int id) const;
@@ -254,6 +270,15 @@ struct dwf_ctx {
     void *ws(const std::string &name, size_t bytes_needed, cudaError_t *err);
     dwf::FieldRef field(const std::string &name, int prec, cudaError_t *err);
 };
+
+namespace dwf {
+// the handle's network on FP32 even fields: which = 0 N, 1 N^dag, 2 M = N N^dag
+int net_apply_f32(dwf_ctx *h, FieldRef r, FieldRef z, cudaStream_t st, int which = 2);
+// out = D^dag D x / out = D x with D the even-odd matrix (FP32 even fields)
+int normal_apply_f32(dwf_ctx *h, FieldRef x, FieldRef out, cudaStream_t st);
+int eo_apply_f32(dwf_ctx *h, FieldRef x, FieldRef out, cudaStream_t st);
+}  // namespace dwf
+void dwf_precond_release(dwf_ctx *h);
 
 // error reporting helpers (capi.cu)
 int dwf_set_error(int status, const std::string &msg);

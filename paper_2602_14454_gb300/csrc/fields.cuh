@@ -204,15 +204,15 @@ __device__ __forceinline__ void finish_reduction(double total, const RedArgs &r)
 }
 
 // Deterministic grid reduction: per-block partials, the last block to finish
-// adds them in index order and applies the scalar operation.
-__device__ __forceinline__ void grid_reduce(double v, const RedArgs &r)
+// adds them in index order and applies the scalar operation.  bid / nb: this
+// block's index among the nb blocks that reduce into r (a batched launch runs
+// one such group of blocks per system).
+__device__ __forceinline__ void grid_reduce(double v, const RedArgs &r, unsigned bid, unsigned nb)
 {
     __shared__ double wsum[32];
     __shared__ bool is_last;
     const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
     const int nt = blockDim.x * blockDim.y * blockDim.z;
-    const unsigned nb = gridDim.x * gridDim.y;
-    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
     double s = block_sum(v, wsum);
     if (tid == 0) {
         r.partials[bid] = s;
@@ -232,6 +232,10 @@ __device__ __forceinline__ void grid_reduce(double v, const RedArgs &r)
             *r.counter = 0u;
         }
     }
+}
+__device__ __forceinline__ void grid_reduce(double v, const RedArgs &r)
+{
+    grid_reduce(v, r, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
 }
 
 // ------------------------------------------------- fifth-direction mixing
@@ -311,6 +315,110 @@ __device__ __forceinline__ void chain_mix(const MixProg<R> *pg, T2 *tile, int ts
                 const int s = up ? Ls - 1 - u : u;
                 base[s * 24] = v[u] * d2[s];
             }
+    }
+}
+
+// ------------------------------------------------- tensor-core mixing
+// Per chirality the mixing of a CTA's tile is one matrix product
+//   D[s][col] = sum_t M[s][t] H[t][col],   col = (site, one of 12 reals),
+// [Ls x Ls] x [Ls x 12 nsites], computed with warp-level TF32 MMAs
+// (m16n8k8, FP32 accumulation; rows padded to 16, contraction to 8).  TF32
+// keeps FP32's exponent range, which the unscaled FP32 tile values need.
+// The matrix is split as M = M_hi + M_lo (both exact TF32 values) so that its
+// rounding does not enter; with NB = 2 the tile is split the same way and the
+// product is M_hi H_hi + M_hi H_lo + M_lo H_hi (FP32-level accuracy, error
+// ~2^-21 relative), with NB = 1 it is M_hi H + M_lo H (error ~2^-11 relative
+// per element of H, the size of the FP16 storage rounding).
+// Tasks are (chirality, 8-column slice); a warp reads all B fragments of its
+// task before it writes the task's results, and the slices are disjoint, so
+// the tile is transformed in place.  Only full warps (32 consecutive threads)
+// take tasks: `nwarps` counts full warps.
+__device__ __forceinline__ uint32_t f32_to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void mma_tf32_1688(float *d, const uint32_t *a, const uint32_t *b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// mt: the mixing matrices in shared memory as the kernels store them,
+// element (chi, s, t) at mt[chi*Ls*Ls + t*Ls + (s % LsN)*NS + s / LsN].
+// tile: nsites sites, site stride tstride_pairs pairs, row s at 12 s pairs.
+template <int NB>
+__device__ __forceinline__ void mma_mix_tile(const float *mt, float *tile, int tstride_pairs, int nsites, int Ls,
+                                             int NS, int warp, int nwarps)
+{
+    if (warp >= nwarps) return;   // a partial last warp must not execute mma.sync
+    int lane;
+    asm("mov.u32 %0, %%laneid;" : "=r"(lane));
+    const int g = lane >> 2, c4 = lane & 3;
+    const int LsN = Ls / NS, LL = Ls * Ls;
+    const int ncols = nsites * 12;
+    const int ntiles = (ncols + 7) >> 3;
+    const int sstride = tstride_pairs * 2;
+    const int nmb = (Ls + 15) >> 4, nkb = (Ls + 7) >> 3;
+    auto aval = [&](int chi, int s, int t) -> float {
+        return (s < Ls && t < Ls) ? mt[chi * LL + t * Ls + (s % LsN) * NS + s / LsN] : 0.f;
+    };
+    // float offset in the tile of real `col` (site, q) of chirality chi, row t
+    auto baddr = [&](int chi, int col, int t) -> int {
+        const int jj = col / 12, q = col - jj * 12;
+        return jj * sstride + t * 24 + 4 * (q >> 1) + 2 * chi + (q & 1);
+    };
+    for (int w = warp; w < 2 * ntiles; w += nwarps) {
+        const int chi = w / ntiles, nt = w - chi * ntiles;
+        const int col = nt * 8 + g;
+        const bool colok = col < ncols;
+        uint32_t bh[4][2], bl[4][2];
+#pragma unroll
+        for (int kb = 0; kb < 4; ++kb)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int t = kb * 8 + c4 + 4 * r;
+                const float v = (colok && t < Ls) ? tile[baddr(chi, col, t)] : 0.f;
+                bh[kb][r] = f32_to_tf32(v);
+                bl[kb][r] = NB == 2 ? f32_to_tf32(v - __uint_as_float(bh[kb][r])) : 0u;
+            }
+        __syncwarp();
+        float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb) {
+            if (mb >= nmb) break;
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb) {
+                if (kb >= nkb) break;
+                const int s0 = mb * 16 + g, t0 = kb * 8 + c4;
+                const float av[4] = {aval(chi, s0, t0), aval(chi, s0 + 8, t0), aval(chi, s0, t0 + 4),
+                                     aval(chi, s0 + 8, t0 + 4)};
+                uint32_t ah[4], al[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    ah[r] = f32_to_tf32(av[r]);
+                    al[r] = f32_to_tf32(av[r] - __uint_as_float(ah[r]));
+                }
+                mma_tf32_1688(acc[mb], ah, bh[kb]);
+                if (NB == 2) mma_tf32_1688(acc[mb], ah, bl[kb]);
+                mma_tf32_1688(acc[mb], al, bh[kb]);
+            }
+        }
+        // accumulator element r: row g + 8 (r >> 1) of the block, column 2 c4 + (r & 1) of the slice
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb) {
+            if (mb >= nmb) break;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int s = mb * 16 + g + (r >> 1) * 8;
+                const int cc = nt * 8 + c4 * 2 + (r & 1);
+                if (s < Ls && cc < ncols) tile[baddr(chi, cc, s)] = acc[mb][r];
+            }
+        }
     }
 }
 

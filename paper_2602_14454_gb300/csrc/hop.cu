@@ -30,111 +30,10 @@
 // accumulator, applies a final mixing and reduces |o|^2 deterministically.
 #include <cstdint>
 
-#include "fields.cuh"
+#include "stencil.cuh"
 
 namespace dwf {
 namespace {
-
-// h = P^{(mu, sig)} psi, spin-paired (see fields.cuh for the pair layout)
-template <int MU, int SIG, typename T2>
-__device__ __forceinline__ void project(const T2 *v, T2 *Hx, T2 *Hy)
-{
-    typedef typename PairReal<T2>::R R;
-    constexpr R s = (R)SIG;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const T2 XU = v[4 * a], XL = v[4 * a + 1], YU = v[4 * a + 2], YL = v[4 * a + 3];
-        if constexpr (MU == 3) {        // h0 = p0 - s p2, h1 = p1 - s p3
-            Hx[a] = p_fma(p_splat(-s), XL, XU);
-            Hy[a] = p_fma(p_splat(-s), YL, YU);
-        } else if constexpr (MU == 2) { // h0 = p0 + s i p2, h1 = p1 - s i p3
-            Hx[a] = p_fma(p_make(-s, s), YL, XU);
-            Hy[a] = p_fma(p_make(s, -s), XL, YU);
-        } else if constexpr (MU == 1) { // h0 = p0 + s p3, h1 = p1 - s p2
-            Hx[a] = p_make(XU.x + s * XL.y, XU.y - s * XL.x);
-            Hy[a] = p_make(YU.x + s * YL.y, YU.y - s * YL.x);
-        } else {                        // h0 = p0 + s i p3, h1 = p1 + s i p2
-            Hx[a] = p_make(XU.x - s * YL.y, XU.y - s * YL.x);
-            Hy[a] = p_make(YU.x + s * XL.y, YU.y + s * XL.x);
-        }
-    }
-}
-
-// acc += [q ; -sig e_mu^dag q]
-template <int MU, int SIG, typename T2>
-__device__ __forceinline__ void reconstruct(T2 *acc, const T2 *Qx, const T2 *Qy)
-{
-    typedef typename PairReal<T2>::R R;
-    constexpr R s = (R)SIG;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        T2 &XU = acc[4 * a], &XL = acc[4 * a + 1], &YU = acc[4 * a + 2], &YL = acc[4 * a + 3];
-        XU = p_add(XU, Qx[a]);
-        YU = p_add(YU, Qy[a]);
-        if constexpr (MU == 3) {        // lower = -s (q0, q1)
-            XL = p_fma(p_splat(-s), Qx[a], XL);
-            YL = p_fma(p_splat(-s), Qy[a], YL);
-        } else if constexpr (MU == 2) { // p2 += -s i q0, p3 += s i q1
-            XL = p_fma(p_make(s, -s), Qy[a], XL);
-            YL = p_fma(p_make(-s, s), Qx[a], YL);
-        } else if constexpr (MU == 1) { // p2 += -s q1, p3 += s q0
-            XL = p_make(XL.x - s * Qx[a].y, XL.y + s * Qx[a].x);
-            YL = p_make(YL.x - s * Qy[a].y, YL.y + s * Qy[a].x);
-        } else {                        // p2 += -s i q1, p3 += -s i q0
-            XL = p_make(XL.x + s * Qy[a].y, XL.y + s * Qy[a].x);
-            YL = p_make(YL.x - s * Qx[a].y, YL.y - s * Qx[a].x);
-        }
-    }
-}
-
-// link (row-major 3x3 complex) -> u[9] complex pairs (re, im); global (RO) or shared
-template <int P, bool GLOBAL, typename T2>
-__device__ __forceinline__ void load_link(const typename Tr<P>::link_t *U, T2 *u)
-{
-    if constexpr (P == DWF_F64) {
-        const double2 *v = reinterpret_cast<const double2 *>(U);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) u[k] = GLOBAL ? __ldg(v + k) : v[k];
-    } else if constexpr (P == DWF_F32) {
-        const float2 *v = reinterpret_cast<const float2 *>(U);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) u[k] = GLOBAL ? __ldg(v + k) : v[k];
-    } else {
-        const __half2 *v = reinterpret_cast<const __half2 *>(U);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) u[k] = __half22float2(GLOBAL ? __ldg(v + k) : v[k]);
-    }
-}
-
-// Q = U H for both spins: Qx[a] = sum_b ur Hx[b] - ui Hy[b], Qy[a] = sum_b ur Hy[b] + ui Hx[b]
-template <typename T2>
-__device__ __forceinline__ void su3_pairs(const T2 *u, const T2 *Hx, const T2 *Hy, T2 *Qx, T2 *Qy)
-{
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        T2 qx = p_zero(Hx[0]), qy = p_zero(Hx[0]);
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const T2 ur = p_splat(u[a * 3 + b].x), ui = p_splat(u[a * 3 + b].y);
-            const T2 nui = p_splat(-u[a * 3 + b].y);
-            qx = p_fma(ur, Hx[b], qx);
-            qx = p_fma(nui, Hy[b], qx);
-            qy = p_fma(ur, Hy[b], qy);
-            qy = p_fma(ui, Hx[b], qy);
-        }
-        Qx[a] = qx;
-        Qy[a] = qy;
-    }
-}
-
-template <int MU, int SIG, typename T2>
-__device__ __forceinline__ void hop_one(T2 *acc, const T2 *u, const T2 *v)
-{
-    T2 Hx[3], Hy[3], Qx[3], Qy[3];
-    project<MU, SIG>(v, Hx, Hy);
-    su3_pairs(u, Hx, Hy, Qx, Qy);
-    reconstruct<MU, SIG>(acc, Qx, Qy);
-}
 
 // one (site, s) of a neighbour site copied to shared memory: the Ls x G block
 // of 16-byte vectors in the global layout, followed (FP16) by its scales
@@ -200,16 +99,23 @@ struct TileCtx {
     int tid, nthr; // this thread among the threads that share the work
 };
 
-// o[n] += (mixing of this thread's rows of the tile).  Dense: Ls x Ls matrix M
-// from shared memory.  Structured: the CTA first transforms the whole tile in
-// place along its chains, then every thread reads its rows back.  The tile
-// must hold the input and be visible to all threads on entry.
+// o[n] += (mixing of this thread's rows of the tile).  MIX 0, dense: Ls x Ls
+// matrix M from shared memory, per thread.  MIX 1, structured: the CTA first
+// transforms the whole tile in place along its chains; MIX 2 / 3, tensor
+// cores: the CTA's full warps transform the tile in place with TF32 MMAs
+// (3 / 2 products, see mma_mix_tile); then every thread reads its rows back.
+// The tile must hold the input and be visible to all threads on entry.
 template <int MIX, int NS, typename T2, typename R, typename Bar>
 __device__ __forceinline__ void mix_into(const void *prog, const R *M, const TileCtx<T2> &tc, T2 *mytile,
                                          int x, int LsN, int Ls, bool active, T2 (*o)[12], const Bar &bar)
 {
-    if constexpr (MIX == 1) {
-        chain_mix<R>(reinterpret_cast<const MixProg<R> *>(prog), tc.tile0, tc.tstride, tc.nsites, Ls, tc.tid, tc.nthr);
+    if constexpr (MIX >= 1) {
+        if constexpr (MIX == 1)
+            chain_mix<R>(reinterpret_cast<const MixProg<R> *>(prog), tc.tile0, tc.tstride, tc.nsites, Ls, tc.tid,
+                         tc.nthr);
+        else
+            mma_mix_tile<MIX == 2 ? 2 : 1>(reinterpret_cast<const float *>(M), reinterpret_cast<float *>(tc.tile0),
+                                           tc.tstride, tc.nsites, Ls, Ls / LsN, tc.tid >> 5, tc.nthr >> 5);
         bar.sync();
         if (active) {
 #pragma unroll
@@ -234,6 +140,8 @@ __device__ __forceinline__ double hop_epilogue_core(const HopArgs &a, T2 (*acc)[
 {
     const int Ls = a.Ls;
     const int msz = 2 * Ls * Ls;
+    // tensor-core mixing: FP16 fields take the two-product form (its error is that of the FP16 storage)
+    constexpr int MX = (MIX == 2 && P == DWF_F16) ? 3 : MIX;
     if (active) {
 #pragma unroll
         for (int n = 0; n < NS; ++n) put_tile(mytile, x + n * LsN, acc[n]);
@@ -245,7 +153,7 @@ __device__ __forceinline__ double hop_epilogue_core(const HopArgs &a, T2 (*acc)[
     for (int n = 0; n < NS; ++n)
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[n][k] = p_splat((R)0);
-    mix_into<MIX, NS>(a.post_prog, mtx, tc, mytile, x, LsN, Ls, active, o, bar);
+    mix_into<MX, NS>(a.post_prog, mtx, tc, mytile, x, LsN, Ls, active, o, bar);
 
     if (a.ymode == 1) {
         if (active) {
@@ -268,7 +176,7 @@ __device__ __forceinline__ double hop_epilogue_core(const HopArgs &a, T2 (*acc)[
             }
         }
         bar.sync();
-        mix_into<MIX, NS>(a.y_prog, mtx + msz, tc, mytile, x, LsN, Ls, active, o, bar);
+        mix_into<MX, NS>(a.y_prog, mtx + msz, tc, mytile, x, LsN, Ls, active, o, bar);
     }
 
     if (a.rin.v && active) {
@@ -319,7 +227,7 @@ __device__ __forceinline__ double hop_epilogue_core(const HopArgs &a, T2 (*acc)[
         for (int n = 0; n < NS; ++n)
 #pragma unroll
             for (int k = 0; k < 12; ++k) z[n][k] = p_splat((R)0);
-        mix_into<MIX, NS>(a.z_prog, mtx + 2 * msz, tc, mytile, x, LsN, Ls, active, z, bar);
+        mix_into<MX, NS>(a.z_prog, mtx + 2 * msz, tc, mytile, x, LsN, Ls, active, z, bar);
         if (active) {
 #pragma unroll
             for (int n = 0; n < NS; ++n) st_pairs<P>(a.out, (size_t)site, x + n * LsN, Ls, z[n]);
@@ -387,8 +295,10 @@ __device__ __forceinline__ void hop_dir(T2 (*acc)[12], const FieldRef &in, int n
     }
 }
 
+// One tile of SB sites: blockDim = (Ls/NS, SB), site = u SB + threadIdx.y.
+// The norm reduction runs over the nb_red tiles that share a.red.
 template <int P, bool DAG, int NS, int MIX>
-__global__ void __launch_bounds__(256) hop_kernel(const HopArgs a)
+__device__ __forceinline__ void hop_direct_tile(const HopArgs &a, int u, unsigned nb_red)
 {
     typedef typename Tr<P>::real R;
     typedef typename Tr<P>::pair T2;
@@ -399,7 +309,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a)
     const int x = threadIdx.x;
     const int j = threadIdx.y;
     const int SB = blockDim.y;
-    const int site = blockIdx.x * SB + j;
+    const int site = u * SB + j;
     const bool active = site < a.Vh;
     const int tstride = Ls * 12 + 2;
     T2 *tile = reinterpret_cast<T2 *>(smem_raw);
@@ -426,7 +336,35 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a)
         hop_dir<P, DAG, 6, NS>(acc, a.in, n8[6], x, LsN, Ls, U);
         hop_dir<P, DAG, 7, NS>(acc, a.in, n8[7], x, LsN, Ls, U);
     }
-    hop_epilogue<P, NS, MIX>(a, acc, tile, j, mtx, site, x, LsN, active);
+    const TileCtx<T2> tc = cta_tile(tile, Ls);
+    const double nrm = hop_epilogue_core<P, NS, MIX>(a, acc, tc, tile + j * tc.tstride, mtx, site, x, LsN, active,
+                                                     CtaBarrier());
+    if (a.red.op != RED_NONE) grid_reduce(nrm, a.red, u, nb_red);
+}
+
+template <int P, bool DAG, int NS, int MIX>
+__global__ void __launch_bounds__(256) hop_kernel(const HopArgs a)
+{
+    hop_direct_tile<P, DAG, NS, MIX>(a, blockIdx.x, gridDim.x);
+}
+
+// Batched form: one launch over nsys systems that share Ls and the CTA shape
+// (each with its own fields, matrices, scalars and reduction buffers).  CTA b
+// works on tile b / nsys of system b % nsys, so that consecutive CTAs read the
+// same sites' links and neighbour indices, which then come from L2 for all
+// systems but the first.  A system whose skip flag is set is left untouched.
+template <int P, bool DAG, int NS, int MIX>
+__global__ void __launch_bounds__(256) hop_batch_kernel(const HopArgs *__restrict__ tab, int nsys)
+{
+    __shared__ __align__(16) unsigned char abuf[sizeof(HopArgs)];
+    const int sys = blockIdx.x % nsys, u = blockIdx.x / nsys;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    const unsigned *src = reinterpret_cast<const unsigned *>(tab + sys);
+    for (int k = tid; k < (int)(sizeof(HopArgs) / 4); k += nt) reinterpret_cast<unsigned *>(abuf)[k] = src[k];
+    __syncthreads();
+    const HopArgs &a = *reinterpret_cast<const HopArgs *>(abuf);
+    if (a.skip && *a.skip) return;
+    hop_direct_tile<P, DAG, NS, MIX>(a, u, (a.Vh + blockDim.y - 1) / blockDim.y);
 }
 
 // ------------------------------------------------- variant 4: blocked tiles
@@ -973,6 +911,38 @@ cudaError_t launch_direct(const HopArgs &a, int SB, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <int P, bool DAG, int NS, int MIX>
+cudaError_t launch_direct_batch(const HopArgs *tab, int nsys, const HopArgs &a0, int SB, cudaStream_t st)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(hop_batch_kernel<P, DAG, NS, MIX>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int LsN = a0.Ls / NS;
+    const long long grid = (long long)((a0.Vh + SB - 1) / SB) * nsys;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    hop_batch_kernel<P, DAG, NS, MIX><<<(unsigned)grid, dim3(LsN, SB), direct_smem<P>(a0.Ls, SB), st>>>(tab, nsys);
+    return cudaGetLastError();
+}
+
+template <int P, bool DAG>
+cudaError_t launch_batch_pd(const HopArgs *tab, int nsys, const HopArgs &a0, int NS, int SB, cudaStream_t st)
+{
+    if (a0.mixmode == 1)
+        return NS == 2 ? launch_direct_batch<P, DAG, 2, 1>(tab, nsys, a0, SB, st)
+                       : launch_direct_batch<P, DAG, 1, 1>(tab, nsys, a0, SB, st);
+    if constexpr (P != DWF_F64) {
+        if (a0.mixmode == 2 && (a0.Ls / NS) * SB >= 32)
+            return NS == 2 ? launch_direct_batch<P, DAG, 2, 2>(tab, nsys, a0, SB, st)
+                           : launch_direct_batch<P, DAG, 1, 2>(tab, nsys, a0, SB, st);
+    }
+    return NS == 2 ? launch_direct_batch<P, DAG, 2, 0>(tab, nsys, a0, SB, st)
+                   : launch_direct_batch<P, DAG, 1, 0>(tab, nsys, a0, SB, st);
+}
+
 template <int P, bool DAG, int NS>
 cudaError_t launch_staged(const HopArgs &a, int SB, cudaStream_t st)
 {
@@ -1114,10 +1084,16 @@ cudaError_t launch_sweep(const HopArgs &a, int SB, cudaStream_t st)
 template <int P, bool DAG>
 cudaError_t launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
 {
-    // the structured fifth-direction mixing is compiled for the direct variant only
+    // the structured and tensor-core mixings are compiled for the direct variant only
     if (a.mixmode == 1) {
         if (NS == 2) return launch_direct<P, DAG, 2, 1>(a, SB, st);
         return launch_direct<P, DAG, 1, 1>(a, SB, st);
+    }
+    if constexpr (P != DWF_F64) {
+        if (a.mixmode == 2 && (a.Ls / NS) * SB >= 32) {
+            if (NS == 2) return launch_direct<P, DAG, 2, 2>(a, SB, st);
+            return launch_direct<P, DAG, 1, 2>(a, SB, st);
+        }
     }
     if (var == 4) {
         if (NS == 2) return launch_block<P, DAG, 2>(a, SB, st);
@@ -1141,7 +1117,11 @@ cudaError_t launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st
 
 }  // namespace
 
-int hop_default_variant(int prec) { return prec == DWF_F64 ? 0 : 1; }
+int hop_default_variant(int prec)
+{
+    (void)prec;
+    return 0;   // direct loads: fastest measured at 16^3x32, Ls 16 in every precision
+}
 
 int hop_default_ns(int prec, int Ls)
 {
@@ -1176,6 +1156,28 @@ size_t hop_pipe_smem_bytes(int prec, int Ls, int SB)
     case DWF_F64: return pipe_smem<DWF_F64>(Ls, SB, pipe_stages<DWF_F64>(Ls, SB), &o1, &o2, &o3, &o4);
     case DWF_F32: return pipe_smem<DWF_F32>(Ls, SB, pipe_stages<DWF_F32>(Ls, SB), &o1, &o2, &o3, &o4);
     default: return pipe_smem<DWF_F16>(Ls, SB, pipe_stages<DWF_F16>(Ls, SB), &o1, &o2, &o3, &o4);
+    }
+}
+
+cudaError_t launch_hop_batch(int prec, bool dag, const HopArgs *tab, int nsys, const HopArgs &a0, int NS, int SB,
+                             cudaStream_t st)
+{
+    if (nsys < 1) return cudaSuccess;
+    if (NS <= 0 || NS > 2 || (a0.Ls % NS) != 0) NS = hop_default_ns(prec, a0.Ls);
+    if (SB <= 0) SB = hop_default_sb(prec, a0.Ls, NS);
+    if ((a0.Ls / NS) * SB > 256) SB = 256 / (a0.Ls / NS);
+    if (SB < 1) SB = 1;
+    switch (prec) {
+    case DWF_F64:
+        return dag ? launch_batch_pd<DWF_F64, true>(tab, nsys, a0, NS, SB, st)
+                   : launch_batch_pd<DWF_F64, false>(tab, nsys, a0, NS, SB, st);
+    case DWF_F32:
+        return dag ? launch_batch_pd<DWF_F32, true>(tab, nsys, a0, NS, SB, st)
+                   : launch_batch_pd<DWF_F32, false>(tab, nsys, a0, NS, SB, st);
+    case DWF_F16:
+        return dag ? launch_batch_pd<DWF_F16, true>(tab, nsys, a0, NS, SB, st)
+                   : launch_batch_pd<DWF_F16, false>(tab, nsys, a0, NS, SB, st);
+    default: return cudaErrorInvalidValue;
     }
 }
 

@@ -17,6 +17,7 @@
 // so that w = D p and D^dag w = Q^-T what - 1/4 P^T H^dag_eo M^T H^dag_oe what.
 // `check_every` iterations are captured once as a CUDA graph and replayed;
 // the host reads the scalars between replays.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -29,6 +30,7 @@ using namespace dwf;
 
 namespace dwf_detail {
 HopArgs hop_args(dwf_ctx *h, int prec, int out_par, FieldRef in, FieldRef out, int post);
+HopArgs with_programs(dwf_ctx *h, int prec, const HopArgs &a0);
 cudaError_t hop(dwf_ctx *h, int prec, bool dag, const HopArgs &a, cudaStream_t st);
 cudaError_t mix(dwf_ctx *h, int prec, FieldRef in, FieldRef out, int id, cudaStream_t st);
 RedArgs red(dwf_ctx *h, int op, CgScalars *scal);
@@ -93,12 +95,18 @@ int get_bufs(dwf_ctx *h, int ps, Bufs &B)
     return DWF_OK;
 }
 
-// One inner iteration (five launches).
-cudaError_t inner_iteration(dwf_ctx *h, const Bufs &B, cudaStream_t st)
+// Arguments of the five launches of one inner iteration; ra / rb: where the
+// alpha and beta reductions go.
+struct IterArgs {
+    CgUpdateArgs ue;
+    HopArgs k[4];   // K_a, K_b (operator), K_c, K_d (adjoint)
+};
+
+IterArgs iteration_args(dwf_ctx *h, const Bufs &B, const RedArgs &ra, const RedArgs &rb)
 {
     const int P = B.ps;
-    cudaError_t e;
-    CgUpdateArgs ue;
+    IterArgs I;
+    CgUpdateArgs &ue = I.ue;
     ue.r = B.rs;
     ue.p = B.p;
     ue.phat = B.ph;
@@ -108,23 +116,20 @@ cudaError_t inner_iteration(dwf_ctx *h, const Bufs &B, cudaStream_t st)
     ue.mixmode = h->mix_mode(P);
     ue.prog = h->prog(P, MAT_P);
     ue.scal = B.cg;
-    h->launches += 1;
-    if ((e = launch_cg_update(P, ue, st)) != cudaSuccess) return e;
 
-    HopArgs ka = hop_args(h, P, 1, B.ph, B.t, MAT_M);
-    if ((e = hop(h, P, false, ka, st)) != cudaSuccess) return e;
+    I.k[0] = hop_args(h, P, 1, B.ph, B.t, MAT_M);
 
-    HopArgs kb = hop_args(h, P, 0, B.t, B.wh, MAT_NQ4);
+    HopArgs &kb = I.k[1];
+    kb = hop_args(h, P, 0, B.t, B.wh, MAT_NQ4);
     kb.y = B.p;
     kb.ymode = 1;
     kb.zmat = h->mat(P, MAT_QT);
-    kb.red = red(h, RED_CG_ALPHA, B.cg);
-    if ((e = hop(h, P, false, kb, st)) != cudaSuccess) return e;
+    kb.red = ra;
 
-    HopArgs kc = hop_args(h, P, 1, B.wh, B.u, MAT_MT);
-    if ((e = hop(h, P, true, kc, st)) != cudaSuccess) return e;
+    I.k[2] = hop_args(h, P, 1, B.wh, B.u, MAT_MT);
 
-    HopArgs kd = hop_args(h, P, 0, B.u, B.rs, MAT_NPT4);
+    HopArgs &kd = I.k[3];
+    kd = hop_args(h, P, 0, B.u, B.rs, MAT_NPT4);
     kd.y = B.wh;
     kd.ymode = 2;
     kd.ymat = h->mat(P, MAT_RA5T);
@@ -133,8 +138,20 @@ cudaError_t inner_iteration(dwf_ctx *h, const Bufs &B, cudaStream_t st)
     kd.xacc = B.xs.v;
     kd.xdir = B.p;
     kd.xalpha = &B.cg->alpha;
-    kd.red = red(h, RED_CG_BETA, B.cg);
-    return hop(h, P, true, kd, st);
+    kd.red = rb;
+    return I;
+}
+
+// One inner iteration (five launches).
+cudaError_t inner_iteration(dwf_ctx *h, const Bufs &B, cudaStream_t st)
+{
+    const IterArgs I = iteration_args(h, B, red(h, RED_CG_ALPHA, B.cg), red(h, RED_CG_BETA, B.cg));
+    cudaError_t e;
+    h->launches += 1;
+    if ((e = launch_cg_update(B.ps, I.ue, st)) != cudaSuccess) return e;
+    for (int k = 0; k < 4; ++k)
+        if ((e = hop(h, B.ps, k >= 2, I.k[k], st)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 // r64 = b~ - D x64 in FP64; |r64|^2 -> n64->last
@@ -168,6 +185,100 @@ cudaError_t normal_residual(dwf_ctx *h, const Bufs &B, cudaStream_t st)
     a2.ymode = 1;
     a2.red = red(h, RED_STORE, B.n64);
     return hop(h, P, true, a2, st);
+}
+
+// Flexible CG (Notay 2000) on D^dag D e = rhs in FP32 with the learned
+// preconditioner z = M r, from e = 0, until |r| <= eta |rhs| or kmax
+// iterations; e is added into B.xs.  beta by the Polak-Ribiere formula
+// (z_new, r_new - r_old) / (z_old, r_old).  When a preconditioned step breaks
+// down (non-positive or non-finite (r, z) or (p, A p)) the cycle continues as
+// plain CG (M = 1) from the current residual.
+int fcg_cycle(dwf_ctx *h, const Bufs &B, FieldRef rhs, double rhs_norm, double eta, int kmax, int &iters, int &napp,
+              int &fallbacks, int &dapp, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    FieldRef r = h->field("fc_r", DWF_F32, &e), ro = h->field("fc_ro", DWF_F32, &e);
+    FieldRef z = h->field("fc_z", DWF_F32, &e), pp = h->field("fc_p", DWF_F32, &e);
+    FieldRef q = h->field("fc_q", DWF_F32, &e);
+    if (!r.v || !ro.v || !z.v || !pp.v || !q.v) return dwf_cuda_error(e, "FCG workspace");
+    const int Vh = h->Vh, Ls = h->Ls;
+    CgScalars *sc = h->scal + 4;
+    CgScalars hs[3];
+    auto dots = [&](int n) -> int {
+        CK(cudaMemcpyAsync(hs, sc, n * sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return DWF_OK;
+    };
+    int rc;
+    bool plain = false;
+    CK(launch_vaxpby(1.f, rhs, 0.f, r, Vh, Ls, st));
+    auto restart_plain = [&]() -> int {
+        plain = true;
+        fallbacks += 1;
+        CK(launch_vaxpby(1.f, r, 0.f, pp, Vh, Ls, st));
+        CK(launch_vdot(r, r, Vh, Ls, red(h, RED_STORE, sc), st));
+        h->launches += 2;
+        return dots(1);
+    };
+    if ((rc = net_apply_f32(h, r, z, st))) return rc;
+    napp += 1;
+    CK(launch_vaxpby(1.f, z, 0.f, pp, Vh, Ls, st));
+    CK(launch_vdot(r, z, Vh, Ls, red(h, RED_STORE, sc), st));
+    h->launches += 2;
+    if ((rc = dots(1))) return rc;
+    double rz = hs[0].last;
+    if (!(rz > 0) || !std::isfinite(rz)) {
+        if ((rc = restart_plain())) return rc;
+        rz = hs[0].last;
+    }
+    for (int k = 0; k < kmax; ++k) {
+        if ((rc = normal_apply_f32(h, pp, q, st))) return rc;
+        dapp += 2;
+        CK(launch_vdot(pp, q, Vh, Ls, red(h, RED_STORE, sc), st));
+        h->launches += 1;
+        if ((rc = dots(1))) return rc;
+        const double pq = hs[0].last;
+        if (!(pq > 0) || !std::isfinite(pq)) {
+            if (plain) return dwf_set_error(DWF_EBREAKDOWN, "CG breakdown in the FCG cycle");
+            if ((rc = restart_plain())) return rc;
+            rz = hs[0].last;
+            continue;
+        }
+        const float alpha = (float)(rz / pq);
+        CK(launch_vaxpby(alpha, pp, 1.f, B.xs, Vh, Ls, st));
+        CK(launch_vaxpby(1.f, r, 0.f, ro, Vh, Ls, st));
+        CK(launch_vaxpby(-alpha, q, 1.f, r, Vh, Ls, st));
+        CK(launch_vdot(r, r, Vh, Ls, red(h, RED_STORE, sc), st));
+        h->launches += 4;
+        if ((rc = dots(1))) return rc;
+        iters += 1;
+        const double rn = std::sqrt(hs[0].last);
+        if (!std::isfinite(rn)) return dwf_set_error(DWF_ENONFINITE, "non-finite FCG residual");
+        if (rn <= eta * rhs_norm) break;
+        if (plain) {
+            CK(launch_vaxpby(1.f, r, 0.f, z, Vh, Ls, st));
+            h->launches += 1;
+        } else {
+            if ((rc = net_apply_f32(h, r, z, st))) return rc;
+            napp += 1;
+        }
+        CK(launch_vdot(r, z, Vh, Ls, red(h, RED_STORE, sc), st));
+        CK(launch_vdot(z, ro, Vh, Ls, red(h, RED_STORE, sc + 1), st));
+        h->launches += 2;
+        if ((rc = dots(2))) return rc;
+        const double rzn = hs[0].last, zro = hs[1].last;
+        if (!(rzn > 0) || !std::isfinite(rzn) || !std::isfinite(zro)) {
+            if (plain) return dwf_set_error(DWF_EBREAKDOWN, "CG breakdown in the FCG cycle");
+            if ((rc = restart_plain())) return rc;
+            rz = hs[0].last;
+            continue;
+        }
+        const float beta = (float)((rzn - zro) / rz);
+        CK(launch_vaxpby(1.f, z, beta, pp, Vh, Ls, st));
+        h->launches += 1;
+        rz = rzn;
+    }
+    return DWF_OK;
 }
 
 int read_scalars(const Bufs &B, CgScalars *host, int n, cudaStream_t st)
@@ -214,6 +325,9 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
     if (ps != DWF_F64 && ps != DWF_F32 && ps != DWF_F16) return dwf_set_error(DWF_EINVAL, "bad inner precision");
     if (!(p->tol > 0) || p->max_iter < 1 || !(p->delta > 0 && p->delta < 1) || p->check_every < 1)
         return dwf_set_error(DWF_EINVAL, "bad solver parameters");
+    if (p->precond && !h->net)
+        return dwf_set_error(DWF_EINVAL, "precond = 1 needs a network (dwf_precond_init or dwf_precond_train)");
+    if (p->precond && ps != DWF_F32) return dwf_set_error(DWF_EINVAL, "the FCG solve runs its inner cycles in FP32");
     Bufs B;
     int rc = get_bufs(h, ps, B);
     if (rc) return rc;
@@ -323,10 +437,21 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
         return DWF_OK;
     };
 
+    int napp = 0, nfall = 0;
     for (int round = 0; round < 3 && status == DWF_OK; ++round) {
         converged = false;
         if ((rc = reliable(round == 0 && !p->use_initial_guess))) return rc;
-        while (!converged) {
+        // learned preconditioner: FCG cycles in FP32, each closed by an FP64 defect correction
+        while (p->precond && !converged) {
+            if (iters >= p->max_iter) {
+                status = DWF_ENOTCONV;
+                break;
+            }
+            if ((rc = fcg_cycle(h, B, B.rs, rmax, 0.01 * p->delta, p->max_iter - iters, iters, napp, nfall, dapp, st)))
+                return rc;
+            if ((rc = reliable(false))) return rc;
+        }
+        while (!p->precond && !converged) {
             if (iters >= p->max_iter) {
                 status = DWF_ENOTCONV;
                 break;
@@ -397,10 +522,598 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
     S.reliable_updates = nru;
     S.d_applications = dapp;
     S.kernel_launches = h->launches - launches0;
+    S.waves = 1;
+    S.precond_applications = napp;
+    S.fallbacks = nfall;
     S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = S;
     if (status != DWF_OK) dwf_set_error(status, "solver did not reach the tolerance");
     return status;
+}
+
+// ------------------------------------------------------------ batched solve
+// Many systems on one lattice, in waves that fit in device memory.  Within a
+// wave every system keeps its own CG state (FP64 solution and source, inner
+// fields, scalars, reduction buffers); the FP64 temporaries of source
+// preparation, reliable updates and the final check are shared, since those
+// steps run one system at a time between graph replays.  The inner iteration
+// runs as batched launches (one per kernel and distinct Ls) over all systems
+// of the wave; systems that have converged set their skip flag.
+namespace {
+
+size_t round256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0, used = 0;
+    void *take(size_t nb)
+    {
+        const size_t o = round256(used);
+        if (!base || o + nb > size) return nullptr;
+        used = o + nb;
+        return base + o;
+    }
+    FieldRef field(int prec, int Vh, int Ls)
+    {
+        FieldRef f;
+        f.v = take(field_bytes(prec, Vh, Ls));
+        if (prec == DWF_F16) f.scale = (float *)take(scale_bytes(prec, Vh, Ls));
+        return f;
+    }
+};
+
+size_t field_total(int prec, int Vh, int Ls) { return round256(field_bytes(prec, Vh, Ls)) + round256(scale_bytes(prec, Vh, Ls)); }
+
+size_t system_bytes(const dwf_ctx *h, int ps)
+{
+    const int xp = ps == DWF_F64 ? DWF_F64 : DWF_F32;
+    return 2 * field_total(DWF_F64, h->Vh, h->Ls) + 6 * field_total(ps, h->Vh, h->Ls) + field_total(xp, h->Vh, h->Ls) +
+           round256(3 * sizeof(CgScalars)) + round256(((size_t)h->Vh + 8192) * 8) + 256 +
+           round256(sizeof(CgUpdateArgs)) + 4 * round256(sizeof(HopArgs));
+}
+
+size_t shared_bytes(int V, int Vh, int Ls) { return 6 * field_total(DWF_F64, Vh, Ls) + round256((size_t)V * Ls * 24 * 8); }
+
+struct SysRun {
+    dwf_ctx *h = nullptr;
+    int idx = 0;                 // position in the caller's arrays
+    Bufs B;
+    double *partials = nullptr;  // this system's reduction buffers
+    unsigned *counter = nullptr;
+    double b5n = 0, btn = 0, target = 0, rtrue = 0, rho = 1, rmax = 0;
+    int iters = 0, nru = 0, dapp = 0, round = 0, status = DWF_OK;
+    bool active = false, converged = false, done = false;
+    dwf_solve_stats S;
+};
+
+// (b_e, b_o) = even / odd halves of b5 = (1 - c D_W) P^dag (0, .., b4) in the
+// internal FP64 layout (the source of Sec. 2.2, as dwf_source_5d), using the
+// canonical buffer v5 and the temporaries ve, vo.
+cudaError_t source_eo(dwf_ctx *h, const void *b4, double *v5, FieldRef ve, FieldRef vo, FieldRef be, FieldRef bo,
+                      cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = launch_chiral_embed((const double *)b4, v5, h->V, h->Ls, st)) != cudaSuccess) return e;
+    if ((e = launch_pack_full(DWF_F64, v5, ve, vo, h->eo2lex, h->Vh, h->V, h->Ls, st)) != cudaSuccess) return e;
+    h->launches += 2;
+    for (int par = 0; par < 2; ++par) {
+        HopArgs a = hop_args(h, DWF_F64, par, par ? ve : vo, par ? bo : be, MAT_SRC_POST);
+        a.y = par ? vo : ve;
+        a.ymode = 2;
+        a.ymat = h->mat(DWF_F64, MAT_SRC_Y);
+        if ((e = hop(h, DWF_F64, false, a, st)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// FP64 true residual; convergence test; else the normal residual in the inner
+// precision and the rescaled beta (as the reliable step of solve_impl).
+int sys_reliable(SysRun &R, bool first, CgScalars *hs, cudaStream_t st)
+{
+    dwf_ctx *h = R.h;
+    Bufs &B = R.B;
+    if (!first) {
+        CK(launch_accum_x((double *)B.x64.v, B.xs.v, B.xp, h->Vh, h->Ls, st));
+        h->launches += 1;
+    }
+    CK(true_residual(h, B, st));
+    CK(cudaMemcpyAsync(&hs[1], B.n64, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    R.dapp += 1;
+    R.rtrue = std::sqrt(hs[1].last);
+    if (!std::isfinite(R.rtrue)) return dwf_set_error(DWF_ENONFINITE, "non-finite residual");
+    if (R.S.n_history < 64) R.S.history[R.S.n_history++] = R.rtrue / R.btn;
+    if (R.rtrue <= R.target) {
+        R.converged = true;
+        return DWF_OK;
+    }
+    CK(normal_residual(h, B, st));
+    reliable_fix_kernel<<<1, 1, 0, st>>>(B.cg, B.n64, first ? 1 : 0);
+    CK(cudaGetLastError());
+    h->launches += 1;
+    R.dapp += 1;
+    CK(cudaMemcpyAsync(hs, B.cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double rn = std::sqrt(hs[0].gamma);
+    R.rmax = rn;
+    R.rho = (rn > 0) ? R.rtrue / rn : 1.0;
+    R.nru += first ? 0 : 1;
+    return DWF_OK;
+}
+
+// Source, b~_e and the first residual of one system.
+int sys_prepare(SysRun &R, const void *b4, double *v5, const dwf_solve_params *p, CgScalars *hs, cudaStream_t st)
+{
+    dwf_ctx *h = R.h;
+    Bufs &B = R.B;
+    CK(source_eo(h, b4, v5, B.r64, B.t64, B.be, B.bo, st));
+    CK(launch_norm2(DWF_F64, B.be, h->Vh, h->Ls, red(h, RED_STORE, B.n64), st));
+    CK(launch_norm2(DWF_F64, B.bo, h->Vh, h->Ls, red(h, RED_STORE, B.aux), st));
+    h->launches += 2;
+    CK(cudaMemcpyAsync(hs, B.cg, 3 * sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    R.b5n = std::sqrt(hs[1].last + hs[2].last);
+    if (!std::isfinite(R.b5n)) return dwf_set_error(DWF_ENONFINITE, "source contains NaN or Inf");
+    CK(launch_zero(DWF_F64, B.x64, h->Vh, h->Ls, st));
+    CK(launch_zero(B.xp, B.xs, h->Vh, h->Ls, st));
+    CK(launch_zero(B.ps, B.p, h->Vh, h->Ls, st));
+    CK(launch_zero(B.ps, B.rs, h->Vh, h->Ls, st));
+    CK(cudaMemsetAsync(B.cg, 0, sizeof(CgScalars), st));
+    if (R.b5n == 0.0) {
+        R.done = true;
+        return DWF_OK;
+    }
+    CK(mix(h, DWF_F64, B.bo, B.t64, MAT_M, st));
+    {
+        HopArgs a = hop_args(h, DWF_F64, 0, B.t64, B.bt, MAT_HALF_Q);
+        a.y = B.be;
+        a.ymode = 2;
+        a.ymat = h->mat(DWF_F64, MAT_Q);
+        a.red = red(h, RED_STORE, B.aux);
+        CK(hop(h, DWF_F64, false, a, st));
+    }
+    CK(cudaMemcpyAsync(hs, B.cg, 3 * sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    R.btn = std::sqrt(hs[2].last);
+    R.target = p->tol * R.b5n / h->fm.dee_norm2 * 0.5;
+    R.active = true;
+    int rc = sys_reliable(R, true, hs, st);
+    if (rc) return rc;
+    if (R.converged) R.active = false;
+    return DWF_OK;
+}
+
+// x_o, the full 5D residual; then either the 4D solution or another round
+// with a tenfold smaller target (at most three rounds, as solve_impl).
+int sys_finish(SysRun &R, const void *b4, void *x4, double *v5, const dwf_solve_params *p, CgScalars *hs,
+               cudaStream_t st)
+{
+    dwf_ctx *h = R.h;
+    Bufs &B = R.B;
+    CK(source_eo(h, b4, v5, B.r64, B.t64, B.be, B.bo, st));
+    CK(mix(h, DWF_F64, B.x64, B.h64, MAT_P, st));
+    {
+        HopArgs a = hop_args(h, DWF_F64, 1, B.h64, B.xo64, MAT_HALF_Q);
+        a.y = B.bo;
+        a.ymode = 2;
+        a.ymat = h->mat(DWF_F64, MAT_Q);
+        CK(hop(h, DWF_F64, false, a, st));
+    }
+    CK(mix(h, DWF_F64, B.xo64, B.t64, MAT_P, st));
+    for (int par = 0; par < 2; ++par) {
+        HopArgs a = hop_args(h, DWF_F64, par, par ? B.h64 : B.t64, B.r64, MAT_NHALF);
+        a.y = par ? B.xo64 : B.x64;
+        a.ymode = 2;
+        a.ymat = h->mat(DWF_F64, MAT_A5R);
+        a.rin = par ? B.bo : B.be;
+        a.ralpha = h->one;
+        a.red = red(h, RED_STORE, par ? B.aux : B.n64);
+        CK(hop(h, DWF_F64, false, a, st));
+    }
+    R.dapp += 2;
+    CK(cudaMemcpyAsync(hs, B.cg, 3 * sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    R.S.true_residual = std::sqrt(hs[1].last + hs[2].last) / R.b5n;
+    R.S.eo_residual = R.rtrue / R.btn;
+    if (R.S.true_residual > p->tol && R.status == DWF_OK && R.round < 2) {
+        R.round += 1;
+        R.target *= 0.1;
+        R.converged = false;
+        R.active = true;
+        int rc = sys_reliable(R, false, hs, st);
+        if (rc) return rc;
+        if (!R.converged) return DWF_OK;
+        return sys_finish(R, b4, x4, v5, p, hs, st);
+    }
+    CK(launch_unpack_full(DWF_F64, B.x64, B.xo64, v5, h->eo2lex, h->Vh, h->V, h->Ls, st));
+    CK(launch_project4d(v5, (double *)x4, h->V, h->Ls, st));
+    h->launches += 2;
+    if (R.status == DWF_OK && R.S.true_residual > p->tol) R.status = DWF_ENOTCONV;
+    R.active = false;
+    R.done = true;
+    return DWF_OK;
+}
+
+int batch_impl(dwf_handle const *hs_in, const void *const *b4, void *const *x4, int n, const dwf_solve_params *p,
+               dwf_solve_stats *stats, cudaStream_t st)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (n == 0) return DWF_OK;
+    const int ps = p->inner_prec;
+    if (ps != DWF_F64 && ps != DWF_F32 && ps != DWF_F16) return dwf_set_error(DWF_EINVAL, "bad inner precision");
+    if (!(p->tol > 0) || p->max_iter < 1 || !(p->delta > 0 && p->delta < 1) || p->check_every < 1 ||
+        p->batch_wave < 0)
+        return dwf_set_error(DWF_EINVAL, "bad solver parameters");
+    dwf_ctx *h0 = hs_in[0];
+    if (!h0) return dwf_set_error(DWF_EINVAL, "NULL handle in batch");
+    int Lsmax = 0;
+    for (int i = 0; i < n; ++i) {
+        dwf_ctx *h = hs_in[i];
+        if (!h || !b4[i] || !x4[i]) return dwf_set_error(DWF_EINVAL, "NULL handle or vector in batch");
+        if (!h->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
+        for (int k = 0; k < 4; ++k)
+            if (h->dims[k] != h0->dims[k]) return dwf_set_error(DWF_EINVAL, "batch handles differ in lattice size");
+        if (h->device != h0->device) return dwf_set_error(DWF_EINVAL, "batch handles on different devices");
+        if (((uintptr_t)b4[i] & 15) || ((uintptr_t)x4[i] & 15))
+            return dwf_set_error(DWF_EINVAL, "vectors must be 16-byte aligned");
+        Lsmax = std::max(Lsmax, h->Ls);
+    }
+    // order: round robin over the distinct handles, so that every wave mixes them
+    std::vector<int> order;
+    std::vector<dwf_ctx *> uniq_handles;
+    {
+        std::vector<dwf_ctx *> &uniq = uniq_handles;
+        std::vector<std::vector<int>> q;
+        for (int i = 0; i < n; ++i) {
+            size_t u = std::find(uniq.begin(), uniq.end(), hs_in[i]) - uniq.begin();
+            if (u == uniq.size()) {
+                uniq.push_back(hs_in[i]);
+                q.emplace_back();
+            }
+            q[u].push_back(i);
+        }
+        for (size_t r = 0; order.size() < (size_t)n; ++r)
+            for (auto &v : q)
+                if (r < v.size()) order.push_back(v[r]);
+    }
+    long long launches0 = 0;
+    for (dwf_ctx *h : uniq_handles) launches0 += h->launches;
+    const int V = h0->V, Vh = h0->Vh;
+    const size_t shared = shared_bytes(V, Vh, Lsmax);
+    size_t freeb = 0, totalb = 0;
+    CK(cudaMemGetInfo(&freeb, &totalb));
+    const size_t reserve = std::max((size_t)2 << 30, totalb / 20);
+    const size_t budget = freeb > shared + reserve ? freeb - shared - reserve : 0;
+    // waves
+    std::vector<std::pair<int, int>> waves;   // [begin, end) in `order`
+    for (int k = 0; k < n;) {
+        size_t used = 0;
+        int e = k;
+        while (e < n && (p->batch_wave == 0 || e - k < p->batch_wave)) {
+            const size_t need = system_bytes(hs_in[order[e]], ps);
+            if (used + need > budget) break;
+            used += need;
+            ++e;
+        }
+        if (e == k) return dwf_set_error(DWF_ENOMEM, "one system of the batch does not fit in device memory");
+        waves.push_back({k, e});
+        k = e;
+    }
+
+    std::vector<SysRun> runs(n);
+    CgScalars *hs_pinned = nullptr;
+    CK(cudaMallocHost(&hs_pinned, sizeof(CgScalars) * (3 * (size_t)n + 4)));
+    cudaStream_t cap = nullptr;
+    int worst = DWF_OK;
+    int rc = DWF_OK;
+    long long launches = 0;
+    const int N = p->check_every;
+    Arena A;
+    int *skip_host = nullptr;
+
+    auto cleanup = [&]() {
+        if (A.base) cudaFree(A.base);
+        A.base = nullptr;
+        if (cap) cudaStreamDestroy(cap);
+        cap = nullptr;
+        if (hs_pinned) cudaFreeHost(hs_pinned);
+        hs_pinned = nullptr;
+        if (skip_host) cudaFreeHost(skip_host);
+        skip_host = nullptr;
+    };
+#define BCK(call)                                                             \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) {                                              \
+            cleanup();                                                        \
+            return dwf_cuda_error(e_, #call);                                 \
+        }                                                                     \
+    } while (0)
+#define BRC(call)                                                             \
+    do {                                                                      \
+        int r_ = (call);                                                      \
+        if (r_) {                                                             \
+            cleanup();                                                        \
+            return r_;                                                        \
+        }                                                                     \
+    } while (0)
+
+    BCK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    BCK(cudaMallocHost(&skip_host, sizeof(int) * (size_t)n));
+    for (auto &w : waves) {
+        const int nw = w.second - w.first;
+        size_t bytes = shared + 4096;
+        for (int k = w.first; k < w.second; ++k) bytes += system_bytes(hs_in[order[k]], ps);
+        bytes += round256(sizeof(int) * (size_t)nw);
+        A.size = bytes;
+        A.used = 0;
+        BCK(cudaMalloc(&A.base, bytes));
+        // shared FP64 temporaries
+        FieldRef be = A.field(DWF_F64, Vh, Lsmax), bo = A.field(DWF_F64, Vh, Lsmax);
+        FieldRef r64 = A.field(DWF_F64, Vh, Lsmax), t64 = A.field(DWF_F64, Vh, Lsmax);
+        FieldRef h64 = A.field(DWF_F64, Vh, Lsmax), xo64 = A.field(DWF_F64, Vh, Lsmax);
+        double *v5 = (double *)A.take((size_t)V * Lsmax * 24 * 8);
+        int *skip_dev = (int *)A.take(sizeof(int) * (size_t)nw);
+        if (!v5 || !skip_dev || !xo64.v) {
+            cleanup();
+            return dwf_set_error(DWF_ENOMEM, "batch arena");
+        }
+        // per-system state
+        for (int k = w.first; k < w.second; ++k) {
+            SysRun &R = runs[k];
+            R.h = hs_in[order[k]];
+            R.idx = order[k];
+            std::memset(&R.S, 0, sizeof(R.S));
+            dwf_ctx *h = R.h;
+            Bufs &B = R.B;
+            B.ps = ps;
+            B.xp = ps == DWF_F64 ? DWF_F64 : DWF_F32;
+            B.be = be, B.bo = bo, B.r64 = r64, B.t64 = t64, B.h64 = h64, B.xo64 = xo64;
+            B.bt = A.field(DWF_F64, Vh, h->Ls);
+            B.x64 = A.field(DWF_F64, Vh, h->Ls);
+            B.p = A.field(ps, Vh, h->Ls);
+            B.ph = A.field(ps, Vh, h->Ls);
+            B.t = A.field(ps, Vh, h->Ls);
+            B.wh = A.field(ps, Vh, h->Ls);
+            B.u = A.field(ps, Vh, h->Ls);
+            B.rs = A.field(ps, Vh, h->Ls);
+            B.xs = A.field(B.xp, Vh, h->Ls);
+            CgScalars *sc = (CgScalars *)A.take(3 * sizeof(CgScalars));
+            R.partials = (double *)A.take(((size_t)Vh + 8192) * 8);
+            R.counter = (unsigned *)A.take(256);
+            if (!sc || !R.partials || !R.counter || !B.xs.v) {
+                cleanup();
+                return dwf_set_error(DWF_ENOMEM, "batch arena");
+            }
+            B.cg = sc, B.n64 = sc + 1, B.aux = sc + 2;
+            BCK(cudaMemsetAsync(sc, 0, 3 * sizeof(CgScalars), st));
+            BCK(cudaMemsetAsync(R.counter, 0, 256, st));
+        }
+        for (int k = w.first; k < w.second; ++k) {
+            SysRun &R = runs[k];
+            BRC(sys_prepare(R, b4[R.idx], v5, p, hs_pinned, st));
+            if (R.done) {   // zero source
+                BCK(cudaMemsetAsync(x4[R.idx], 0, (size_t)V * 24 * 8, st));
+            } else if (R.converged) {
+                BRC(sys_finish(R, b4[R.idx], x4[R.idx], v5, p, hs_pinned, st));
+            }
+        }
+        // batched launch tables, one group per distinct Ls
+        std::vector<int> lsv;
+        for (int k = w.first; k < w.second; ++k)
+            if (std::find(lsv.begin(), lsv.end(), runs[k].h->Ls) == lsv.end()) lsv.push_back(runs[k].h->Ls);
+        struct Group {
+            std::vector<int> mem;   // indices into runs
+            CgUpdateArgs *ue = nullptr;
+            HopArgs *k[4] = {nullptr, nullptr, nullptr, nullptr};
+            CgUpdateArgs ue0;
+            HopArgs k0[4];
+            int ns = 0, sb = 0;
+        };
+        std::vector<Group> groups(lsv.size());
+        for (size_t g = 0; g < lsv.size(); ++g) {
+            Group &G = groups[g];
+            for (int k = w.first; k < w.second; ++k)
+                if (runs[k].h->Ls == lsv[g]) G.mem.push_back(k);
+            const int m = (int)G.mem.size();
+            std::vector<CgUpdateArgs> ue(m);
+            std::vector<HopArgs> kt[4];
+            for (int q = 0; q < m; ++q) {
+                SysRun &R = runs[G.mem[q]];
+                RedArgs ra, rb;
+                ra.partials = rb.partials = R.partials;
+                ra.counter = rb.counter = R.counter;
+                ra.scal = rb.scal = R.B.cg;
+                ra.op = RED_CG_ALPHA;
+                rb.op = RED_CG_BETA;
+                IterArgs I = iteration_args(R.h, R.B, ra, rb);
+                I.ue.skip = skip_dev + (G.mem[q] - w.first);
+                ue[q] = I.ue;
+                for (int j = 0; j < 4; ++j) {
+                    HopArgs a = with_programs(R.h, ps, I.k[j]);
+                    a.skip = I.ue.skip;
+                    kt[j].push_back(a);
+                }
+            }
+            // one mixing mode per group (the kernels are compiled per mode); the
+            // dense matrices are always present, so disagreement falls back to them
+            int mixm = kt[0][0].mixmode;
+            for (int j = 0; j < 4; ++j)
+                for (int q = 0; q < m; ++q)
+                    if (kt[j][q].mixmode != mixm) mixm = 0;
+            for (int j = 0; j < 4; ++j)
+                for (int q = 0; q < m; ++q) kt[j][q].mixmode = mixm;
+            for (int q = 0; q < m; ++q) ue[q].mixmode = (mixm == 1) ? 1 : 0;
+            G.ue0 = ue[0];
+            for (int j = 0; j < 4; ++j) G.k0[j] = kt[j][0];
+            dwf_ctx *hg = runs[G.mem[0]].h;
+            G.ns = hg->hop_var[ps] == 0 ? hg->hop_ns[ps] : 0;
+            G.sb = hg->hop_var[ps] == 0 ? hg->hop_sb[ps] : 0;
+            G.ue = (CgUpdateArgs *)A.take(sizeof(CgUpdateArgs) * m);
+            for (int j = 0; j < 4; ++j) G.k[j] = (HopArgs *)A.take(sizeof(HopArgs) * m);
+            if (!G.ue || !G.k[3]) {
+                cleanup();
+                return dwf_set_error(DWF_ENOMEM, "batch arena");
+            }
+            BCK(cudaMemcpyAsync(G.ue, ue.data(), sizeof(CgUpdateArgs) * m, cudaMemcpyHostToDevice, st));
+            for (int j = 0; j < 4; ++j)
+                BCK(cudaMemcpyAsync(G.k[j], kt[j].data(), sizeof(HopArgs) * m, cudaMemcpyHostToDevice, st));
+        }
+        auto launch_iteration = [&](cudaStream_t s2) -> cudaError_t {
+            cudaError_t e;
+            for (auto &G : groups) {
+                const int m = (int)G.mem.size();
+                if ((e = launch_cg_update_batch(ps, G.ue, m, G.ue0, s2)) != cudaSuccess) return e;
+                for (int j = 0; j < 4; ++j)
+                    if ((e = launch_hop_batch(ps, j >= 2, G.k[j], m, G.k0[j], G.ns, G.sb, s2)) != cudaSuccess)
+                        return e;
+            }
+            return cudaSuccess;
+        };
+        cudaGraphExec_t exec = nullptr;
+        if (p->use_graph) {
+            BCK(cudaStreamSynchronize(st));
+            cudaGraph_t g;
+            BCK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+            for (int k = 0; k < N; ++k) {
+                cudaError_t e = launch_iteration(cap);
+                if (e != cudaSuccess) {
+                    cudaStreamEndCapture(cap, &g);
+                    cleanup();
+                    return dwf_cuda_error(e, "graph capture");
+                }
+            }
+            BCK(cudaStreamEndCapture(cap, &g));
+            cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            BCK(e);
+        }
+        // lock-step iteration of the wave
+        for (;;) {
+            int nact = 0;
+            for (int k = w.first; k < w.second; ++k) {
+                skip_host[k - w.first] = runs[k].active ? 0 : 1;
+                nact += runs[k].active ? 1 : 0;
+            }
+            if (nact == 0) break;
+            BCK(cudaMemcpyAsync(skip_dev, skip_host, sizeof(int) * nw, cudaMemcpyHostToDevice, st));
+            if (exec) {
+                cudaError_t e = cudaGraphLaunch(exec, st);
+                if (e != cudaSuccess) {
+                    cudaGraphExecDestroy(exec);
+                    BCK(e);
+                }
+            } else {
+                for (int k = 0; k < N; ++k) BCK(launch_iteration(st));
+            }
+            launches += (long long)N * 5 * (long long)groups.size();
+            for (int k = w.first; k < w.second; ++k)
+                BCK(cudaMemcpyAsync(&hs_pinned[3 * (k - w.first)], runs[k].B.cg, sizeof(CgScalars),
+                                    cudaMemcpyDeviceToHost, st));
+            BCK(cudaStreamSynchronize(st));
+            for (int k = w.first; k < w.second; ++k) {
+                SysRun &R = runs[k];
+                if (!R.active) continue;
+                const CgScalars c = hs_pinned[3 * (k - w.first)];
+                R.iters += N;
+                R.dapp += 2 * N;
+                const double rn = std::sqrt(c.gamma);
+                const bool bad = (c.flags != 0) || !std::isfinite(rn);
+                CgScalars *hsl = hs_pinned + 3 * (size_t)n;   // scratch for the single-system steps
+                if (bad && (c.flags & 2)) {
+                    BCK(launch_zero(R.B.xp, R.B.xs, R.h->Vh, R.h->Ls, st));
+                    BCK(launch_zero(ps, R.B.p, R.h->Vh, R.h->Ls, st));
+                    BRC(sys_reliable(R, true, hsl, st));
+                    if (++R.nru > 200) {
+                        R.status = DWF_ENONFINITE;
+                        R.active = false;
+                    }
+                } else if (bad || rn < p->delta * R.rmax || R.rho * rn < R.target || R.iters >= p->max_iter) {
+                    BRC(sys_reliable(R, false, hsl, st));
+                    if (R.nru > 1000) R.status = DWF_ENOTCONV;
+                }
+                if (R.status == DWF_OK && !R.converged && R.iters >= p->max_iter) R.status = DWF_ENOTCONV;
+                if (R.converged || R.status != DWF_OK) {
+                    R.active = false;
+                    BRC(sys_finish(R, b4[R.idx], x4[R.idx], v5, p, hsl, st));
+                }
+            }
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        BCK(cudaStreamSynchronize(st));
+        cudaFree(A.base);
+        A.base = nullptr;
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    h0->launches += launches;
+    long long own = 0;
+    for (dwf_ctx *h : uniq_handles) own += h->launches;
+    own -= launches0;
+    for (auto &R : runs) {
+        R.S.status = R.status;
+        R.S.iterations = R.iters;
+        R.S.reliable_updates = R.nru;
+        R.S.d_applications = R.dapp;
+        R.S.seconds = secs;
+        R.S.waves = (int)waves.size();
+        if (R.status > worst) worst = R.status;
+    }
+    for (auto &R : runs) R.S.kernel_launches = own;
+    if (stats)
+        for (auto &R : runs) stats[R.idx] = R.S;
+    cleanup();
+#undef BCK
+#undef BRC
+    (void)rc;
+    if (worst != DWF_OK) dwf_set_error(worst, "a system of the batch did not reach the tolerance");
+    return worst;
+}
+
+}  // namespace
+
+// out = D x on FP32 even fields (K_e..K_b of the inner iteration without the
+// CG updates and the final Q^T mixing)
+int dwf::eo_apply_f32(dwf_ctx *h, FieldRef x, FieldRef out, cudaStream_t st)
+{
+    const int P = DWF_F32;
+    cudaError_t e = cudaSuccess;
+    FieldRef ph = h->field("na_ph", P, &e), t = h->field("na_t", P, &e);
+    if (!ph.v || !t.v) return dwf_cuda_error(e, "workspace");
+    CK(mix(h, P, x, ph, MAT_P, st));
+    HopArgs a1 = hop_args(h, P, 1, ph, t, MAT_M);
+    CK(hop(h, P, false, a1, st));
+    HopArgs a2 = hop_args(h, P, 0, t, out, MAT_NQ4);
+    a2.y = x;
+    a2.ymode = 1;
+    CK(hop(h, P, false, a2, st));
+    return DWF_OK;
+}
+
+// out = D^dag D x on FP32 even fields: w = D x (as K_e..K_b of the inner
+// iteration, without its CG updates), then D^dag w (as K_c, K_d).
+int dwf::normal_apply_f32(dwf_ctx *h, FieldRef x, FieldRef out, cudaStream_t st)
+{
+    const int P = DWF_F32;
+    cudaError_t e = cudaSuccess;
+    FieldRef ph = h->field("na_ph", P, &e), t = h->field("na_t", P, &e);
+    FieldRef wh = h->field("na_wh", P, &e), u = h->field("na_u", P, &e);
+    if (!ph.v || !t.v || !wh.v || !u.v) return dwf_cuda_error(e, "workspace");
+    CK(mix(h, P, x, ph, MAT_P, st));
+    HopArgs a1 = hop_args(h, P, 1, ph, t, MAT_M);
+    CK(hop(h, P, false, a1, st));
+    HopArgs a2 = hop_args(h, P, 0, t, wh, MAT_NQ4);
+    a2.y = x;
+    a2.ymode = 1;
+    a2.zmat = h->mat(P, MAT_QT);
+    CK(hop(h, P, false, a2, st));
+    HopArgs a3 = hop_args(h, P, 1, wh, u, MAT_MT);
+    CK(hop(h, P, true, a3, st));
+    HopArgs a4 = hop_args(h, P, 0, u, out, MAT_NPT4);
+    a4.y = wh;
+    a4.ymode = 2;
+    a4.ymat = h->mat(P, MAT_RA5T);
+    CK(hop(h, P, true, a4, st));
+    return DWF_OK;
 }
 
 extern "C" {
@@ -418,6 +1131,7 @@ void dwf_solve_params_default(dwf_solve_params *p)
     p->precond = 0;
     p->use_initial_guess = 0;
     p->verbose = 0;
+    p->batch_wave = 0;
 }
 
 int dwf_solve(dwf_handle h, const void *b5, void *x5, const dwf_solve_params *p, dwf_solve_stats *stats, void *stream)
@@ -462,25 +1176,10 @@ int dwf_propagator_host(dwf_handle h, const double *b4_host, double *x4_host, co
 int dwf_solve_batch(dwf_handle const *hs, const void *const *b4, void *const *x4, int n, const dwf_solve_params *p,
                     dwf_solve_stats *stats, void *stream)
 {
-    if (!hs || !b4 || !x4 || n < 0) return dwf_set_error(DWF_EINVAL, "NULL argument");
-    int worst = DWF_OK;
-    for (int i = 0; i < n; ++i) {
-        dwf_handle h = hs[i];
-        if (!h) return dwf_set_error(DWF_EINVAL, "NULL handle in batch");
-        cudaError_t e = cudaSuccess;
-        const size_t b5b = (size_t)h->V * 24 * 8 * h->Ls;
-        void *b5 = h->ws("bt_b5", b5b, &e);
-        void *x5 = h->ws("bt_x5", b5b, &e);
-        if (!b5 || !x5) return dwf_cuda_error(e, "workspace");
-        int rc = dwf_source_5d(h, b4[i], b5, stream);
-        if (rc) return rc;
-        rc = dwf_solve(h, b5, x5, p, stats ? stats + i : nullptr, stream);
-        if (rc != DWF_OK && rc != DWF_ENOTCONV) return rc;
-        if (rc > worst) worst = rc;
-        rc = dwf_project_4d(h, x5, x4[i], stream);
-        if (rc) return rc;
-    }
-    return worst;
+    if (n < 0 || (n > 0 && (!hs || !b4 || !x4))) return dwf_set_error(DWF_EINVAL, "NULL argument");
+    dwf_solve_params def;
+    dwf_solve_params_default(&def);
+    return batch_impl(hs, b4, x4, n, p ? p : &def, stats, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -32,13 +32,16 @@ EXPORTED = ["dwf_create", "dwf_destroy", "dwf_strerror", "dwf_last_error", "dwf_
             "dwf_solve_params_default", "dwf_solve", "dwf_propagator_host", "dwf_solve_batch",
             "dwf_fifth_matrix", "dwf_device_bytes", "dwf_time_hop", "dwf_launch_count",
             "dwf_set_hop_config", "dwf_get_hop_config", "dwf_autotune", "dwf_device_status",
-            "dwf_set_mix_mode", "dwf_get_mix_mode", "dwf_apply_eo_noalloc"]
+            "dwf_set_mix_mode", "dwf_get_mix_mode", "dwf_apply_eo_noalloc",
+            "dwf_train_params_default", "dwf_precond_init", "dwf_precond_set_weights", "dwf_precond_get_weights",
+            "dwf_precond_apply", "dwf_precond_loss_grad", "dwf_precond_train"]
 
 
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner_prec", ctypes.c_int),
                 ("delta", ctypes.c_double), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("precond", ctypes.c_int), ("use_initial_guess", ctypes.c_int), ("verbose", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("use_initial_guess", ctypes.c_int), ("verbose", ctypes.c_int),
+                ("batch_wave", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -46,13 +49,35 @@ class SolveStats(ctypes.Structure):
                 ("d_applications", ctypes.c_int), ("true_residual", ctypes.c_double),
                 ("eo_residual", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("history", ctypes.c_double * 64), ("n_history", ctypes.c_int),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("waves", ctypes.c_int),
+                ("precond_applications", ctypes.c_int), ("fallbacks", ctypes.c_int)]
 
     def as_dict(self):
         return dict(status=STATUS.get(self.status, self.status), iterations=self.iterations,
                     reliable_updates=self.reliable_updates, d_applications=self.d_applications,
                     true_residual=self.true_residual, eo_residual=self.eo_residual, seconds=self.seconds,
-                    history=list(self.history[:self.n_history]), kernel_launches=self.kernel_launches)
+                    history=list(self.history[:self.n_history]), kernel_launches=self.kernel_launches,
+                    waves=self.waves, precond_applications=self.precond_applications,
+                    fallbacks=self.fallbacks)
+
+
+class TrainParams(ctypes.Structure):
+    _fields_ = [("layers", ctypes.c_int), ("epochs", ctypes.c_int), ("batch", ctypes.c_int),
+                ("lr", ctypes.c_double), ("solve_inner_prec", ctypes.c_int), ("solve_tol", ctypes.c_double),
+                ("seed", ctypes.c_ulonglong), ("noise", ctypes.c_double), ("verbose", ctypes.c_int)]
+
+
+class TrainStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("pairs", ctypes.c_int), ("epochs", ctypes.c_int),
+                ("steps", ctypes.c_int), ("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double),
+                ("loss_history", ctypes.c_double * 64), ("n_history", ctypes.c_int),
+                ("seconds", ctypes.c_double), ("solve_seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(status=STATUS.get(self.status, self.status), pairs=self.pairs, epochs=self.epochs,
+                    steps=self.steps, loss_first=self.loss_first, loss_last=self.loss_last,
+                    loss_history=list(self.loss_history[:self.n_history]), seconds=self.seconds,
+                    solve_seconds=self.solve_seconds)
 
 
 class DwfError(RuntimeError):
@@ -105,6 +130,16 @@ def lib():
     L.dwf_autotune.argtypes = [vp, i, ctypes.c_char_p, vp]
     L.dwf_launch_count.argtypes = [vp]
     L.dwf_launch_count.restype = ctypes.c_longlong
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.dwf_train_params_default.argtypes = [ctypes.POINTER(TrainParams)]
+    L.dwf_train_params_default.restype = None
+    L.dwf_precond_init.argtypes = [vp, i, ctypes.c_ulonglong, d]
+    L.dwf_precond_set_weights.argtypes = [vp, i, dp]
+    L.dwf_precond_get_weights.argtypes = [vp, i, i, dp]
+    L.dwf_precond_apply.argtypes = [vp, i, vp, vp, vp]
+    L.dwf_precond_loss_grad.argtypes = [vp, i, ctypes.POINTER(vp), ctypes.POINTER(vp), dp, dp, vp]
+    L.dwf_precond_train.argtypes = [vp, i, ctypes.POINTER(vp), ctypes.POINTER(TrainParams),
+                                    ctypes.POINTER(TrainStats), vp]
     _lib = L
     return L
 
@@ -153,6 +188,8 @@ class Operator:
         check(lib().dwf_create(d, self.Ls, float(M0), float(mf), float(b), float(c), FORM[form],
                                float(alpha), bcp, ctypes.byref(h)))
         self._h = h
+        self.M0, self.mf, self.b, self.c = float(M0), float(mf), float(b), float(c)
+        self.form, self.alpha = form, float(alpha)
         Lx, Ly, Lz, Lt = self.dims
         self.site_shape = (Lt, Lz, Ly, Lx)
         self.V = Lx * Ly * Lz * Lt
@@ -263,6 +300,54 @@ class Operator:
 
     def device_bytes(self):
         return int(lib().dwf_device_bytes(self._h))
+
+    # ------------------------------------------------ learned preconditioner
+    def _wshape(self, layers):
+        return (int(layers), 9, 2, self.Ls, self.Ls)
+
+    def precond_init(self, layers=3, seed=7, noise=1e-3):
+        check(lib().dwf_precond_init(self._h, int(layers), int(seed), float(noise)))
+
+    def precond_set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.complex128)
+        check(lib().dwf_precond_set_weights(self._h, int(w.shape[0]),
+                                            w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def precond_get_weights(self, layers=3, compute_copy=True):
+        w = np.empty(self._wshape(layers), dtype=np.complex128)
+        check(lib().dwf_precond_get_weights(self._h, int(layers), int(bool(compute_copy)),
+                                            w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return w
+
+    def precond_apply(self, r, out=None, which="N"):
+        """which: "N" the network, "Ndag" its adjoint, "M" = N N^dag."""
+        if out is None:
+            out = self._new(r.shape)
+        check(lib().dwf_precond_apply(self._h, {"N": 0, "Ndag": 1, "M": 2}[which], _ptr(r), _ptr(out), _stream()))
+        return out
+
+    def precond_loss_grad(self, bs, xs, layers=3):
+        n = len(bs)
+        B = (ctypes.c_void_p * n)(*[_ptr(b).value for b in bs])
+        X = (ctypes.c_void_p * n)(*[_ptr(x).value for x in xs])
+        loss = ctypes.c_double()
+        g = np.empty(self._wshape(layers), dtype=np.complex128)
+        check(lib().dwf_precond_loss_grad(self._h, n, B, X, ctypes.byref(loss),
+                                          g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream()))
+        return loss.value, g
+
+    def precond_train(self, b4s, **kw):
+        p = TrainParams()
+        lib().dwf_train_params_default(ctypes.byref(p))
+        for k, v in kw.items():
+            if k == "solve_inner_prec":
+                v = PREC[v]
+            setattr(p, k, v)
+        n = len(b4s)
+        B = (ctypes.c_void_p * n)(*[_ptr(b).value for b in b4s])
+        st = TrainStats()
+        check(lib().dwf_precond_train(self._h, n, B, ctypes.byref(p), ctypes.byref(st), _stream()))
+        return st.as_dict()
 
     def time_hop(self, prec="f32", reps=20, flush_l2=True):
         us = ctypes.c_double()

@@ -1,0 +1,47 @@
+"""Time the even-odd hop kernel on one workload (for profiling runs).
+
+    python -m paper_2602_14454_gb300.hopprof --prec f16 --reps 4
+    python -m paper_2602_14454_gb300.hopprof --workload c1_4^4_ls8_shamir --prec f32
+
+Builds the operator of the named workload (links from the seeded generator of
+``inputs``), optionally pins a hop configuration or a mixing mode, and times
+``reps`` hop launches with CUDA events, L2 flushed between them.  Prints one
+JSON line: microseconds per launch, algorithmic bytes per launch and GB/s.
+"""
+
+import argparse
+import json
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="c2_16^3x32_ls16_mobius")
+    ap.add_argument("--prec", default="f16", choices=["f64", "f32", "f16"])
+    ap.add_argument("--reps", type=int, default=4)
+    ap.add_argument("--form", default="neff", choices=["neff", "standard"])
+    ap.add_argument("--alpha", type=float, default=0.5)
+    ap.add_argument("--config", default=None, help="variant,ns,sb (default: the library's choice)")
+    ap.add_argument("--mix", type=int, default=None, help="fifth-direction mixing mode")
+    args = ap.parse_args(argv)
+
+    import torch
+    from . import build, dwf, inputs
+    build.build()
+    w = inputs.WORKLOADS[args.workload]
+    op = dwf.Operator(w["dims"], w["Ls"], w["M0"], w["mf"], w["b"], w["c"], form=args.form, alpha=args.alpha)
+    op.set_gauge(torch.from_numpy(inputs.workload_links(w)).cuda())
+    if args.config:
+        v, ns, sb = (int(t) for t in args.config.split(","))
+        op.set_hop_config(args.prec, v, ns, sb)
+    if args.mix is not None:
+        op.set_mix_mode(args.prec, args.mix)
+    us, nbytes = op.time_hop(args.prec, reps=args.reps, flush_l2=True)
+    op.device_status()
+    print(json.dumps({"workload": args.workload, "prec": args.prec, "config": op.hop_config(args.prec),
+                      "mix": op.mix_mode(args.prec), "us_per_launch": us, "algorithmic_bytes": nbytes,
+                      "gbs": nbytes / (us * 1e-6) / 1e9}))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

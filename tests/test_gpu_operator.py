@@ -167,12 +167,18 @@ MIX_CASES = [
 
 
 @pytest.mark.parametrize("case", MIX_CASES, ids=lambda c: "Ls%d_b%g_c%g_%s" % (c[1], c[4], c[5], c[6]))
-@pytest.mark.parametrize("mix", [0, 1])
+@pytest.mark.parametrize("mix", [0, 1, 2])
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
 def test_dense_and_structured_mixing(case, mix, prec):
-    """The dense Ls x Ls mixing and its structured (recurrence) form give the same operators."""
+    """The dense Ls x Ls mixing, its structured (recurrence) form and the tensor-core
+    product give the same operators."""
+    from paper_2602_14454_gb300 import dwf
     dims, Ls, M0, mf, b, c, form, alpha = case
     op, ref = make_pair(dims, Ls, M0, mf, b, c, form, alpha, seed=71)
+    if mix == 2 and prec == "f64":
+        with pytest.raises(dwf.DwfError):
+            op.set_mix_mode(prec, mix)
+        return
     op.set_mix_mode(prec, mix)
     assert op.mix_mode(prec) == mix
     x = ref.to_eo(inputs.gaussian_5d(dims, Ls, 72), 0)
@@ -181,6 +187,36 @@ def test_dense_and_structured_mixing(case, mix, prec):
     xf = inputs.gaussian_5d(dims, Ls, 73)
     for dag in (False, True):
         assert rel(to_np(op.apply(to_gpu(xf), op="full", prec=prec, dag=dag)), ref.apply(xf, dag=dag)) < TOL[prec]
+
+
+@pytest.mark.parametrize("ns,sb", [(1, 1), (1, 3), (1, 5), (1, 7), (1, 16), (2, 5), (2, 11)])
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_tensor_core_mixing_tile_shapes(prec, ns, sb):
+    """Tensor-core mixing for CTAs of fewer than 32 threads (dense fallback), with a
+    partial last warp, and with a ragged last tile (Vh = 96 sites)."""
+    dims, Ls = (4, 4, 2, 6), 12
+    op, ref = make_pair(dims, Ls, 1.8, 0.02, 1.5, 0.5, "neff", 0.5, seed=75)
+    op.set_mix_mode(prec, 2)
+    op.set_hop_config(prec, 0, ns, sb)
+    x = ref.to_eo(inputs.gaussian_5d(dims, Ls, 76), 0)
+    for dag in (False, True):
+        assert rel(to_np(op.apply(to_gpu(x), op="eo", prec=prec, dag=dag)), ref.d_pc(x, dag=dag)) < TOL[prec]
+    op.device_status()
+
+
+def test_tensor_core_mixing_full_size():
+    """16^3x32, Ls = 16: the tensor-core mixing against the dense mixing (FP32 fields
+    with the split product agree to FP32 rounding)."""
+    dims, Ls = (16, 16, 16, 32), 16
+    U = inputs.random_links(dims, 0.3, 1002)
+    op, ref = make_pair(dims, Ls, 1.8, 0.01, 1.5, 0.5, "neff", 0.5, seed=77, U=U)
+    x = to_gpu(ref.to_eo(inputs.gaussian_5d(dims, Ls, 78), 0))
+    for prec, tol in (("f32", 5e-6), ("f16", 2e-3)):
+        want = [to_np(op.apply(x, op="eo", prec=prec, dag=d)) for d in (False, True)]
+        op.set_mix_mode(prec, 2)
+        for d, w in zip((False, True), want):
+            assert rel(to_np(op.apply(x, op="eo", prec=prec, dag=d)), w) < tol
+        op.set_mix_mode(prec, 0)
 
 
 def test_structured_mixing_refused_when_unstable():

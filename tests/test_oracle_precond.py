@@ -127,6 +127,23 @@ def test_layer_adjoint_identity(bc):
     assert abs(lhs - rhs) < 1e-12 * abs(lhs)
 
 
+def test_net_adjoint_and_preconditioner_hermiticity():
+    """<y, N r> = <N^dag y, r>; M = N N^dag is Hermitian and positive."""
+    Ls = 3
+    U = inputs.random_links(DIMS, 0.6, 57)
+    net = pc.Net(U, DIMS, BC, cweights(3, Ls, 58))
+    r = cfield(Ls, DIMS, 59).reshape(Ls, -1, 4, 3)[:, net.even]
+    y = cfield(Ls, DIMS, 60).reshape(Ls, -1, 4, 3)[:, net.even]
+    lhs = np.vdot(y.ravel(), net.forward(r).ravel())
+    rhs = np.vdot(net.adjoint(y).ravel(), r.ravel())
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    a = np.vdot(y.ravel(), net.precondition(r).ravel())
+    b = np.vdot(net.precondition(y).ravel(), r.ravel())
+    assert abs(a - b) < 1e-12 * abs(a)
+    q = np.vdot(r.ravel(), net.precondition(r).ravel())
+    assert abs(q.imag) < 1e-12 * abs(q) and q.real > 0
+
+
 def test_loss_gradient_against_finite_differences():
     Ls = 2
     dims = (2, 2, 2, 4)
@@ -215,7 +232,7 @@ def test_fcg_with_exact_inverse_takes_one_iteration():
 
 
 def test_training_lowers_the_loss():
-    """A few Adam steps on pairs (b = A x, x) lower the loss from the identity start."""
+    """A few Adam steps on pairs (b = D x, x) lower the loss from the identity start."""
     ref, bt, A = _small_system()
     Ls = ref.Ls
     W = np.zeros((3, pc.NHOP, 2, Ls, Ls), dtype=np.complex128)
@@ -224,7 +241,7 @@ def test_training_lowers_the_loss():
     pairs = []
     for k in range(3):
         x = ref.to_eo(inputs.gaussian_5d((2, 2, 2, 4), Ls, 60 + k), 0)
-        pairs.append((A(x), x))
+        pairs.append((ref.d_pc(x), x))
     L0, _ = net.loss_and_grad(pairs)
     m = np.zeros_like(W)
     v = np.zeros_like(W)
