@@ -129,9 +129,10 @@ typedef struct {
     int check_every;    /* inner iterations between host convergence checks;
                            they are captured as one CUDA graph; default 16     */
     int use_graph;      /* 1: replay the inner iterations as a CUDA graph       */
-    int precond;        /* 0: CG with reliable updates; 1: flexible CG with the
-                           handle's learned network as preconditioner (FP32
-                           inner, FP64 defect correction; dwf_precond_*)       */
+    int precond;        /* 0: CG with reliable updates; 1: CG on the normal
+                           equation left-preconditioned by the handle's learned
+                           network (FP32 cycles, FP64 defect correction;
+                           dwf_precond_*); needs inner_prec = DWF_F32         */
     int use_initial_guess; /* 1: x5 holds the initial guess on entry; 0: zero   */
     int verbose;        /* 0 quiet                                              */
     int batch_wave;     /* dwf_solve_batch: at most this many systems per wave;
@@ -151,7 +152,7 @@ typedef struct {
     long long kernel_launches; /* device kernels launched by the call           */
     int waves;                /* memory waves of the call (1 for dwf_solve)     */
     int precond_applications; /* applications of the learned preconditioner     */
-    int fallbacks;            /* FCG cycles that fell back to plain CG          */
+    int fallbacks;            /* switches from the learned preconditioner to N = 1 */
 } dwf_solve_stats;
 
 void dwf_solve_params_default(dwf_solve_params *p);
@@ -221,9 +222,13 @@ long long dwf_launch_count(dwf_handle h);
  * persistent kernel whose producer warp streams the neighbour sites through a
  * ring of shared-memory stages for the consumer warps, variant 3 is a
  * persistent kernel sweeping consecutive tiles, variant 4 takes each CTA's
- * sites as a 4D block of the half lattice (neighbour reuse in L1); ns fifth-direction
- * slices per thread (1, or 2 when Ls is even); sb four-dimensional sites per
- * CTA.  -1 / 0 select the built-in defaults.  No numerical effect. */
+ * sites as a 4D block of the half lattice (neighbour reuse in L1), variant 5
+ * (DWF_F16 only, dense mixing; else variant 0) is variant 0 with the spin
+ * projection and SU(3) product in FP16 arithmetic on the stored FP16 values
+ * (FP32 accumulation; rounding at the FP16 storage level); ns fifth-direction
+ * slices per thread (1, 2 when it divides Ls, 4 for variant 5); sb
+ * four-dimensional sites per CTA.  -1 / 0 select the built-in defaults.
+ * Variants 0-4 have no numerical effect beyond summation order. */
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb);
 int dwf_get_hop_config(dwf_handle h, int prec, int *variant, int *ns, int *sb);
 
@@ -285,9 +290,13 @@ int dwf_time_hop(dwf_handle h, int prec, int reps, int flush_l2, double *us_per_
 
 /* ------------------------------------------------ learned preconditioner
  * No counterpart in the paper (it solves with plain CG).  A gauge-covariant
- * linear stencil network N approximates D^-1 for the even-odd matrix D;
- * M = N N^dag (Hermitian, positive semi-definite) preconditions flexible CG on
- * D^dag D (dwf_solve with params.precond = 1).
+ * linear stencil network N approximates D^-1 for the even-odd matrix D and
+ * preconditions it from the left: dwf_solve with params.precond = 1 runs FP32
+ * cycles of CG on (N D)^dag (N D) e = (N D)^dag N r, each closed by an FP64
+ * defect correction (r the FP64 residual of the even-odd system); if the
+ * preconditioned operator loses positivity the solve continues with N = 1.
+ * N^dag N is Hermitian positive semi-definite (dwf_precond_apply, which = 2,
+ * gives N N^dag).
  * Channels are the Ls fifth-direction slices (Ls <= 16).  Layer l maps a
  * field psi of Ls channels to
  *   out(x, c) = sum_p sum_c' W[l][p][chi][c][c'] T_p(x, c'),
@@ -301,8 +310,9 @@ int dwf_time_hop(dwf_handle h, int prec, int reps, int flush_l2, double *us_per_
  * the FP32 kernels.
  *
  * Training: loss L = (1/K) sum_k |N(b_k) - x_k|^2 / |x_k|^2 over pairs
- * D x_k = b_k, x_k = even part of the solution of D5 x5 = b5(b4_k) (dwf_solve)
- * and b_k = D x_k; Adam (beta 0.9, 0.999, eps 1e-8) over minibatches.  The
+ * D x_k = b_k: x_k = even part of the solution of D5 x5 = b5(b4_k) (dwf_solve)
+ * and, as many by default, white-noise x_k (Gaussian, counter-based), with
+ * b_k = D x_k; Adam (beta 0.9, 0.999, eps 1e-8) over minibatches.  The
  * output layer starts scaled by the least-squares factor
  * s = sum Re<b,x>/|x|^2 / sum |b|^2/|x|^2.
  */
@@ -316,6 +326,8 @@ typedef struct {
     unsigned long long seed; /* initial weights and pair order                    */
     double noise;            /* scale of the random part of the initial weights   */
     int verbose;
+    int random_pairs;        /* white-noise pairs (x Gaussian, b = D x) added to
+                                the solution pairs; -1 (default): as many        */
 } dwf_train_params;
 
 typedef struct {

@@ -507,8 +507,9 @@ long long dwf_launch_count(dwf_handle h) { return h ? h->launches : 0; }
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb)
 {
     if (!h || prec < 0 || prec > 2) return dwf_set_error(DWF_EINVAL, "bad handle or precision");
-    if (variant < -1 || variant > 4) return dwf_set_error(DWF_EINVAL, "variant must be -1 or 0..4");
-    if (ns < 0 || ns > 2 || (ns == 2 && h->Ls % 2)) return dwf_set_error(DWF_EINVAL, "ns must be 0, 1 or 2 (2 needs even Ls)");
+    if (variant < -1 || variant > 5) return dwf_set_error(DWF_EINVAL, "variant must be -1 or 0..5");
+    if (ns < 0 || ns > 4 || ns == 3 || (ns && h->Ls % ns) || (ns == 4 && variant != 5))
+        return dwf_set_error(DWF_EINVAL, "ns must be 0, 1, 2 or (variant 5) 4, and divide Ls");
     const int nsv = ns ? ns : hop_default_ns(prec, h->Ls);
     if (sb < 0 || (sb && (h->Ls / nsv) * sb > 256)) return dwf_set_error(DWF_EINVAL, "sb out of range (CTA > 256 threads)");
     h->hop_var[prec] = variant;

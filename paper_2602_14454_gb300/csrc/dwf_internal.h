@@ -277,6 +277,7 @@ int net_apply_f32(dwf_ctx *h, FieldRef r, FieldRef z, cudaStream_t st, int which
 // out = D^dag D x / out = D x with D the even-odd matrix (FP32 even fields)
 int normal_apply_f32(dwf_ctx *h, FieldRef x, FieldRef out, cudaStream_t st);
 int eo_apply_f32(dwf_ctx *h, FieldRef x, FieldRef out, cudaStream_t st);
+int eo_dag_apply_f32(dwf_ctx *h, FieldRef w, FieldRef out, cudaStream_t st);   // out = D^dag w
 }  // namespace dwf
 void dwf_precond_release(dwf_ctx *h);
 

@@ -295,9 +295,82 @@ __device__ __forceinline__ void hop_dir(T2 (*acc)[12], const FieldRef &in, int n
     }
 }
 
+// FP16 fields with FP16 arithmetic for the projection and the SU(3) product
+// (variant 5): the link's splats are formed once per direction for the NS
+// slices of the thread; Q is converted to FP32, scaled by the neighbour's
+// (site, s) scale and reconstructed into the FP32 accumulator.
+template <bool DAG, int D, int NS>
+__device__ __forceinline__ void hop_dir_h2(float2 (*acc)[12], const FieldRef &in, int nb, int x, int LsN, int Ls,
+                                           const __half *U)
+{
+    constexpr int MU = D & 3;
+    constexpr int SIG = (D < 4 ? 1 : -1) * (DAG ? -1 : 1);
+    const __half2 *Uh = reinterpret_cast<const __half2 *>(U + D * 18);
+    __half2 ur[9], ui[9], nui[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const __half2 u = __ldg(Uh + k);
+        ur[k] = __low2half2(u);
+        ui[k] = __high2half2(u);
+        nui[k] = __hneg2(ui[k]);
+    }
+    const uint4 *base = reinterpret_cast<const uint4 *>(in.v) + ((size_t)nb * 3) * Ls;
+    const float *sbase = in.scale + (size_t)nb * ((Ls + 3) & ~3);
+#pragma unroll
+    for (int n = 0; n < NS; ++n) {
+        const int s = x + n * LsN;
+        __half2 v[12];
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            const uint4 q = __ldg(base + (size_t)g * Ls + s);
+            v[4 * g] = *reinterpret_cast<const __half2 *>(&q.x);
+            v[4 * g + 1] = *reinterpret_cast<const __half2 *>(&q.y);
+            v[4 * g + 2] = *reinterpret_cast<const __half2 *>(&q.z);
+            v[4 * g + 3] = *reinterpret_cast<const __half2 *>(&q.w);
+        }
+        const float sc = __ldg(sbase + s);
+        __half2 Hx[3], Hy[3], Qx[3], Qy[3];
+        project_h2<MU, SIG>(v, Hx, Hy);
+        su3_h2(ur, ui, nui, Hx, Hy, Qx, Qy);
+        float2 Fx[3], Fy[3];
+        const float2 scp = make_float2(sc, sc);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Fx[a] = p_mul(__half22float2(Qx[a]), scp);
+            Fy[a] = p_mul(__half22float2(Qy[a]), scp);
+        }
+        reconstruct<MU, SIG>(acc[n], Fx, Fy);
+    }
+}
+
+template <int P, bool DAG, int NS, bool H2>
+__device__ __forceinline__ void gather8(typename Tr<P>::pair (*acc)[12], const HopArgs &a, const int *n8, int x,
+                                        int LsN, int Ls, const typename Tr<P>::link_t *U)
+{
+    if constexpr (H2 && P == DWF_F16) {
+        hop_dir_h2<DAG, 0, NS>(acc, a.in, n8[0], x, LsN, Ls, U);
+        hop_dir_h2<DAG, 1, NS>(acc, a.in, n8[1], x, LsN, Ls, U);
+        hop_dir_h2<DAG, 2, NS>(acc, a.in, n8[2], x, LsN, Ls, U);
+        hop_dir_h2<DAG, 3, NS>(acc, a.in, n8[3], x, LsN, Ls, U);
+        hop_dir_h2<DAG, 4, NS>(acc, a.in, n8[4], x, LsN, Ls, U);
+        hop_dir_h2<DAG, 5, NS>(acc, a.in, n8[5], x, LsN, Ls, U);
+        hop_dir_h2<DAG, 6, NS>(acc, a.in, n8[6], x, LsN, Ls, U);
+        hop_dir_h2<DAG, 7, NS>(acc, a.in, n8[7], x, LsN, Ls, U);
+    } else {
+        hop_dir<P, DAG, 0, NS>(acc, a.in, n8[0], x, LsN, Ls, U);
+        hop_dir<P, DAG, 1, NS>(acc, a.in, n8[1], x, LsN, Ls, U);
+        hop_dir<P, DAG, 2, NS>(acc, a.in, n8[2], x, LsN, Ls, U);
+        hop_dir<P, DAG, 3, NS>(acc, a.in, n8[3], x, LsN, Ls, U);
+        hop_dir<P, DAG, 4, NS>(acc, a.in, n8[4], x, LsN, Ls, U);
+        hop_dir<P, DAG, 5, NS>(acc, a.in, n8[5], x, LsN, Ls, U);
+        hop_dir<P, DAG, 6, NS>(acc, a.in, n8[6], x, LsN, Ls, U);
+        hop_dir<P, DAG, 7, NS>(acc, a.in, n8[7], x, LsN, Ls, U);
+    }
+}
+
 // One tile of SB sites: blockDim = (Ls/NS, SB), site = u SB + threadIdx.y.
 // The norm reduction runs over the nb_red tiles that share a.red.
-template <int P, bool DAG, int NS, int MIX>
+template <int P, bool DAG, int NS, int MIX, bool H2 = false>
 __device__ __forceinline__ void hop_direct_tile(const HopArgs &a, int u, unsigned nb_red)
 {
     typedef typename Tr<P>::real R;
@@ -327,14 +400,7 @@ __device__ __forceinline__ void hop_direct_tile(const HopArgs &a, int u, unsigne
         int n8[8];
 #pragma unroll
         for (int d = 0; d < 8; ++d) n8[d] = __ldg(nb + d);
-        hop_dir<P, DAG, 0, NS>(acc, a.in, n8[0], x, LsN, Ls, U);
-        hop_dir<P, DAG, 1, NS>(acc, a.in, n8[1], x, LsN, Ls, U);
-        hop_dir<P, DAG, 2, NS>(acc, a.in, n8[2], x, LsN, Ls, U);
-        hop_dir<P, DAG, 3, NS>(acc, a.in, n8[3], x, LsN, Ls, U);
-        hop_dir<P, DAG, 4, NS>(acc, a.in, n8[4], x, LsN, Ls, U);
-        hop_dir<P, DAG, 5, NS>(acc, a.in, n8[5], x, LsN, Ls, U);
-        hop_dir<P, DAG, 6, NS>(acc, a.in, n8[6], x, LsN, Ls, U);
-        hop_dir<P, DAG, 7, NS>(acc, a.in, n8[7], x, LsN, Ls, U);
+        gather8<P, DAG, NS, H2>(acc, a, n8, x, LsN, Ls, U);
     }
     const TileCtx<T2> tc = cta_tile(tile, Ls);
     const double nrm = hop_epilogue_core<P, NS, MIX>(a, acc, tc, tile + j * tc.tstride, mtx, site, x, LsN, active,
@@ -342,10 +408,10 @@ __device__ __forceinline__ void hop_direct_tile(const HopArgs &a, int u, unsigne
     if (a.red.op != RED_NONE) grid_reduce(nrm, a.red, u, nb_red);
 }
 
-template <int P, bool DAG, int NS, int MIX>
+template <int P, bool DAG, int NS, int MIX, bool H2 = false>
 __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a)
 {
-    hop_direct_tile<P, DAG, NS, MIX>(a, blockIdx.x, gridDim.x);
+    hop_direct_tile<P, DAG, NS, MIX, H2>(a, blockIdx.x, gridDim.x);
 }
 
 // Batched form: one launch over nsys systems that share Ls and the CTA shape
@@ -353,7 +419,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a)
 // works on tile b / nsys of system b % nsys, so that consecutive CTAs read the
 // same sites' links and neighbour indices, which then come from L2 for all
 // systems but the first.  A system whose skip flag is set is left untouched.
-template <int P, bool DAG, int NS, int MIX>
+template <int P, bool DAG, int NS, int MIX, bool H2 = false>
 __global__ void __launch_bounds__(256) hop_batch_kernel(const HopArgs *__restrict__ tab, int nsys)
 {
     __shared__ __align__(16) unsigned char abuf[sizeof(HopArgs)];
@@ -364,7 +430,7 @@ __global__ void __launch_bounds__(256) hop_batch_kernel(const HopArgs *__restric
     __syncthreads();
     const HopArgs &a = *reinterpret_cast<const HopArgs *>(abuf);
     if (a.skip && *a.skip) return;
-    hop_direct_tile<P, DAG, NS, MIX>(a, u, (a.Vh + blockDim.y - 1) / blockDim.y);
+    hop_direct_tile<P, DAG, NS, MIX, H2>(a, u, (a.Vh + blockDim.y - 1) / blockDim.y);
 }
 
 // ------------------------------------------------- variant 4: blocked tiles
@@ -896,18 +962,18 @@ size_t direct_smem(int Ls, int SB)
     return (size_t)SB * (Ls * 12 + 2) * sizeof(T2) + (size_t)3 * 2 * Ls * Ls * sizeof(R);
 }
 
-template <int P, bool DAG, int NS, int MIX = 0>
+template <int P, bool DAG, int NS, int MIX = 0, bool H2 = false>
 cudaError_t launch_direct(const HopArgs &a, int SB, cudaStream_t st)
 {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(hop_kernel<P, DAG, NS, MIX>,
+        cudaError_t e = cudaFuncSetAttribute(hop_kernel<P, DAG, NS, MIX, H2>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int LsN = a.Ls / NS;
-    hop_kernel<P, DAG, NS, MIX><<<(a.Vh + SB - 1) / SB, dim3(LsN, SB), direct_smem<P>(a.Ls, SB), st>>>(a);
+    hop_kernel<P, DAG, NS, MIX, H2><<<(a.Vh + SB - 1) / SB, dim3(LsN, SB), direct_smem<P>(a.Ls, SB), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1084,6 +1150,16 @@ cudaError_t launch_sweep(const HopArgs &a, int SB, cudaStream_t st)
 template <int P, bool DAG>
 cudaError_t launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
 {
+    // variant 5: FP16 fields with FP16 projection and SU(3) arithmetic (dense mixing)
+    if constexpr (P == DWF_F16) {
+        if (var == 5 && a.mixmode == 0) {
+            if (NS == 4) return launch_direct<P, DAG, 4, 0, true>(a, SB, st);
+            if (NS == 2) return launch_direct<P, DAG, 2, 0, true>(a, SB, st);
+            return launch_direct<P, DAG, 1, 0, true>(a, SB, st);
+        }
+    }
+    if (var == 5) var = 0;
+    if (NS == 4) NS = 2;
     // the structured and tensor-core mixings are compiled for the direct variant only
     if (a.mixmode == 1) {
         if (NS == 2) return launch_direct<P, DAG, 2, 1>(a, SB, st);
@@ -1183,8 +1259,8 @@ cudaError_t launch_hop_batch(int prec, bool dag, const HopArgs *tab, int nsys, c
 
 cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
 {
-    if (var < 0 || var > 4) var = hop_default_variant(prec);
-    if (NS <= 0 || NS > 2 || (a.Ls % NS) != 0) NS = hop_default_ns(prec, a.Ls);
+    if (var < 0 || var > 5) var = hop_default_variant(prec);
+    if (NS <= 0 || NS > 4 || NS == 3 || (a.Ls % NS) != 0 || (NS == 4 && var != 5)) NS = hop_default_ns(prec, a.Ls);
     if (SB <= 0) SB = hop_default_sb(prec, a.Ls, NS);
     if ((a.Ls / NS) * SB > 256) SB = 256 / (a.Ls / NS);
     if (SB < 1) SB = 1;

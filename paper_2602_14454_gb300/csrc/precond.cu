@@ -407,6 +407,25 @@ __global__ void __launch_bounds__(256) net_loss_kernel(const float4 *y, const fl
     grid_reduce(acc, red);
 }
 
+// Gaussian N(0, 1) reals for white-noise training vectors: counter-based
+// (SplitMix64 of seed and index, Steele, Lea and Flood 2014), Box-Muller.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z)
+{
+    z += 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+__global__ void fill_gaussian_kernel(float *x, size_t n, unsigned long long seed)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long r = splitmix64(seed * 0x100000001b3ULL + i);
+        const float u1 = ((float)(r >> 40) + 1.0f) * (1.0f / 16777217.0f);   // (0, 1]
+        const float u2 = (float)((r >> 16) & 0xffffffULL) * (1.0f / 16777216.0f);
+        x[i] = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    }
+}
+
 int reduce_grid(size_t n4)
 {
     size_t b = (n4 + 255) / 256;
@@ -750,6 +769,7 @@ void dwf_train_params_default(dwf_train_params *p)
     p->seed = 7;
     p->noise = 1e-3;
     p->verbose = 0;
+    p->random_pairs = -1;
 }
 
 int dwf_precond_init(dwf_handle h, int layers, unsigned long long seed, double noise)
@@ -857,7 +877,9 @@ int dwf_precond_train(dwf_handle h, int nsrc, const void *const *b4, const dwf_t
     if (!h || nsrc < 1 || !b4) return dwf_set_error(DWF_EINVAL, "bad argument");
     dwf_train_params defp;
     dwf_train_params_default(&defp);
-    const dwf_train_params *p = tp ? tp : &defp;
+    dwf_train_params pv = tp ? *tp : defp;
+    if (pv.random_pairs < 0) pv.random_pairs = nsrc;
+    const dwf_train_params *p = &pv;
     if (p->epochs < 0 || p->batch < 1 || !(p->lr > 0)) return dwf_set_error(DWF_EINVAL, "bad training parameters");
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t st = (cudaStream_t)stream;
@@ -908,6 +930,29 @@ int dwf_precond_train(dwf_handle h, int nsrc, const void *const *b4, const dwf_t
         N->pb.push_back(fbb);
         N->pxn2.push_back(hs.last);
     }
+    // white-noise pairs: x Gaussian, b = D x (they constrain N on the modes the
+    // solutions of smooth sources hardly contain)
+    for (int k = 0; k < p->random_pairs; ++k) {
+        void *mem = nullptr;
+        CK(cudaMalloc(&mem, 2 * ((fb + 255) & ~(size_t)255)));
+        N->pair_mem.push_back(mem);
+        FieldRef fx, fbb;
+        fx.v = mem;
+        fbb.v = (char *)mem + ((fb + 255) & ~(size_t)255);
+        const size_t nreal = fb / 4;
+        fill_gaussian_kernel<<<reduce_grid(nreal / 4), 256, 0, st>>>((float *)fx.v, nreal, p->seed * 7919ULL + k);
+        CK(cudaGetLastError());
+        h->launches += 1;
+        if ((rc = eo_apply_f32(h, fx, fbb, st))) return rc;
+        CK(launch_norm2(DWF_F32, fx, h->Vh, h->Ls, red(h, RED_STORE, sc), st));
+        CgScalars hs;
+        CK(cudaMemcpyAsync(&hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        N->px.push_back(fx);
+        N->pb.push_back(fbb);
+        N->pxn2.push_back(hs.last);
+    }
+    nsrc = (int)N->px.size();
     S.solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - ts).count();
     // least-squares scale of the output layer: N = s I minimises sum |s b - x|^2/|x|^2
     {

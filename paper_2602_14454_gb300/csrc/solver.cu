@@ -187,96 +187,76 @@ cudaError_t normal_residual(dwf_ctx *h, const Bufs &B, cudaStream_t st)
     return hop(h, P, true, a2, st);
 }
 
-// Flexible CG (Notay 2000) on D^dag D e = rhs in FP32 with the learned
-// preconditioner z = M r, from e = 0, until |r| <= eta |rhs| or kmax
-// iterations; e is added into B.xs.  beta by the Polak-Ribiere formula
-// (z_new, r_new - r_old) / (z_old, r_old).  When a preconditioned step breaks
-// down (non-positive or non-finite (r, z) or (p, A p)) the cycle continues as
-// plain CG (M = 1) from the current residual.
-int fcg_cycle(dwf_ctx *h, const Bufs &B, FieldRef rhs, double rhs_norm, double eta, int kmax, int &iters, int &napp,
-              int &fallbacks, int &dapp, cudaStream_t st)
+// One FP32 cycle of CG on the normal equation of the left-preconditioned
+// system N D e = N r (N the handle's network, trained so that N D ~ 1):
+//     (N D)^dag (N D) e = (N D)^dag N r,
+// from e = 0 until the residual of this equation fell below eta times its
+// initial norm, or kmax iterations; e is added into B.xs.  With plain = true
+// N is the identity (CG on D^dag D).  A non-positive or non-finite curvature
+// (p, B p) of the preconditioned operator ends the cycle and sets `plain` for
+// the rest of the solve (the caller's FP64 defect correction continues from
+// the iterate reached).
+int lpcg_cycle(dwf_ctx *h, const Bufs &B, FieldRef r32, double eta, int kmax, bool &plain, int &iters, int &napp,
+               int &fallbacks, int &dapp, cudaStream_t st)
 {
     cudaError_t e = cudaSuccess;
-    FieldRef r = h->field("fc_r", DWF_F32, &e), ro = h->field("fc_ro", DWF_F32, &e);
-    FieldRef z = h->field("fc_z", DWF_F32, &e), pp = h->field("fc_p", DWF_F32, &e);
-    FieldRef q = h->field("fc_q", DWF_F32, &e);
-    if (!r.v || !ro.v || !z.v || !pp.v || !q.v) return dwf_cuda_error(e, "FCG workspace");
+    FieldRef rr = h->field("lp_r", DWF_F32, &e), pp = h->field("lp_p", DWF_F32, &e);
+    FieldRef q = h->field("lp_q", DWF_F32, &e), t1 = h->field("lp_t1", DWF_F32, &e);
+    FieldRef t2 = h->field("lp_t2", DWF_F32, &e);
+    if (!rr.v || !pp.v || !q.v || !t1.v || !t2.v) return dwf_cuda_error(e, "workspace");
     const int Vh = h->Vh, Ls = h->Ls;
     CgScalars *sc = h->scal + 4;
-    CgScalars hs[3];
-    auto dots = [&](int n) -> int {
-        CK(cudaMemcpyAsync(hs, sc, n * sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    CgScalars hs[2];
+    int rc;
+    auto dot = [&](FieldRef x, FieldRef y, double &out) -> int {
+        CK(launch_vdot(x, y, Vh, Ls, red(h, RED_STORE, sc), st));
+        h->launches += 1;
+        CK(cudaMemcpyAsync(hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        out = hs[0].last;
         return DWF_OK;
     };
-    int rc;
-    bool plain = false;
-    CK(launch_vaxpby(1.f, rhs, 0.f, r, Vh, Ls, st));
-    auto restart_plain = [&]() -> int {
-        plain = true;
-        fallbacks += 1;
-        CK(launch_vaxpby(1.f, r, 0.f, pp, Vh, Ls, st));
-        CK(launch_vdot(r, r, Vh, Ls, red(h, RED_STORE, sc), st));
-        h->launches += 2;
-        return dots(1);
+    // y = (N D)^dag N v (learned) or D^dag v (plain), from v (destroys t1, t2)
+    auto lhs_of = [&](FieldRef v, FieldRef y) -> int {
+        int r2;
+        if (plain) return eo_dag_apply_f32(h, v, y, st);
+        if ((r2 = net_apply_f32(h, v, t2, st, 0))) return r2;
+        if ((r2 = net_apply_f32(h, t2, t1, st, 1))) return r2;
+        napp += 2;
+        return eo_dag_apply_f32(h, t1, y, st);
     };
-    if ((rc = net_apply_f32(h, r, z, st))) return rc;
-    napp += 1;
-    CK(launch_vaxpby(1.f, z, 0.f, pp, Vh, Ls, st));
-    CK(launch_vdot(r, z, Vh, Ls, red(h, RED_STORE, sc), st));
-    h->launches += 2;
-    if ((rc = dots(1))) return rc;
-    double rz = hs[0].last;
-    if (!(rz > 0) || !std::isfinite(rz)) {
-        if ((rc = restart_plain())) return rc;
-        rz = hs[0].last;
-    }
+    if ((rc = lhs_of(r32, rr))) return rc;
+    dapp += 1;
+    CK(launch_vaxpby(1.f, rr, 0.f, pp, Vh, Ls, st));
+    h->launches += 1;
+    double rz;
+    if ((rc = dot(rr, rr, rz))) return rc;
+    const double r0 = std::sqrt(rz);
+    if (!(r0 > 0) || !std::isfinite(r0)) return DWF_OK;
     for (int k = 0; k < kmax; ++k) {
-        if ((rc = normal_apply_f32(h, pp, q, st))) return rc;
+        if ((rc = eo_apply_f32(h, pp, q, st))) return rc;   // q = D p
+        if ((rc = lhs_of(q, q))) return rc;                  // q = (N D)^dag N D p
         dapp += 2;
-        CK(launch_vdot(pp, q, Vh, Ls, red(h, RED_STORE, sc), st));
-        h->launches += 1;
-        if ((rc = dots(1))) return rc;
-        const double pq = hs[0].last;
+        double pq;
+        if ((rc = dot(pp, q, pq))) return rc;
         if (!(pq > 0) || !std::isfinite(pq)) {
-            if (plain) return dwf_set_error(DWF_EBREAKDOWN, "CG breakdown in the FCG cycle");
-            if ((rc = restart_plain())) return rc;
-            rz = hs[0].last;
-            continue;
+            if (plain) return dwf_set_error(DWF_EBREAKDOWN, "CG breakdown");
+            plain = true;
+            fallbacks += 1;
+            return DWF_OK;
         }
         const float alpha = (float)(rz / pq);
         CK(launch_vaxpby(alpha, pp, 1.f, B.xs, Vh, Ls, st));
-        CK(launch_vaxpby(1.f, r, 0.f, ro, Vh, Ls, st));
-        CK(launch_vaxpby(-alpha, q, 1.f, r, Vh, Ls, st));
-        CK(launch_vdot(r, r, Vh, Ls, red(h, RED_STORE, sc), st));
-        h->launches += 4;
-        if ((rc = dots(1))) return rc;
-        iters += 1;
-        const double rn = std::sqrt(hs[0].last);
-        if (!std::isfinite(rn)) return dwf_set_error(DWF_ENONFINITE, "non-finite FCG residual");
-        if (rn <= eta * rhs_norm) break;
-        if (plain) {
-            CK(launch_vaxpby(1.f, r, 0.f, z, Vh, Ls, st));
-            h->launches += 1;
-        } else {
-            if ((rc = net_apply_f32(h, r, z, st))) return rc;
-            napp += 1;
-        }
-        CK(launch_vdot(r, z, Vh, Ls, red(h, RED_STORE, sc), st));
-        CK(launch_vdot(z, ro, Vh, Ls, red(h, RED_STORE, sc + 1), st));
+        CK(launch_vaxpby(-alpha, q, 1.f, rr, Vh, Ls, st));
         h->launches += 2;
-        if ((rc = dots(2))) return rc;
-        const double rzn = hs[0].last, zro = hs[1].last;
-        if (!(rzn > 0) || !std::isfinite(rzn) || !std::isfinite(zro)) {
-            if (plain) return dwf_set_error(DWF_EBREAKDOWN, "CG breakdown in the FCG cycle");
-            if ((rc = restart_plain())) return rc;
-            rz = hs[0].last;
-            continue;
-        }
-        const float beta = (float)((rzn - zro) / rz);
-        CK(launch_vaxpby(1.f, z, beta, pp, Vh, Ls, st));
+        double rn2;
+        if ((rc = dot(rr, rr, rn2))) return rc;
+        iters += 1;
+        if (!std::isfinite(rn2)) return dwf_set_error(DWF_ENONFINITE, "non-finite residual in the CG cycle");
+        if (std::sqrt(rn2) <= eta * r0) break;
+        CK(launch_vaxpby(1.f, rr, (float)(rn2 / rz), pp, Vh, Ls, st));
         h->launches += 1;
-        rz = rzn;
+        rz = rn2;
     }
     return DWF_OK;
 }
@@ -438,16 +418,24 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
     };
 
     int napp = 0, nfall = 0;
+    bool lp_plain = false;
+    cudaError_t ce = cudaSuccess;
     for (int round = 0; round < 3 && status == DWF_OK; ++round) {
         converged = false;
         if ((rc = reliable(round == 0 && !p->use_initial_guess))) return rc;
-        // learned preconditioner: FCG cycles in FP32, each closed by an FP64 defect correction
+        // learned preconditioner: FP32 cycles of left-preconditioned CGNR, each
+        // closed by an FP64 defect correction (x64 += e, r64 = b~ - D x64)
         while (p->precond && !converged) {
             if (iters >= p->max_iter) {
                 status = DWF_ENOTCONV;
                 break;
             }
-            if ((rc = fcg_cycle(h, B, B.rs, rmax, 0.01 * p->delta, p->max_iter - iters, iters, napp, nfall, dapp, st)))
+            FieldRef r32 = h->field("lp_r32", DWF_F32, &ce);
+            if (!r32.v) return dwf_cuda_error(ce, "workspace");
+            CK(launch_convert(DWF_F64, B.r64, DWF_F32, r32, h->Vh, h->Ls, st));
+            h->launches += 1;
+            if ((rc = lpcg_cycle(h, B, r32, 0.01 * p->delta, p->max_iter - iters, lp_plain, iters, napp, nfall, dapp,
+                                 st)))
                 return rc;
             if ((rc = reliable(false))) return rc;
         }
@@ -1086,6 +1074,24 @@ int dwf::eo_apply_f32(dwf_ctx *h, FieldRef x, FieldRef out, cudaStream_t st)
     a2.y = x;
     a2.ymode = 1;
     CK(hop(h, P, false, a2, st));
+    return DWF_OK;
+}
+
+// out = D^dag w on FP32 even fields (K_c, K_d of the inner iteration on Q^T w)
+int dwf::eo_dag_apply_f32(dwf_ctx *h, FieldRef w, FieldRef out, cudaStream_t st)
+{
+    const int P = DWF_F32;
+    cudaError_t e = cudaSuccess;
+    FieldRef wh = h->field("nd_wh", P, &e), u = h->field("nd_u", P, &e);
+    if (!wh.v || !u.v) return dwf_cuda_error(e, "workspace");
+    CK(mix(h, P, w, wh, MAT_QT, st));
+    HopArgs a3 = hop_args(h, P, 1, wh, u, MAT_MT);
+    CK(hop(h, P, true, a3, st));
+    HopArgs a4 = hop_args(h, P, 0, u, out, MAT_NPT4);
+    a4.y = wh;
+    a4.ymode = 2;
+    a4.ymat = h->mat(P, MAT_RA5T);
+    CK(hop(h, P, true, a4, st));
     return DWF_OK;
 }
 

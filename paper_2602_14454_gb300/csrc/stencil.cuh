@@ -114,5 +114,53 @@ __device__ __forceinline__ void hop_one(T2 *acc, const T2 *u, const T2 *v)
     reconstruct<MU, SIG>(acc, Qx, Qy);
 }
 
+// ---------------------------------------------- FP16 arithmetic (half2 pairs)
+// The same projection and SU(3) product on raw FP16 pairs (no conversion of
+// the stored spinor or link): h = psi_u - sig e_mu psi_l in half2, Q = U h
+// with HFMA2.  The caller converts Q to FP32, applies the site scale and
+// reconstructs in FP32.  Inputs are normalised per (site, s) (|values| <= 1)
+// and links are unitary, so no intermediate leaves the FP16 range.
+template <int MU, int SIG>
+__device__ __forceinline__ void project_h2(const __half2 *v, __half2 *Hx, __half2 *Hy)
+{
+    const __half s = __float2half((float)SIG), ms = __float2half((float)-SIG);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const __half2 XU = v[4 * a], XL = v[4 * a + 1], YU = v[4 * a + 2], YL = v[4 * a + 3];
+        if constexpr (MU == 3) {        // h0 = p0 - s p2, h1 = p1 - s p3
+            Hx[a] = __hfma2(__halves2half2(ms, ms), XL, XU);
+            Hy[a] = __hfma2(__halves2half2(ms, ms), YL, YU);
+        } else if constexpr (MU == 2) { // h0 = p0 + s i p2, h1 = p1 - s i p3
+            Hx[a] = __hfma2(__halves2half2(ms, s), YL, XU);
+            Hy[a] = __hfma2(__halves2half2(s, ms), XL, YU);
+        } else if constexpr (MU == 1) { // h0 = p0 + s p3, h1 = p1 - s p2
+            Hx[a] = __hfma2(__halves2half2(s, ms), __lowhigh2highlow(XL), XU);
+            Hy[a] = __hfma2(__halves2half2(s, ms), __lowhigh2highlow(YL), YU);
+        } else {                        // h0 = p0 + s i p3, h1 = p1 + s i p2
+            Hx[a] = __hfma2(__halves2half2(ms, ms), __lowhigh2highlow(YL), XU);
+            Hy[a] = __hfma2(__halves2half2(s, s), __lowhigh2highlow(XL), YU);
+        }
+    }
+}
+
+// Q = U H with the link's splats precomputed: ur[k] = (re, re), ui[k] = (im, im), nui[k] = -ui[k]
+__device__ __forceinline__ void su3_h2(const __half2 *ur, const __half2 *ui, const __half2 *nui, const __half2 *Hx,
+                                       const __half2 *Hy, __half2 *Qx, __half2 *Qy)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        __half2 qx = __float2half2_rn(0.f), qy = __float2half2_rn(0.f);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            qx = __hfma2(ur[a * 3 + b], Hx[b], qx);
+            qx = __hfma2(nui[a * 3 + b], Hy[b], qx);
+            qy = __hfma2(ur[a * 3 + b], Hy[b], qy);
+            qy = __hfma2(ui[a * 3 + b], Hx[b], qy);
+        }
+        Qx[a] = qx;
+        Qy[a] = qy;
+    }
+}
+
 }  // namespace
 }  // namespace dwf

@@ -64,7 +64,8 @@ class SolveStats(ctypes.Structure):
 class TrainParams(ctypes.Structure):
     _fields_ = [("layers", ctypes.c_int), ("epochs", ctypes.c_int), ("batch", ctypes.c_int),
                 ("lr", ctypes.c_double), ("solve_inner_prec", ctypes.c_int), ("solve_tol", ctypes.c_double),
-                ("seed", ctypes.c_ulonglong), ("noise", ctypes.c_double), ("verbose", ctypes.c_int)]
+                ("seed", ctypes.c_ulonglong), ("noise", ctypes.c_double), ("verbose", ctypes.c_int),
+                ("random_pairs", ctypes.c_int)]
 
 
 class TrainStats(ctypes.Structure):

@@ -1,0 +1,152 @@
+"""Measurement runs of the larger workloads (one JSON line each).
+
+    python -m paper_2602_14454_gb300.workloads batch      # 24^3x48: 12 point sources x 3 masses x Ls {8,12,16}
+    python -m paper_2602_14454_gb300.workloads learned    # 16^4, Ls 16: train on 256 sources, FCG vs CG
+    python -m paper_2602_14454_gb300.workloads large      # 32^3x64, Ls 16: mixed precision vs FP64 CG
+
+Every run uses the seeded generators of ``inputs``; times are wall clock
+around the library call after a synchronisation (device work included).
+"""
+
+import argparse
+import json
+import time
+
+
+def _sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def _links(w):
+    import torch
+    from . import inputs
+    return torch.from_numpy(inputs.workload_links(w)).cuda()
+
+
+def run_batch(args):
+    import torch
+    from . import dwf, inputs
+    w = inputs.WORKLOADS["c3_24^3x48_batched"]
+    dims = w["dims"]
+    if args.small:
+        dims = (8, 8, 8, 16)
+        w = dict(w, dims=dims)
+    U = _links(w)
+    ops = {}
+    for Ls in w["Ls_list"]:
+        for mf in w["mf_list"]:
+            op = dwf.Operator(dims, Ls, w["M0"], mf, w["b"], w["c"], form="standard")
+            op.set_gauge(U)
+            ops[(Ls, mf)] = op
+    hs, b4s = [], []
+    for spin in range(4):
+        for col in range(3):
+            b4 = torch.from_numpy(inputs.point_source(dims, spin=spin, colour=col)).cuda()
+            for key, op in ops.items():
+                hs.append(op)
+                b4s.append(b4)
+    _sync()
+    t0 = time.perf_counter()
+    x4s, st = dwf.solve_batch(hs, b4s, inner_prec=args.inner, tol=1e-10, batch_wave=args.wave)
+    _sync()
+    dt = time.perf_counter() - t0
+    out = {"workload": "c3_24^3x48_batched" if not args.small else "batched 8^3x16 (reduced)",
+           "dims": list(dims), "systems": len(hs), "inner_precision": args.inner,
+           "seconds": dt, "systems_per_s": len(hs) / dt, "waves": st[0]["waves"],
+           "iterations": {"min": min(s["iterations"] for s in st), "max": max(s["iterations"] for s in st)},
+           "true_residual_max": max(s["true_residual"] for s in st),
+           "status": sorted({s["status"] for s in st}), "kernel_launches": st[0]["kernel_launches"]}
+    print(json.dumps(out), flush=True)
+
+
+def run_learned(args):
+    import torch
+    from . import dwf, inputs
+    w = inputs.WORKLOADS["c4_16^4_ls16_neff"]
+    dims = w["dims"]
+    U = _links(w)
+    op = dwf.Operator(dims, w["Ls"], w["M0"], w["mf"], w["b"], w["c"], form="neff", alpha=w["alpha"])
+    op.set_gauge(U)
+    ntrain = args.ntrain
+    b4s = [torch.from_numpy(inputs.gaussian_4d(dims, s)).cuda() for s in list(w["train_seeds"])[:ntrain]]
+    tests = [torch.from_numpy(inputs.gaussian_4d(dims, s)).cuda() for s in list(w["test_seeds"])[:args.ntest]]
+
+    def solve_all(**kw):
+        rows = []
+        for b4 in tests:
+            b5 = op.source_5d(b4)
+            _sync()
+            t0 = time.perf_counter()
+            _, s = op.solve(b5, **kw)
+            _sync()
+            rows.append((s["iterations"], time.perf_counter() - t0, s["true_residual"],
+                         s.get("precond_applications", 0)))
+        return rows
+
+    fp64 = solve_all(inner_prec="f64")
+    mixed = solve_all(inner_prec="f32")
+    op.precond_init(3, seed=1, noise=0.0)
+    ident = solve_all(inner_prec="f32", precond=1)
+    _sync()
+    t0 = time.perf_counter()
+    st = op.precond_train(b4s, epochs=args.epochs, batch=16, lr=args.lr)
+    _sync()
+    ttrain = time.perf_counter() - t0
+    learned = solve_all(inner_prec="f32", precond=1)
+
+    def summ(rows):
+        return {"iterations": [r[0] for r in rows], "seconds": [round(r[1], 4) for r in rows],
+                "true_residual_max": max(r[2] for r in rows), "precond_applications": [r[3] for r in rows]}
+    out = {"workload": "c4_16^4_ls16_neff", "train_sources": ntrain, "test_sources": len(tests),
+           "train_seconds": ttrain, "train_solve_seconds": st["solve_seconds"], "loss_first": st["loss_first"],
+           "loss_last": st["loss_last"], "epochs": st["epochs"],
+           "fp64_cg": summ(fp64), "mixed_f32_cg": summ(mixed), "fcg_identity": summ(ident),
+           "fcg_learned": summ(learned)}
+    print(json.dumps(out), flush=True)
+
+
+def run_large(args):
+    from . import dwf, inputs
+    w = inputs.WORKLOADS["c5_32^3x64_ls16_mobius"]
+    U = _links(w)
+    op = dwf.Operator(w["dims"], w["Ls"], w["M0"], w["mf"], w["b"], w["c"], form="neff", alpha=w["alpha"])
+    op.set_gauge(U)
+    import torch
+    b4 = torch.from_numpy(inputs.gaussian_4d(w["dims"], w["src_seed"])).cuda()
+    res = {}
+    for name, kw in (("mixed_f16", dict(inner_prec="f16")), ("mixed_f32", dict(inner_prec="f32")),
+                     ("fp64_cg", dict(inner_prec="f64"))):
+        b5 = op.source_5d(b4)
+        _sync()
+        t0 = time.perf_counter()
+        _, s = op.solve(b5, **kw)
+        _sync()
+        res[name] = {"seconds": time.perf_counter() - t0, "iterations": s["iterations"],
+                     "true_residual": s["true_residual"], "reliable_updates": s["reliable_updates"]}
+    us, by = op.time_hop("f16", reps=10, flush_l2=True)
+    res["hop_f16"] = {"us": us, "gbs": by / us / 1e3}
+    us, by = op.time_hop("f32", reps=10, flush_l2=True)
+    res["hop_f32"] = {"us": us, "gbs": by / us / 1e3}
+    print(json.dumps({"workload": "c5_32^3x64_ls16_mobius", "device_bytes": op.device_bytes(), **res}), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["batch", "learned", "large"])
+    ap.add_argument("--inner", default="f32", choices=["f16", "f32", "f64"])
+    ap.add_argument("--wave", type=int, default=0)
+    ap.add_argument("--small", action="store_true", help="batch: 8^3x16 instead of 24^3x48")
+    ap.add_argument("--ntrain", type=int, default=256)
+    ap.add_argument("--ntest", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    args = ap.parse_args(argv)
+    from . import build
+    build.build()
+    {"batch": run_batch, "learned": run_learned, "large": run_large}[args.what](args)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

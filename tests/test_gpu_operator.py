@@ -133,7 +133,7 @@ def test_full_size_eo_parity():
 
 
 HOP_CONFIGS = [(4, 1, 4), (4, 2, 6), (4, 1, 12), (4, 2, 16), (4, 1, 5), (3, 1, 3), (3, 2, 8), (3, 1, 8), (0, 1, 3), (0, 2, 5), (1, 1, 3), (1, 2, 7), (1, 1, 16), (1, 2, 1),
-               (2, 1, 8), (2, 2, 5), (2, 1, 3), (2, 2, 1), (2, 1, 16)]
+               (2, 1, 8), (2, 2, 5), (2, 1, 3), (2, 2, 1), (2, 1, 16), (5, 1, 8), (5, 2, 5), (5, 4, 3), (5, 4, 16)]
 
 
 @pytest.mark.parametrize("cfg", HOP_CONFIGS, ids=lambda c: "var%d_ns%d_sb%d" % c)

@@ -63,6 +63,19 @@ def test_c1_solve_with_tensor_core_mixing(c1_reference, prec):
     assert rel(ref.project_4d(x5), x4_ref) < 1e-9
 
 
+@pytest.mark.parametrize("ns", [1, 4])
+def test_c1_solve_with_fp16_arithmetic_hop(c1_reference, ns):
+    """Hop variant 5 (FP16 projection and SU(3) arithmetic) as the inner operator:
+    the FP64 reliable updates still take the solve to the oracle's solution."""
+    U, b4, b5, x5_ref, x4_ref = c1_reference
+    op, ref = make_pair(C1["dims"], C1["Ls"], C1["M0"], C1["mf"], C1["b"], C1["c"], "neff", 0.5, U=U)
+    op.set_hop_config("f16", 5, ns, 0)
+    x5, st = op.solve(to_gpu(b5), inner_prec="f16", tol=1e-10)
+    x5 = to_np(x5)
+    assert rel(ref.apply(x5), b5) <= 1e-10
+    assert rel(ref.project_4d(x5), x4_ref) < 1e-9
+
+
 def test_c1_fp64_residual_history_matches_oracle(c1_reference):
     """Plain FP64 CG on the GPU and the oracle's CGNR are the same iteration: after K
     iterations from a zero guess both have the same eo residual ||b~ - D x_K|| / ||b~||."""
