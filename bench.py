@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "c2_16^3x32_ls16_mobius"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 METRIC = "DWF CG time-to-solution @1e-10 residual; 5D Dslash GB/s vs HBM peak"
 
 
@@ -130,18 +131,27 @@ def peaks():
         return None
 
 
+HOP_SOURCES = ("hop.cu", "stencil.cuh", "fields.cuh", "dwf_internal.h")
+
+
+def hop_source_key():
+    """sha256 (16 hex digits) of every source file the hop kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in HOP_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2602_14454_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def hop_traffic(prec):
     """DRAM bytes per hop launch from the committed ncu summary, if it was taken
-    from the current hop kernel source (else null)."""
+    from the current hop kernel sources (else null)."""
     path = os.path.join(ROOT, "profiles", "hop_traffic.json")
     try:
         d = json.load(open(path))
     except Exception:
         return None
-    src = open(os.path.join(ROOT, "paper_2602_14454_gb300", "csrc", "hop.cu"), "rb").read()
-    h = hashlib.sha256(src).hexdigest()[:16]
     e = d.get(prec)
-    if not e or e.get("hop_cu_sha256_16") != h:
+    if not e or e.get("hop_sources_sha256_16") != hop_source_key():
         return None
     return e.get("dram_bytes_per_launch_full_size")
 
@@ -287,6 +297,7 @@ def main():
     pk = peaks()
     peak = pk["hbm_gbs"] if pk else 6800.0
     achieved = nbytes / (us * 1e-6) / 1e9
+    hop_flops = float(op.V // 2) * w["Ls"] * (1320 + 48 * w["Ls"])
 
     out = None
     if rank == 0:
@@ -331,6 +342,13 @@ def main():
                          "us_per_launch": us, "algorithmic_bytes_per_launch": nbytes,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured" if pk
                          else "fallback 6.8 TB/s"},
+            # cross-check: the same launch against the FP32 arithmetic peak derived from the
+            # unit counts (152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz = 80.5 TFLOP/s); the
+            # hop's useful flops per 5D site are 1320 (Wilson hop) + 48 Ls (dense Ls mixing)
+            "roofline_alu": {"bound": "alu", "achieved": hop_flops / (us * 1e-6) / 1e12,
+                             "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": hop_flops / (us * 1e-6) / 1e12 / FP32_PEAK_TFLOPS,
+                             "flops_per_launch": hop_flops},
             "cpu_baseline": base,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(b4_host.nbytes),
                     "d2h_bytes_per_step": int(b4_host.nbytes), "true_residual": s2["true_residual"]},

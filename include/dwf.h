@@ -224,8 +224,9 @@ long long dwf_launch_count(dwf_handle h);
  * persistent kernel sweeping consecutive tiles, variant 4 takes each CTA's
  * sites as a 4D block of the half lattice (neighbour reuse in L1), variant 5
  * (DWF_F16 only, dense mixing; else variant 0) is variant 0 with the spin
- * projection and SU(3) product in FP16 arithmetic on the stored FP16 values
- * (FP32 accumulation; rounding at the FP16 storage level); ns fifth-direction
+ * projection in FP16 arithmetic on the stored FP16 values (one rounding at the
+ * FP16 storage level) and the SU(3) product in FP32 shared by the thread's
+ * slices; ns fifth-direction
  * slices per thread (1, 2 when it divides Ls, 4 for variant 5); sb
  * four-dimensional sites per CTA.  -1 / 0 select the built-in defaults.
  * Variants 0-4 have no numerical effect beyond summation order. */

@@ -27,7 +27,7 @@ __device__ __forceinline__ void load_mat(R *dst, const void *src, int Ls)
 // tile must be complete and visible; every thread of the CTA must call it.
 template <int MIX, typename T2, typename R>
 __device__ __forceinline__ void mix_tile_any(const void *prog, const R *mtx, T2 *tile, int tstride, int j,
-                                             int s, int Ls, bool active, T2 (*o)[12])
+                                             int s, int Ls, bool active, T2 (*o)[12], int band = 0)
 {
     if constexpr (MIX == 1) {
         chain_mix<R>(reinterpret_cast<const MixProg<R> *>(prog), tile, tstride, blockDim.y, Ls,
@@ -40,7 +40,10 @@ __device__ __forceinline__ void mix_tile_any(const void *prog, const R *mtx, T2 
             for (int k = 0; k < 12; ++k) o[0][k] = p_add(o[0][k], h[k]);
         }
     } else if (active) {
-        mix_pairs<1>(mtx, tile + j * tstride, s, Ls, o);
+        if (band)
+            mix_pairs_band<1>(mtx, tile + j * tstride, s, Ls, o);
+        else
+            mix_pairs<1>(mtx, tile + j * tstride, s, Ls, o);
     }
 }
 
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(256) mix_kernel(const MixArgs a)
     T2 o[1][12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) o[0][k] = p_splat((R)0);
-    mix_tile_any<MIX>(a.prog, mtx, tile, tstride, j, s, Ls, active, o);
+    mix_tile_any<MIX>(a.prog, mtx, tile, tstride, j, s, Ls, active, o, a.band);
     if (active) st_pairs<P>(a.out, (size_t)site, s, Ls, o[0]);
 }
 
@@ -108,7 +111,7 @@ __device__ __forceinline__ void cg_update_tile(const CgUpdateArgs &a, int u)
     T2 o[1][12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) o[0][k] = p_splat((R)0);
-    mix_tile_any<MIX>(a.prog, mtx, tile, tstride, j, s, Ls, active, o);
+    mix_tile_any<MIX>(a.prog, mtx, tile, tstride, j, s, Ls, active, o, a.band);
     if (active) st_pairs<P>(a.phat, (size_t)site, s, Ls, o[0]);
 }
 

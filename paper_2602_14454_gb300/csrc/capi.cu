@@ -45,6 +45,9 @@ int dwf_ctx::mix_mode(int prec) const
     const int m = mixmode[prec];
     if (m == 1) return fm.structured ? 1 : 0;
     if (m == 2) return prec == DWF_F64 ? 0 : 2;
+    // default: the structured form in FP64, where the FP64 pipe bounds the hop
+    // (measured 2014 us vs 2217 us at 16^3x32, Ls 16); dense elsewhere
+    if (m < 0 && prec == DWF_F64 && fm.structured) return 1;
     return 0;
 }
 
@@ -130,6 +133,12 @@ HopArgs hop_args(dwf_ctx *h, int prec, int out_par, FieldRef in, FieldRef out, i
 HopArgs with_programs(dwf_ctx *h, int prec, const HopArgs &a0)
 {
     HopArgs a = a0;
+    {
+        const int ip = mat_id_of(h, prec, a.post), iy = mat_id_of(h, prec, a.ymat), iz = mat_id_of(h, prec, a.zmat);
+        a.post_band = ip >= 0 && h->fm.band[ip];
+        a.y_band = iy >= 0 && h->fm.band[iy];
+        a.z_band = iz >= 0 && h->fm.band[iz];
+    }
     a.mixmode = h->mix_mode(prec);
     if (a.mixmode == 1) {
         const int ip = mat_id_of(h, prec, a.post), iy = mat_id_of(h, prec, a.ymat), iz = mat_id_of(h, prec, a.zmat);
@@ -160,6 +169,7 @@ cudaError_t mix(dwf_ctx *h, int prec, FieldRef in, FieldRef out, int id, cudaStr
     m.mat = h->mat(prec, id);
     m.mixmode = h->mix_mode(prec);
     m.prog = h->prog(prec, id);
+    m.band = h->fm.band[id];
     h->launches += 1;
     return launch_mix(prec, m, st);
 }

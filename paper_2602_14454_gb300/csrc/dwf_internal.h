@@ -112,6 +112,7 @@ struct HopArgs {
     int mixmode = 0;               // 0 dense matrices, 1 structured programs (MixProg), 2 tensor-core product
     const void *post_prog = nullptr, *y_prog = nullptr, *z_prog = nullptr;
     const int *skip = nullptr;     // batched launches: the system is left untouched while *skip != 0
+    int post_band = 0, y_band = 0, z_band = 0;   // the matrix is cyclic tridiagonal (dense mode reads 3 per row)
 };
 
 struct MixArgs {
@@ -120,6 +121,7 @@ struct MixArgs {
     const void *mat = nullptr;     // [2][Ls][Ls] transposed
     int mixmode = 0;
     const void *prog = nullptr;
+    int band = 0;
 };
 
 // p = r + beta p ; phat = P p   (or with init: p = r)
@@ -132,6 +134,7 @@ struct CgUpdateArgs {
     int mixmode = 0;
     const void *prog = nullptr;
     const int *skip = nullptr;     // batched launches: the system is left untouched while *skip != 0
+    int band = 0;
 };
 
 // ------------------------------------------------------------ launchers
@@ -193,6 +196,9 @@ struct FifthMatrices {
     std::vector<double> A5[2], A5inv[2], B[2], R[2], Rinv[2];
     std::vector<double> mats[MAT_COUNT][2];
     double dee_norm2 = 0;   // spectral norm of D_ee (max over chiralities)
+    // nonzeros only on the cyclic tridiagonal (t = s - 1, s, s + 1): the dense
+    // mixing then reads three coefficients per row (P, P^T, A5 R, diagonals)
+    bool band[MAT_COUNT] = {};
     // structured form of every matrix (see MixProg); valid when `structured`
     bool structured = false;
     struct Prog {

@@ -267,54 +267,50 @@ __device__ __forceinline__ void chain_mix(const MixProg<R> *pg, T2 *tile, int ts
                                           int nthr)
 {
     R *t = reinterpret_cast<R *>(tile);
-    const R kappa = pg->kappa, a0inv = pg->a0inv, mneg = pg->mneg;
+    const R kappa = pg->kappa, a0inv = pg->a0inv, mneg = pg->mneg, s0 = pg->s0, s1 = pg->s1;
+    // Streaming form: each pass walks the chain in shared memory (u = 0 .. Ls-1
+    // in the direction of K) with O(1) registers; the d1 / d2 scalings are
+    // folded into the first read and the last write.
     for (int c = tid; c < nsites * 24; c += nthr) {
         const int jj = c / 24, k = c % 24;
         const int chi = (k >> 1) & 1;
         R *base = t + (size_t)jj * tstride * 2 + k;
         const bool up = pg->up[chi] != 0;
         const R *d1 = pg->d1[chi], *d2 = pg->d2[chi];
-        R v[LS_MAX];
-        R last = 0;
-#pragma unroll
-        for (int u = 0; u < LS_MAX; ++u)
-            if (u < Ls) {
-                const int s = up ? Ls - 1 - u : u;
-                v[u] = base[s * 24] * d1[s];
-            }
+        const int s_last = up ? 0 : Ls - 1;   // slice of u = Ls - 1
         if (pg->inv) {
             R acc = 0;
-#pragma unroll
-            for (int u = 0; u < LS_MAX; ++u)
-                if (u < Ls) acc = kappa * acc + v[u];
-            R prev = mneg * (acc * a0inv * pg->corner);
-#pragma unroll
-            for (int u = 0; u < LS_MAX; ++u)
-                if (u < Ls) {
-                    v[u] = v[u] * a0inv + kappa * prev;
-                    prev = v[u];
-                }
-        }
-        if (pg->shift) {
-#pragma unroll
-            for (int u = 0; u < LS_MAX; ++u)
-                if (u == Ls - 1) last = v[u];
-            const R s0 = pg->s0, s1 = pg->s1;
-            R prev = mneg * last;
-#pragma unroll
-            for (int u = 0; u < LS_MAX; ++u)
-                if (u < Ls) {
-                    const R tt = v[u];
-                    v[u] = s0 * tt + s1 * prev;
-                    prev = tt;
-                }
-        }
-#pragma unroll
-        for (int u = 0; u < LS_MAX; ++u)
-            if (u < Ls) {
+            for (int u = 0; u < Ls; ++u) {
                 const int s = up ? Ls - 1 - u : u;
-                base[s * 24] = v[u] * d2[s];
+                acc = kappa * acc + base[s * 24] * d1[s];
             }
+            R prev = mneg * (acc * a0inv * pg->corner);
+            const bool fin = !pg->shift;
+            for (int u = 0; u < Ls; ++u) {
+                const int s = up ? Ls - 1 - u : u;
+                const R w = base[s * 24] * d1[s] * a0inv + kappa * prev;
+                prev = w;
+                base[s * 24] = fin ? w * d2[s] : w;
+            }
+            if (fin) continue;
+            R prevs = mneg * base[s_last * 24];
+            for (int u = 0; u < Ls; ++u) {
+                const int s = up ? Ls - 1 - u : u;
+                const R tt = base[s * 24];
+                base[s * 24] = (s0 * tt + s1 * prevs) * d2[s];
+                prevs = tt;
+            }
+        } else if (pg->shift) {
+            R prevs = mneg * base[s_last * 24] * d1[s_last];
+            for (int u = 0; u < Ls; ++u) {
+                const int s = up ? Ls - 1 - u : u;
+                const R tt = base[s * 24] * d1[s];
+                base[s * 24] = (s0 * tt + s1 * prevs) * d2[s];
+                prevs = tt;
+            }
+        } else {
+            for (int u = 0; u < Ls; ++u) base[u * 24] *= d1[u] * d2[u];
+        }
     }
 }
 
@@ -424,6 +420,32 @@ __device__ __forceinline__ void mma_mix_tile(const float *mt, float *tile, int t
 
 // The tile rows must be 16-byte aligned (row stride 12 pairs, site stride a
 // multiple of 2 pairs).
+// Cyclic tridiagonal matrix: only t = s - 1, s, s + 1 contribute to row s.
+template <int NS, typename T2, typename R>
+__device__ __forceinline__ void mix_pairs_band(const R *mt, const T2 *tile, int x, int Ls, T2 (*o)[12])
+{
+    const int LL = Ls * Ls;
+    const int LsN = Ls / NS;
+#pragma unroll
+    for (int n = 0; n < NS; ++n) {
+        const int s = x + n * LsN;
+#pragma unroll
+        for (int dt = -1; dt <= 1; ++dt) {
+            int t = s + dt;
+            t = t < 0 ? t + Ls : (t >= Ls ? t - Ls : t);
+            T2 h[12];
+            ld_tile_row(tile + t * 12, h);
+            const T2 cu = p_splat(mt[t * Ls + x * NS + n]);
+            const T2 cl = p_splat(mt[LL + t * Ls + x * NS + n]);
+#pragma unroll
+            for (int p = 0; p < 12; p += 2) {
+                o[n][p] = p_fma(cu, h[p], o[n][p]);
+                o[n][p + 1] = p_fma(cl, h[p + 1], o[n][p + 1]);
+            }
+        }
+    }
+}
+
 template <int NS, typename T2, typename R>
 __device__ __forceinline__ void mix_pairs(const R *mt, const T2 *tile, int x, int Ls, T2 (*o)[12])
 {

@@ -107,7 +107,8 @@ struct TileCtx {
 // The tile must hold the input and be visible to all threads on entry.
 template <int MIX, int NS, typename T2, typename R, typename Bar>
 __device__ __forceinline__ void mix_into(const void *prog, const R *M, const TileCtx<T2> &tc, T2 *mytile,
-                                         int x, int LsN, int Ls, bool active, T2 (*o)[12], const Bar &bar)
+                                         int x, int LsN, int Ls, bool active, T2 (*o)[12], const Bar &bar,
+                                         int band = 0)
 {
     if constexpr (MIX >= 1) {
         if constexpr (MIX == 1)
@@ -127,7 +128,10 @@ __device__ __forceinline__ void mix_into(const void *prog, const R *M, const Til
             }
         }
     } else if (active) {
-        mix_pairs<NS>(M, mytile, x, Ls, o);
+        if (band)
+            mix_pairs_band<NS>(M, mytile, x, Ls, o);
+        else
+            mix_pairs<NS>(M, mytile, x, Ls, o);
     }
 }
 
@@ -153,7 +157,7 @@ __device__ __forceinline__ double hop_epilogue_core(const HopArgs &a, T2 (*acc)[
     for (int n = 0; n < NS; ++n)
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[n][k] = p_splat((R)0);
-    mix_into<MX, NS>(a.post_prog, mtx, tc, mytile, x, LsN, Ls, active, o, bar);
+    mix_into<MX, NS>(a.post_prog, mtx, tc, mytile, x, LsN, Ls, active, o, bar, a.post_band);
 
     if (a.ymode == 1) {
         if (active) {
@@ -176,7 +180,7 @@ __device__ __forceinline__ double hop_epilogue_core(const HopArgs &a, T2 (*acc)[
             }
         }
         bar.sync();
-        mix_into<MX, NS>(a.y_prog, mtx + msz, tc, mytile, x, LsN, Ls, active, o, bar);
+        mix_into<MX, NS>(a.y_prog, mtx + msz, tc, mytile, x, LsN, Ls, active, o, bar, a.y_band);
     }
 
     if (a.rin.v && active) {
@@ -227,7 +231,7 @@ __device__ __forceinline__ double hop_epilogue_core(const HopArgs &a, T2 (*acc)[
         for (int n = 0; n < NS; ++n)
 #pragma unroll
             for (int k = 0; k < 12; ++k) z[n][k] = p_splat((R)0);
-        mix_into<MX, NS>(a.z_prog, mtx + 2 * msz, tc, mytile, x, LsN, Ls, active, z, bar);
+        mix_into<MX, NS>(a.z_prog, mtx + 2 * msz, tc, mytile, x, LsN, Ls, active, z, bar, a.z_band);
         if (active) {
 #pragma unroll
             for (int n = 0; n < NS; ++n) st_pairs<P>(a.out, (size_t)site, x + n * LsN, Ls, z[n]);
@@ -295,10 +299,12 @@ __device__ __forceinline__ void hop_dir(T2 (*acc)[12], const FieldRef &in, int n
     }
 }
 
-// FP16 fields with FP16 arithmetic for the projection and the SU(3) product
-// (variant 5): the link's splats are formed once per direction for the NS
-// slices of the thread; Q is converted to FP32, scaled by the neighbour's
-// (site, s) scale and reconstructed into the FP32 accumulator.
+// FP16 fields (variant 5): the spin projection runs in FP16 arithmetic on the
+// stored half2 pairs (one rounding, at the level of the FP16 storage), only the
+// six half-spinor pairs are converted to FP32, and the SU(3) product runs in
+// FP32 for all NS slices of the thread at once, so that every link splat
+// serves NS slices; the product is scaled by the neighbour's (site, s) scale
+// and reconstructed into the FP32 accumulator.
 template <bool DAG, int D, int NS>
 __device__ __forceinline__ void hop_dir_h2(float2 (*acc)[12], const FieldRef &in, int nb, int x, int LsN, int Ls,
                                            const __half *U)
@@ -306,16 +312,13 @@ __device__ __forceinline__ void hop_dir_h2(float2 (*acc)[12], const FieldRef &in
     constexpr int MU = D & 3;
     constexpr int SIG = (D < 4 ? 1 : -1) * (DAG ? -1 : 1);
     const __half2 *Uh = reinterpret_cast<const __half2 *>(U + D * 18);
-    __half2 ur[9], ui[9], nui[9];
+    float2 u[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const __half2 u = __ldg(Uh + k);
-        ur[k] = __low2half2(u);
-        ui[k] = __high2half2(u);
-        nui[k] = __hneg2(ui[k]);
-    }
+    for (int k = 0; k < 9; ++k) u[k] = __half22float2(__ldg(Uh + k));
     const uint4 *base = reinterpret_cast<const uint4 *>(in.v) + ((size_t)nb * 3) * Ls;
     const float *sbase = in.scale + (size_t)nb * ((Ls + 3) & ~3);
+    float2 Hx[NS][3], Hy[NS][3];
+    float sc[NS];
 #pragma unroll
     for (int n = 0; n < NS; ++n) {
         const int s = x + n * LsN;
@@ -328,18 +331,41 @@ __device__ __forceinline__ void hop_dir_h2(float2 (*acc)[12], const FieldRef &in
             v[4 * g + 2] = *reinterpret_cast<const __half2 *>(&q.z);
             v[4 * g + 3] = *reinterpret_cast<const __half2 *>(&q.w);
         }
-        const float sc = __ldg(sbase + s);
-        __half2 Hx[3], Hy[3], Qx[3], Qy[3];
-        project_h2<MU, SIG>(v, Hx, Hy);
-        su3_h2(ur, ui, nui, Hx, Hy, Qx, Qy);
-        float2 Fx[3], Fy[3];
-        const float2 scp = make_float2(sc, sc);
+        sc[n] = __ldg(sbase + s);
+        __half2 hx[3], hy[3];
+        project_h2<MU, SIG>(v, hx, hy);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            Fx[a] = p_mul(__half22float2(Qx[a]), scp);
-            Fy[a] = p_mul(__half22float2(Qy[a]), scp);
+            Hx[n][a] = __half22float2(hx[a]);
+            Hy[n][a] = __half22float2(hy[a]);
         }
-        reconstruct<MU, SIG>(acc[n], Fx, Fy);
+    }
+    float2 Qx[NS][3], Qy[NS][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int n = 0; n < NS; ++n) Qx[n][a] = Qy[n][a] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float2 ur = p_splat(u[a * 3 + b].x), ui = p_splat(u[a * 3 + b].y), nui = p_splat(-u[a * 3 + b].y);
+#pragma unroll
+            for (int n = 0; n < NS; ++n) {
+                Qx[n][a] = p_fma(ur, Hx[n][b], Qx[n][a]);
+                Qx[n][a] = p_fma(nui, Hy[n][b], Qx[n][a]);
+                Qy[n][a] = p_fma(ur, Hy[n][b], Qy[n][a]);
+                Qy[n][a] = p_fma(ui, Hx[n][b], Qy[n][a]);
+            }
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NS; ++n) {
+        const float2 scp = p_splat(sc[n]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Qx[n][a] = p_mul(Qx[n][a], scp);
+            Qy[n][a] = p_mul(Qy[n][a], scp);
+        }
+        reconstruct<MU, SIG>(acc[n], Qx[n], Qy[n]);
     }
 }
 
@@ -977,12 +1003,12 @@ cudaError_t launch_direct(const HopArgs &a, int SB, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int P, bool DAG, int NS, int MIX>
+template <int P, bool DAG, int NS, int MIX, bool H2 = false>
 cudaError_t launch_direct_batch(const HopArgs *tab, int nsys, const HopArgs &a0, int SB, cudaStream_t st)
 {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(hop_batch_kernel<P, DAG, NS, MIX>,
+        cudaError_t e = cudaFuncSetAttribute(hop_batch_kernel<P, DAG, NS, MIX, H2>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -990,13 +1016,18 @@ cudaError_t launch_direct_batch(const HopArgs *tab, int nsys, const HopArgs &a0,
     const int LsN = a0.Ls / NS;
     const long long grid = (long long)((a0.Vh + SB - 1) / SB) * nsys;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    hop_batch_kernel<P, DAG, NS, MIX><<<(unsigned)grid, dim3(LsN, SB), direct_smem<P>(a0.Ls, SB), st>>>(tab, nsys);
+    hop_batch_kernel<P, DAG, NS, MIX, H2><<<(unsigned)grid, dim3(LsN, SB), direct_smem<P>(a0.Ls, SB), st>>>(tab, nsys);
     return cudaGetLastError();
 }
 
 template <int P, bool DAG>
 cudaError_t launch_batch_pd(const HopArgs *tab, int nsys, const HopArgs &a0, int NS, int SB, cudaStream_t st)
 {
+    if constexpr (P == DWF_F16) {   // FP16 arithmetic (as hop variant 5) with dense mixing
+        if (a0.mixmode == 0)
+            return NS == 2 ? launch_direct_batch<P, DAG, 2, 0, true>(tab, nsys, a0, SB, st)
+                           : launch_direct_batch<P, DAG, 1, 0, true>(tab, nsys, a0, SB, st);
+    }
     if (a0.mixmode == 1)
         return NS == 2 ? launch_direct_batch<P, DAG, 2, 1>(tab, nsys, a0, SB, st)
                        : launch_direct_batch<P, DAG, 1, 1>(tab, nsys, a0, SB, st);
@@ -1193,17 +1224,16 @@ cudaError_t launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st
 
 }  // namespace
 
-int hop_default_variant(int prec)
-{
-    (void)prec;
-    return 0;   // direct loads: fastest measured at 16^3x32, Ls 16 in every precision
-}
+// Defaults from the sweeps on 16^3x32, Ls 16 (GB300), chosen by the time to
+// solution: FP16 variant 5 with one slice per thread (0.206 s vs 0.210 s for
+// variant 0), FP32 variant 0 with two slices (110.7 us vs 116.6 us per hop),
+// FP64 variant 0 with one.
+int hop_default_variant(int prec) { return prec == DWF_F16 ? 5 : 0; }
 
 int hop_default_ns(int prec, int Ls)
 {
-    (void)prec;
-    (void)Ls;
-    return 1;
+    if (prec != DWF_F32 || (Ls & 1)) return 1;
+    return 2;
 }
 
 int hop_default_sb(int prec, int Ls, int NS)

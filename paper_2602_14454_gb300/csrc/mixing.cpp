@@ -177,6 +177,20 @@ bool build_fifth_matrices(int Ls, double M0, double mf, double b, double c, int 
         dee = std::fmax(dee, spectral_norm(A5R, n));
     }
     out.dee_norm2 = dee;
+    // banded matrices: nonzeros only at t = s - 1, s, s + 1 (cyclic), for both chiralities
+    for (int id = 0; id < MAT_COUNT; ++id) {
+        bool band = n >= 3;
+        for (int chi = 0; chi < 2 && band; ++chi)
+            for (int s = 0; s < n && band; ++s)
+                for (int t = 0; t < n; ++t) {
+                    const int d = (t - s + n) % n;
+                    if (d != 0 && d != 1 && d != n - 1 && out.mats[id][chi][(size_t)s * n + t] != 0.0) {
+                        band = false;
+                        break;
+                    }
+                }
+        out.band[id] = band;
+    }
     build_programs(n, alpha0, beta0, b, c, mf, M0, a, out);
     return true;
 }

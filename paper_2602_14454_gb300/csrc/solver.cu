@@ -115,6 +115,7 @@ IterArgs iteration_args(dwf_ctx *h, const Bufs &B, const RedArgs &ra, const RedA
     ue.mat = h->mat(P, MAT_P);
     ue.mixmode = h->mix_mode(P);
     ue.prog = h->prog(P, MAT_P);
+    ue.band = h->fm.band[MAT_P];
     ue.scal = B.cg;
 
     I.k[0] = hop_args(h, P, 1, B.ph, B.t, MAT_M);
@@ -364,7 +365,9 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
     // graph of N inner iterations
     GraphCache &G = X.graph;
     char keybuf[256];
-    std::snprintf(keybuf, sizeof keybuf, "%d/%d/%p/%p/%p/%d", ps, N, B.p.v, B.rs.v, B.xs.v, p->use_graph);
+    // the captured kernels depend on the hop configuration and mixing mode too
+    std::snprintf(keybuf, sizeof keybuf, "%d/%d/%p/%p/%p/%d/%d/%d/%d/%d", ps, N, B.p.v, B.rs.v, B.xs.v, p->use_graph,
+                  h->hop_var[ps], h->hop_ns[ps], h->hop_sb[ps], h->mix_mode(ps));
     if (p->use_graph && G.key != keybuf) {
         if (G.exec) cudaGraphExecDestroy(G.exec);
         G.exec = nullptr;
@@ -390,6 +393,8 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
             CK(launch_accum_x((double *)B.x64.v, B.xs.v, B.xp, h->Vh, h->Ls, st));
             h->launches += 1;
         }
+        // always the full FP64 recomputation: r64 -= D xs in lower precision would carry
+        // an error of about eps |D| |x|, i.e. eps kappa(D) |b~|, which stalls CG at light masses
         CK(true_residual(h, B, st));
         CgScalars n64;
         CK(cudaMemcpyAsync(&hs[1], B.n64, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));

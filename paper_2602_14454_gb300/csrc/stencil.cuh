@@ -115,11 +115,9 @@ __device__ __forceinline__ void hop_one(T2 *acc, const T2 *u, const T2 *v)
 }
 
 // ---------------------------------------------- FP16 arithmetic (half2 pairs)
-// The same projection and SU(3) product on raw FP16 pairs (no conversion of
-// the stored spinor or link): h = psi_u - sig e_mu psi_l in half2, Q = U h
-// with HFMA2.  The caller converts Q to FP32, applies the site scale and
-// reconstructs in FP32.  Inputs are normalised per (site, s) (|values| <= 1)
-// and links are unitary, so no intermediate leaves the FP16 range.
+// The same projection on raw FP16 pairs (no conversion of the stored spinor):
+// h = psi_u - sig e_mu psi_l in half2.  Inputs are normalised per (site, s)
+// (|values| <= 1), so h stays within [-2, 2].
 template <int MU, int SIG>
 __device__ __forceinline__ void project_h2(const __half2 *v, __half2 *Hx, __half2 *Hy)
 {
@@ -140,25 +138,6 @@ __device__ __forceinline__ void project_h2(const __half2 *v, __half2 *Hx, __half
             Hx[a] = __hfma2(__halves2half2(ms, ms), __lowhigh2highlow(YL), XU);
             Hy[a] = __hfma2(__halves2half2(s, s), __lowhigh2highlow(XL), YU);
         }
-    }
-}
-
-// Q = U H with the link's splats precomputed: ur[k] = (re, re), ui[k] = (im, im), nui[k] = -ui[k]
-__device__ __forceinline__ void su3_h2(const __half2 *ur, const __half2 *ui, const __half2 *nui, const __half2 *Hx,
-                                       const __half2 *Hy, __half2 *Qx, __half2 *Qy)
-{
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        __half2 qx = __float2half2_rn(0.f), qy = __float2half2_rn(0.f);
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            qx = __hfma2(ur[a * 3 + b], Hx[b], qx);
-            qx = __hfma2(nui[a * 3 + b], Hy[b], qx);
-            qy = __hfma2(ur[a * 3 + b], Hy[b], qy);
-            qy = __hfma2(ui[a * 3 + b], Hx[b], qy);
-        }
-        Qx[a] = qx;
-        Qy[a] = qy;
     }
 }
 

@@ -3,6 +3,7 @@
     python -m paper_2602_14454_gb300.workloads batch      # 24^3x48: 12 point sources x 3 masses x Ls {8,12,16}
     python -m paper_2602_14454_gb300.workloads learned    # 16^4, Ls 16: train on 256 sources, FCG vs CG
     python -m paper_2602_14454_gb300.workloads large      # 32^3x64, Ls 16: mixed precision vs FP64 CG
+    python -m paper_2602_14454_gb300.workloads alpha      # 16^3x32, Ls 16: iterations against alpha
 
 Every run uses the seeded generators of ``inputs``; times are wall clock
 around the library call after a synchronisation (device work included).
@@ -131,9 +132,36 @@ def run_large(args):
     print(json.dumps({"workload": "c5_32^3x64_ls16_mobius", "device_bytes": op.device_bytes(), **res}), flush=True)
 
 
+def run_alpha(args):
+    """CG iterations and time against Neff's alpha (Sec. 3: the paper finds the
+    fewest iterations near alpha = 0.4-0.6); alpha = 1 is the standard form."""
+    import torch
+    from . import dwf, inputs
+    w = inputs.WORKLOADS["c2_16^3x32_ls16_mobius"]
+    U = _links(w)
+    b4 = torch.from_numpy(inputs.gaussian_4d(w["dims"], w["src_seed"])).cuda()
+    rows = []
+    for alpha in (0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 1.0):
+        form = "standard" if alpha == 1.0 else "neff"
+        op = dwf.Operator(w["dims"], w["Ls"], w["M0"], w["mf"], w["b"], w["c"], form=form, alpha=alpha)
+        op.set_gauge(U)
+        b5 = op.source_5d(b4)
+        op.solve(b5, inner_prec=args.inner)
+        _sync()
+        t0 = time.perf_counter()
+        x5, s = op.solve(b5, inner_prec=args.inner)
+        _sync()
+        x4 = op.project_4d(x5)
+        rows.append({"alpha": alpha, "iterations": s["iterations"], "seconds": time.perf_counter() - t0,
+                     "true_residual": s["true_residual"], "x4_norm": float(torch.linalg.vector_norm(x4))})
+        op.close()
+    print(json.dumps({"workload": "c2_16^3x32_ls16_mobius", "inner_precision": args.inner, "scan": rows}),
+          flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["batch", "learned", "large"])
+    ap.add_argument("what", choices=["batch", "learned", "large", "alpha"])
     ap.add_argument("--inner", default="f32", choices=["f16", "f32", "f64"])
     ap.add_argument("--wave", type=int, default=0)
     ap.add_argument("--small", action="store_true", help="batch: 8^3x16 instead of 24^3x48")
@@ -144,7 +172,7 @@ def main(argv=None):
     args = ap.parse_args(argv)
     from . import build
     build.build()
-    {"batch": run_batch, "learned": run_learned, "large": run_large}[args.what](args)
+    {"batch": run_batch, "learned": run_learned, "large": run_large, "alpha": run_alpha}[args.what](args)
     return 0
 
 
