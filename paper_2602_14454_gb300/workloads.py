@@ -146,17 +146,17 @@ def run_alpha(args):
         op = dwf.Operator(w["dims"], w["Ls"], w["M0"], w["mf"], w["b"], w["c"], form=form, alpha=alpha)
         op.set_gauge(U)
         b5 = op.source_5d(b4)
-        op.solve(b5, inner_prec=args.inner)
+        op.solve(b5, inner_prec=args.inner, check_every=args.check)
         _sync()
         t0 = time.perf_counter()
-        x5, s = op.solve(b5, inner_prec=args.inner)
+        x5, s = op.solve(b5, inner_prec=args.inner, check_every=args.check)
         _sync()
         x4 = op.project_4d(x5)
         rows.append({"alpha": alpha, "iterations": s["iterations"], "seconds": time.perf_counter() - t0,
                      "true_residual": s["true_residual"], "x4_norm": float(torch.linalg.vector_norm(x4))})
         op.close()
-    print(json.dumps({"workload": "c2_16^3x32_ls16_mobius", "inner_precision": args.inner, "scan": rows}),
-          flush=True)
+    print(json.dumps({"workload": "c2_16^3x32_ls16_mobius", "inner_precision": args.inner,
+                      "check_every": args.check, "scan": rows}), flush=True)
 
 
 def main(argv=None):
@@ -169,6 +169,7 @@ def main(argv=None):
     ap.add_argument("--ntest", type=int, default=4)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--check", type=int, default=16, help="alpha: inner iterations between convergence checks")
     args = ap.parse_args(argv)
     from . import build
     build.build()
