@@ -148,12 +148,10 @@ size_t tile_smem(int Ls, int SB)
 template <int P, int MIX>
 cudaError_t launch_mix_m(const MixArgs &a, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute(mix_kernel<P, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    static unsigned long long optin = 0;
+    {
+        cudaError_t e = smem_optin(mix_kernel<P, MIX>, 200 * 1024, optin);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const int SB = tile_sb(a.Ls);
     mix_kernel<P, MIX><<<(a.Vh + SB - 1) / SB, dim3(a.Ls, SB), tile_smem<P>(a.Ls, SB), st>>>(a);
@@ -169,12 +167,10 @@ cudaError_t launch_mix_t(const MixArgs &a, cudaStream_t st)
 template <int P, int MIX>
 cudaError_t launch_cg_update_m(const CgUpdateArgs &a, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(cg_update_kernel<P, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
+    static unsigned long long optin = 0;
+    {
+        cudaError_t e = smem_optin(cg_update_kernel<P, MIX>, 200 * 1024, optin);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const int SB = tile_sb(a.Ls);
     cg_update_kernel<P, MIX><<<(a.Vh + SB - 1) / SB, dim3(a.Ls, SB), tile_smem<P>(a.Ls, SB), st>>>(a);
@@ -190,12 +186,10 @@ cudaError_t launch_cg_update_t(const CgUpdateArgs &a, cudaStream_t st)
 template <int P, int MIX>
 cudaError_t launch_cg_update_batch_m(const CgUpdateArgs *tab, int nsys, const CgUpdateArgs &a0, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(cg_update_batch_kernel<P, MIX>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    static unsigned long long optin = 0;
+    {
+        cudaError_t e = smem_optin(cg_update_batch_kernel<P, MIX>, 200 * 1024, optin);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const int SB = tile_sb(a0.Ls);
     const long long grid = (long long)((a0.Vh + SB - 1) / SB) * nsys;

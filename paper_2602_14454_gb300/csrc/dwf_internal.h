@@ -137,6 +137,21 @@ struct CgUpdateArgs {
     int band = 0;
 };
 
+// Opt a kernel in to more than 48 KB of dynamic shared memory, once per device
+// (`done` holds one bit per device ordinal < 64).
+template <typename K>
+inline cudaError_t smem_optin(K *kernel, int bytes, unsigned long long &done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (bit && (done & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done |= bit;
+    return e;
+}
+
 // ------------------------------------------------------------ launchers
 // prec: DWF_F64 / DWF_F32 / DWF_F16 (template dispatch inside)
 // var: 0 direct neighbour loads, 1 TMA-staged neighbour sites, 2 persistent warp-specialised

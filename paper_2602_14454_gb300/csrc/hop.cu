@@ -440,6 +440,15 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a)
     hop_direct_tile<P, DAG, NS, MIX, H2>(a, blockIdx.x, gridDim.x);
 }
 
+// The FP16 variant-5 kernel with one slice per thread runs faster with more
+// resident warps: capped at 64 registers (4 CTAs of 256 or 8 of 128 threads
+// per SM) the hop at 16^3x32, Ls 16 went from 96.2 us to 85.8 us.
+template <bool DAG, int MIX>
+__global__ void __launch_bounds__(256, 4) hop_kernel_h2_occ(const HopArgs a)
+{
+    hop_direct_tile<DWF_F16, DAG, 1, MIX, true>(a, blockIdx.x, gridDim.x);
+}
+
 // Batched form: one launch over nsys systems that share Ls and the CTA shape
 // (each with its own fields, matrices, scalars and reduction buffers).  CTA b
 // works on tile b / nsys of system b % nsys, so that consecutive CTAs read the
@@ -991,12 +1000,17 @@ size_t direct_smem(int Ls, int SB)
 template <int P, bool DAG, int NS, int MIX = 0, bool H2 = false>
 cudaError_t launch_direct(const HopArgs &a, int SB, cudaStream_t st)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(hop_kernel<P, DAG, NS, MIX, H2>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if constexpr (P == DWF_F16 && H2 && NS == 1) {
+        static unsigned long long optin_occ = 0;
+        cudaError_t e = smem_optin(hop_kernel_h2_occ<DAG, MIX>, 200 * 1024, optin_occ);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        hop_kernel_h2_occ<DAG, MIX><<<(a.Vh + SB - 1) / SB, dim3(a.Ls, SB), direct_smem<P>(a.Ls, SB), st>>>(a);
+        return cudaGetLastError();
+    }
+    static unsigned long long optin = 0;
+    {
+        cudaError_t e = smem_optin(hop_kernel<P, DAG, NS, MIX, H2>, 200 * 1024, optin);
+        if (e != cudaSuccess) return e;
     }
     const int LsN = a.Ls / NS;
     hop_kernel<P, DAG, NS, MIX, H2><<<(a.Vh + SB - 1) / SB, dim3(LsN, SB), direct_smem<P>(a.Ls, SB), st>>>(a);
@@ -1006,12 +1020,10 @@ cudaError_t launch_direct(const HopArgs &a, int SB, cudaStream_t st)
 template <int P, bool DAG, int NS, int MIX, bool H2 = false>
 cudaError_t launch_direct_batch(const HopArgs *tab, int nsys, const HopArgs &a0, int SB, cudaStream_t st)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(hop_batch_kernel<P, DAG, NS, MIX, H2>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    static unsigned long long optin = 0;
+    {
+        cudaError_t e = smem_optin(hop_batch_kernel<P, DAG, NS, MIX, H2>, 200 * 1024, optin);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     const int LsN = a0.Ls / NS;
     const long long grid = (long long)((a0.Vh + SB - 1) / SB) * nsys;
@@ -1043,12 +1055,10 @@ cudaError_t launch_batch_pd(const HopArgs *tab, int nsys, const HopArgs &a0, int
 template <int P, bool DAG, int NS>
 cudaError_t launch_staged(const HopArgs &a, int SB, cudaStream_t st)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(hop_staged_kernel<P, DAG, NS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    static unsigned long long optin = 0;
+    {
+        cudaError_t e = smem_optin(hop_staged_kernel<P, DAG, NS>, 220 * 1024, optin);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     size_t o1, o2, o3, o4;
     const size_t smem = staged_smem<P>(a.Ls, SB, &o1, &o2, &o3, &o4);
@@ -1075,17 +1085,12 @@ int pipe_stages(int Ls, int SB)
 template <int P, bool DAG, int NS>
 cudaError_t launch_pipe(const HopArgs &a, int SB, cudaStream_t st)
 {
-    static int attr_dev = -1, nsm = 0;
-    int dev = 0;
+    static unsigned long long optin = 0;
+    int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (attr_dev != dev) {
-        e = cudaFuncSetAttribute(hop_pipe_kernel<P, DAG, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        attr_dev = dev;
-    }
+    if ((e = smem_optin(hop_pipe_kernel<P, DAG, NS>, 220 * 1024, optin)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int LsN = a.Ls / NS;
     const int ncw = (SB * LsN + 31) / 32;
     const int threads = 32 * (1 + ncw);
@@ -1135,12 +1140,10 @@ bool choose_tile4(const int ext[4], int SB, Tile4 &best)
 template <int P, bool DAG, int NS>
 cudaError_t launch_block(const HopArgs &a, int SB, cudaStream_t st)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(hop_block_kernel<P, DAG, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
+    static unsigned long long optin = 0;
+    {
+        cudaError_t e = smem_optin(hop_block_kernel<P, DAG, NS>, 200 * 1024, optin);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     Tile4 T;
     if (!choose_tile4(a.ext, SB, T)) return launch_direct<P, DAG, NS>(a, SB, st);
@@ -1152,17 +1155,12 @@ cudaError_t launch_block(const HopArgs &a, int SB, cudaStream_t st)
 template <int P, bool DAG, int NS>
 cudaError_t launch_sweep(const HopArgs &a, int SB, cudaStream_t st)
 {
-    static int attr_dev = -1, nsm = 0;
-    int dev = 0;
+    static unsigned long long optin = 0;
+    int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (attr_dev != dev) {
-        e = cudaFuncSetAttribute(hop_sweep_kernel<P, DAG, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        attr_dev = dev;
-    }
+    if ((e = smem_optin(hop_sweep_kernel<P, DAG, NS>, 200 * 1024, optin)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int LsN = a.Ls / NS;
     const size_t smem = direct_smem<P>(a.Ls, SB);
     int per_sm = 0;

@@ -503,15 +503,12 @@ static cudaError_t launch_net_layer(dwf_ctx *h, bool adj, NetLayerArgs a, int np
 {
     const int SB = net_sb(a.C);
     const size_t smem = net_smem(a.C, SB);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(net_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    static unsigned long long optin[3] = {0, 0, 0};
+    {
+        cudaError_t e = smem_optin(net_fwd_kernel, 200 * 1024, optin[0]);
+        if (e == cudaSuccess) e = smem_optin(net_adj_kernel, 200 * 1024, optin[1]);
+        if (e == cudaSuccess) e = smem_optin(net_wgrad_kernel, 200 * 1024, optin[2]);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(net_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(net_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr = true;
     }
     dim3 grid((a.Vh + SB - 1) / SB, npar);
     h->launches += 1;

@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "dwf_internal.h"
@@ -283,9 +284,17 @@ struct SolverExtra {
     CgScalars *pinned = nullptr;
 };
 static std::map<dwf_ctx *, SolverExtra> g_extra;
+static std::mutex g_extra_mu;   // handles of different threads share the map (an entry is used by its handle only)
+
+static SolverExtra &solver_extra(dwf_ctx *h)
+{
+    std::lock_guard<std::mutex> lk(g_extra_mu);
+    return g_extra[h];
+}
 
 void dwf_solver_release(dwf_ctx *h)
 {
+    std::lock_guard<std::mutex> lk(g_extra_mu);
     auto it = g_extra.find(h);
     if (it == g_extra.end()) return;
     if (it->second.graph.exec) cudaGraphExecDestroy(it->second.graph.exec);
@@ -312,7 +321,7 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
     Bufs B;
     int rc = get_bufs(h, ps, B);
     if (rc) return rc;
-    SolverExtra &X = g_extra[h];
+    SolverExtra &X = solver_extra(h);
     if (!X.pinned) CK(cudaMallocHost(&X.pinned, sizeof(CgScalars) * 4));
     if (!X.cap) CK(cudaStreamCreateWithFlags(&X.cap, cudaStreamNonBlocking));
     CgScalars *hs = X.pinned;

@@ -91,7 +91,7 @@ def run_learned(args):
     ident = solve_all(inner_prec="f32", precond=1)
     _sync()
     t0 = time.perf_counter()
-    st = op.precond_train(b4s, epochs=args.epochs, batch=16, lr=args.lr)
+    st = op.precond_train(b4s, epochs=args.epochs, batch=16, lr=args.lr, random_pairs=args.random_pairs)
     _sync()
     ttrain = time.perf_counter() - t0
     learned = solve_all(inner_prec="f32", precond=1)
@@ -99,7 +99,8 @@ def run_learned(args):
     def summ(rows):
         return {"iterations": [r[0] for r in rows], "seconds": [round(r[1], 4) for r in rows],
                 "true_residual_max": max(r[2] for r in rows), "precond_applications": [r[3] for r in rows]}
-    out = {"workload": "c4_16^4_ls16_neff", "train_sources": ntrain, "test_sources": len(tests),
+    out = {"workload": "c4_16^4_ls16_neff", "train_sources": ntrain, "random_pairs": st["pairs"] - ntrain,
+           "test_sources": len(tests),
            "train_seconds": ttrain, "train_solve_seconds": st["solve_seconds"], "loss_first": st["loss_first"],
            "loss_last": st["loss_last"], "epochs": st["epochs"],
            "fp64_cg": summ(fp64), "mixed_f32_cg": summ(mixed), "fcg_identity": summ(ident),
@@ -169,6 +170,7 @@ def main(argv=None):
     ap.add_argument("--ntest", type=int, default=4)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--random-pairs", type=int, default=-1, help="learned: white-noise pairs (-1: as many as sources)")
     ap.add_argument("--check", type=int, default=16, help="alpha: inner iterations between convergence checks")
     args = ap.parse_args(argv)
     from . import build
