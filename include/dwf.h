@@ -233,7 +233,7 @@ long long dwf_launch_count(dwf_handle h);
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb);
 int dwf_get_hop_config(dwf_handle h, int prec, int *variant, int *ns, int *sb);
 
-/* Autotuner: times every hop configuration (all variants, ns in {1, 2},
+/* Autotuner: times every hop configuration (all variants, ns in {1, 2, 4},
  * CTAs of 64 to 256 threads, every available mixing mode) on this handle's lattice with CUDA events on
  * `stream` and keeps the fastest.  cache_path (host string, may be NULL)
  * names a text file of earlier results keyed by device name, lattice, Ls and

@@ -590,11 +590,13 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
     double best = 1e30;
     int bvar = -1, bns = 0, bsb = 0, bmix = 0;
     for (int mix = 0; mix <= 2; ++mix)
-        for (int var = 0; var <= 4; ++var)
-            for (int ns = 1; ns <= 2; ++ns) {
+        for (int var = 0; var <= 5; ++var)
+            for (int ns = 1; ns <= 4; ns *= 2) {
                 if (mix == 1 && !h->fm.structured) continue;
                 if (mix == 2 && prec == DWF_F64) continue;
                 if (mix != 0 && var != 0) continue;   // those mixings exist in the direct variant only
+                if (var == 5 && prec != DWF_F16) continue;
+                if (ns == 4 && var != 5) continue;
                 if (h->Ls % ns) continue;
                 const int LsN = h->Ls / ns;
                 for (int threads = 64; threads <= 256; threads += 64) {

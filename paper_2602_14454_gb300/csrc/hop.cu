@@ -440,13 +440,15 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a)
     hop_direct_tile<P, DAG, NS, MIX, H2>(a, blockIdx.x, gridDim.x);
 }
 
-// The FP16 variant-5 kernel with one slice per thread runs faster with more
-// resident warps: capped at 64 registers (4 CTAs of 256 or 8 of 128 threads
-// per SM) the hop at 16^3x32, Ls 16 went from 96.2 us to 85.8 us.
-template <bool DAG, int MIX>
-__global__ void __launch_bounds__(256, 4) hop_kernel_h2_occ(const HopArgs a)
+// With one slice per thread the FP16 variant-5 and the FP32 direct kernels run
+// faster with more resident warps (the gathers are latency bound): capped at
+// 64 registers (FP16: 8 CTAs of 128 threads per SM) the hop at 16^3x32, Ls 16
+// went from 96.2 us to 85.8 us, capped at 85 (FP32: 6 CTAs) from 117.8 us to
+// 106.3 us.
+template <int P, bool DAG, int MIX, bool H2>
+__global__ void __launch_bounds__(256, P == DWF_F16 ? 4 : 3) hop_kernel_occ(const HopArgs a)
 {
-    hop_direct_tile<DWF_F16, DAG, 1, MIX, true>(a, blockIdx.x, gridDim.x);
+    hop_direct_tile<P, DAG, 1, MIX, H2>(a, blockIdx.x, gridDim.x);
 }
 
 // Batched form: one launch over nsys systems that share Ls and the CTA shape
@@ -1000,11 +1002,11 @@ size_t direct_smem(int Ls, int SB)
 template <int P, bool DAG, int NS, int MIX = 0, bool H2 = false>
 cudaError_t launch_direct(const HopArgs &a, int SB, cudaStream_t st)
 {
-    if constexpr (P == DWF_F16 && H2 && NS == 1) {
+    if constexpr (NS == 1 && MIX == 0 && ((P == DWF_F16 && H2) || (P == DWF_F32 && !H2))) {
         static unsigned long long optin_occ = 0;
-        cudaError_t e = smem_optin(hop_kernel_h2_occ<DAG, MIX>, 200 * 1024, optin_occ);
+        cudaError_t e = smem_optin(hop_kernel_occ<P, DAG, MIX, H2>, 200 * 1024, optin_occ);
         if (e != cudaSuccess) return e;
-        hop_kernel_h2_occ<DAG, MIX><<<(a.Vh + SB - 1) / SB, dim3(a.Ls, SB), direct_smem<P>(a.Ls, SB), st>>>(a);
+        hop_kernel_occ<P, DAG, MIX, H2><<<(a.Vh + SB - 1) / SB, dim3(a.Ls, SB), direct_smem<P>(a.Ls, SB), st>>>(a);
         return cudaGetLastError();
     }
     static unsigned long long optin = 0;
@@ -1223,15 +1225,16 @@ cudaError_t launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st
 }  // namespace
 
 // Defaults from the sweeps on 16^3x32, Ls 16 (GB300), chosen by the time to
-// solution: FP16 variant 5 with one slice per thread (0.206 s vs 0.210 s for
-// variant 0), FP32 variant 0 with two slices (110.7 us vs 116.6 us per hop),
-// FP64 variant 0 with one.
+// solution: FP16 variant 5 (0.206 s vs 0.210 s for variant 0), FP32 and FP64
+// variant 0; one slice per thread (with the register caps above, the FP32 hop
+// takes 106.3 us against 122.8 us with two slices).
 int hop_default_variant(int prec) { return prec == DWF_F16 ? 5 : 0; }
 
 int hop_default_ns(int prec, int Ls)
 {
-    if (prec != DWF_F32 || (Ls & 1)) return 1;
-    return 2;
+    (void)prec;
+    (void)Ls;
+    return 1;
 }
 
 int hop_default_sb(int prec, int Ls, int NS)

@@ -237,6 +237,10 @@ def test_autotuner_picks_a_valid_configuration(tmp_path):
     cache = str(tmp_path / "tune.txt")
     cfg = op.autotune("f32", cache)
     assert cfg[0] in range(5) and cfg[1] in (1, 2) and cfg[2] >= 1
+    c16 = op.autotune("f16")
+    assert c16[0] in range(6) and c16[1] in (1, 2, 4) and c16[2] >= 1
+    x = ref.to_eo(inputs.gaussian_5d(dims, 16, 63), 0)
+    assert rel(to_np(op.apply(to_gpu(x), op="eo", prec="f16")), ref.d_pc(x)) < TOL["f16"]
     op2, _ = make_pair(dims, 16, 1.8, 0.01, 1.5, 0.5, "standard", 1.0, seed=61)
     assert op2.autotune("f32", cache) == cfg          # cache hit
     x = ref.to_eo(inputs.gaussian_5d(dims, 16, 62), 0)
