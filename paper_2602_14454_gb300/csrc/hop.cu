@@ -456,8 +456,8 @@ __global__ void __launch_bounds__(256, P == DWF_F16 ? 4 : 3) hop_kernel_occ(cons
 // works on tile b / nsys of system b % nsys, so that consecutive CTAs read the
 // same sites' links and neighbour indices, which then come from L2 for all
 // systems but the first.  A system whose skip flag is set is left untouched.
-template <int P, bool DAG, int NS, int MIX, bool H2 = false>
-__global__ void __launch_bounds__(256) hop_batch_kernel(const HopArgs *__restrict__ tab, int nsys)
+template <int P, bool DAG, int NS, int MIX, bool H2>
+__device__ __forceinline__ void hop_batch_body(const HopArgs *__restrict__ tab, int nsys)
 {
     __shared__ __align__(16) unsigned char abuf[sizeof(HopArgs)];
     const int sys = blockIdx.x % nsys, u = blockIdx.x / nsys;
@@ -468,6 +468,20 @@ __global__ void __launch_bounds__(256) hop_batch_kernel(const HopArgs *__restric
     const HopArgs &a = *reinterpret_cast<const HopArgs *>(abuf);
     if (a.skip && *a.skip) return;
     hop_direct_tile<P, DAG, NS, MIX, H2>(a, u, (a.Vh + blockDim.y - 1) / blockDim.y);
+}
+
+template <int P, bool DAG, int NS, int MIX, bool H2 = false>
+__global__ void __launch_bounds__(256) hop_batch_kernel(const HopArgs *__restrict__ tab, int nsys)
+{
+    hop_batch_body<P, DAG, NS, MIX, H2>(tab, nsys);
+}
+
+// the occupancy-capped form of the batched hop (see hop_kernel_occ)
+template <int P, bool DAG, int MIX, bool H2>
+__global__ void __launch_bounds__(256, P == DWF_F16 ? 4 : 3) hop_batch_kernel_occ(const HopArgs *__restrict__ tab,
+                                                                                 int nsys)
+{
+    hop_batch_body<P, DAG, 1, MIX, H2>(tab, nsys);
 }
 
 // ------------------------------------------------- variant 4: blocked tiles
@@ -1022,6 +1036,15 @@ cudaError_t launch_direct(const HopArgs &a, int SB, cudaStream_t st)
 template <int P, bool DAG, int NS, int MIX, bool H2 = false>
 cudaError_t launch_direct_batch(const HopArgs *tab, int nsys, const HopArgs &a0, int SB, cudaStream_t st)
 {
+    if constexpr (NS == 1 && MIX == 0 && ((P == DWF_F16 && H2) || (P == DWF_F32 && !H2))) {
+        static unsigned long long optin_occ = 0;
+        cudaError_t e = smem_optin(hop_batch_kernel_occ<P, DAG, MIX, H2>, 200 * 1024, optin_occ);
+        if (e != cudaSuccess) return e;
+        const long long g = (long long)((a0.Vh + SB - 1) / SB) * nsys;
+        if (g > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        hop_batch_kernel_occ<P, DAG, MIX, H2><<<(unsigned)g, dim3(a0.Ls, SB), direct_smem<P>(a0.Ls, SB), st>>>(tab, nsys);
+        return cudaGetLastError();
+    }
     static unsigned long long optin = 0;
     {
         cudaError_t e = smem_optin(hop_batch_kernel<P, DAG, NS, MIX, H2>, 200 * 1024, optin);

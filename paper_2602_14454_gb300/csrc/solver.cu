@@ -172,6 +172,15 @@ cudaError_t true_residual(dwf_ctx *h, const Bufs &B, cudaStream_t st)
     return hop(h, DWF_F64, false, a2, st);
 }
 
+// The true residual of the zero iterate: r64 = b~, whose norm the b~ hop left in
+// aux; no FP64 operator application is needed.
+cudaError_t zero_iterate_residual(dwf_ctx *h, const Bufs &B, cudaStream_t st)
+{
+    cudaError_t e = cudaMemcpyAsync(B.r64.v, B.bt.v, field_bytes(DWF_F64, h->Vh, h->Ls), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(&B.n64->last, &B.aux->last, sizeof(double), cudaMemcpyDeviceToDevice, st);
+}
+
 // rs = D^dag r64 evaluated in the inner precision; |rs|^2 -> n64->last
 cudaError_t normal_residual(dwf_ctx *h, const Bufs &B, cudaStream_t st)
 {
@@ -397,19 +406,25 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
         G.key = keybuf;
     }
 
-    auto reliable = [&](bool first) -> int {
+    double q_rate = 0, rn_last = 0;   // per-iteration reduction of the inner residual, last inner residual
+    // xzero: x64 is still zero (first update without an initial guess)
+    auto reliable = [&](bool first, bool xzero) -> int {
         if (!first) {
             CK(launch_accum_x((double *)B.x64.v, B.xs.v, B.xp, h->Vh, h->Ls, st));
             h->launches += 1;
         }
         // always the full FP64 recomputation: r64 -= D xs in lower precision would carry
         // an error of about eps |D| |x|, i.e. eps kappa(D) |b~|, which stalls CG at light masses
-        CK(true_residual(h, B, st));
+        if (xzero) {
+            CK(zero_iterate_residual(h, B, st));
+        } else {
+            CK(true_residual(h, B, st));
+            dapp += 1;
+        }
         CgScalars n64;
         CK(cudaMemcpyAsync(&hs[1], B.n64, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         n64 = hs[1];
-        dapp += 1;
         rtrue = std::sqrt(n64.last);
         if (!std::isfinite(rtrue)) return dwf_set_error(DWF_ENONFINITE, "non-finite residual");
         if (S.n_history < 64) S.history[S.n_history++] = rtrue / btn;
@@ -426,6 +441,7 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
         CK(cudaStreamSynchronize(st));
         const double rn = std::sqrt(hs[0].gamma);
         rmax = rn;
+        rn_last = rn;
         rho = (rn > 0) ? rtrue / rn : 1.0;
         nru += first ? 0 : 1;
         return DWF_OK;
@@ -436,7 +452,8 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
     cudaError_t ce = cudaSuccess;
     for (int round = 0; round < 3 && status == DWF_OK; ++round) {
         converged = false;
-        if ((rc = reliable(round == 0 && !p->use_initial_guess))) return rc;
+        const bool fresh = round == 0 && !p->use_initial_guess;
+        if ((rc = reliable(fresh, fresh))) return rc;
         // learned preconditioner: FP32 cycles of left-preconditioned CGNR, each
         // closed by an FP64 defect correction (x64 += e, r64 = b~ - D x64)
         while (p->precond && !converged) {
@@ -451,23 +468,32 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
             if ((rc = lpcg_cycle(h, B, r32, 0.01 * p->delta, p->max_iter - iters, lp_plain, iters, napp, nfall, dapp,
                                  st)))
                 return rc;
-            if ((rc = reliable(false))) return rc;
+            if ((rc = reliable(false, false))) return rc;
         }
         while (!p->precond && !converged) {
             if (iters >= p->max_iter) {
                 status = DWF_ENOTCONV;
                 break;
             }
-            if (p->use_graph) {
+            // near convergence, run only the iterations the last block's residual
+            // reduction rate predicts (no overshoot by up to check_every - 1)
+            int nrun = N;
+            if (q_rate > 0 && q_rate < 1 && rn_last > 0 && rho * rn_last > target) {
+                const double k = std::ceil(std::log(target / (rho * rn_last)) / std::log(q_rate));
+                if (k >= 1 && k < N) nrun = (int)k;
+            }
+            if (nrun == N && p->use_graph) {
                 CK(cudaGraphLaunch(G.exec, st));
                 h->launches += 5LL * N;
             } else {
-                for (int k = 0; k < N; ++k) CK(inner_iteration(h, B, st));
+                for (int k = 0; k < nrun; ++k) CK(inner_iteration(h, B, st));
             }
-            iters += N;
-            dapp += 2 * N;
+            iters += nrun;
+            dapp += 2 * nrun;
             if ((rc = read_scalars(B, hs, 1, st))) return rc;
             const double rn = std::sqrt(hs[0].gamma);
+            if (rn_last > 0 && rn > 0 && std::isfinite(rn)) q_rate = std::pow(rn / rn_last, 1.0 / nrun);
+            rn_last = rn;
             const bool bad = (hs[0].flags != 0) || !std::isfinite(rn);
             if (p->verbose)
                 std::fprintf(stderr, "[dwf] it %d |r_n| %.3e est %.3e target %.3e\n", iters, rn, rho * rn, target);
@@ -476,12 +502,12 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
                     // non-finite inner state: restart from the FP64 iterate
                     CK(launch_zero(B.xp, B.xs, h->Vh, h->Ls, st));
                     CK(launch_zero(ps, B.p, h->Vh, h->Ls, st));
-                    if ((rc = reliable(true))) return rc;
+                    if ((rc = reliable(true, false))) return rc;
                     if (nru > 200) return dwf_set_error(DWF_ENONFINITE, "inner iteration keeps producing NaN");
                     ++nru;
                     continue;
                 }
-                if ((rc = reliable(false))) return rc;
+                if ((rc = reliable(false, false))) return rc;
                 if (nru > 1000) {
                     status = DWF_ENOTCONV;
                     break;
@@ -610,7 +636,7 @@ cudaError_t source_eo(dwf_ctx *h, const void *b4, double *v5, FieldRef ve, Field
 
 // FP64 true residual; convergence test; else the normal residual in the inner
 // precision and the rescaled beta (as the reliable step of solve_impl).
-int sys_reliable(SysRun &R, bool first, CgScalars *hs, cudaStream_t st)
+int sys_reliable(SysRun &R, bool first, CgScalars *hs, cudaStream_t st, bool xzero = false)
 {
     dwf_ctx *h = R.h;
     Bufs &B = R.B;
@@ -618,10 +644,14 @@ int sys_reliable(SysRun &R, bool first, CgScalars *hs, cudaStream_t st)
         CK(launch_accum_x((double *)B.x64.v, B.xs.v, B.xp, h->Vh, h->Ls, st));
         h->launches += 1;
     }
-    CK(true_residual(h, B, st));
+    if (xzero) {
+        CK(zero_iterate_residual(h, B, st));
+    } else {
+        CK(true_residual(h, B, st));
+        R.dapp += 1;
+    }
     CK(cudaMemcpyAsync(&hs[1], B.n64, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    R.dapp += 1;
     R.rtrue = std::sqrt(hs[1].last);
     if (!std::isfinite(R.rtrue)) return dwf_set_error(DWF_ENONFINITE, "non-finite residual");
     if (R.S.n_history < 64) R.S.history[R.S.n_history++] = R.rtrue / R.btn;
@@ -679,7 +709,7 @@ int sys_prepare(SysRun &R, const void *b4, double *v5, const dwf_solve_params *p
     R.btn = std::sqrt(hs[2].last);
     R.target = p->tol * R.b5n / h->fm.dee_norm2 * 0.5;
     R.active = true;
-    int rc = sys_reliable(R, true, hs, st);
+    int rc = sys_reliable(R, true, hs, st, true);
     if (rc) return rc;
     if (R.converged) R.active = false;
     return DWF_OK;
