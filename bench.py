@@ -294,6 +294,7 @@ def main():
     # roofline of the dominant kernel (the hop), CUDA events around each launch, L2 flushed
     hop_prec = args.inner
     us, nbytes = op.time_hop(hop_prec, reps=30, flush_l2=True)
+    iteration = op.time_iteration(hop_prec, reps=10, flush_l2=True)
     pk = peaks()
     peak = pk["hbm_gbs"] if pk else 6800.0
     achieved = nbytes / (us * 1e-6) / 1e9
@@ -349,6 +350,14 @@ def main():
                              "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": hop_flops / (us * 1e-6) / 1e12 / FP32_PEAK_TFLOPS,
                              "flops_per_launch": hop_flops},
+            # the five launches of one inner CG iteration (back to back, L2 flushed before
+            # each iteration): device time and algorithmic bytes per launch
+            "iteration_kernels": {
+                "kernels": {k: {"us": round(v[0], 2), "bytes": v[1], "gbs": round(v[1] / (v[0] * 1e-6) / 1e9, 1)}
+                            for k, v in iteration.items()},
+                "us": sum(v[0] for v in iteration.values()),
+                "frac_of_hbm_peak": sum(v[1] for v in iteration.values()) /
+                                    (sum(v[0] for v in iteration.values()) * 1e-6) / 1e9 / peak},
             "cpu_baseline": base,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(b4_host.nbytes),
                     "d2h_bytes_per_step": int(b4_host.nbytes), "true_residual": s2["true_residual"]},

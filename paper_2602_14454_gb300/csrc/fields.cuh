@@ -166,6 +166,32 @@ __device__ __forceinline__ double block_sum(double v, double *wsum)
     return s;
 }
 
+// The same for FP32 per-thread values (partial sums of FP32 or FP16 fields):
+// the warp level in FP32, across warps in FP64.  FP64 arithmetic is slow on
+// GB300 (a warp-wide FP64 operation holds the SM's FP64 unit for about 16
+// cycles), so per-element work stays in FP32 and only per-warp sums are FP64.
+__device__ __forceinline__ double block_sum(float v, double *wsum)
+{
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    const int lane = tid & 31, w = tid >> 5;
+    const int nw = (nt + 31) >> 5;
+    const int wl = (w == nw - 1) ? (nt - 32 * w) : 32;
+    const unsigned mask = (wl == 32) ? 0xffffffffu : ((1u << wl) - 1u);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        float o = __shfl_down_sync(mask, v, off);
+        if (lane + off < wl) v += o;
+    }
+    if (lane == 0) wsum[w] = (double)v;
+    __syncthreads();
+    double s = 0;
+    if (tid == 0)
+        for (int i = 0; i < nw; ++i) s += wsum[i];
+    __syncthreads();
+    return s;
+}
+
 __device__ __forceinline__ void finish_reduction(double total, const RedArgs &r)
 {
     CgScalars *sc = r.scal;
@@ -207,7 +233,9 @@ __device__ __forceinline__ void finish_reduction(double total, const RedArgs &r)
 // adds them in index order and applies the scalar operation.  bid / nb: this
 // block's index among the nb blocks that reduce into r (a batched launch runs
 // one such group of blocks per system).
-__device__ __forceinline__ void grid_reduce(double v, const RedArgs &r, unsigned bid, unsigned nb)
+// v: this thread's partial sum, FP64 or FP32 (block_sum above).
+template <typename V>
+__device__ __forceinline__ void grid_reduce(V v, const RedArgs &r, unsigned bid, unsigned nb)
 {
     __shared__ double wsum[32];
     __shared__ bool is_last;
@@ -233,7 +261,8 @@ __device__ __forceinline__ void grid_reduce(double v, const RedArgs &r, unsigned
         }
     }
 }
-__device__ __forceinline__ void grid_reduce(double v, const RedArgs &r)
+template <typename V>
+__device__ __forceinline__ void grid_reduce(V v, const RedArgs &r)
 {
     grid_reduce(v, r, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
 }

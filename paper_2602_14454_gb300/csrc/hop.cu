@@ -138,7 +138,7 @@ __device__ __forceinline__ void mix_into(const void *prog, const R *M, const Til
 // acc: hop result of this thread's NS slices.  Every thread taking part in
 // `bar` must call it.  Returns this thread's contribution to |o|^2.
 template <int P, int NS, int MIX = 0, typename T2, typename R, typename Bar>
-__device__ __forceinline__ double hop_epilogue_core(const HopArgs &a, T2 (*acc)[12], const TileCtx<T2> &tc,
+__device__ __forceinline__ R hop_epilogue_core(const HopArgs &a, T2 (*acc)[12], const TileCtx<T2> &tc,
                                                     T2 *mytile, const R *mtx, int site, int x, int LsN, bool active,
                                                     const Bar &bar)
 {
@@ -210,13 +210,16 @@ __device__ __forceinline__ double hop_epilogue_core(const HopArgs &a, T2 (*acc)[
         }
     }
 
-    double nrm = 0;
+    // |o|^2 of this thread in the arithmetic precision (FP32 for FP32 and FP16
+    // fields); the grid reduction adds the per-warp sums in FP64
+    R nrm = 0;
     if (active && a.red.op != RED_NONE) {
+        T2 s2 = p_splat((R)0);
 #pragma unroll
         for (int n = 0; n < NS; ++n)
 #pragma unroll
-            for (int k = 0; k < 12; ++k)
-                nrm += (double)o[n][k].x * (double)o[n][k].x + (double)o[n][k].y * (double)o[n][k].y;
+            for (int k = 0; k < 12; ++k) s2 = p_fma(o[n][k], o[n][k], s2);
+        nrm = s2.x + s2.y;
     }
 
     if (a.zmat) {
@@ -262,7 +265,7 @@ __device__ __forceinline__ void hop_epilogue(const HopArgs &a, T2 (*acc)[12], T2
                                              int site, int x, int LsN, bool active)
 {
     const TileCtx<T2> tc = cta_tile(tile0, a.Ls);
-    const double nrm = hop_epilogue_core<P, NS, MIX>(a, acc, tc, tile0 + j * tc.tstride, mtx, site, x, LsN, active,
+    const auto nrm = hop_epilogue_core<P, NS, MIX>(a, acc, tc, tile0 + j * tc.tstride, mtx, site, x, LsN, active,
                                                 CtaBarrier());
     if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
 }
@@ -429,7 +432,7 @@ __device__ __forceinline__ void hop_direct_tile(const HopArgs &a, int u, unsigne
         gather8<P, DAG, NS, H2>(acc, a, n8, x, LsN, Ls, U);
     }
     const TileCtx<T2> tc = cta_tile(tile, Ls);
-    const double nrm = hop_epilogue_core<P, NS, MIX>(a, acc, tc, tile + j * tc.tstride, mtx, site, x, LsN, active,
+    const auto nrm = hop_epilogue_core<P, NS, MIX>(a, acc, tc, tile + j * tc.tstride, mtx, site, x, LsN, active,
                                                      CtaBarrier());
     if (a.red.op != RED_NONE) grid_reduce(nrm, a.red, u, nb_red);
 }

@@ -374,7 +374,8 @@ __global__ void __launch_bounds__(256) vdot_kernel(const float4 *x, const float4
     double s = 0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
         const float4 a = x[i], b = y[i];
-        s += (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z + (double)a.w * b.w;
+        // four products in FP32, one FP64 addition (FP64 arithmetic is slow on GB300)
+        s += (double)fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
     }
     grid_reduce(s, red);
 }
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(256) net_loss_kernel(const float4 *y, const fl
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
         const float4 a = y[i], b = x[i];
         const float4 d = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
-        acc += (double)d.x * d.x + (double)d.y * d.y + (double)d.z * d.z + (double)d.w * d.w;
+        acc += (double)fmaf(d.w, d.w, fmaf(d.z, d.z, fmaf(d.y, d.y, d.x * d.x)));
         G[i] = make_float4(s * d.x, s * d.y, s * d.z, s * d.w);
     }
     grid_reduce(acc, red);

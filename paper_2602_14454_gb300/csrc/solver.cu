@@ -1232,4 +1232,68 @@ int dwf_solve_batch(dwf_handle const *hs, const void *const *b4, void *const *x4
     return batch_impl(hs, b4, x4, n, p ? p : &def, stats, (cudaStream_t)stream);
 }
 
+int dwf_time_iteration(dwf_handle h, int prec, int reps, int flush_l2, double *us5, double *bytes5, void *stream)
+{
+    if (!h || reps < 1 || !us5 || !bytes5) return dwf_set_error(DWF_EINVAL, "bad argument");
+    if (!h->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
+    if (prec != DWF_F64 && prec != DWF_F32 && prec != DWF_F16) return dwf_set_error(DWF_EINVAL, "bad precision");
+    cudaStream_t st = (cudaStream_t)stream;
+    Bufs B;
+    int rc = get_bufs(h, prec, B);
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    const size_t flush_bytes = (size_t)512 << 20;
+    void *flush = nullptr;
+    if (flush_l2) {
+        flush = h->ws("th_flush", flush_bytes, &e);
+        if (!flush) return dwf_cuda_error(e, "workspace");
+    }
+    const FieldRef inner[] = {B.p, B.ph, B.t, B.wh, B.u, B.rs};
+    const size_t fb = field_bytes(prec, h->Vh, h->Ls), sb = scale_bytes(prec, h->Vh, h->Ls);
+    CgScalars c0;
+    std::memset(&c0, 0, sizeof c0);
+    c0.gamma = 1.0;
+    const IterArgs I = iteration_args(h, B, red(h, RED_CG_ALPHA, B.cg), red(h, RED_CG_BETA, B.cg));
+    cudaEvent_t ev[6];
+    for (auto &x : ev) CK(cudaEventCreate(&x));
+    double tot[5] = {0, 0, 0, 0, 0};
+    // two untimed iterations, then reps timed ones, each from the same synthetic
+    // state: inner fields of bytes 0x3c, FP16 scales of bytes 0x3f, x accumulator 0
+    for (int r = -2; r < reps; ++r) {
+        for (const FieldRef &f : inner) {
+            CK(cudaMemsetAsync(f.v, 0x3c, fb, st));
+            if (f.scale) CK(cudaMemsetAsync(f.scale, 0x3f, sb, st));
+        }
+        CK(cudaMemsetAsync(B.xs.v, 0, field_bytes(B.xp, h->Vh, h->Ls), st));
+        CK(cudaMemcpyAsync(B.cg, &c0, sizeof c0, cudaMemcpyHostToDevice, st));
+        if (flush) CK(cudaMemsetAsync(flush, r & 0xff, flush_bytes, st));
+        CK(cudaEventRecord(ev[0], st));
+        CK(launch_cg_update(prec, I.ue, st));
+        CK(cudaEventRecord(ev[1], st));
+        for (int k = 0; k < 4; ++k) {
+            CK(hop(h, prec, k >= 2, I.k[k], st));
+            CK(cudaEventRecord(ev[k + 2], st));
+        }
+        CK(cudaEventSynchronize(ev[5]));
+        if (r < 0) continue;
+        for (int k = 0; k < 5; ++k) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+            tot[k] += ms;
+        }
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+    // algorithmic bytes: F an inner field (with its FP16 scales), X the x accumulator, L the links
+    const double F = (double)fb + (prec == DWF_F16 ? (double)h->Vh * h->Ls * 4 : 0.0);
+    const double X = (double)field_bytes(B.xp, h->Vh, h->Ls);
+    const double L = (double)h->Vh * 8 * 18 * (prec == DWF_F64 ? 8 : (prec == DWF_F32 ? 4 : 2));
+    const double by[5] = {4 * F, 2 * F + L, 3 * F + L, 2 * F + L, 5 * F + L + 2 * X};
+    for (int k = 0; k < 5; ++k) {
+        us5[k] = 1000.0 * tot[k] / reps;
+        bytes5[k] = by[k];
+    }
+    h->launches += reps + 2;   // the p updates (hop() counts the hops)
+    return DWF_OK;
+}
+
 }  // extern "C"

@@ -30,7 +30,7 @@ STATUS = {0: "DWF_OK", 1: "DWF_EINVAL", 2: "DWF_ENOMEM", 3: "DWF_ECUDA", 4: "DWF
 EXPORTED = ["dwf_create", "dwf_destroy", "dwf_strerror", "dwf_last_error", "dwf_set_gauge",
             "dwf_apply", "dwf_apply_dag", "dwf_source_5d", "dwf_project_4d",
             "dwf_solve_params_default", "dwf_solve", "dwf_propagator_host", "dwf_solve_batch",
-            "dwf_fifth_matrix", "dwf_device_bytes", "dwf_time_hop", "dwf_launch_count",
+            "dwf_fifth_matrix", "dwf_device_bytes", "dwf_time_hop", "dwf_time_iteration", "dwf_launch_count",
             "dwf_set_hop_config", "dwf_get_hop_config", "dwf_autotune", "dwf_device_status",
             "dwf_set_mix_mode", "dwf_get_mix_mode", "dwf_apply_eo_noalloc",
             "dwf_train_params_default", "dwf_precond_init", "dwf_precond_set_weights", "dwf_precond_get_weights",
@@ -122,6 +122,7 @@ def lib():
     L.dwf_device_bytes.argtypes = [vp]
     L.dwf_device_bytes.restype = ctypes.c_size_t
     L.dwf_time_hop.argtypes = [vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]
+    L.dwf_time_iteration.argtypes = [vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]
     L.dwf_set_hop_config.argtypes = [vp, i, i, i, i]
     L.dwf_get_hop_config.argtypes = [vp, i, ip, ip, ip]
     L.dwf_device_status.argtypes = [vp, vp]
@@ -356,6 +357,16 @@ class Operator:
         check(lib().dwf_time_hop(self._h, PREC[prec], int(reps), int(bool(flush_l2)), ctypes.byref(us),
                                  ctypes.byref(by), _stream()))
         return us.value, by.value
+
+    ITERATION_KERNELS = ("p_update", "hop_a", "hop_b", "hop_c_dag", "hop_d_dag")
+
+    def time_iteration(self, prec="f16", reps=10, flush_l2=True):
+        """Per-launch device time (us) and algorithmic bytes of the five launches
+        of one inner CG iteration, as {name: (us, bytes)}."""
+        us = (ctypes.c_double * 5)()
+        by = (ctypes.c_double * 5)()
+        check(lib().dwf_time_iteration(self._h, PREC[prec], int(reps), int(bool(flush_l2)), us, by, _stream()))
+        return {k: (us[i], by[i]) for i, k in enumerate(self.ITERATION_KERNELS)}
 
 
 def solve_batch(ops, b4s, x4s=None, allow_notconv=False, **kw):

@@ -2,11 +2,14 @@
 
     python -m paper_2602_14454_gb300.hopprof --prec f16 --reps 4
     python -m paper_2602_14454_gb300.hopprof --workload c1_4^4_ls8_shamir --prec f32
+    python -m paper_2602_14454_gb300.hopprof --prec f16 --iteration   # the 5 launches of one CG iteration
 
 Builds the operator of the named workload (links from the seeded generator of
 ``inputs``), optionally pins a hop configuration or a mixing mode, and times
 ``reps`` hop launches with CUDA events, L2 flushed between them.  Prints one
 JSON line: microseconds per launch, algorithmic bytes per launch and GB/s.
+With ``--iteration`` it times the five launches of one inner CG iteration of
+the solver instead (p update and the four hops with their fused epilogues).
 """
 
 import argparse
@@ -22,6 +25,7 @@ def main(argv=None):
     ap.add_argument("--alpha", type=float, default=0.5)
     ap.add_argument("--config", default=None, help="variant,ns,sb (default: the library's choice)")
     ap.add_argument("--mix", type=int, default=None, help="fifth-direction mixing mode")
+    ap.add_argument("--iteration", action="store_true", help="time the launches of one CG iteration")
     args = ap.parse_args(argv)
 
     import torch
@@ -35,6 +39,18 @@ def main(argv=None):
         op.set_hop_config(args.prec, v, ns, sb)
     if args.mix is not None:
         op.set_mix_mode(args.prec, args.mix)
+    if args.iteration:
+        t = op.time_iteration(args.prec, reps=args.reps, flush_l2=True)
+        op.device_status()
+        tot_us = sum(v[0] for v in t.values())
+        tot_by = sum(v[1] for v in t.values())
+        print(json.dumps({"workload": args.workload, "prec": args.prec, "config": op.hop_config(args.prec),
+                          "mix": op.mix_mode(args.prec),
+                          "kernels": {k: {"us": v[0], "algorithmic_bytes": v[1], "gbs": v[1] / (v[0] * 1e-6) / 1e9}
+                                      for k, v in t.items()},
+                          "iteration_us": tot_us, "iteration_bytes": tot_by,
+                          "iteration_gbs": tot_by / (tot_us * 1e-6) / 1e9}))
+        return 0
     us, nbytes = op.time_hop(args.prec, reps=args.reps, flush_l2=True)
     op.device_status()
     print(json.dumps({"workload": args.workload, "prec": args.prec, "config": op.hop_config(args.prec),

@@ -112,6 +112,27 @@ def test_zero_source_and_nan():
     assert e.value.status == 5
 
 
+@pytest.mark.parametrize("prec", ["f16", "f32"])
+def test_time_iteration_reports_the_five_launches(c1_reference, prec):
+    """dwf_time_iteration: positive times, the documented algorithmic bytes, and a
+    solve on the same handle afterwards is unaffected (the timing overwrites the
+    solver's workspace)."""
+    U, b4, b5, x5_ref, x4_ref = c1_reference
+    op, ref = make_pair(C1["dims"], C1["Ls"], C1["M0"], C1["mf"], C1["b"], C1["c"], "neff", 0.5, U=U)
+    t = op.time_iteration(prec, reps=3)
+    assert list(t) == ["p_update", "hop_a", "hop_b", "hop_c_dag", "hop_d_dag"]
+    assert all(us > 0 for us, _ in t.values())
+    vh = int(np.prod(C1["dims"])) // 2
+    sl = vh * C1["Ls"]
+    F = sl * 24 * (2 if prec == "f16" else 4) + (sl * 4 if prec == "f16" else 0)
+    L = vh * 8 * 18 * (2 if prec == "f16" else 4)
+    X = sl * 24 * 4
+    assert [b for _, b in t.values()] == [4 * F, 2 * F + L, 3 * F + L, 2 * F + L, 5 * F + L + 2 * X]
+    x5, st = op.solve(to_gpu(b5), inner_prec=prec)
+    assert rel(ref.apply(to_np(x5)), b5) <= 1e-10
+    assert rel(ref.project_4d(to_np(x5)), x4_ref) < 1e-9
+
+
 def test_max_iter_returns_best_iterate():
     from paper_2602_14454_gb300 import dwf
     op, ref = make_pair((4, 4, 4, 4), 8, 1.8, 0.01, 1.5, 0.5, "standard", 1.0)
