@@ -292,11 +292,13 @@ int dwf_time_hop(dwf_handle h, int prec, int reps, int flush_l2, double *us_per_
 /* Profiling aid: times the five launches of one inner CG iteration of
  * dwf_solve in precision prec (DWF_F16, DWF_F32, DWF_F64) on the handle's
  * solver workspace, reset before every iteration to a synthetic state (inner
- * fields of bytes 0x3c, FP16 scales of bytes 0x3f, x accumulator 0, |r|^2 = 1).
- * k = 0: p = r + beta p and P p; k = 1, 2: the even-odd matrix D_pc (Sec. 2.3) in its two
- * hops (M H_oe, then the Q H_eo hop with the identity term, its norm and the
- * Q^T mixing of the dagger); k = 3, 4: the dagger hops, the last one fused
- * with r -= alpha D^dag D p, x += alpha p and |r|^2.  The launches of an
+ * fields of bytes 0x3c, FP16 scales of bytes 0x3f, x accumulator 0, |r|^2 = 1,
+ * alpha = 0.5).
+ * k = 0: x += alpha p of the previous iteration, p = r + beta p and P p;
+ * k = 1, 2: the even-odd matrix D_pc (Sec. 2.3) in its two hops (M H_oe, then
+ * the Q H_eo hop with the identity term, its norm and the Q^T mixing of the
+ * dagger); k = 3, 4: the dagger hops, the last one fused with
+ * r -= alpha D^dag D p and |r|^2.  The launches of an
  * iteration run back to back (as in the solver); with flush_l2 != 0 a 512 MB
  * buffer is written between iterations.  Writes us5[k], the mean device time
  * in microseconds of launch k (CUDA events on `stream`, reps iterations after

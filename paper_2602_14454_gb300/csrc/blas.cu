@@ -93,11 +93,24 @@ __device__ __forceinline__ void cg_update_tile(const CgUpdateArgs &a, int u)
     if (active) {
         T2 r[12], p[12];
         ld_pairs<P, false>(a.r, (size_t)site, s, Ls, r);
+        const double xal = a.xacc ? a.scal->alpha : 0.0;
+        if (!a.init || xal != 0.0) ld_pairs<P, false>(a.p, (size_t)site, s, Ls, p);
+        if (xal != 0.0) {
+            // x += alpha p of the previous iteration (same arithmetic as in the hop epilogue)
+            constexpr int XP = (P == DWF_F64) ? DWF_F64 : DWF_F32;
+            FieldRef xf;
+            xf.v = a.xacc;
+            T2 xv[12];
+            ld_pairs<XP, false>(xf, (size_t)site, s, Ls, xv);
+            const T2 xa = p_splat((R)xal);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) xv[k] = p_fma(xa, p[k], xv[k]);
+            st_pairs<XP>(xf, (size_t)site, s, Ls, xv);
+        }
         if (a.init) {
 #pragma unroll
             for (int k = 0; k < 12; ++k) p[k] = r[k];
         } else {
-            ld_pairs<P, false>(a.p, (size_t)site, s, Ls, p);
             const T2 be = p_splat((R)a.scal->beta);
 #pragma unroll
             for (int k = 0; k < 12; ++k) p[k] = p_fma(be, p[k], r[k]);
@@ -290,10 +303,16 @@ __global__ void convert_kernel(FieldRef in, FieldRef out, int Vh, int Ls)
     }
 }
 
-template <int XP>
-__global__ void accum_x_kernel(double *x64, void *xs, int Vh, int Ls)
+// x64 += xs + alpha p, xs = 0: the accumulated x of the inner iterations with
+// the last iteration's deferred update alpha p added in the accumulator's
+// precision (the arithmetic of the p update kernel), then folded into FP64
+template <int XP, int P>
+__global__ void accum_x_kernel(double *x64, void *xs, FieldRef pf, const double *alpha, int Vh, int Ls)
 {
+    typedef typename Tr<XP>::real R;
+    typedef typename Tr<XP>::pair T2;
     const size_t n = (size_t)Vh * Ls;
+    const R al = alpha ? (R)*alpha : (R)0;
     FieldRef fx;
     fx.v = x64;
     FieldRef fs;
@@ -301,13 +320,21 @@ __global__ void accum_x_kernel(double *x64, void *xs, int Vh, int Ls)
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
         const int s = (int)(idx % Ls);
         const size_t site = idx / Ls;
-        double2 x[12], d[12];
-        ld_pairs<DWF_F64, false>(fx, site, s, Ls, x);
+        T2 d[12];
         ld_pairs<XP, false>(fs, site, s, Ls, d);
+        if (al != (R)0) {
+            T2 q[12];
+            ld_pairs<P, false>(pf, site, s, Ls, q);
+            const T2 a2 = p_splat(al);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) d[k] = p_fma(a2, q[k], d[k]);
+        }
+        double2 x[12];
+        ld_pairs<DWF_F64, false>(fx, site, s, Ls, x);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            x[k] = p_add(x[k], d[k]);
-            d[k] = make_double2(0.0, 0.0);
+            x[k] = p_add(x[k], make_double2((double)d[k].x, (double)d[k].y));
+            d[k] = p_splat((R)0);
         }
         st_pairs<DWF_F64>(fx, site, s, Ls, x);
         st_pairs<XP>(fs, site, s, Ls, d);
@@ -550,11 +577,18 @@ cudaError_t launch_convert(int pi, FieldRef in, int po, FieldRef out, int Vh, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_accum_x(double *x64, void *xs, int xs_prec, int Vh, int Ls, cudaStream_t st)
+cudaError_t launch_accum_x(double *x64, void *xs, int xs_prec, FieldRef p, int p_prec, const double *alpha, int Vh,
+                           int Ls, cudaStream_t st)
 {
     const int g = grid_cap((size_t)Vh * Ls);
-    if (xs_prec == DWF_F64) accum_x_kernel<DWF_F64><<<g, kThreads, 0, st>>>(x64, xs, Vh, Ls);
-    else accum_x_kernel<DWF_F32><<<g, kThreads, 0, st>>>(x64, xs, Vh, Ls);
+    if (xs_prec == DWF_F64 && p_prec == DWF_F64)
+        accum_x_kernel<DWF_F64, DWF_F64><<<g, kThreads, 0, st>>>(x64, xs, p, alpha, Vh, Ls);
+    else if (xs_prec == DWF_F32 && p_prec == DWF_F32)
+        accum_x_kernel<DWF_F32, DWF_F32><<<g, kThreads, 0, st>>>(x64, xs, p, alpha, Vh, Ls);
+    else if (xs_prec == DWF_F32 && p_prec == DWF_F16)
+        accum_x_kernel<DWF_F32, DWF_F16><<<g, kThreads, 0, st>>>(x64, xs, p, alpha, Vh, Ls);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -135,6 +135,10 @@ struct CgUpdateArgs {
     const void *prog = nullptr;
     const int *skip = nullptr;     // batched launches: the system is left untouched while *skip != 0
     int band = 0;
+    // if set, xacc += scal->alpha * p (p before its update): the x update of the
+    // previous CG iteration, deferred to this launch, which reads p anyway
+    // (FP64 accumulator for FP64 fields, else FP32)
+    void *xacc = nullptr;
 };
 
 // Opt a kernel in to more than 48 KB of dynamic shared memory, once per device
@@ -186,7 +190,10 @@ cudaError_t launch_unpack_eo(int prec, FieldRef f, double *canon, int Vh, int Ls
 // precision conversion between internal fields of the same parity
 cudaError_t launch_convert(int prec_in, FieldRef in, int prec_out, FieldRef out, int Vh, int Ls, cudaStream_t st);
 // x64 += xs (xs: FP64 if xs_prec == DWF_F64 else FP32); then xs = 0
-cudaError_t launch_accum_x(double *x64, void *xs, int xs_prec, int Vh, int Ls, cudaStream_t st);
+// x64 += xs + (*alpha) p (the deferred x update, in the accumulator's
+// precision; alpha may be null), then xs = 0
+cudaError_t launch_accum_x(double *x64, void *xs, int xs_prec, FieldRef p, int p_prec, const double *alpha, int Vh,
+                           int Ls, cudaStream_t st);
 // norm^2 of an internal field, reduced with op into scal (or partial sums)
 cudaError_t launch_norm2(int prec, FieldRef f, int Vh, int Ls, const RedArgs &red, cudaStream_t st);
 cudaError_t launch_zero(int prec, FieldRef f, int Vh, int Ls, cudaStream_t st);

@@ -251,9 +251,23 @@ __device__ __forceinline__ void grid_reduce(V v, const RedArgs &r, unsigned bid,
     __syncthreads();
     if (is_last) {
         __threadfence();
+        // thread t adds the contiguous run [t per, (t + 1) per) of partials (per
+        // even, so the pairs are 16-byte loads; .cg loads read L2, where the other
+        // blocks' stores are), several loads in flight per thread; the order of
+        // the additions is fixed, so the total does not depend on which block
+        // finished last
+        const unsigned per = (((nb + nt - 1) / nt) + 1) & ~1u;
+        const unsigned lo = min(nb, (unsigned)tid * per), hi = min(nb, lo + per);
+        const double2 *p2 = reinterpret_cast<const double2 *>(r.partials);
         double acc = 0;
-        const volatile double *pp = r.partials;
-        for (unsigned i = tid; i < nb; i += nt) acc += pp[i];
+        unsigned i = lo;
+#pragma unroll 2
+        for (; i + 8 <= hi; i += 8) {
+            const double2 q0 = __ldcg(p2 + i / 2), q1 = __ldcg(p2 + i / 2 + 1);
+            const double2 q2 = __ldcg(p2 + i / 2 + 2), q3 = __ldcg(p2 + i / 2 + 3);
+            acc += ((q0.x + q0.y) + (q1.x + q1.y)) + ((q2.x + q2.y) + (q3.x + q3.y));
+        }
+        for (; i < hi; ++i) acc += __ldcg(r.partials + i);
         double tot = block_sum(acc, wsum);
         if (tid == 0) {
             finish_reduction(tot, r);

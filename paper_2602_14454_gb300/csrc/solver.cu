@@ -8,12 +8,14 @@
 //   * the final FP64 check of the full 5D residual after x_o is rebuilt.
 //
 // One inner iteration is five launches on the device, no host round trip:
-//   K_e  p = r + beta p ;  phat = P p                     (P = B R)
+//   K_e  x += alpha p (the previous iteration's step, deferred to the launch
+//        that reads p anyway) ; p = r + beta p ;  phat = P p      (P = B R)
 //   K_a  t = M H_oe phat                                  (M = B A5^-1)
 //   K_b  w = p - 1/4 Q H_eo t ; what = Q^T w ; alpha = gamma / |w|^2
 //   K_c  u = M^T gamma5-hop_oe what
-//   K_d  r -= alpha (Q^-T what - 1/4 P^T gamma5-hop_eo u) ; x += alpha p ;
+//   K_d  r -= alpha (Q^-T what - 1/4 P^T gamma5-hop_eo u) ;
 //        beta = |r|^2 / gamma ; gamma = |r|^2
+// The step of the last iteration before a reliable update is added there.
 // so that w = D p and D^dag w = Q^-T what - 1/4 P^T H^dag_eo M^T H^dag_oe what.
 // `check_every` iterations are captured once as a CUDA graph and replayed;
 // the host reads the scalars between replays.
@@ -118,6 +120,7 @@ IterArgs iteration_args(dwf_ctx *h, const Bufs &B, const RedArgs &ra, const RedA
     ue.prog = h->prog(P, MAT_P);
     ue.band = h->fm.band[MAT_P];
     ue.scal = B.cg;
+    ue.xacc = B.xs.v;   // x += alpha p of the previous iteration
 
     I.k[0] = hop_args(h, P, 1, B.ph, B.t, MAT_M);
 
@@ -137,9 +140,6 @@ IterArgs iteration_args(dwf_ctx *h, const Bufs &B, const RedArgs &ra, const RedA
     kd.ymat = h->mat(P, MAT_RA5T);
     kd.rin = B.rs;
     kd.ralpha = &B.cg->alpha;
-    kd.xacc = B.xs.v;
-    kd.xdir = B.p;
-    kd.xalpha = &B.cg->alpha;
     kd.red = rb;
     return I;
 }
@@ -410,9 +410,11 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
     // xzero: x64 is still zero (first update without an initial guess)
     auto reliable = [&](bool first, bool xzero) -> int {
         if (!first) {
-            CK(launch_accum_x((double *)B.x64.v, B.xs.v, B.xp, h->Vh, h->Ls, st));
+            CK(launch_accum_x((double *)B.x64.v, B.xs.v, B.xp, B.p, B.ps, &B.cg->alpha, h->Vh, h->Ls, st));
             h->launches += 1;
         }
+        // the deferred x update is done (or void after a restart)
+        CK(cudaMemsetAsync(&B.cg->alpha, 0, sizeof(double), st));
         // always the full FP64 recomputation: r64 -= D xs in lower precision would carry
         // an error of about eps |D| |x|, i.e. eps kappa(D) |b~|, which stalls CG at light masses
         if (xzero) {
@@ -641,9 +643,10 @@ int sys_reliable(SysRun &R, bool first, CgScalars *hs, cudaStream_t st, bool xze
     dwf_ctx *h = R.h;
     Bufs &B = R.B;
     if (!first) {
-        CK(launch_accum_x((double *)B.x64.v, B.xs.v, B.xp, h->Vh, h->Ls, st));
+        CK(launch_accum_x((double *)B.x64.v, B.xs.v, B.xp, B.p, B.ps, &B.cg->alpha, h->Vh, h->Ls, st));
         h->launches += 1;
     }
+    CK(cudaMemsetAsync(&B.cg->alpha, 0, sizeof(double), st));   // the deferred x update is done
     if (xzero) {
         CK(zero_iterate_residual(h, B, st));
     } else {
@@ -1253,6 +1256,7 @@ int dwf_time_iteration(dwf_handle h, int prec, int reps, int flush_l2, double *u
     CgScalars c0;
     std::memset(&c0, 0, sizeof c0);
     c0.gamma = 1.0;
+    c0.alpha = 0.5;   // a pending x update, as in every iteration but the first
     const IterArgs I = iteration_args(h, B, red(h, RED_CG_ALPHA, B.cg), red(h, RED_CG_BETA, B.cg));
     cudaEvent_t ev[6];
     for (auto &x : ev) CK(cudaEventCreate(&x));
@@ -1287,7 +1291,7 @@ int dwf_time_iteration(dwf_handle h, int prec, int reps, int flush_l2, double *u
     const double F = (double)fb + (prec == DWF_F16 ? (double)h->Vh * h->Ls * 4 : 0.0);
     const double X = (double)field_bytes(B.xp, h->Vh, h->Ls);
     const double L = (double)h->Vh * 8 * 18 * (prec == DWF_F64 ? 8 : (prec == DWF_F32 ? 4 : 2));
-    const double by[5] = {4 * F, 2 * F + L, 3 * F + L, 2 * F + L, 5 * F + L + 2 * X};
+    const double by[5] = {4 * F + 2 * X, 2 * F + L, 3 * F + L, 2 * F + L, 4 * F + L};
     for (int k = 0; k < 5; ++k) {
         us5[k] = 1000.0 * tot[k] / reps;
         bytes5[k] = by[k];
