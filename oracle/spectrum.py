@@ -1,0 +1,46 @@
+"""Spectrum of D^dag D for the even-odd matrix (test infrastructure only).
+
+Sec. 3.2 ("Condition number"): the paper measures the smallest and largest
+eigenvalues of D^dag D, D the even-odd preconditioned matrix of Sec. 2.3 in
+the standard or Neff form, and takes their ratio as the condition number that
+governs CG.  Here the dense matrix of D is built column by column from
+DWF.d_pc applied to unit vectors of the even half field, and numpy's Hermitian
+eigenvalue routine gives every eigenvalue of D^dag D.  Tiny lattices only
+(the dense matrix has (Ls * Vh * 12)^2 entries).
+
+Pinned in tests/test_oracle_spectrum.py by Rayleigh quotients computed with
+DWF.d_pc itself, by the alpha = 1 Neff form equalling the standard form, and
+by the similarity D^(alpha) = R^-1 D R of Sec. 2.3 (the eigenvalues of D do not
+depend on alpha, those of D^dag D do).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+
+def d_pc_dense(op) -> np.ndarray:
+    """Dense matrix of the even-odd operator D: column k = D e_k, the unit vectors
+    e_k of the even half field (Ls, Vh, 4, 3) in C order."""
+    eo = op._eo_setup()
+    shape = (op.Ls, len(eo["even"]), 4, 3)
+    n = int(np.prod(shape))
+    D = np.empty((n, n), dtype=np.complex128)
+    e = np.zeros(shape, dtype=np.complex128)
+    for k in range(n):
+        e.flat[k] = 1.0
+        D[:, k] = op.d_pc(e).ravel()
+        e.flat[k] = 0.0
+    return D
+
+
+def normal_spectrum(op) -> np.ndarray:
+    """All eigenvalues of D^dag D in ascending order."""
+    D = d_pc_dense(op)
+    return np.linalg.eigvalsh(D.conj().T @ D)
+
+
+def condition_number(op):
+    """(lambda_min, lambda_max, lambda_max / lambda_min) of D^dag D (Sec. 3.2)."""
+    ev = normal_spectrum(op)
+    return ev[0], ev[-1], ev[-1] / ev[0]
