@@ -30,7 +30,7 @@ STATUS = {0: "DWF_OK", 1: "DWF_EINVAL", 2: "DWF_ENOMEM", 3: "DWF_ECUDA", 4: "DWF
 EXPORTED = ["dwf_create", "dwf_destroy", "dwf_strerror", "dwf_last_error", "dwf_set_gauge",
             "dwf_apply", "dwf_apply_dag", "dwf_source_5d", "dwf_project_4d",
             "dwf_solve_params_default", "dwf_solve", "dwf_propagator_host", "dwf_solve_batch",
-            "dwf_fifth_matrix", "dwf_device_bytes", "dwf_time_hop", "dwf_time_iteration", "dwf_launch_count",
+            "dwf_fifth_matrix", "dwf_device_bytes", "dwf_time_hop", "dwf_time_iteration", "dwf_spectrum_bounds", "dwf_launch_count",
             "dwf_set_hop_config", "dwf_get_hop_config", "dwf_autotune", "dwf_device_status",
             "dwf_set_mix_mode", "dwf_get_mix_mode", "dwf_apply_eo_noalloc",
             "dwf_train_params_default", "dwf_precond_init", "dwf_precond_set_weights", "dwf_precond_get_weights",
@@ -123,6 +123,7 @@ def lib():
     L.dwf_device_bytes.restype = ctypes.c_size_t
     L.dwf_time_hop.argtypes = [vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]
     L.dwf_time_iteration.argtypes = [vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]
+    L.dwf_spectrum_bounds.argtypes = [vp, i, d, ctypes.c_ulonglong, ctypes.POINTER(d), ctypes.POINTER(d), ip, vp]
     L.dwf_set_hop_config.argtypes = [vp, i, i, i, i]
     L.dwf_get_hop_config.argtypes = [vp, i, ip, ip, ip]
     L.dwf_device_status.argtypes = [vp, vp]
@@ -357,6 +358,13 @@ class Operator:
         check(lib().dwf_time_hop(self._h, PREC[prec], int(reps), int(bool(flush_l2)), ctypes.byref(us),
                                  ctypes.byref(by), _stream()))
         return us.value, by.value
+
+    def spectrum_bounds(self, max_steps=2000, rtol=1e-8, seed=1):
+        """(lambda_min, lambda_max, steps) of D^dag D, D the even-odd matrix (FP64 Lanczos)."""
+        lo, hi, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        check(lib().dwf_spectrum_bounds(self._h, int(max_steps), float(rtol), int(seed), ctypes.byref(lo),
+                                        ctypes.byref(hi), ctypes.byref(n), _stream()))
+        return lo.value, hi.value, n.value
 
     ITERATION_KERNELS = ("p_update", "hop_a", "hop_b", "hop_c_dag", "hop_d_dag")
 

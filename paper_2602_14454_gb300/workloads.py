@@ -4,6 +4,7 @@
     python -m paper_2602_14454_gb300.workloads learned    # 16^4, Ls 16: train on 256 sources, FCG vs CG
     python -m paper_2602_14454_gb300.workloads large      # 32^3x64, Ls 16: mixed precision vs FP64 CG
     python -m paper_2602_14454_gb300.workloads alpha      # 16^3x32, Ls 16: iterations against alpha
+    python -m paper_2602_14454_gb300.workloads alpha --spectrum   # ... and the condition number
 
 Every run uses the seeded generators of ``inputs``; times are wall clock
 around the library call after a synchronisation (device work included).
@@ -135,7 +136,8 @@ def run_large(args):
 
 def run_alpha(args):
     """CG iterations and time against Neff's alpha (Sec. 3: the paper finds the
-    fewest iterations near alpha = 0.4-0.6); alpha = 1 is the standard form."""
+    fewest iterations near alpha = 0.4-0.6); alpha = 1 is the standard form.
+    With --spectrum also the condition number of D^dag D (Sec. 3.2)."""
     import torch
     from . import dwf, inputs
     w = inputs.WORKLOADS["c2_16^3x32_ls16_mobius"]
@@ -152,9 +154,15 @@ def run_alpha(args):
         t0 = time.perf_counter()
         x5, s = op.solve(b5, inner_prec=args.inner, check_every=args.check)
         _sync()
+        secs = time.perf_counter() - t0
         x4 = op.project_4d(x5)
-        rows.append({"alpha": alpha, "iterations": s["iterations"], "seconds": time.perf_counter() - t0,
-                     "true_residual": s["true_residual"], "x4_norm": float(torch.linalg.vector_norm(x4))})
+        row = {"alpha": alpha, "iterations": s["iterations"], "seconds": secs,
+               "true_residual": s["true_residual"], "x4_norm": float(torch.linalg.vector_norm(x4))}
+        if args.spectrum:
+            # condition number of D^dag D (Sec. 3.2), FP64 Lanczos
+            lo, hi, n = op.spectrum_bounds(max_steps=args.lanczos_steps, rtol=1e-6, seed=1)
+            row.update(lambda_min=lo, lambda_max=hi, condition_number=hi / lo, lanczos_steps=n)
+        rows.append(row)
         op.close()
     print(json.dumps({"workload": "c2_16^3x32_ls16_mobius", "inner_precision": args.inner,
                       "check_every": args.check, "scan": rows}), flush=True)
@@ -172,6 +180,8 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--random-pairs", type=int, default=-1, help="learned: white-noise pairs (-1: as many as sources)")
     ap.add_argument("--check", type=int, default=16, help="alpha: inner iterations between convergence checks")
+    ap.add_argument("--spectrum", action="store_true", help="alpha: also the extremal eigenvalues of D^dag D")
+    ap.add_argument("--lanczos-steps", type=int, default=2000, help="alpha --spectrum: Lanczos step cap")
     args = ap.parse_args(argv)
     from . import build
     build.build()
