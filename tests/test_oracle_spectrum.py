@@ -85,3 +85,27 @@ def test_alpha_changes_the_normal_spectrum_not_the_spectrum_of_d(neff05):
 def test_condition_number_is_the_ratio():
     lo, hi, k = spectrum.condition_number(make("standard", 1.0, b=1.0, c=0.0))
     assert 0 < lo < hi and k == pytest.approx(hi / lo, rel=1e-15)
+
+
+def test_second_even_odd_form_is_similar_to_d_and_alpha_free(neff05):
+    """D' = 1 - D_eo D_oo^-1 D_oe D_ee^-1 = D_ee D D_ee^-1 (same eigenvalues as D), and,
+    as Sec. 2.3 argues, the Neff factor cancels in it: D'^dag D' is the same for
+    every alpha."""
+    op, D05 = neff05
+    A05 = spectrum.alt_dense(op)
+    e_d = np.linalg.eigvals(D05)
+    e_a = np.linalg.eigvals(A05)
+    rest = list(e_a)
+    scale = np.abs(e_a).max()
+    for z in e_d:
+        k = int(np.argmin(np.abs(np.array(rest) - z)))
+        assert abs(rest[k] - z) <= 1e-8 * scale
+        rest.pop(k)
+    s05 = np.linalg.eigvalsh(A05.conj().T @ A05)
+    s10 = spectrum.normal_spectrum(make("standard", 1.0), eo_form=1)
+    s03 = spectrum.normal_spectrum(make("neff", 0.3), eo_form=1)
+    assert np.allclose(s05, s10, rtol=1e-10, atol=1e-12 * s10[-1])
+    assert np.allclose(s03, s10, rtol=1e-10, atol=1e-12 * s10[-1])
+    # and it is not the spectrum of D^dag D (the forms differ by the non-unitary D_ee)
+    s_d = np.linalg.eigvalsh(D05.conj().T @ D05)
+    assert abs(s_d[-1] / s_d[0] - s05[-1] / s05[0]) > 1e-3 * (s05[-1] / s05[0])
