@@ -312,17 +312,21 @@ int dwf_time_iteration(dwf_handle h, int prec, int reps, int flush_l2, double *u
 /* Extremal eigenvalues of D^dag D, D the even-odd matrix D_pc of the handle's
  * form (Sec. 2.3; for Neff's form the alpha-dependent one): Sec. 3.2 takes
  * lambda_max / lambda_min as the condition number that governs CG and studies
- * it against alpha.  FP64 Lanczos recurrence on the device from a
+ * it against alpha.  eo_form = 0: D = D_pc of eq. (even-odd_linear_equation),
+ * the matrix dwf_solve iterates on; eo_form = 1: D = 1 - D_eo D_oo^-1 D_oe D_ee^-1
+ * of eq. (another_even-odd_linear_equation), in which alpha cancels (Sec. 2.3).
+ * FP64 Lanczos recurrence on the device from a
  * pseudo-random start vector (SplitMix64 at counter `seed`), no restarts;
  * every 10 steps the extremal eigenvalues of the tridiagonal matrix are taken
  * (Sturm bisection on the host) and the recurrence stops when both changed by
  * at most rtol (relative) since the previous check, after at least 20 steps,
  * at max_steps, or when the Krylov space is exhausted.  Writes lambda_min,
  * lambda_max and (if steps is non-null) the steps taken.  Uses FP64 workspace
- * of seven even fields.  Errors: DWF_EINVAL (max_steps < 2, rtol <= 0, null
- * outputs), DWF_ENOGAUGE, DWF_ENONFINITE, DWF_ECUDA. */
-int dwf_spectrum_bounds(dwf_handle h, int max_steps, double rtol, unsigned long long seed, double *lambda_min,
-                        double *lambda_max, int *steps, void *stream);
+ * of up to nine even fields.  Errors: DWF_EINVAL (eo_form not 0 or 1,
+ * max_steps < 2, rtol <= 0, null outputs), DWF_ENOGAUGE, DWF_ENONFINITE,
+ * DWF_ECUDA. */
+int dwf_spectrum_bounds(dwf_handle h, int eo_form, int max_steps, double rtol, unsigned long long seed,
+                        double *lambda_min, double *lambda_max, int *steps, void *stream);
 
 /* ------------------------------------------------ learned preconditioner
  * No counterpart in the paper (it solves with plain CG).  A gauge-covariant

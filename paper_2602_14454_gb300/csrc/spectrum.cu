@@ -108,6 +108,60 @@ int normal_apply_f64(dwf_ctx *h, FieldRef x, FieldRef out, cudaStream_t st)
     return DWF_OK;
 }
 
+// out = D x, D the even-odd matrix (as dwf_apply with DWF_OP_EO_PREC), FP64
+int eo_apply_f64(dwf_ctx *h, FieldRef x, FieldRef out, cudaStream_t st)
+{
+    const int P = DWF_F64;
+    cudaError_t e = cudaSuccess;
+    FieldRef ph = h->field("lz_ph", P, &e), t = h->field("lz_t", P, &e);
+    if (!ph.v || !t.v) return dwf_cuda_error(e, "workspace");
+    CK(mix(h, P, x, ph, MAT_P, st));
+    HopArgs a1 = hop_args(h, P, 1, ph, t, MAT_M);
+    CK(hop(h, P, false, a1, st));
+    HopArgs a2 = hop_args(h, P, 0, t, out, MAT_NQ4);
+    a2.y = x;
+    a2.ymode = 1;
+    CK(hop(h, P, false, a2, st));
+    return DWF_OK;
+}
+
+// out = D^dag x, FP64
+int eo_dag_apply_f64(dwf_ctx *h, FieldRef x, FieldRef out, cudaStream_t st)
+{
+    const int P = DWF_F64;
+    cudaError_t e = cudaSuccess;
+    FieldRef wh = h->field("lz_wh", P, &e), u = h->field("lz_u", P, &e);
+    if (!wh.v || !u.v) return dwf_cuda_error(e, "workspace");
+    CK(mix(h, P, x, wh, MAT_QT, st));
+    HopArgs a1 = hop_args(h, P, 1, wh, u, MAT_MT);
+    CK(hop(h, P, true, a1, st));
+    HopArgs a2 = hop_args(h, P, 0, u, out, MAT_NPT4);
+    a2.y = x;
+    a2.ymode = 1;
+    CK(hop(h, P, true, a2, st));
+    return DWF_OK;
+}
+
+// out = D'^dag D' x for the second even-odd form of Sec. 2.3,
+// eq. (another_even-odd_linear_equation): D' = 1 - D_eo D_oo^-1 D_oe D_ee^-1 =
+// D_ee D D_ee^-1 with D_ee = A5 R and D_ee^-1 = Q, so that
+// D'^dag D' = Q^T D^dag (A5 R)^T (A5 R) D Q (the mixings are real per chirality)
+int alt_normal_apply_f64(dwf_ctx *h, FieldRef x, FieldRef out, cudaStream_t st)
+{
+    const int P = DWF_F64;
+    cudaError_t e = cudaSuccess;
+    FieldRef a = h->field("lz_a", P, &e), b = h->field("lz_b", P, &e);
+    if (!a.v || !b.v) return dwf_cuda_error(e, "workspace");
+    int rc;
+    CK(mix(h, P, x, a, MAT_Q, st));
+    if ((rc = eo_apply_f64(h, a, b, st))) return rc;
+    CK(mix(h, P, b, a, MAT_A5R, st));
+    CK(mix(h, P, a, b, MAT_RA5T, st));
+    if ((rc = eo_dag_apply_f64(h, b, a, st))) return rc;
+    CK(mix(h, P, a, out, MAT_QT, st));
+    return DWF_OK;
+}
+
 // number of eigenvalues of the symmetric tridiagonal matrix (diagonal a,
 // off-diagonal b[i] between rows i and i + 1) below x: the sign changes of
 // the Sturm sequence, i.e. the negative pivots of the LDL^T factorisation of T - x
@@ -148,10 +202,10 @@ double tridiag_eig(const std::vector<double> &a, const std::vector<double> &b, i
 
 }  // namespace
 
-extern "C" int dwf_spectrum_bounds(dwf_handle h, int max_steps, double rtol, unsigned long long seed,
+extern "C" int dwf_spectrum_bounds(dwf_handle h, int eo_form, int max_steps, double rtol, unsigned long long seed,
                                    double *lambda_min, double *lambda_max, int *steps, void *stream)
 {
-    if (!h || max_steps < 2 || !(rtol > 0) || !lambda_min || !lambda_max)
+    if (!h || (eo_form != 0 && eo_form != 1) || max_steps < 2 || !(rtol > 0) || !lambda_min || !lambda_max)
         return dwf_set_error(DWF_EINVAL, "bad argument");
     if (!h->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
     cudaStream_t st = (cudaStream_t)stream;
@@ -193,7 +247,7 @@ extern "C" int dwf_spectrum_bounds(dwf_handle h, int max_steps, double rtol, uns
     int k = 0;
     for (k = 0; k < max_steps; ++k) {
         // w = A v1 - beta_k v0 ; alpha = (w, v1) ; w -= alpha v1 ; beta = |w|
-        if ((rc = normal_apply_f64(h, v1, w, st))) return rc;
+        if ((rc = eo_form ? alt_normal_apply_f64(h, v1, w, st) : normal_apply_f64(h, v1, w, st))) return rc;
         if (k > 0 && (rc = axpby(-be.back(), v0, 1.0, w))) return rc;
         double a;
         if ((rc = dot(w, v1, a))) return rc;

@@ -123,7 +123,7 @@ def lib():
     L.dwf_device_bytes.restype = ctypes.c_size_t
     L.dwf_time_hop.argtypes = [vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]
     L.dwf_time_iteration.argtypes = [vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]
-    L.dwf_spectrum_bounds.argtypes = [vp, i, d, ctypes.c_ulonglong, ctypes.POINTER(d), ctypes.POINTER(d), ip, vp]
+    L.dwf_spectrum_bounds.argtypes = [vp, i, i, d, ctypes.c_ulonglong, ctypes.POINTER(d), ctypes.POINTER(d), ip, vp]
     L.dwf_set_hop_config.argtypes = [vp, i, i, i, i]
     L.dwf_get_hop_config.argtypes = [vp, i, ip, ip, ip]
     L.dwf_device_status.argtypes = [vp, vp]
@@ -359,11 +359,12 @@ class Operator:
                                  ctypes.byref(by), _stream()))
         return us.value, by.value
 
-    def spectrum_bounds(self, max_steps=2000, rtol=1e-8, seed=1):
-        """(lambda_min, lambda_max, steps) of D^dag D, D the even-odd matrix (FP64 Lanczos)."""
+    def spectrum_bounds(self, max_steps=2000, rtol=1e-8, seed=1, eo_form=0):
+        """(lambda_min, lambda_max, steps) of D^dag D, D the even-odd matrix (FP64 Lanczos);
+        eo_form 1: the second even-odd form 1 - D_eo D_oo^-1 D_oe D_ee^-1."""
         lo, hi, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
-        check(lib().dwf_spectrum_bounds(self._h, int(max_steps), float(rtol), int(seed), ctypes.byref(lo),
-                                        ctypes.byref(hi), ctypes.byref(n), _stream()))
+        check(lib().dwf_spectrum_bounds(self._h, int(eo_form), int(max_steps), float(rtol), int(seed),
+                                        ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(n), _stream()))
         return lo.value, hi.value, n.value
 
     ITERATION_KERNELS = ("p_update", "hop_a", "hop_b", "hop_c_dag", "hop_d_dag")

@@ -162,6 +162,9 @@ def run_alpha(args):
             # condition number of D^dag D (Sec. 3.2), FP64 Lanczos
             lo, hi, n = op.spectrum_bounds(max_steps=args.lanczos_steps, rtol=1e-6, seed=1)
             row.update(lambda_min=lo, lambda_max=hi, condition_number=hi / lo, lanczos_steps=n)
+            # the second even-odd form, in which alpha cancels (Sec. 2.3): a control
+            lo, hi, n = op.spectrum_bounds(max_steps=args.lanczos_steps, rtol=1e-6, seed=1, eo_form=1)
+            row.update(condition_number_second_form=hi / lo)
         rows.append(row)
         op.close()
     print(json.dumps({"workload": "c2_16^3x32_ls16_mobius", "inner_precision": args.inner,

@@ -31,6 +31,19 @@ def test_extremal_eigenvalues_match_the_dense_oracle(form, alpha, b, c):
     assert abs(hi / hi_ref - 1) < 1e-8
 
 
+@pytest.mark.parametrize("form,alpha", [("standard", 1.0), ("neff", 0.5), ("neff", 0.3)])
+def test_second_even_odd_form_matches_the_dense_oracle(form, alpha):
+    """eo_form 1 (eq. another_even-odd_linear_equation): the oracle's spectrum, which
+    does not depend on alpha."""
+    from oracle import spectrum
+    U = inputs.random_links(TINY, 0.5, 311)
+    op, ref = make_pair(TINY, 4, 1.8, 0.05, 1.5, 0.5, form, alpha, U=U)
+    lo_ref, hi_ref, _ = spectrum.condition_number(ref, eo_form=1)
+    lo, hi, steps = op.spectrum_bounds(max_steps=1500, rtol=1e-13, seed=7, eo_form=1)
+    assert abs(lo / lo_ref - 1) < 1e-8
+    assert abs(hi / hi_ref - 1) < 1e-8
+
+
 def test_bounds_do_not_depend_on_the_start_vector():
     dims, Ls = (4, 4, 4, 4), 8
     op, ref = make_pair(dims, Ls, 1.8, 0.04, 1.5, 0.5, "neff", 0.5, seed=1001)
@@ -48,3 +61,5 @@ def test_bad_arguments():
     assert e.value.status == 1
     with pytest.raises(dwf.DwfError):
         op.spectrum_bounds(rtol=0.0)
+    with pytest.raises(dwf.DwfError):
+        op.spectrum_bounds(eo_form=2)
