@@ -209,6 +209,21 @@ int dwf_solve_batch(dwf_handle const *hs, const void *const *b4, void *const *x4
  * chirality: 0 for P_+ components, 1 for P_-. */
 int dwf_fifth_matrix(dwf_handle h, int which, int chirality, double *out_host);
 
+/* The same without a handle or a device (host code only): the matrices for
+ * the parameters of dwf_create, FP64 row-major Ls x Ls.  which 0..3 as above,
+ * or 16 + k for the k-th per-chirality matrix the kernels apply in the fifth
+ * direction (Sec. 2.3 even-odd algebra; B = b + cK, R the Neff factor):
+ *   k = 0 P = B R, 1 P^T, 2 Q = R^-1 A5^-1 (D_ee^-1), 3 Q^T, 4 M = B A5^-1,
+ *   5 M^T, 6 A5 R (D_ee), 7 (A5 R)^T, 8 -1/2, 9 -1/2 R B^T, 10 -1/4 Q,
+ *   11 -1/4 P^T, 12 1, 13 +1/2 Q, 14 c/2 (hop part of 1 - c D_W),
+ *   15 1 - c (4 - M0) (its diagonal part).
+ * *banded (if non-null): 1 when every nonzero of the matrix lies on the cyclic
+ * tridiagonal, which the kernels then read as three coefficients per row
+ * (always 0 for which 0..3).  Errors: DWF_EINVAL (Ls outside 2..32, form,
+ * which, chirality, null out, or A5 singular). */
+int dwf_fifth_matrix_host(int Ls, double M0, double mf, double b, double c, int form, double alpha, int which,
+                          int chirality, double *out_host, int *banded);
+
 /* Number of device bytes the handle holds. */
 size_t dwf_device_bytes(dwf_handle h);
 

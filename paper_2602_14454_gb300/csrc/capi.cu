@@ -495,6 +495,32 @@ int dwf_fifth_matrix(dwf_handle h, int which, int chi, double *out)
     return DWF_OK;
 }
 
+int dwf_fifth_matrix_host(int Ls, double M0, double mf, double b, double c, int form, double alpha, int which,
+                          int chi, double *out, int *banded)
+{
+    if (Ls < 2 || Ls > LS_MAX || (form != DWF_STANDARD && form != DWF_NEFF) || chi < 0 || chi > 1 || !out)
+        return dwf_set_error(DWF_EINVAL, "bad argument");
+    if (!(which >= 0 && which <= 3) && !(which >= 16 && which < 16 + MAT_COUNT))
+        return dwf_set_error(DWF_EINVAL, "bad matrix id");
+    if (!std::isfinite(M0) || !std::isfinite(mf) || !std::isfinite(b) || !std::isfinite(c) ||
+        (form == DWF_NEFF && !(alpha != 0.0 && std::isfinite(alpha))))
+        return dwf_set_error(DWF_EINVAL, "non-finite parameter or alpha = 0");
+    FifthMatrices fm;
+    std::string err;
+    if (!build_fifth_matrices(Ls, M0, mf, b, c, form, alpha, fm, err)) return dwf_set_error(DWF_EINVAL, err.c_str());
+    const std::vector<double> *m = nullptr;
+    switch (which) {
+    case 0: m = &fm.A5[chi]; break;
+    case 1: m = &fm.A5inv[chi]; break;
+    case 2: m = &fm.B[chi]; break;
+    case 3: m = &fm.R[chi]; break;
+    default: m = &fm.mats[which - 16][chi]; break;
+    }
+    std::memcpy(out, m->data(), m->size() * sizeof(double));
+    if (banded) *banded = which >= 16 ? (fm.band[which - 16] ? 1 : 0) : 0;
+    return DWF_OK;
+}
+
 size_t dwf_device_bytes(dwf_handle h) { return h ? h->bytes : 0; }
 
 int dwf_device_status(dwf_handle h, void *stream)

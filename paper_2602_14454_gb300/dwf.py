@@ -30,7 +30,7 @@ STATUS = {0: "DWF_OK", 1: "DWF_EINVAL", 2: "DWF_ENOMEM", 3: "DWF_ECUDA", 4: "DWF
 EXPORTED = ["dwf_create", "dwf_destroy", "dwf_strerror", "dwf_last_error", "dwf_set_gauge",
             "dwf_apply", "dwf_apply_dag", "dwf_source_5d", "dwf_project_4d",
             "dwf_solve_params_default", "dwf_solve", "dwf_propagator_host", "dwf_solve_batch",
-            "dwf_fifth_matrix", "dwf_device_bytes", "dwf_time_hop", "dwf_time_iteration", "dwf_spectrum_bounds", "dwf_launch_count",
+            "dwf_fifth_matrix", "dwf_fifth_matrix_host", "dwf_device_bytes", "dwf_time_hop", "dwf_time_iteration", "dwf_spectrum_bounds", "dwf_launch_count",
             "dwf_set_hop_config", "dwf_get_hop_config", "dwf_autotune", "dwf_device_status",
             "dwf_set_mix_mode", "dwf_get_mix_mode", "dwf_apply_eo_noalloc",
             "dwf_train_params_default", "dwf_precond_init", "dwf_precond_set_weights", "dwf_precond_get_weights",
@@ -119,6 +119,7 @@ def lib():
     L.dwf_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i,
                                   ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), vp]
     L.dwf_fifth_matrix.argtypes = [vp, i, i, ctypes.POINTER(ctypes.c_double)]
+    L.dwf_fifth_matrix_host.argtypes = [i, d, d, d, d, i, d, i, i, ctypes.POINTER(ctypes.c_double), ip]
     L.dwf_device_bytes.argtypes = [vp]
     L.dwf_device_bytes.restype = ctypes.c_size_t
     L.dwf_time_hop.argtypes = [vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]
@@ -376,6 +377,21 @@ class Operator:
         by = (ctypes.c_double * 5)()
         check(lib().dwf_time_iteration(self._h, PREC[prec], int(reps), int(bool(flush_l2)), us, by, _stream()))
         return {k: (us[i], by[i]) for i, k in enumerate(self.ITERATION_KERNELS)}
+
+
+KERNEL_MATRICES = ("P", "PT", "Q", "QT", "M", "MT", "A5R", "RA5T", "NHALF", "NHALF_RBT", "NQ4", "NPT4", "ID",
+                   "HALF_Q", "SRC_POST", "SRC_Y")
+
+
+def fifth_matrix_host(Ls, M0, mf, b, c, form="standard", alpha=1.0, which=0, chirality=0):
+    """(matrix, banded) without a device: which 0..3 (A5, A5^-1, B, R) or a name of
+    KERNEL_MATRICES (the per-chirality matrices the kernels apply)."""
+    w = which if isinstance(which, int) else 16 + KERNEL_MATRICES.index(which)
+    out = (ctypes.c_double * (Ls * Ls))()
+    band = ctypes.c_int()
+    check(lib().dwf_fifth_matrix_host(int(Ls), float(M0), float(mf), float(b), float(c), FORM[form], float(alpha),
+                                      int(w), int(chirality), out, ctypes.byref(band)))
+    return np.array(out, dtype=np.float64).reshape(Ls, Ls), bool(band.value)
 
 
 def solve_batch(ops, b4s, x4s=None, allow_notconv=False, **kw):
