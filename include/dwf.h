@@ -92,9 +92,12 @@ int dwf_destroy(dwf_handle h);
 const char *dwf_strerror(int status);
 const char *dwf_last_error(void);
 
-/* Copy the links (device, layout above) into the handle: the boundary phases
- * are folded in and an internal copy in FP64, FP32 and FP16 is made for each
- * output parity.  Must be called before any operator call. */
+/* Copy the links U_mu(x) of the 4D Wilson kernel, eq. (Wilson_matrix)
+ * (device, layout above, SU(3) expected but not checked) into the handle: the
+ * boundary phases are folded in and an internal copy in FP64, FP32 and FP16
+ * is made for each output parity; the caller's buffer is not kept.  Must be
+ * called before any operator call; calling it again replaces the links.
+ * Errors: DWF_EINVAL (NULL handle or U, U not 16-byte aligned), DWF_ECUDA. */
 int dwf_set_gauge(dwf_handle h, const void *U, void *stream);
 
 /*
@@ -103,18 +106,22 @@ int dwf_set_gauge(dwf_handle h, const void *U, void *stream);
  * whole matrix of Sec. 2.2 or 2.3).  op = DWF_OP_EO_PREC: in/out are EO 5D
  * fields and D is the even-odd preconditioned matrix.  in and out must not
  * overlap.  Input and output are always complex double; prec selects the
- * device arithmetic.
+ * device arithmetic.  Errors: DWF_EINVAL (NULL handle or vector, unaligned
+ * vector, bad prec or op), DWF_ENOGAUGE, DWF_ECUDA.
  */
 int dwf_apply(dwf_handle h, int op, int prec, const void *in, void *out, void *stream);
 int dwf_apply_dag(dwf_handle h, int op, int prec, const void *in, void *out, void *stream);
 
 /* b5 = (-D_-) P^dag (0, ..., 0, b4)^T  (Sec. 2.3, with D_- = diag_s(c D_W - 1)):
  * b5(s=1) = (1 - c D_W) P_+ b4, b5(s=Ls) = (1 - c D_W) P_- b4, zero elsewhere.
- * b4 is a 4D field, b5 a 5D field.  FP64. */
+ * b4 is a 4D field, b5 a 5D field (device, caller-owned).  FP64.
+ * Errors: DWF_EINVAL (NULL or unaligned vector), DWF_ENOGAUGE, DWF_ECUDA. */
 int dwf_source_5d(dwf_handle h, const void *b4, void *b5, void *stream);
 
 /* x4 = [P^dag x5]_{s=1} = P_- x5(s=1) + P_+ x5(s=Ls)  (Sec. 2.3 and the 4D
- * quark field of Sec. 2.2).  The same formula holds for both forms. */
+ * quark field of Sec. 2.2).  The same formula holds for both forms.  x5 a 5D
+ * field, x4 a 4D field (device, caller-owned), FP64.
+ * Errors: DWF_EINVAL (NULL handle or vector, unaligned vector), DWF_ECUDA. */
 int dwf_project_4d(dwf_handle h, const void *x5, void *x4, void *stream);
 
 /* ---------------------------------------------------------------- solver */
@@ -163,17 +170,24 @@ void dwf_solve_params_default(dwf_solve_params *p);
  * D the even-odd matrix (inner precision as asked, FP64 reliable updates);
  * x_o = D_oo^-1 (b_o - D_oe x_e); final FP64 residual of the full system
  * (Sec. 2.3).  x5 is the initial guess when p->use_initial_guess is set,
- * otherwise the initial guess is zero.  stats may be NULL.
- * DWF_ENOTCONV: x5 holds the best iterate and stats are filled.
+ * otherwise the initial guess is zero.  stats may be NULL.  b5 and x5 are
+ * caller-owned device 5D fields (16-byte aligned, not overlapping).
+ * Errors: DWF_EINVAL (NULL or unaligned vector, bad parameters, precond
+ * without a network or with inner_prec != DWF_F32), DWF_ENOGAUGE,
+ * DWF_ENONFINITE (NaN/Inf in b5 or in the iteration), DWF_EBREAKDOWN,
+ * DWF_ECUDA, DWF_ENOTCONV (x5 holds the best iterate and stats are filled).
  */
 int dwf_solve(dwf_handle h, const void *b5, void *x5, const dwf_solve_params *p,
               dwf_solve_stats *stats, void *stream);
 
 /*
- * The user-level propagator call with HOST buffers: x4 = [P^dag D^-1 b5(b4)]_{s=1}.
+ * The user-level propagator call with HOST buffers: x4 = [P^dag D^-1 b5(b4)]_{s=1}
+ * (Sec. 2.3: the 4D quark propagator from a 4D source).
  * b4_host and x4_host are host pointers to 4D fields (complex double); the
  * call copies b4 to the device, builds b5, solves, projects and copies x4
  * back, all on the given stream, and synchronises before returning.
+ * Errors: as dwf_solve (DWF_EINVAL also for NULL host pointers); on
+ * DWF_ENOTCONV x4_host holds the projection of the best iterate.
  */
 int dwf_propagator_host(dwf_handle h, const double *b4_host, double *x4_host,
                         const dwf_solve_params *p, dwf_solve_stats *stats, void *stream);
@@ -206,7 +220,9 @@ int dwf_solve_batch(dwf_handle const *hs, const void *const *b4, void *const *x4
 /* Host copy of one per-chirality fifth-direction matrix of the handle, FP64,
  * row-major Ls x Ls.  which: 0 A5 = D_ee restricted to one chirality,
  * 1 A5^-1, 2 B = b + c K, 3 R (Neff factor, identity for DWF_STANDARD).
- * chirality: 0 for P_+ components, 1 for P_-. */
+ * chirality: 0 for P_+ components, 1 for P_-.  (Sec. 2.2-2.3; out_host holds
+ * Ls*Ls doubles.)  Errors: DWF_EINVAL (NULL handle or out, bad which or
+ * chirality). */
 int dwf_fifth_matrix(dwf_handle h, int which, int chirality, double *out_host);
 
 /* The same without a handle or a device (host code only): the matrices for
@@ -224,11 +240,12 @@ int dwf_fifth_matrix(dwf_handle h, int which, int chirality, double *out_host);
 int dwf_fifth_matrix_host(int Ls, double M0, double mf, double b, double c, int form, double alpha, int which,
                           int chirality, double *out_host, int *banded);
 
-/* Number of device bytes the handle holds. */
+/* Number of device bytes the handle holds (0 for a NULL handle). */
 size_t dwf_device_bytes(dwf_handle h);
 
 /* Number of device kernels launched through the handle since its creation
- * (every entry point counts the kernels it launches, graph replays included). */
+ * (every entry point counts the kernels it launches, graph replays included;
+ * 0 for a NULL handle). */
 long long dwf_launch_count(dwf_handle h);
 
 /* Configuration of the hop kernel in precision prec: variant 0 loads the
@@ -244,7 +261,10 @@ long long dwf_launch_count(dwf_handle h);
  * slices; ns fifth-direction
  * slices per thread (1, 2 when it divides Ls, 4 for variant 5); sb
  * four-dimensional sites per CTA.  -1 / 0 select the built-in defaults.
- * Variants 0-4 have no numerical effect beyond summation order. */
+ * Variants 0-4 have no numerical effect beyond summation order.
+ * Errors: DWF_EINVAL (NULL handle or pointer, bad prec, variant outside
+ * -1..5, ns not 0, 1, 2 or (variant 5) 4 dividing Ls, sb making a CTA of more
+ * than 256 threads). */
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb);
 int dwf_get_hop_config(dwf_handle h, int prec, int *variant, int *ns, int *sb);
 
@@ -253,7 +273,7 @@ int dwf_get_hop_config(dwf_handle h, int prec, int *variant, int *ns, int *sb);
  * `stream` and keeps the fastest.  cache_path (host string, may be NULL)
  * names a text file of earlier results keyed by device name, lattice, Ls and
  * precision: a hit skips the timing, a miss appends the new result.  Needs
- * the gauge field. */
+ * the gauge field.  Errors: DWF_EINVAL, DWF_ENOGAUGE, DWF_ECUDA. */
 int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream);
 
 /* Fifth-direction mixing in precision prec: 0 applies the dense per-chirality
@@ -265,9 +285,11 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream);
  * and FP16 only).  Modes 1 and 2 are compiled for the direct hop variant,
  * which they then select (mode 2 needs CTAs of at least 32 threads, else the
  * dense form runs); the vector kernels outside the hop keep the dense form in
- * mode 2.  -1 restores the default (dense).  mode 1 is refused when the
- * handle's parameters make the structured form unavailable
- * (|kappa| = |beta0/alpha0| >= 0.95), mode 2 for prec = DWF_F64. */
+ * mode 2.  -1 restores the default (dense for DWF_F32 and DWF_F16, the
+ * structured form for DWF_F64 when it is available).  mode 1 is refused when
+ * the handle's parameters make the structured form unavailable
+ * (|kappa| = |beta0/alpha0| >= 0.95), mode 2 for prec = DWF_F64; both with
+ * DWF_EINVAL, as a NULL handle or pointer and a bad prec or mode. */
 int dwf_set_mix_mode(dwf_handle h, int prec, int mode);
 int dwf_get_mix_mode(dwf_handle h, int prec, int *mode);
 
@@ -300,7 +322,10 @@ int dwf_device_status(dwf_handle h, void *stream);
  * (the dominant kernel of every application of D) `reps` times on stream and
  * writes the mean device time per launch in microseconds, measured with CUDA
  * events on that stream, together with the kernel's algorithmic bytes per
- * launch (inputs read once, outputs written once, links read once). */
+ * launch (inputs read once, outputs written once, links read once).  With
+ * flush_l2 != 0 a 512 MB buffer is written before every timed launch.
+ * Errors: DWF_EINVAL (reps < 1, NULL outputs, bad prec), DWF_ENOGAUGE,
+ * DWF_ECUDA. */
 int dwf_time_hop(dwf_handle h, int prec, int reps, int flush_l2, double *us_per_launch,
                  double *bytes_per_launch, void *stream);
 
@@ -398,22 +423,32 @@ typedef struct {
 void dwf_train_params_default(dwf_train_params *p);
 
 /* Identity network (self weights 1 on every channel and chirality) plus
- * seeded normal noise of the given scale. */
+ * seeded normal noise of the given scale.  Errors: DWF_EINVAL (NULL handle,
+ * layers outside 1..8, Ls > 16), DWF_ENOGAUGE, DWF_ECUDA. */
 int dwf_precond_init(dwf_handle h, int layers, unsigned long long seed, double noise);
-/* Host weights in, FP64 (layout above); the Adam state is reset. */
+/* Host weights in, FP64 (layout above); the Adam state is reset.
+ * Errors: DWF_EINVAL (NULL pointer, layers outside 1..8, Ls > 16),
+ * DWF_ENOGAUGE, DWF_ECUDA. */
 int dwf_precond_set_weights(dwf_handle h, int layers, const double *w);
 /* Host weights out: the FP64 master copy, or (compute_copy != 0) the
- * BF16-rounded values the kernels use. */
+ * BF16-rounded values the kernels use.  Errors: DWF_EINVAL (NULL pointer, no
+ * network, layers different from the network's), DWF_ECUDA. */
 int dwf_precond_get_weights(dwf_handle h, int layers, int compute_copy, double *w);
 /* out = N in (which = 0), N^dag in (1) or M in = N N^dag in (2) on EO fields
- * (device, complex double, layout of DWF_OP_EO_PREC); FP32 kernels. */
+ * (device, complex double, layout of DWF_OP_EO_PREC); FP32 kernels.
+ * Errors: DWF_EINVAL (no network, bad which, NULL or unaligned vector),
+ * DWF_ENOGAUGE, DWF_ECUDA. */
 int dwf_precond_apply(dwf_handle h, int which, const void *in, void *out, void *stream);
 /* Loss over npairs pairs (EO fields b[k], x[k], device) and its gradient with
  * respect to the weights (host, layout above, may be NULL); FP32 kernels
- * with the BF16-rounded weights, FP64 accumulation across thread blocks. */
+ * with the BF16-rounded weights, FP64 accumulation across thread blocks.
+ * Errors: DWF_EINVAL (no network, npairs < 1, NULL pointers), DWF_ENOGAUGE,
+ * DWF_ECUDA. */
 int dwf_precond_loss_grad(dwf_handle h, int npairs, const void *const *b, const void *const *x,
                           double *loss, double *grad, void *stream);
-/* Make the pairs from nsrc 4D sources b4[k] (device) and train (above). */
+/* Make the pairs from nsrc 4D sources b4[k] (device) and train (above).
+ * Errors: DWF_EINVAL (nsrc < 1, NULL pointers, bad parameters, Ls > 16),
+ * DWF_ENOGAUGE, DWF_ECUDA, and the solver's errors while making the pairs. */
 int dwf_precond_train(dwf_handle h, int nsrc, const void *const *b4, const dwf_train_params *p,
                       dwf_train_stats *stats, void *stream);
 
