@@ -83,8 +83,11 @@ class Block:
 class DWF:
     """Domain-wall fermion operator on one gauge field.
 
-    form = "standard": eq. (domainwall_general) with constant (b, c).
-    form = "neff":     eq. (domainwall_neff) with parameter alpha.
+    form = "standard": eq. (domainwall_general); b and c are numbers, or
+                       sequences of Ls numbers b_i, c_i (row i of the matrix
+                       holds D_+^(i) = b_i D_W + 1 and D_-^(i) = c_i D_W - 1).
+    form = "neff":     eq. (domainwall_neff) with parameter alpha (constant b, c:
+                       the form is printed for coefficients independent of i).
     """
     U: np.ndarray
     dims: tuple
@@ -103,6 +106,11 @@ class DWF:
         self.U = np.ascontiguousarray(self.U, dtype=np.complex128)
         if self.form not in ("standard", "neff"):
             raise ValueError(self.form)
+        # per-row coefficients b_i, c_i (Sec. 2.2)
+        self._bs = np.broadcast_to(np.asarray(self.b, dtype=np.float64), (self.Ls,)).copy()
+        self._cs = np.broadcast_to(np.asarray(self.c, dtype=np.float64), (self.Ls,)).copy()
+        if self.form == "neff" and (np.ptp(self._bs) != 0 or np.ptp(self._cs) != 0):
+            raise ValueError("the Neff form takes coefficients independent of s")
         self._blocks = self.blocks()
         self._eo = None
 
@@ -120,7 +128,7 @@ class DWF:
     def blocks(self):
         """Nonzero blocks of the printed 5D matrix, 0-based s, t.
 
-        D_+ = b D_W + 1, D_- = c D_W - 1 (Sec. 2.2).
+        D_+ = b D_W + 1, D_- = c D_W - 1 (Sec. 2.2); row s takes b_s, c_s.
         standard, eq. (domainwall_general):
           (s,s)     D_+            (s,s+1) D_- P_-        (s,s-1) D_- P_+
           (1,Ls)   -m D_- P_+      (Ls,1)  -m D_- P_-
@@ -129,10 +137,11 @@ class DWF:
         (1,Ls) and (Ls,1) unchanged.
         Blocks that land on the same position (Ls = 2) are summed.
         """
-        Ls, b, c, m = self.Ls, self.b, self.c, self.mf
+        Ls, m = self.Ls, self.mf
         a = self.alpha if self.form == "neff" else 1.0
         out = []
         for s in range(Ls):
+            b, c = float(self._bs[s]), float(self._cs[s])
             if self.form == "neff" and s == 0:
                 out.append(Block(s, s, b, 1.0, P_MINUS + a * P_PLUS))
             elif self.form == "neff" and s == Ls - 1:
@@ -143,8 +152,8 @@ class DWF:
                 out.append(Block(s, s + 1, a * c, -a * 1.0, P_MINUS))
             if s - 1 >= 0:
                 out.append(Block(s, s - 1, a * c, -a * 1.0, P_PLUS))
-        out.append(Block(0, Ls - 1, -m * c, m, P_PLUS))
-        out.append(Block(Ls - 1, 0, -m * c, m, P_MINUS))
+        out.append(Block(0, Ls - 1, -m * float(self._cs[0]), m, P_PLUS))
+        out.append(Block(Ls - 1, 0, -m * float(self._cs[Ls - 1]), m, P_MINUS))
         return out
 
     def apply(self, x5: np.ndarray, dag: bool = False) -> np.ndarray:
@@ -206,8 +215,9 @@ class DWF:
 
     # ------------------------------------------------- 4D source / 4D solution
     def d_minus(self, x5, dag=False):
-        """D_- = diag_s(c D_W - 1)."""
-        return self.c * self.dw(x5, dag=dag) - x5
+        """D_- = diag_s(c_s D_W - 1)."""
+        cs = self._cs.reshape((self.Ls,) + (1,) * (x5.ndim - 1))
+        return cs * self.dw(x5, dag=dag) - x5
 
     def source_5d(self, b4: np.ndarray) -> np.ndarray:
         """b5 = (-D_-) P^dag (0, ..., 0, b4)^T (Sec. 2.3)."""
