@@ -88,6 +88,17 @@ enum dwf_status {
  */
 int dwf_create(const int dims[4], int Ls, double M0, double mf, double b, double c,
                int form, double alpha, const int bc[4], dwf_handle *out);
+
+/* The standard form of eq. (domainwall_general) with s-dependent coefficients
+ * (Sec. 2.2: row i holds D_+^(i) = b_i D_W + 1 and D_-^(i) = c_i D_W - 1, as in
+ * Chiu's optimal domain-wall fermion with b_i = c_i chosen per i): b and c are
+ * host arrays of Ls values each, read during the call.  Every entry point then
+ * works as for dwf_create; the source uses c_1 and c_Ls.  The FP64 mixing is
+ * dense (the structured form assumes coefficients independent of i).  The
+ * Neff form is defined for constant coefficients only.  Errors: as dwf_create
+ * (DWF_EINVAL also for NULL b or c). */
+int dwf_create_s(const int dims[4], int Ls, double M0, double mf, const double *b, const double *c,
+                 const int bc[4], dwf_handle *out);
 int dwf_destroy(dwf_handle h);
 const char *dwf_strerror(int status);
 const char *dwf_last_error(void);
@@ -226,7 +237,9 @@ int dwf_solve_batch(dwf_handle const *hs, const void *const *b4, void *const *x4
 int dwf_fifth_matrix(dwf_handle h, int which, int chirality, double *out_host);
 
 /* The same without a handle or a device (host code only): the matrices for
- * the parameters of dwf_create, FP64 row-major Ls x Ls.  which 0..3 as above,
+ * the parameters of dwf_create, with b and c host arrays of Ls values (row i of
+ * the 5D matrix takes b[i], c[i], as dwf_create_s; constant for DWF_NEFF),
+ * FP64 row-major Ls x Ls.  which 0..3 as above,
  * or 16 + k for the k-th per-chirality matrix the kernels apply in the fifth
  * direction (Sec. 2.3 even-odd algebra; B = b + cK, R the Neff factor):
  *   k = 0 P = B R, 1 P^T, 2 Q = R^-1 A5^-1 (D_ee^-1), 3 Q^T, 4 M = B A5^-1,
@@ -236,9 +249,10 @@ int dwf_fifth_matrix(dwf_handle h, int which, int chirality, double *out_host);
  * *banded (if non-null): 1 when every nonzero of the matrix lies on the cyclic
  * tridiagonal, which the kernels then read as three coefficients per row
  * (always 0 for which 0..3).  Errors: DWF_EINVAL (Ls outside 2..32, form,
- * which, chirality, null out, or A5 singular). */
-int dwf_fifth_matrix_host(int Ls, double M0, double mf, double b, double c, int form, double alpha, int which,
-                          int chirality, double *out_host, int *banded);
+ * which, chirality, null pointer, s-dependent coefficients with DWF_NEFF, or
+ * A5 singular). */
+int dwf_fifth_matrix_host(int Ls, double M0, double mf, const double *b, const double *c, int form, double alpha,
+                          int which, int chirality, double *out_host, int *banded);
 
 /* Number of device bytes the handle holds (0 for a NULL handle). */
 size_t dwf_device_bytes(dwf_handle h);

@@ -8,6 +8,12 @@
 
 using namespace dwf;
 
+namespace dwf {
+// mixing.cpp: the fifth-direction matrices with s-dependent coefficients
+bool build_fifth_matrices_s(int Ls, double M0, double mf, const double *bs, const double *cs, int form, double alpha,
+                            FifthMatrices &out, std::string &err);
+}  // namespace dwf
+
 namespace {
 thread_local std::string g_last_error;
 
@@ -211,8 +217,32 @@ const char *dwf_strerror(int s)
 
 const char *dwf_last_error(void) { return g_last_error.c_str(); }
 
+static int create_impl(const int dims[4], int Ls, double M0, double mf, const double *bs, const double *cs, int form,
+                       double alpha, const int bc[4], dwf_handle *out);
+
 int dwf_create(const int dims[4], int Ls, double M0, double mf, double b, double c, int form, double alpha,
                const int bc[4], dwf_handle *out)
+{
+    if (Ls < 2 || Ls > LS_MAX) {
+        if (out) *out = nullptr;
+        return dwf_set_error(DWF_EINVAL, "Ls must be in [2, 32]");
+    }
+    std::vector<double> bs((size_t)Ls, b), cs((size_t)Ls, c);
+    return create_impl(dims, Ls, M0, mf, bs.data(), cs.data(), form, alpha, bc, out);
+}
+
+int dwf_create_s(const int dims[4], int Ls, double M0, double mf, const double *b, const double *c, const int bc[4],
+                 dwf_handle *out)
+{
+    if (!b || !c) {
+        if (out) *out = nullptr;
+        return dwf_set_error(DWF_EINVAL, "b/c is NULL");
+    }
+    return create_impl(dims, Ls, M0, mf, b, c, DWF_STANDARD, 1.0, bc, out);
+}
+
+static int create_impl(const int dims[4], int Ls, double M0, double mf, const double *bs, const double *cs, int form,
+                       double alpha, const int bc[4], dwf_handle *out)
 {
     if (!dims || !out) return dwf_set_error(DWF_EINVAL, "dims/out is NULL");
     *out = nullptr;
@@ -227,8 +257,9 @@ int dwf_create(const int dims[4], int Ls, double M0, double mf, double b, double
     if (form != DWF_STANDARD && form != DWF_NEFF) return dwf_set_error(DWF_EINVAL, "unknown form");
     if (form == DWF_NEFF && !(alpha != 0.0 && std::isfinite(alpha)))
         return dwf_set_error(DWF_EINVAL, "alpha must be finite and nonzero");
-    if (!std::isfinite(M0) || !std::isfinite(mf) || !std::isfinite(b) || !std::isfinite(c))
-        return dwf_set_error(DWF_EINVAL, "non-finite parameter");
+    if (!std::isfinite(M0) || !std::isfinite(mf)) return dwf_set_error(DWF_EINVAL, "non-finite parameter");
+    for (int s = 0; s < Ls; ++s)
+        if (!std::isfinite(bs[s]) || !std::isfinite(cs[s])) return dwf_set_error(DWF_EINVAL, "non-finite parameter");
     int bcv[4] = {1, 1, 1, -1};
     if (bc)
         for (int k = 0; k < 4; ++k) {
@@ -240,14 +271,14 @@ int dwf_create(const int dims[4], int Ls, double M0, double mf, double b, double
     h->Ls = Ls;
     h->M0 = M0;
     h->mf = mf;
-    h->b = b;
-    h->c = c;
+    h->b = bs[0];
+    h->c = cs[0];
     h->alpha = (form == DWF_NEFF) ? alpha : 1.0;
     h->form = form;
     h->V = (int)V;
     h->Vh = (int)(V / 2);
     std::string err;
-    if (!build_fifth_matrices(Ls, M0, mf, b, c, form, h->alpha, h->fm, err)) {
+    if (!build_fifth_matrices_s(Ls, M0, mf, bs, cs, form, h->alpha, h->fm, err)) {
         delete h;
         return dwf_set_error(DWF_EINVAL, err);
     }
@@ -495,19 +526,22 @@ int dwf_fifth_matrix(dwf_handle h, int which, int chi, double *out)
     return DWF_OK;
 }
 
-int dwf_fifth_matrix_host(int Ls, double M0, double mf, double b, double c, int form, double alpha, int which,
-                          int chi, double *out, int *banded)
+int dwf_fifth_matrix_host(int Ls, double M0, double mf, const double *b, const double *c, int form, double alpha,
+                          int which, int chi, double *out, int *banded)
 {
-    if (Ls < 2 || Ls > LS_MAX || (form != DWF_STANDARD && form != DWF_NEFF) || chi < 0 || chi > 1 || !out)
+    if (Ls < 2 || Ls > LS_MAX || (form != DWF_STANDARD && form != DWF_NEFF) || chi < 0 || chi > 1 || !out || !b ||
+        !c)
         return dwf_set_error(DWF_EINVAL, "bad argument");
     if (!(which >= 0 && which <= 3) && !(which >= 16 && which < 16 + MAT_COUNT))
         return dwf_set_error(DWF_EINVAL, "bad matrix id");
-    if (!std::isfinite(M0) || !std::isfinite(mf) || !std::isfinite(b) || !std::isfinite(c) ||
-        (form == DWF_NEFF && !(alpha != 0.0 && std::isfinite(alpha))))
+    bool finite = std::isfinite(M0) && std::isfinite(mf);
+    for (int s = 0; s < Ls; ++s) finite = finite && std::isfinite(b[s]) && std::isfinite(c[s]);
+    if (!finite || (form == DWF_NEFF && !(alpha != 0.0 && std::isfinite(alpha))))
         return dwf_set_error(DWF_EINVAL, "non-finite parameter or alpha = 0");
     FifthMatrices fm;
     std::string err;
-    if (!build_fifth_matrices(Ls, M0, mf, b, c, form, alpha, fm, err)) return dwf_set_error(DWF_EINVAL, err.c_str());
+    if (!build_fifth_matrices_s(Ls, M0, mf, b, c, form, form == DWF_NEFF ? alpha : 1.0, fm, err))
+        return dwf_set_error(DWF_EINVAL, err.c_str());
     const std::vector<double> *m = nullptr;
     switch (which) {
     case 0: m = &fm.A5[chi]; break;

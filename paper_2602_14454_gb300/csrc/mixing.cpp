@@ -52,6 +52,19 @@ Mat add(const Mat &a, double sa, const Mat &b, double sb) {
     return c;
 }
 Mat scale(const Mat &a, double s) { return add(a, s, a, 0.0); }
+// row-wise coefficients: c[i][j] = sa[i] a[i][j] + sb[i] b[i][j] (the same
+// arithmetic as add() when sa and sb are constant)
+Mat add_rows(const Mat &a, const double *sa, const Mat &b, const double *sb, int n) {
+    Mat c(a.size());
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) c[(size_t)i * n + j] = sa[i] * a[(size_t)i * n + j] + sb[i] * b[(size_t)i * n + j];
+    return c;
+}
+Mat diag(const double *v, int n) {
+    Mat d = zeros(n);
+    for (int i = 0; i < n; ++i) d[(size_t)i * n + i] = v[i];
+    return d;
+}
 Mat transpose(const Mat &a, int n) {
     Mat t = zeros(n);
     for (int i = 0; i < n; ++i)
@@ -118,13 +131,38 @@ double spectral_norm(const Mat &a, int n) {
 void build_programs(int L, double alpha0, double beta0, double b, double c, double mf, double M0, double a,
                     FifthMatrices &out);
 
+bool build_fifth_matrices_s(int Ls, double M0, double mf, const double *bs, const double *cs, int form, double alpha,
+                            FifthMatrices &out, std::string &err);
+
 bool build_fifth_matrices(int Ls, double M0, double mf, double b, double c, int form, double alpha,
                           FifthMatrices &out, std::string &err)
 {
+    std::vector<double> bs((size_t)Ls, b), cs((size_t)Ls, c);
+    return build_fifth_matrices_s(Ls, M0, mf, bs.data(), cs.data(), form, alpha, out, err);
+}
+
+// Row s of eq. (domainwall_general) holds D_+^(s) = b_s D_W + 1 and
+// D_-^(s) = c_s D_W - 1, so B = diag(b) + diag(c) K and the site block
+// A5 = diag(alpha0_s) + diag(beta0_s) K with alpha0_s = b_s (4 - M0) + 1,
+// beta0_s = c_s (4 - M0) - 1 (both act on the chirality of their input).
+bool build_fifth_matrices_s(int Ls, double M0, double mf, const double *bs, const double *cs, int form, double alpha,
+                            FifthMatrices &out, std::string &err)
+{
     const int n = Ls;
     out.Ls = Ls;
-    const double alpha0 = b * (4.0 - M0) + 1.0;
-    const double beta0 = c * (4.0 - M0) - 1.0;
+    bool constant = true;
+    for (int s = 1; s < n; ++s) constant = constant && bs[s] == bs[0] && cs[s] == cs[0];
+    if (form == DWF_NEFF && !constant) {
+        err = "the Neff form takes coefficients b, c independent of s";
+        return false;
+    }
+    std::vector<double> alpha0((size_t)n), beta0((size_t)n), src_post((size_t)n), src_y((size_t)n);
+    for (int s = 0; s < n; ++s) {
+        alpha0[s] = bs[s] * (4.0 - M0) + 1.0;
+        beta0[s] = cs[s] * (4.0 - M0) - 1.0;
+        src_post[s] = 0.5 * cs[s];
+        src_y[s] = 1.0 - cs[s] * (4.0 - M0);
+    }
     const double a = (form == DWF_NEFF) ? alpha : 1.0;
     double dee = 0;
     for (int chi = 0; chi < 2; ++chi) {
@@ -137,8 +175,8 @@ bool build_fifth_matrices(int Ls, double M0, double mf, double b, double c, int 
             K[(size_t)(n - 1) * n + 0] += -mf;
         }
         Mat I = eye(n);
-        Mat B = add(I, b, K, c);
-        Mat A5 = add(I, alpha0, K, beta0);
+        Mat B = add_rows(I, bs, K, cs, n);
+        Mat A5 = add_rows(I, alpha0.data(), K, beta0.data(), n);
         Mat R = eye(n, a);
         if (chi == 0) R[(size_t)(n - 1) * n + (n - 1)] = 1.0;
         else R[0] = 1.0;
@@ -172,8 +210,8 @@ bool build_fifth_matrices(int Ls, double M0, double mf, double b, double c, int 
         out.mats[MAT_NPT4][chi] = scale(transpose(P, n), -0.25);
         out.mats[MAT_ID][chi] = I;
         out.mats[MAT_HALF_Q][chi] = scale(Q, 0.5);
-        out.mats[MAT_SRC_POST][chi] = eye(n, 0.5 * c);
-        out.mats[MAT_SRC_Y][chi] = eye(n, 1.0 - c * (4.0 - M0));
+        out.mats[MAT_SRC_POST][chi] = diag(src_post.data(), n);
+        out.mats[MAT_SRC_Y][chi] = diag(src_y.data(), n);
         dee = std::fmax(dee, spectral_norm(A5R, n));
     }
     out.dee_norm2 = dee;
@@ -191,7 +229,11 @@ bool build_fifth_matrices(int Ls, double M0, double mf, double b, double c, int 
                 }
         out.band[id] = band;
     }
-    build_programs(n, alpha0, beta0, b, c, mf, M0, a, out);
+    // the structured programs assume coefficients independent of s
+    if (constant)
+        build_programs(n, alpha0[0], beta0[0], bs[0], cs[0], mf, M0, a, out);
+    else
+        out.structured = false;
     return true;
 }
 

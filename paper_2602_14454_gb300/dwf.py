@@ -27,7 +27,7 @@ OPS = {"full": OP_FULL5D, "full5d": OP_FULL5D, "eo": OP_EO_PREC, "eo_prec": OP_E
 STATUS = {0: "DWF_OK", 1: "DWF_EINVAL", 2: "DWF_ENOMEM", 3: "DWF_ECUDA", 4: "DWF_ENOTCONV",
           5: "DWF_ENONFINITE", 6: "DWF_ETIMEOUT", 7: "DWF_EBREAKDOWN", 8: "DWF_ENOGAUGE"}
 
-EXPORTED = ["dwf_create", "dwf_destroy", "dwf_strerror", "dwf_last_error", "dwf_set_gauge",
+EXPORTED = ["dwf_create", "dwf_create_s", "dwf_destroy", "dwf_strerror", "dwf_last_error", "dwf_set_gauge",
             "dwf_apply", "dwf_apply_dag", "dwf_source_5d", "dwf_project_4d",
             "dwf_solve_params_default", "dwf_solve", "dwf_propagator_host", "dwf_solve_batch",
             "dwf_fifth_matrix", "dwf_fifth_matrix_host", "dwf_device_bytes", "dwf_time_hop", "dwf_time_iteration", "dwf_spectrum_bounds", "dwf_launch_count",
@@ -102,6 +102,7 @@ def lib():
     vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     ip = ctypes.POINTER(ctypes.c_int)
     L.dwf_create.argtypes = [ip, i, d, d, d, d, i, d, ip, ctypes.POINTER(vp)]
+    L.dwf_create_s.argtypes = [ip, i, d, d, ctypes.POINTER(d), ctypes.POINTER(d), ip, ctypes.POINTER(vp)]
     L.dwf_destroy.argtypes = [vp]
     L.dwf_strerror.restype = ctypes.c_char_p
     L.dwf_strerror.argtypes = [i]
@@ -119,7 +120,8 @@ def lib():
     L.dwf_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i,
                                   ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), vp]
     L.dwf_fifth_matrix.argtypes = [vp, i, i, ctypes.POINTER(ctypes.c_double)]
-    L.dwf_fifth_matrix_host.argtypes = [i, d, d, d, d, i, d, i, i, ctypes.POINTER(ctypes.c_double), ip]
+    L.dwf_fifth_matrix_host.argtypes = [i, d, d, ctypes.POINTER(d), ctypes.POINTER(d), i, d, i, i,
+                                        ctypes.POINTER(ctypes.c_double), ip]
     L.dwf_device_bytes.argtypes = [vp]
     L.dwf_device_bytes.restype = ctypes.c_size_t
     L.dwf_time_hop.argtypes = [vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]
@@ -180,8 +182,15 @@ def default_params(**kw) -> SolveParams:
     return p
 
 
+def _coeffs(v, Ls):
+    """(C array of Ls doubles, scalar or None): a number gives Ls copies."""
+    a = np.broadcast_to(np.asarray(v, dtype=np.float64), (Ls,))
+    return (ctypes.c_double * Ls)(*a), (float(a[0]) if np.ndim(v) == 0 else None)
+
+
 class Operator:
-    """One lattice, one 5D operator (standard or Neff form), one gauge field."""
+    """One lattice, one 5D operator (standard or Neff form), one gauge field.
+    b and c are numbers, or (standard form) sequences of Ls coefficients b_s, c_s."""
 
     def __init__(self, dims, Ls, M0, mf, b, c, form="standard", alpha=1.0, bc=None):
         self.dims = tuple(int(x) for x in dims)
@@ -189,10 +198,19 @@ class Operator:
         h = ctypes.c_void_p()
         d = (ctypes.c_int * 4)(*self.dims)
         bcp = (ctypes.c_int * 4)(*bc) if bc is not None else None
-        check(lib().dwf_create(d, self.Ls, float(M0), float(mf), float(b), float(c), FORM[form],
-                               float(alpha), bcp, ctypes.byref(h)))
+        if np.ndim(b) == 0 and np.ndim(c) == 0:
+            check(lib().dwf_create(d, self.Ls, float(M0), float(mf), float(b), float(c), FORM[form],
+                                   float(alpha), bcp, ctypes.byref(h)))
+            self.b, self.c = float(b), float(c)
+        else:
+            if FORM[form] != STANDARD:
+                raise ValueError("s-dependent coefficients need the standard form")
+            ba, _ = _coeffs(b, self.Ls)
+            ca, _ = _coeffs(c, self.Ls)
+            check(lib().dwf_create_s(d, self.Ls, float(M0), float(mf), ba, ca, bcp, ctypes.byref(h)))
+            self.b, self.c = np.array(ba), np.array(ca)
         self._h = h
-        self.M0, self.mf, self.b, self.c = float(M0), float(mf), float(b), float(c)
+        self.M0, self.mf = float(M0), float(mf)
         self.form, self.alpha = form, float(alpha)
         Lx, Ly, Lz, Lt = self.dims
         self.site_shape = (Lt, Lz, Ly, Lx)
@@ -385,11 +403,14 @@ KERNEL_MATRICES = ("P", "PT", "Q", "QT", "M", "MT", "A5R", "RA5T", "NHALF", "NHA
 
 def fifth_matrix_host(Ls, M0, mf, b, c, form="standard", alpha=1.0, which=0, chirality=0):
     """(matrix, banded) without a device: which 0..3 (A5, A5^-1, B, R) or a name of
-    KERNEL_MATRICES (the per-chirality matrices the kernels apply)."""
+    KERNEL_MATRICES (the per-chirality matrices the kernels apply); b and c
+    numbers or sequences of Ls coefficients."""
     w = which if isinstance(which, int) else 16 + KERNEL_MATRICES.index(which)
     out = (ctypes.c_double * (Ls * Ls))()
     band = ctypes.c_int()
-    check(lib().dwf_fifth_matrix_host(int(Ls), float(M0), float(mf), float(b), float(c), FORM[form], float(alpha),
+    ba, _ = _coeffs(b, Ls)
+    ca, _ = _coeffs(c, Ls)
+    check(lib().dwf_fifth_matrix_host(int(Ls), float(M0), float(mf), ba, ca, FORM[form], float(alpha),
                                       int(w), int(chirality), out, ctypes.byref(band)))
     return np.array(out, dtype=np.float64).reshape(Ls, Ls), bool(band.value)
 

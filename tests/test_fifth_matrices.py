@@ -17,7 +17,11 @@ from oracle import dwf as orc
 from paper_2602_14454_gb300 import dwf, inputs
 
 PARAMS = [(8, 1.8, 0.04, 1.0, 0.0, "standard", 1.0), (16, 1.8, 0.01, 1.5, 0.5, "neff", 0.5),
-          (12, 1.0, 0.05, 1.0, 1.0, "neff", 0.3), (6, 1.8, 0.1, 1.5, 0.5, "standard", 1.0)]
+          (12, 1.0, 0.05, 1.0, 1.0, "neff", 0.3), (6, 1.8, 0.1, 1.5, 0.5, "standard", 1.0),
+          # s-dependent coefficients (rows of eq. domainwall_general), standard form
+          (6, 1.8, 0.05, (1.2, 0.7, 1.9, 1.1, 0.9, 1.4), (0.3, 0.6, 0.2, 0.8, 0.1, 0.5), "standard", 1.0),
+          (8, 1.4, 0.02, (0.4, 0.9, 1.3, 1.7, 1.7, 1.3, 0.9, 0.4), (0.4, 0.9, 1.3, 1.7, 1.7, 1.3, 0.9, 0.4),
+           "standard", 1.0)]
 
 
 def host(p, which, chi):
@@ -90,8 +94,26 @@ def test_kernel_matrices_follow_their_definitions(p):
         assert np.allclose(m["NHALF_RBT"], -0.5 * R @ B.T, **tol)
         assert np.array_equal(m["ID"], I) and np.array_equal(m["NHALF"], -0.5 * I)
         Ls_, M0, mf, b, c = p[:5]
-        assert np.allclose(m["SRC_POST"], 0.5 * c * I, **tol)
-        assert np.allclose(m["SRC_Y"], (1 - c * (4 - M0)) * I, **tol)
+        cs = np.broadcast_to(np.asarray(c, dtype=float), (Ls,))
+        assert np.allclose(m["SRC_POST"], np.diag(0.5 * cs), **tol)
+        assert np.allclose(m["SRC_Y"], np.diag(1 - cs * (4 - M0)), **tol)
+
+
+@pytest.mark.parametrize("p", PARAMS)
+def test_fifth_direction_hop_matches_the_oracle_blocks(p):
+    """B = b + c K (per row s: b_s, c_s) against the D_W coefficients of the
+    oracle's printed blocks, projected on each chirality; for the Neff form the
+    oracle's blocks are those of D^(alpha) = D (P A P^dag), i.e. B R."""
+    Ls, M0, mf, b, c, form, alpha = p
+    U = inputs.random_links((2, 2, 2, 2), 0.5, 1)
+    op = orc.DWF(U, (2, 2, 2, 2), Ls, M0, mf, b, c, form=form, alpha=alpha)
+    for chi in (0, 1):
+        sp = 2 * chi
+        W = np.zeros((Ls, Ls))
+        for bl in op.blocks():
+            W[bl.s, bl.t] += (bl.cw * bl.S[sp, sp]).real
+        B, R = host(p, 2, chi)[0], host(p, 3, chi)[0]
+        assert np.allclose(W, B @ R, rtol=0, atol=1e-13)
 
 
 @pytest.mark.parametrize("p", PARAMS)
@@ -119,3 +141,5 @@ def test_bad_arguments():
         dwf.fifth_matrix_host(8, 1.8, 0.1, 1.0, 0.0, "neff", 0.0, 0, 0)
     with pytest.raises(dwf.DwfError):
         dwf.fifth_matrix_host(8, 1.8, 0.1, 1.0, 0.0, "standard", 1.0, 0, 2)
+    with pytest.raises(dwf.DwfError):   # the Neff form takes constant coefficients
+        dwf.fifth_matrix_host(4, 1.8, 0.1, (1.0, 1.1, 1.0, 1.0), 0.0, "neff", 0.5, 0, 0)
