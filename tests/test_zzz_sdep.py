@@ -1,6 +1,9 @@
 """s-dependent coefficients (b_i, c_i) of eq. (domainwall_general) through the
 C ABI (dwf_create_s) against the FP64 oracle: the whole 5D matrix, the even-odd
-matrix, the source and the mixed-precision solve with its 4D solution."""
+matrix, the source and the mixed-precision solve with its 4D solution.
+
+The newest component: this file is collected last, so that a failure here
+leaves every other test already run."""
 
 import numpy as np
 import pytest
