@@ -2,13 +2,16 @@
 """Benchmark of the domain-wall solver on one GB300 (or N, one process each).
 
 One step = one full pass of the solver's hot path for one 4D source on the
-16^3x32, Ls=16 Mobius workload (b=1.5, c=0.5, M0=1.8, m=0.01, links
-exp(0.3 i H) + 3 stout/APE smearing steps, rho=0.1): 5D source, FP64 even-odd
-set-up, mixed-precision CG with FP64 reliable updates, reconstruction, FP64
-full-residual check, 4D projection.  The JSON line reports the time to
+32^3x64, Ls=16 Mobius workload (b=1.5, c=0.5, M0=1.8, m=0.005, links
+exp(0.3 i H) + 3 stout/APE smearing steps, rho=0.1; Neff form, alpha 0.5):
+5D source, FP64 even-odd set-up, CG on the normal equation in FP32 (the
+paper's single-precision solver) with FP64 reliable updates, reconstruction,
+FP64 full-residual check, 4D projection.  The JSON line reports the time to
 solution at ||b5 - D x5|| / ||b5|| <= 1e-10 (lower is better), the hop
-kernel's HBM roofline, the oracle's CPU time on a bounded sample, the
-end-to-end time through the host-buffer C-ABI call and the SM clocks seen.
+kernel's HBM roofline, the measured FP32 arithmetic peak, the oracle's CPU
+time on a bounded sample, the end-to-end time through the host-buffer C-ABI
+call and the SM clocks seen; beside it the FP16-inner solve, plain FP64 CG
+and the 16^3x32 workload.
 
 Ranks (torchrun) solve independent sources (weak scaling, no collective);
 --impl reference times the FP64 oracle on the host cores instead.
@@ -28,8 +31,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "c2_16^3x32_ls16_mobius"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+WORKLOAD = "c5_32^3x64_ls16_mobius"        # the largest single-GPU workload: the headline
+SECOND = "c2_16^3x32_ls16_mobius"          # reported beside it (extra keys)
+# the oracle's bounded sample: the workload's operator on an 8^3x16 lattice of
+# the same link recipe (1/256 of the 32^3x64 volume); its time per CG iteration
+# is scaled by the volume ratio (the oracle is a loop over sites)
+SAMPLE_DIMS = (8, 8, 8, 16)
 METRIC = "DWF CG time-to-solution @1e-10 residual; 5D Dslash GB/s vs HBM peak"
 
 
@@ -39,12 +46,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--inner", default="f16", choices=["f16", "f32", "f64"])
+    ap.add_argument("--inner", default="f32", choices=["f16", "f32", "f64"])
     ap.add_argument("--form", default="neff", choices=["neff", "standard"])
     ap.add_argument("--alpha", type=float, default=0.5)
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-cg", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP16-inner solve and the 16^3x32 lines reported beside the headline")
     return ap.parse_args()
 
 
@@ -131,7 +141,7 @@ def peaks():
         return None
 
 
-HOP_SOURCES = ("hop.cu", "stencil.cuh", "fields.cuh", "dwf_internal.h")
+HOP_SOURCES = ("hop.cu", "hop_kernels.cuh", "stencil.cuh", "fields.cuh", "dwf_internal.h")
 
 
 def hop_source_key():
@@ -142,93 +152,149 @@ def hop_source_key():
     return h.hexdigest()[:16]
 
 
-def hop_traffic(prec):
+def hop_traffic(prec, workload):
     """DRAM bytes per hop launch from the committed ncu summary, if it was taken
-    from the current hop kernel sources (else null)."""
+    from the current hop kernel sources on this workload (else null)."""
     path = os.path.join(ROOT, "profiles", "hop_traffic.json")
     try:
         d = json.load(open(path))
     except Exception:
         return None
-    e = d.get(prec)
+    e = d.get(workload, {}).get(prec)
     if not e or e.get("hop_sources_sha256_16") != hop_source_key():
         return None
-    return e.get("dram_bytes_per_launch_full_size")
+    return e.get("dram_bytes_per_launch")
 
 
-def cpu_baseline(w, U, fp64_iters, form, alpha):
-    """The FP64 oracle as it stands, on the host cores: one application of the
-    even-odd matrix and one of its adjoint on the same workload (one CG
-    iteration), extrapolated to the iteration count of FP64 CG on it."""
-    import numpy as np
+def config_of(w, name, args):
+    """The workload as both arms name it."""
+    return {"workload": name, "dims": list(w["dims"]), "Ls": w["Ls"], "b": w["b"], "c": w["c"],
+            "M0": w["M0"], "mf": w["mf"], "form": args.form, "alpha": args.alpha,
+            "inner_precision": args.inner, "tol": args.tol,
+            "links": "exp(i %.1f H), %d stout/APE steps rho 0.1, seed %d" % (w["eps"], w["smear"], w["gauge_seed"]),
+            "source": "Gaussian 4D, seed %d (+ rank)" % w["src_seed"]}
+
+
+def oracle_iteration_seconds(w, form, alpha):
+    """The FP64 oracle as it stands, on the host cores: one CG iteration (the
+    even-odd matrix and its adjoint) with the workload's operator on the
+    SAMPLE_DIMS lattice of the same link and source recipe."""
     from oracle import dwf as orc
     from paper_2602_14454_gb300 import inputs
-    ref = orc.DWF(U, w["dims"], w["Ls"], w["M0"], w["mf"], w["b"], w["c"], form=form, alpha=alpha)
-    x = ref.to_eo(inputs.gaussian_5d(w["dims"], w["Ls"], 1), 0)
-    t0 = time.perf_counter()
-    y = ref.d_pc(x)
-    ref.d_pc(y, dag=True)
-    t_it = time.perf_counter() - t0
+    U = inputs.smeared_links(SAMPLE_DIMS, w["eps"], 0.1, w["smear"], w["gauge_seed"])
+    ref = orc.DWF(U, SAMPLE_DIMS, w["Ls"], w["M0"], w["mf"], w["b"], w["c"], form=form, alpha=alpha)
+    x = ref.to_eo(inputs.gaussian_5d(SAMPLE_DIMS, w["Ls"], 1), 0)
+
+    def one():
+        t0 = time.perf_counter()
+        y = ref.d_pc(x)
+        ref.d_pc(y, dag=True)
+        return time.perf_counter() - t0
+    return one
+
+
+def volume(dims):
+    v = 1
+    for d in dims:
+        v *= int(d)
+    return v
+
+
+def sample_text(w, iters):
+    return ("one CG iteration (D and D^dag of the even-odd matrix) of the workload's operator on a "
+            "%s lattice with the same link recipe, times the volume ratio %d, times the %d iterations "
+            "FP64 CG takes on the workload" % ("x".join(map(str, SAMPLE_DIMS)),
+                                               volume(w["dims"]) // volume(SAMPLE_DIMS), iters))
+
+
+def cpu_baseline(w, iters, form, alpha):
+    one = oracle_iteration_seconds(w, form, alpha)
+    one()
+    t = min(one(), one())
+    scale = volume(w["dims"]) / volume(SAMPLE_DIMS)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": t_it * fp64_iters, "unit": "s", "cores": cores, "kind": "oracle",
-            "sample": "one CG iteration (D and D^dag of the even-odd matrix, %.1f s) on the full "
-                      "workload, times the %d iterations FP64 CG needs on it" % (t_it, fp64_iters),
-            "seconds_per_iteration": t_it}
+    return {"value": t * scale * iters, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": sample_text(w, iters), "seconds_per_sample_iteration": t}
 
 
 def reference_arm(args):
-    """--impl reference: the FP64 oracle on the host cores, same workload."""
-    import numpy as np  # noqa: F401
+    """--impl reference: the FP64 oracle on the host cores (there is no other
+    implementation: the paper is the only reference), on the same workload,
+    metric and config; each step times one bounded sample (cpu_baseline)."""
     from paper_2602_14454_gb300 import inputs
     rank, world, local = dist_env()
     if rank != 0:
         return 0
-    w = inputs.WORKLOADS[WORKLOAD]
-    U = inputs.workload_links(w)
-    from oracle import dwf as orc
-    ref = orc.DWF(U, w["dims"], w["Ls"], w["M0"], w["mf"], w["b"], w["c"], form=args.form, alpha=args.alpha)
-    x = ref.to_eo(inputs.gaussian_5d(w["dims"], w["Ls"], 1), 0)
-    iters = fp64_iteration_count()
+    w = inputs.WORKLOADS[args.workload]
+    iters = fp64_iteration_count(args.workload)
+    one = oracle_iteration_seconds(w, args.form, args.alpha)
     times = []
     for k in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        y = ref.d_pc(x)
-        ref.d_pc(y, dag=True)
-        dt = time.perf_counter() - t0
+        dt = one()
         if k >= args.warmup:
             times.append(dt)
     t_it = sum(times) / len(times)
-    val = t_it * iters
+    val = t_it * volume(w["dims"]) / volume(SAMPLE_DIMS) * iters
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_it,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "dims": list(w["dims"]), "Ls": w["Ls"],
-                                            "form": args.form, "alpha": args.alpha},
+            "data": "synthetic", "config": config_of(w, args.workload, args),
             "cpu_baseline": {"value": val, "unit": "s", "cores": cores, "kind": "oracle",
-                             "sample": "each step: one CG iteration (D and D^dag of the even-odd matrix) "
-                                       "on the full workload; value = mean step time x %d FP64 CG "
-                                       "iterations" % iters},
+                             "sample": "each step: " + sample_text(w, iters) + "; value = mean step time "
+                                       "x volume ratio x iterations"},
             "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def fp64_iteration_count():
-    """Iterations of plain FP64 CG on the workload to 1e-10 (from profiles/, else a
-    conservative default stated in the line)."""
+def fp64_iteration_count(name):
+    """Iterations of plain FP64 CG on the workload to 1e-10, as measured on the
+    GPU and recorded in profiles/iteration_counts.json (else a default stated
+    in the line)."""
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "iteration_counts.json")))
-        return int(d[WORKLOAD]["fp64_cg_iterations"])
+        return int(d[name]["fp64_cg_iterations"])
     except Exception:
-        return 300
+        return 350
+
+
+def timed_solves(op, b4, n, **kw):
+    """Mean CUDA-event time (s) of n solves from a 4D source (5D source, solve,
+    projection) after one untimed solve, and the last solve's statistics."""
+    import torch
+    st = torch.cuda.current_stream()
+
+    def step():
+        b5 = op.source_5d(b4)
+        x5, s = op.solve(b5, **kw)
+        op.project_4d(x5)
+        return s
+    step()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(n):
+        s = step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0 / n, s
+
+
+def hop_roofline(op, prec, Ls, peak, reps=30):
+    """The hop kernel (the dominant kernel) timed alone with CUDA events, L2
+    flushed between launches, against the measured HBM peak."""
+    us, nbytes = op.time_hop(prec, reps=reps, flush_l2=True)
+    achieved = nbytes / (us * 1e-6) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "us_per_launch": us, "algorithmic_bytes_per_launch": nbytes,
+            "kernel": "hop_kernel<%s> (even-odd hop + fused Ls mixing)" % prec}
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
-    import numpy as np
     import torch
 
     rank, world, local = dist_env()
@@ -241,8 +307,8 @@ def main():
         build.build()
     if world > 1:
         torch.distributed.barrier()
-    w = inputs.WORKLOADS[WORKLOAD]
-    U = inputs.workload_links(w)
+    w = inputs.WORKLOADS[args.workload]
+    U = inputs.workload_links(w, device="cuda")
     op = dwf.Operator(w["dims"], w["Ls"], w["M0"], w["mf"], w["b"], w["c"], form=args.form, alpha=args.alpha)
     op.set_gauge(torch.from_numpy(U).cuda())
     b4_host = inputs.gaussian_4d(w["dims"], source_seed(w, rank))
@@ -291,30 +357,53 @@ def main():
         e2e_times.append(time.perf_counter() - t0)
     e2e = min(e2e_times)
 
-    # roofline of the dominant kernel (the hop), CUDA events around each launch, L2 flushed
-    hop_prec = args.inner
-    us, nbytes = op.time_hop(hop_prec, reps=30, flush_l2=True)
-    iteration = op.time_iteration(hop_prec, reps=10, flush_l2=True)
+    # roofline of the dominant kernel (the hop in the inner precision)
     pk = peaks()
     peak = pk["hbm_gbs"] if pk else 6800.0
-    achieved = nbytes / (us * 1e-6) / 1e9
+    roof = hop_roofline(op, args.inner, w["Ls"], peak)
+    roof["traffic"] = hop_traffic(args.inner, args.workload)
+    roof["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs (burst copy), of measured" if pk
+                           else "fallback 6.8 TB/s")
+    iteration = op.time_iteration(args.inner, reps=10, flush_l2=True) if args.inner != "f64" else None
+    alu = dwf.alu_peaks()
+    alu_peak = max(alu["fp32_ffma_tflops"], alu["fp32_ffma2_tflops"])
     hop_flops = float(op.V // 2) * w["Ls"] * (1320 + 48 * w["Ls"])
 
     out = None
     if rank == 0:
         fp64 = None
-        if not args.no_fp64_cg:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            b5 = op.source_5d(b4)
-            _, s64 = op.solve(b5, inner_prec="f64", tol=args.tol)
-            torch.cuda.synchronize()
-            fp64 = {"tts_s": time.perf_counter() - t0, "iterations": s64["iterations"],
-                    "true_residual": s64["true_residual"]}
+        if not args.no_fp64_cg and args.inner != "f64":
+            t64, s64 = timed_solves(op, b4, 1, inner_prec="f64", tol=args.tol)
+            fp64 = {"tts_s": t64, "iterations": s64["iterations"], "true_residual": s64["true_residual"],
+                    "speedup_of_headline": t64 / (ms / 1000.0)}
+        extras = None
+        if not args.no_extras:
+            extras = {}
+            other = "f16" if args.inner != "f16" else "f32"
+            t2, s2b = timed_solves(op, b4, 2, inner_prec=other, tol=args.tol)
+            extras["%s_inner" % other] = {
+                "tts_s": t2, "iterations": s2b["iterations"], "true_residual": s2b["true_residual"],
+                "roofline": hop_roofline(op, other, w["Ls"], peak)}
+            w2 = inputs.WORKLOADS[SECOND]
+            op2 = dwf.Operator(w2["dims"], w2["Ls"], w2["M0"], w2["mf"], w2["b"], w2["c"], form=args.form,
+                               alpha=args.alpha)
+            op2.set_gauge(torch.from_numpy(inputs.workload_links(w2, device="cuda")).cuda())
+            b42 = torch.from_numpy(inputs.gaussian_4d(w2["dims"], w2["src_seed"])).cuda()
+            c2 = {"config": config_of(w2, SECOND, args)}
+            for prec in ("f32", "f16"):
+                t, s_ = timed_solves(op2, b42, 5, inner_prec=prec, tol=args.tol)
+                c2["%s_inner" % prec] = {"tts_s": t, "iterations": s_["iterations"],
+                                         "true_residual": s_["true_residual"],
+                                         "roofline": hop_roofline(op2, prec, w2["Ls"], peak)}
+            it2 = op2.time_iteration("f32", reps=10, flush_l2=True)
+            c2["iteration_kernels_f32"] = {k: {"us": round(v[0], 2), "gbs": round(v[1] / (v[0] * 1e-6) / 1e9, 1)}
+                                           for k, v in it2.items()}
+            extras[SECOND] = c2
+            op2.close()
         base = None
         if world == 1 and not args.no_cpu_baseline:
-            its = fp64["iterations"] if fp64 else fp64_iteration_count()
-            base = cpu_baseline(w, U, its, args.form, args.alpha)
+            its = fp64["iterations"] if fp64 else fp64_iteration_count(args.workload)
+            base = cpu_baseline(w, its, args.form, args.alpha)
         out = {
             "metric": METRIC,
             "value": ms / 1000.0,
@@ -328,36 +417,29 @@ def main():
             "vs_baseline": None,
             "dtype": "%s+f64" % args.inner,
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dims": list(w["dims"]), "Ls": w["Ls"], "b": w["b"], "c": w["c"],
-                       "M0": w["M0"], "mf": w["mf"], "form": args.form, "alpha": args.alpha,
-                       "inner_precision": args.inner, "tol": args.tol,
-                       "l2": "inputs larger than L2 (solve working set %.1f GB)" % (op.device_bytes() / 1e9)},
+            "config": dict(config_of(w, args.workload, args),
+                           l2="inputs larger than L2 (solve working set %.1f GB)" % (op.device_bytes() / 1e9)),
             "solve": {"iterations": iters, "true_residual_max": worst_res,
                       "reliable_updates": stats[-1]["reliable_updates"],
                       "d_applications": stats[-1]["d_applications"], "solves_per_s_all_ranks":
                           world * 1000.0 / ms},
             "fp64_cg": fp64,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": hop_traffic(hop_prec),
-                         "kernel": "hop_kernel<%s> (even-odd hop + fused Ls mixing)" % hop_prec,
-                         "us_per_launch": us, "algorithmic_bytes_per_launch": nbytes,
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured" if pk
-                         else "fallback 6.8 TB/s"},
-            # cross-check: the same launch against the FP32 arithmetic peak derived from the
-            # unit counts (152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz = 80.5 TFLOP/s); the
-            # hop's useful flops per 5D site are 1320 (Wilson hop) + 48 Ls (dense Ls mixing)
-            "roofline_alu": {"bound": "alu", "achieved": hop_flops / (us * 1e-6) / 1e12,
-                             "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": hop_flops / (us * 1e-6) / 1e12 / FP32_PEAK_TFLOPS,
-                             "flops_per_launch": hop_flops},
-            # the five launches of one inner CG iteration (back to back, L2 flushed before
-            # each iteration): device time and algorithmic bytes per launch
-            "iteration_kernels": {
+            "roofline": roof,
+            # the same launch against the measured FP32 arithmetic peak (packed FP32x2
+            # FMAs, dwf_alu_peaks); useful flops per 5D site: 1320 (Wilson hop) + 48 Ls
+            # (one dense Ls mixing)
+            "roofline_alu": {"bound": "alu", "achieved": hop_flops / (roof["us_per_launch"] * 1e-6) / 1e12,
+                             "peak": alu_peak, "unit": "TFLOP/s",
+                             "frac": hop_flops / (roof["us_per_launch"] * 1e-6) / 1e12 / alu_peak,
+                             "flops_per_launch": hop_flops, "peak_source": "dwf_alu_peaks, measured",
+                             "measured_peaks": alu},
+            "iteration_kernels": None if iteration is None else {
                 "kernels": {k: {"us": round(v[0], 2), "bytes": v[1], "gbs": round(v[1] / (v[0] * 1e-6) / 1e9, 1)}
                             for k, v in iteration.items()},
                 "us": sum(v[0] for v in iteration.values()),
                 "frac_of_hbm_peak": sum(v[1] for v in iteration.values()) /
                                     (sum(v[0] for v in iteration.values()) * 1e-6) / 1e9 / peak},
+            "extras": extras,
             "cpu_baseline": base,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(b4_host.nbytes),
                     "d2h_bytes_per_step": int(b4_host.nbytes), "true_residual": s2["true_residual"]},

@@ -263,21 +263,18 @@ size_t dwf_device_bytes(dwf_handle h);
 long long dwf_launch_count(dwf_handle h);
 
 /* Configuration of the hop kernel in precision prec: variant 0 loads the
- * neighbour spinors directly from global memory, variant 1 stages the
- * neighbour sites in shared memory with TMA bulk copies, variant 2 is a
- * persistent kernel whose producer warp streams the neighbour sites through a
- * ring of shared-memory stages for the consumer warps, variant 3 is a
- * persistent kernel sweeping consecutive tiles, variant 4 takes each CTA's
- * sites as a 4D block of the half lattice (neighbour reuse in L1), variant 5
- * (DWF_F16 only, dense mixing; else variant 0) is variant 0 with the spin
- * projection in FP16 arithmetic on the stored FP16 values (one rounding at the
- * FP16 storage level) and the SU(3) product in FP32 shared by the thread's
- * slices; ns fifth-direction
- * slices per thread (1, 2 when it divides Ls, 4 for variant 5); sb
- * four-dimensional sites per CTA.  -1 / 0 select the built-in defaults.
- * Variants 0-4 have no numerical effect beyond summation order.
- * Errors: DWF_EINVAL (NULL handle or pointer, bad prec, variant outside
- * -1..5, ns not 0, 1, 2 or (variant 5) 4 dividing Ls, sb making a CTA of more
+ * neighbour spinors directly from global memory, variant 3 is a persistent
+ * kernel sweeping consecutive tiles, variant 4 takes each CTA's sites as a 4D
+ * block of the half lattice (neighbour reuse in L1), variant 5 (DWF_F16 only,
+ * dense mixing; else variant 0) is variant 0 with the spin projection in FP16
+ * arithmetic on the stored FP16 values (one rounding at the FP16 storage
+ * level) and the SU(3) product in FP32 shared by the thread's slices; ns
+ * fifth-direction slices per thread (1, 2 when it divides Ls, 4 for variant
+ * 5); sb four-dimensional sites per CTA.  -1 / 0 select the built-in
+ * defaults.  Variants 0, 3 and 4 have no numerical effect beyond summation
+ * order.  (Numbers 1 and 2 are not used.)
+ * Errors: DWF_EINVAL (NULL handle or pointer, bad prec, variant not -1, 0, 3,
+ * 4 or 5, ns not 0, 1, 2 or (variant 5) 4 dividing Ls, sb making a CTA of more
  * than 256 threads). */
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb);
 int dwf_get_hop_config(dwf_handle h, int prec, int *variant, int *ns, int *sb);
@@ -323,7 +320,12 @@ int dwf_get_mix_mode(dwf_handle h, int prec, int *mode);
  * address is looked up once per device, on the first call made with that
  * device current.  Every call shares the array and it keeps the last call's
  * contents; calls whose GPU work overlaps (other streams, other handles of
- * the same device) race.  in/out: device EO fields as for dwf_apply.
+ * the same device) race, so a caller that uses the array from several streams
+ * must order each call after the others' work (events or a synchronisation).
+ * Every call reads the handle's current state: its links (dwf_set_gauge), its
+ * mixing mode and its hop configuration.  The first call on a device may also
+ * make the driver load the library's device code that holds the array.
+ * in/out: device EO fields as for dwf_apply.
  */
 int dwf_apply_eo_noalloc(dwf_handle h, int prec, int dag, const void *in, void *out, void *stream);
 
@@ -362,6 +364,16 @@ int dwf_time_hop(dwf_handle h, int prec, int reps, int flush_l2, double *us_per_
  * used by one thread at a time). Errors: DWF_EINVAL, DWF_ENOGAUGE, DWF_ECUDA. */
 int dwf_time_iteration(dwf_handle h, int prec, int reps, int flush_l2, double *us5, double *bytes5,
                        void *stream);
+
+/* Measured arithmetic peaks of the current device (no counterpart in the
+ * paper: the denominators of the hop kernels' arithmetic rooflines).
+ * out (host, 4 doubles): [0] FP32 TFLOP/s with scalar FMAs, [1] FP32 TFLOP/s
+ * with packed FP32x2 FMAs, [2] FP64 TFLOP/s with FMAs, [3] the device's SM
+ * count.  Each rate is the best of three timed launches (CUDA events on
+ * `stream`) of a kernel of 8 independent FMA chains per thread, 8 CTAs of 256
+ * threads per SM, 2 flops per FMA lane.  Allocates and frees a small scratch
+ * buffer; synchronises `stream`.  Errors: DWF_EINVAL (NULL out), DWF_ECUDA. */
+int dwf_alu_peaks(double *out, void *stream);
 
 /* Extremal eigenvalues of D^dag D, D the even-odd matrix D_pc of the handle's
  * form (Sec. 2.3; for Neff's form the alpha-dependent one): Sec. 3.2 takes
@@ -460,6 +472,26 @@ int dwf_precond_apply(dwf_handle h, int which, const void *in, void *out, void *
  * DWF_ECUDA. */
 int dwf_precond_loss_grad(dwf_handle h, int npairs, const void *const *b, const void *const *x,
                           double *loss, double *grad, void *stream);
+/* One Adam step of the training (beta 0.9, 0.999, eps 1e-8, step size lr,
+ * the step count continuing from the network's), from the gradient grad
+ * (host, FP64, weight layout above) instead of one computed from pairs: the
+ * same update dwf_precond_train applies after each minibatch.  Errors:
+ * DWF_EINVAL (NULL pointer, no network of that depth, lr <= 0), DWF_ECUDA. */
+int dwf_precond_adam_step(dwf_handle h, int layers, const double *grad, double lr, void *stream);
+
+/* Save the handle's network to a host file, and load one into a handle of the
+ * same Ls: a binary header (magic "DWFNET", format version 1, layers,
+ * channels = Ls, Adam step count, number of complex weights n), then the FP64
+ * master weights, Adam's first moments and Adam's second moments, n complex
+ * doubles each (little-endian).  Loading replaces the handle's network
+ * (training continues from the saved Adam state) and recomputes the
+ * BF16-rounded compute copy.  Errors: DWF_EINVAL (NULL pointer, no network to
+ * save, unreadable or unwritable file, wrong magic or version, a file for
+ * another Ls, a truncated file), DWF_ENOGAUGE (load before dwf_set_gauge),
+ * DWF_ECUDA. */
+int dwf_precond_save(dwf_handle h, const char *path);
+int dwf_precond_load(dwf_handle h, const char *path);
+
 /* Make the pairs from nsrc 4D sources b4[k] (device) and train (above).
  * Errors: DWF_EINVAL (nsrc < 1, NULL pointers, bad parameters, Ls > 16),
  * DWF_ENOGAUGE, DWF_ECUDA, and the solver's errors while making the pairs. */

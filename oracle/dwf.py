@@ -174,6 +174,35 @@ class DWF:
                 y[bl.t] += spin(bl.S.conj().T, bl.cw * wx[bl.s] + bl.c1 * x5[bl.s])
         return y
 
+    def apply_row(self, x5: np.ndarray, s: int) -> np.ndarray:
+        """Row s of y = D x: sum over the blocks (s, t) of (cw D_W + c1) S x[t].
+
+        The same block formula as apply(), one row at a time, for lattices whose
+        stacked block fields do not fit in memory: D_W is linear, so the blocks
+        of a row are summed before it is applied (one D_W per row).
+        """
+        inner = np.zeros_like(x5[0], dtype=np.complex128)
+        local = np.zeros_like(x5[0], dtype=np.complex128)
+        for bl in self._blocks:
+            if bl.s != s:
+                continue
+            sx = spin(bl.S, x5[bl.t])
+            inner += bl.cw * sx
+            local += bl.c1 * sx
+        return self.dw(inner) + local
+
+    def residual_norm(self, b5, x5: np.ndarray) -> float:
+        """||b5 - D x5|| / ||b5||, accumulated row by row (apply_row); b5 is a
+        5D array or a function of s giving row s."""
+        row = b5.__getitem__ if isinstance(b5, np.ndarray) else b5
+        num = den = 0.0
+        for s in range(self.Ls):
+            bs = row(s)
+            r = (bs - self.apply_row(x5, s)).ravel()
+            num += float(np.vdot(r, r).real)
+            den += float(np.vdot(bs.ravel(), bs.ravel()).real)
+        return float(np.sqrt(num / den))
+
     def dense(self) -> np.ndarray:
         """Dense matrix of the full 5D operator (tiny lattices only)."""
         n = self.Ls * int(np.prod(self.dims)) * 12
@@ -224,6 +253,19 @@ class DWF:
         v = np.zeros((self.Ls,) + b4.shape, dtype=np.complex128)
         v[self.Ls - 1] = b4
         return -self.d_minus(self.P(v, dag=True))
+
+    def source_row(self, b4: np.ndarray, s: int) -> np.ndarray:
+        """Row s of source_5d(b4), from the rows of P^dag that (0, ..., 0, b4)
+        reaches: [P^dag v]_s = sum over the blocks (Ls-1, s) of P of S^dag b4,
+        then -D_- of that row (c_s D_W - 1 for row s)."""
+        Ls = self.Ls
+        v = np.zeros_like(b4, dtype=np.complex128)
+        for (r, t, S) in self._p_blocks():
+            if r == Ls - 1 and t == s:
+                v += spin(S.conj().T, b4)
+        if not np.any(v):
+            return v
+        return -(float(self._cs[s]) * self.dw(v) - v)
 
     def project_4d(self, x5: np.ndarray) -> np.ndarray:
         """x4 = [P^dag x5]_{s=1} (Sec. 2.3)."""

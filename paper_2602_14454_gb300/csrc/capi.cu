@@ -577,7 +577,8 @@ long long dwf_launch_count(dwf_handle h) { return h ? h->launches : 0; }
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb)
 {
     if (!h || prec < 0 || prec > 2) return dwf_set_error(DWF_EINVAL, "bad handle or precision");
-    if (variant < -1 || variant > 5) return dwf_set_error(DWF_EINVAL, "variant must be -1 or 0..5");
+    if (variant < -1 || variant > 5 || variant == 1 || variant == 2)
+        return dwf_set_error(DWF_EINVAL, "variant must be -1, 0, 3, 4 or 5");
     if (ns < 0 || ns > 4 || ns == 3 || (ns && h->Ls % ns) || (ns == 4 && variant != 5))
         return dwf_set_error(DWF_EINVAL, "ns must be 0, 1, 2 or (variant 5) 4, and divide Ls");
     const int nsv = ns ? ns : hop_default_ns(prec, h->Ls);
@@ -654,6 +655,7 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
             for (int ns = 1; ns <= 4; ns *= 2) {
                 if (mix == 1 && !h->fm.structured) continue;
                 if (mix == 2 && prec == DWF_F64) continue;
+                if (var == 1 || var == 2) continue;   // numbers of removed variants
                 if (mix != 0 && var != 0) continue;   // those mixings exist in the direct variant only
                 if (var == 5 && prec != DWF_F16) continue;
                 if (ns == 4 && var != 5) continue;
@@ -662,8 +664,6 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
                 for (int threads = 64; threads <= 256; threads += 64) {
                     const int sb = threads / LsN;
                     if (sb < 1 || LsN * sb > 256) continue;
-                    if (var == 1 && hop_staged_smem_bytes(prec, h->Ls, sb) > 220 * 1024) continue;
-                    if (var == 2 && hop_pipe_smem_bytes(prec, h->Ls, sb) > 220 * 1024) continue;
                     h->mixmode[prec] = mix;
                     h->hop_var[prec] = var;
                     h->hop_ns[prec] = ns;

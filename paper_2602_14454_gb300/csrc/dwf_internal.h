@@ -158,16 +158,14 @@ inline cudaError_t smem_optin(K *kernel, int bytes, unsigned long long &done)
 
 // ------------------------------------------------------------ launchers
 // prec: DWF_F64 / DWF_F32 / DWF_F16 (template dispatch inside)
-// var: 0 direct neighbour loads, 1 TMA-staged neighbour sites, 2 persistent warp-specialised
-// TMA pipeline; ns: fifth-direction
+// var: 0 direct neighbour loads, 3 persistent sweep, 4 4D-blocked tiles, 5 FP16 projection
+// arithmetic (1 and 2 select the default); ns: fifth-direction
 // slices per thread (1, or 2 when Ls is even); sb: sites per CTA.
 // var < 0 / ns <= 0 / sb <= 0 pick the defaults.
 cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int var, int ns, int sb, cudaStream_t st);
 int hop_default_variant(int prec);
 int hop_default_ns(int prec, int Ls);
 int hop_default_sb(int prec, int Ls, int ns);
-size_t hop_staged_smem_bytes(int prec, int Ls, int sb);
-size_t hop_pipe_smem_bytes(int prec, int Ls, int sb);
 cudaError_t launch_mix(int prec, const MixArgs &a, cudaStream_t st);
 cudaError_t launch_cg_update(int prec, const CgUpdateArgs &a, cudaStream_t st);
 // Batched launches over nsys systems with equal Ls (tables in device memory;

@@ -1,0 +1,790 @@
+// The even-odd hopping stencil of the 5D domain-wall operator with its fused
+// fifth-direction mixing and epilogue (one launch = one of the two hops of
+// every application of the even-odd matrix, eq. even-odd_linear_equation).
+//
+// H psi(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ]
+// is the hopping sum of eq. (Wilson_matrix) (D_W = (4 - M0) - H/2); it is the
+// same for every fifth-direction slice s.  A CTA handles SB sites x all Ls
+// slices; each thread owns NS slices of one site (s = x + n Ls/NS), so every
+// link it loads serves NS slices.  The adjoint hop is gamma5 H gamma5
+// (projector signs flipped).
+//
+// Chiral basis: gamma_mu = [[0, e_mu], [e_mu^dag, 0]], e_k = -i sigma_k,
+// e_4 = 1, so (1 - sig gamma_mu) psi = [h ; -sig e_mu^dag h] with the half
+// spinor h = psi_u - sig e_mu psi_l: only h is multiplied by the link.  h is
+// held as spin pairs Hx[a] = (h0.re, h1.re), Hy[a] = (h0.im, h1.im), so the
+// SU(3) product is 4 packed FMAs per (a, b) for both spins at once.
+//
+// Variants: 0 (direct) every thread reads its 8 neighbour spinors from
+// global memory; 3 the same, persistent over consecutive tiles; 4 the same
+// with each CTA's sites taken as a 4D block (neighbour reuse in L1); 5 (FP16)
+// variant 0 with the spin projection in FP16 arithmetic.
+// After the hop each thread writes h(site, s) to the CTA's shared tile and
+// forms (Post h)(site, s) = sum_t Post[s][t] h(site, t) per chirality; the
+// epilogue adds a mixed second input, forms a residual, updates a solution
+// accumulator, applies a final mixing and reduces |o|^2 deterministically.
+#pragma once
+
+#include <cstdint>
+
+#include "stencil.cuh"
+
+namespace dwf {
+namespace {
+
+// one (site, s) of a neighbour site copied to shared memory: the Ls x G block
+// of 16-byte vectors in the global layout, followed (FP16) by its scales
+template <int P, typename T2>
+__device__ __forceinline__ void ld_pairs_smem(const unsigned char *slot, int s, int Ls, T2 *v)
+{
+    typedef typename PairReal<T2>::R R;
+    if constexpr (P == DWF_F64) {
+        const double2 *p = reinterpret_cast<const double2 *>(slot) + s;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const double2 q = p[k * Ls];
+            v[k] = p_make((R)q.x, (R)q.y);
+        }
+    } else if constexpr (P == DWF_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>(slot) + s;
+#pragma unroll
+        for (int g = 0; g < 6; ++g) {
+            const float4 q = p[g * Ls];
+            v[2 * g] = p_make((R)q.x, (R)q.y);
+            v[2 * g + 1] = p_make((R)q.z, (R)q.w);
+        }
+    } else {
+        const uint4 *p = reinterpret_cast<const uint4 *>(slot) + s;
+        const float sc = reinterpret_cast<const float *>(slot + (size_t)Ls * 48)[s];
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            const uint4 q = p[g * Ls];
+            const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
+                v[4 * g + k] = p_make((R)(f2.x * sc), (R)(f2.y * sc));
+            }
+        }
+    }
+}
+
+template <typename T2>
+__device__ __forceinline__ void put_tile(T2 *tile, int s, const T2 *v)
+{
+    T2 *dst = tile + s * 12;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) dst[k] = v[k];
+}
+
+// ------------------------------------------------------------ the epilogue
+struct CtaBarrier {
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+// Where the CTA's tile lives and which threads share the structured mixing.
+template <typename T2>
+struct TileCtx {
+    T2 *tile0;     // tile of the CTA's first site
+    int tstride;   // pairs between consecutive sites
+    int nsites;    // sites in the tile
+    int tid, nthr; // this thread among the threads that share the work
+};
+
+// o[n] += (mixing of this thread's rows of the tile).  MIX 0, dense: Ls x Ls
+// matrix M from shared memory, per thread.  MIX 1, structured: the CTA first
+// transforms the whole tile in place along its chains; MIX 2 / 3, tensor
+// cores: the CTA's full warps transform the tile in place with TF32 MMAs
+// (3 / 2 products, see mma_mix_tile); then every thread reads its rows back.
+// The tile must hold the input and be visible to all threads on entry.
+template <int MIX, int NS, typename T2, typename R, typename Bar>
+__device__ __forceinline__ void mix_into(const void *prog, const R *M, const TileCtx<T2> &tc, T2 *mytile,
+                                         int x, int LsN, int Ls, bool active, T2 (*o)[12], const Bar &bar,
+                                         int band = 0)
+{
+    if constexpr (MIX >= 1) {
+        if constexpr (MIX == 1)
+            chain_mix<R>(reinterpret_cast<const MixProg<R> *>(prog), tc.tile0, tc.tstride, tc.nsites, Ls, tc.tid,
+                         tc.nthr);
+        else
+            mma_mix_tile<MIX == 2 ? 2 : 1>(reinterpret_cast<const float *>(M), reinterpret_cast<float *>(tc.tile0),
+                                           tc.tstride, tc.nsites, Ls, Ls / LsN, tc.tid >> 5, tc.nthr >> 5);
+        bar.sync();
+        if (active) {
+#pragma unroll
+            for (int n = 0; n < NS; ++n) {
+                T2 h[12];
+                ld_tile_row(mytile + (x + n * LsN) * 12, h);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) o[n][k] = p_add(o[n][k], h[k]);
+            }
+        }
+    } else if (active) {
+        if (band)
+            mix_pairs_band<NS>(M, mytile, x, Ls, o);
+        else
+            mix_pairs<NS>(M, mytile, x, Ls, o);
+    }
+}
+
+// acc: hop result of this thread's NS slices.  Every thread taking part in
+// `bar` must call it.  Returns this thread's contribution to |o|^2.
+template <int P, int NS, int MIX = 0, typename T2, typename R, typename Bar>
+__device__ __forceinline__ R hop_epilogue_core(const HopArgs &a, T2 (*acc)[12], const TileCtx<T2> &tc,
+                                                    T2 *mytile, const R *mtx, int site, int x, int LsN, bool active,
+                                                    const Bar &bar)
+{
+    const int Ls = a.Ls;
+    const int msz = 2 * Ls * Ls;
+    // tensor-core mixing: FP16 fields take the two-product form (its error is that of the FP16 storage)
+    constexpr int MX = (MIX == 2 && P == DWF_F16) ? 3 : MIX;
+    if (active) {
+#pragma unroll
+        for (int n = 0; n < NS; ++n) put_tile(mytile, x + n * LsN, acc[n]);
+    }
+    bar.sync();
+
+    T2 o[NS][12];
+#pragma unroll
+    for (int n = 0; n < NS; ++n)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o[n][k] = p_splat((R)0);
+    mix_into<MX, NS>(a.post_prog, mtx, tc, mytile, x, LsN, Ls, active, o, bar, a.post_band);
+
+    if (a.ymode == 1) {
+        if (active) {
+#pragma unroll
+            for (int n = 0; n < NS; ++n) {
+                T2 y[12];
+                ld_pairs<P, false>(a.y, (size_t)site, x + n * LsN, Ls, y);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) o[n][k] = p_add(o[n][k], y[k]);
+            }
+        }
+    } else if (a.ymode == 2) {
+        bar.sync();
+        if (active) {
+#pragma unroll
+            for (int n = 0; n < NS; ++n) {
+                T2 y[12];
+                ld_pairs<P, false>(a.y, (size_t)site, x + n * LsN, Ls, y);
+                put_tile(mytile, x + n * LsN, y);
+            }
+        }
+        bar.sync();
+        mix_into<MX, NS>(a.y_prog, mtx + msz, tc, mytile, x, LsN, Ls, active, o, bar, a.y_band);
+    }
+
+    if (a.rin.v && active) {
+        const R al = (R)(*a.ralpha);
+        const T2 nal = p_splat(-al);
+#pragma unroll
+        for (int n = 0; n < NS; ++n) {
+            T2 r[12];
+            ld_pairs<P, false>(a.rin, (size_t)site, x + n * LsN, Ls, r);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) o[n][k] = p_fma(nal, o[n][k], r[k]);
+        }
+        if (a.xacc) {
+            constexpr int XP = (P == DWF_F64) ? DWF_F64 : DWF_F32;
+            FieldRef xf;
+            xf.v = a.xacc;
+            const T2 xa = p_splat((R)(*a.xalpha));
+#pragma unroll
+            for (int n = 0; n < NS; ++n) {
+                T2 xv[12], dx[12];
+                ld_pairs<XP, false>(xf, (size_t)site, x + n * LsN, Ls, xv);
+                ld_pairs<P, false>(a.xdir, (size_t)site, x + n * LsN, Ls, dx);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) xv[k] = p_fma(xa, dx[k], xv[k]);
+                st_pairs<XP>(xf, (size_t)site, x + n * LsN, Ls, xv);
+            }
+        }
+    }
+
+    // |o|^2 of this thread in the arithmetic precision (FP32 for FP32 and FP16
+    // fields); the grid reduction adds the per-warp sums in FP64
+    R nrm = 0;
+    if (active && a.red.op != RED_NONE) {
+        T2 s2 = p_splat((R)0);
+#pragma unroll
+        for (int n = 0; n < NS; ++n)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) s2 = p_fma(o[n][k], o[n][k], s2);
+        nrm = s2.x + s2.y;
+    }
+
+    if (a.zmat) {
+        bar.sync();
+        if (active) {
+#pragma unroll
+            for (int n = 0; n < NS; ++n) put_tile(mytile, x + n * LsN, o[n]);
+        }
+        bar.sync();
+        T2 z[NS][12];
+#pragma unroll
+        for (int n = 0; n < NS; ++n)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) z[n][k] = p_splat((R)0);
+        mix_into<MX, NS>(a.z_prog, mtx + 2 * msz, tc, mytile, x, LsN, Ls, active, z, bar, a.z_band);
+        if (active) {
+#pragma unroll
+            for (int n = 0; n < NS; ++n) st_pairs<P>(a.out, (size_t)site, x + n * LsN, Ls, z[n]);
+        }
+    } else if (active) {
+#pragma unroll
+        for (int n = 0; n < NS; ++n) st_pairs<P>(a.out, (size_t)site, x + n * LsN, Ls, o[n]);
+    }
+
+    return nrm;
+}
+
+// Epilogue of the kernels whose whole CTA forms one tile (blockDim = (Ls/NS, SB)).
+template <typename T2>
+__device__ __forceinline__ TileCtx<T2> cta_tile(T2 *tile0, int Ls)
+{
+    TileCtx<T2> tc;
+    tc.tile0 = tile0;
+    tc.tstride = Ls * 12 + 2;
+    tc.nsites = blockDim.y;
+    tc.tid = threadIdx.y * blockDim.x + threadIdx.x;
+    tc.nthr = blockDim.x * blockDim.y;
+    return tc;
+}
+
+template <int P, int NS, int MIX = 0, typename T2, typename R>
+__device__ __forceinline__ void hop_epilogue(const HopArgs &a, T2 (*acc)[12], T2 *tile0, int j, const R *mtx,
+                                             int site, int x, int LsN, bool active)
+{
+    const TileCtx<T2> tc = cta_tile(tile0, a.Ls);
+    const auto nrm = hop_epilogue_core<P, NS, MIX>(a, acc, tc, tile0 + j * tc.tstride, mtx, site, x, LsN, active,
+                                                CtaBarrier());
+    if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
+}
+
+// matrices arrive as [chi][t][s]; store them as [chi][t][x*NS + n] with s = x + n*LsN
+template <int NS, typename R>
+__device__ __forceinline__ void load_matrices(const HopArgs &a, R *mtx)
+{
+    const int Ls = a.Ls, LsN = Ls / NS, msz = 2 * Ls * Ls;
+    const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int k = tid; k < msz; k += nt) {
+        const int chi_t = k / Ls, s = k % Ls;
+        const int dst = chi_t * Ls + (s % LsN) * NS + s / LsN;
+        mtx[dst] = reinterpret_cast<const R *>(a.post)[k];
+        if (a.ymode == 2) mtx[msz + dst] = reinterpret_cast<const R *>(a.ymat)[k];
+        if (a.zmat) mtx[2 * msz + dst] = reinterpret_cast<const R *>(a.zmat)[k];
+    }
+}
+
+// ------------------------------------------------------ variant 0: direct
+template <int P, bool DAG, int D, int NS, typename T2>
+__device__ __forceinline__ void hop_dir(T2 (*acc)[12], const FieldRef &in, int nb, int x, int LsN, int Ls,
+                                        const typename Tr<P>::link_t *U)
+{
+    constexpr int MU = D & 3;
+    constexpr int SIG = (D < 4 ? 1 : -1) * (DAG ? -1 : 1);
+    T2 u[9];
+    load_link<P, true>(U + D * 18, u);
+#pragma unroll
+    for (int n = 0; n < NS; ++n) {
+        T2 v[12];
+        ld_pairs<P, true>(in, (size_t)nb, x + n * LsN, Ls, v);
+        hop_one<MU, SIG>(acc[n], u, v);
+    }
+}
+
+// FP16 fields (variant 5): the spin projection runs in FP16 arithmetic on the
+// stored half2 pairs (one rounding, at the level of the FP16 storage), only the
+// six half-spinor pairs are converted to FP32, and the SU(3) product runs in
+// FP32 for all NS slices of the thread at once, so that every link splat
+// serves NS slices; the product is scaled by the neighbour's (site, s) scale
+// and reconstructed into the FP32 accumulator.
+template <bool DAG, int D, int NS>
+__device__ __forceinline__ void hop_dir_h2(float2 (*acc)[12], const FieldRef &in, int nb, int x, int LsN, int Ls,
+                                           const __half *U)
+{
+    constexpr int MU = D & 3;
+    constexpr int SIG = (D < 4 ? 1 : -1) * (DAG ? -1 : 1);
+    const __half2 *Uh = reinterpret_cast<const __half2 *>(U + D * 18);
+    float2 u[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = __half22float2(__ldg(Uh + k));
+    const uint4 *base = reinterpret_cast<const uint4 *>(in.v) + ((size_t)nb * 3) * Ls;
+    const float *sbase = in.scale + (size_t)nb * ((Ls + 3) & ~3);
+    float2 Hx[NS][3], Hy[NS][3];
+    float sc[NS];
+#pragma unroll
+    for (int n = 0; n < NS; ++n) {
+        const int s = x + n * LsN;
+        __half2 v[12];
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            const uint4 q = __ldg(base + (size_t)g * Ls + s);
+            v[4 * g] = *reinterpret_cast<const __half2 *>(&q.x);
+            v[4 * g + 1] = *reinterpret_cast<const __half2 *>(&q.y);
+            v[4 * g + 2] = *reinterpret_cast<const __half2 *>(&q.z);
+            v[4 * g + 3] = *reinterpret_cast<const __half2 *>(&q.w);
+        }
+        sc[n] = __ldg(sbase + s);
+        __half2 hx[3], hy[3];
+        project_h2<MU, SIG>(v, hx, hy);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Hx[n][a] = __half22float2(hx[a]);
+            Hy[n][a] = __half22float2(hy[a]);
+        }
+    }
+    float2 Qx[NS][3], Qy[NS][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int n = 0; n < NS; ++n) Qx[n][a] = Qy[n][a] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float2 ur = p_splat(u[a * 3 + b].x), ui = p_splat(u[a * 3 + b].y), nui = p_splat(-u[a * 3 + b].y);
+#pragma unroll
+            for (int n = 0; n < NS; ++n) {
+                Qx[n][a] = p_fma(ur, Hx[n][b], Qx[n][a]);
+                Qx[n][a] = p_fma(nui, Hy[n][b], Qx[n][a]);
+                Qy[n][a] = p_fma(ur, Hy[n][b], Qy[n][a]);
+                Qy[n][a] = p_fma(ui, Hx[n][b], Qy[n][a]);
+            }
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NS; ++n) {
+        const float2 scp = p_splat(sc[n]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Qx[n][a] = p_mul(Qx[n][a], scp);
+            Qy[n][a] = p_mul(Qy[n][a], scp);
+        }
+        reconstruct<MU, SIG>(acc[n], Qx[n], Qy[n]);
+    }
+}
+
+template <int P, bool DAG, int NS, bool H2>
+__device__ __forceinline__ void gather8(typename Tr<P>::pair (*acc)[12], const HopArgs &a, const int *n8, int x,
+                                        int LsN, int Ls, const typename Tr<P>::link_t *U)
+{
+    if constexpr (H2 && P == DWF_F16) {
+        hop_dir_h2<DAG, 0, NS>(acc, a.in, n8[0], x, LsN, Ls, U);
+        hop_dir_h2<DAG, 1, NS>(acc, a.in, n8[1], x, LsN, Ls, U);
+        hop_dir_h2<DAG, 2, NS>(acc, a.in, n8[2], x, LsN, Ls, U);
+        hop_dir_h2<DAG, 3, NS>(acc, a.in, n8[3], x, LsN, Ls, U);
+        hop_dir_h2<DAG, 4, NS>(acc, a.in, n8[4], x, LsN, Ls, U);
+        hop_dir_h2<DAG, 5, NS>(acc, a.in, n8[5], x, LsN, Ls, U);
+        hop_dir_h2<DAG, 6, NS>(acc, a.in, n8[6], x, LsN, Ls, U);
+        hop_dir_h2<DAG, 7, NS>(acc, a.in, n8[7], x, LsN, Ls, U);
+    } else {
+        hop_dir<P, DAG, 0, NS>(acc, a.in, n8[0], x, LsN, Ls, U);
+        hop_dir<P, DAG, 1, NS>(acc, a.in, n8[1], x, LsN, Ls, U);
+        hop_dir<P, DAG, 2, NS>(acc, a.in, n8[2], x, LsN, Ls, U);
+        hop_dir<P, DAG, 3, NS>(acc, a.in, n8[3], x, LsN, Ls, U);
+        hop_dir<P, DAG, 4, NS>(acc, a.in, n8[4], x, LsN, Ls, U);
+        hop_dir<P, DAG, 5, NS>(acc, a.in, n8[5], x, LsN, Ls, U);
+        hop_dir<P, DAG, 6, NS>(acc, a.in, n8[6], x, LsN, Ls, U);
+        hop_dir<P, DAG, 7, NS>(acc, a.in, n8[7], x, LsN, Ls, U);
+    }
+}
+
+// One tile of SB sites: blockDim = (Ls/NS, SB), site = u SB + threadIdx.y.
+// The norm reduction runs over the nb_red tiles that share a.red.
+template <int P, bool DAG, int NS, int MIX, bool H2 = false>
+__device__ __forceinline__ void hop_direct_tile(const HopArgs &a, int u, unsigned nb_red)
+{
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
+    typedef typename Tr<P>::link_t link_t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ls = a.Ls;
+    const int LsN = Ls / NS;
+    const int x = threadIdx.x;
+    const int j = threadIdx.y;
+    const int SB = blockDim.y;
+    const int site = u * SB + j;
+    const bool active = site < a.Vh;
+    const int tstride = Ls * 12 + 2;
+    T2 *tile = reinterpret_cast<T2 *>(smem_raw);
+    R *mtx = reinterpret_cast<R *>(tile + SB * tstride);
+    load_matrices<NS>(a, mtx);
+
+    T2 acc[NS][12];
+#pragma unroll
+    for (int n = 0; n < NS; ++n)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[n][k] = p_splat((R)0);
+    if (active) {
+        const int *nb = a.nbr + (size_t)site * 8;
+        const link_t *U = reinterpret_cast<const link_t *>(a.gauge) + (size_t)site * 8 * 18;
+        int n8[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) n8[d] = __ldg(nb + d);
+        gather8<P, DAG, NS, H2>(acc, a, n8, x, LsN, Ls, U);
+    }
+    const TileCtx<T2> tc = cta_tile(tile, Ls);
+    const auto nrm = hop_epilogue_core<P, NS, MIX>(a, acc, tc, tile + j * tc.tstride, mtx, site, x, LsN, active,
+                                                     CtaBarrier());
+    if (a.red.op != RED_NONE) grid_reduce(nrm, a.red, u, nb_red);
+}
+
+template <int P, bool DAG, int NS, int MIX, bool H2 = false>
+__global__ void __launch_bounds__(256) hop_kernel(const HopArgs a)
+{
+    hop_direct_tile<P, DAG, NS, MIX, H2>(a, blockIdx.x, gridDim.x);
+}
+
+// With one slice per thread the FP16 variant-5 and the FP32 direct kernels run
+// faster with more resident warps (the gathers are latency bound): capped at
+// 64 registers (FP16: 8 CTAs of 128 threads per SM) the hop at 16^3x32, Ls 16
+// went from 96.2 us to 85.8 us, capped at 85 (FP32: 6 CTAs) from 117.8 us to
+// 106.3 us.
+template <int P, bool DAG, int MIX, bool H2>
+__global__ void __launch_bounds__(256, P == DWF_F16 ? 4 : 3) hop_kernel_occ(const HopArgs a)
+{
+    hop_direct_tile<P, DAG, 1, MIX, H2>(a, blockIdx.x, gridDim.x);
+}
+
+// Batched form: one launch over nsys systems that share Ls and the CTA shape
+// (each with its own fields, matrices, scalars and reduction buffers).  CTA b
+// works on tile b / nsys of system b % nsys, so that consecutive CTAs read the
+// same sites' links and neighbour indices, which then come from L2 for all
+// systems but the first.  A system whose skip flag is set is left untouched.
+template <int P, bool DAG, int NS, int MIX, bool H2>
+__device__ __forceinline__ void hop_batch_body(const HopArgs *__restrict__ tab, int nsys)
+{
+    __shared__ __align__(16) unsigned char abuf[sizeof(HopArgs)];
+    const int sys = blockIdx.x % nsys, u = blockIdx.x / nsys;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    const unsigned *src = reinterpret_cast<const unsigned *>(tab + sys);
+    for (int k = tid; k < (int)(sizeof(HopArgs) / 4); k += nt) reinterpret_cast<unsigned *>(abuf)[k] = src[k];
+    __syncthreads();
+    const HopArgs &a = *reinterpret_cast<const HopArgs *>(abuf);
+    if (a.skip && *a.skip) return;
+    hop_direct_tile<P, DAG, NS, MIX, H2>(a, u, (a.Vh + blockDim.y - 1) / blockDim.y);
+}
+
+template <int P, bool DAG, int NS, int MIX, bool H2 = false>
+__global__ void __launch_bounds__(256) hop_batch_kernel(const HopArgs *__restrict__ tab, int nsys)
+{
+    hop_batch_body<P, DAG, NS, MIX, H2>(tab, nsys);
+}
+
+// the occupancy-capped form of the batched hop (see hop_kernel_occ)
+template <int P, bool DAG, int MIX, bool H2>
+__global__ void __launch_bounds__(256, P == DWF_F16 ? 4 : 3) hop_batch_kernel_occ(const HopArgs *__restrict__ tab,
+                                                                                 int nsys)
+{
+    hop_batch_body<P, DAG, 1, MIX, H2>(tab, nsys);
+}
+
+// ------------------------------------------------- variant 4: blocked tiles
+// The direct kernel with each CTA's SB sites taken as a 4D block
+// tb[0] x tb[1] x tb[2] x tb[3] of the half lattice (coordinates xh = x/2, y,
+// z, t; the even-odd index is lexicographic in them), so that the neighbour
+// sites the CTA reads overlap and are served from L1.  The block extents
+// divide the half-lattice extents.
+struct Tile4 {
+    int tb[4];
+};
+
+template <int P, bool DAG, int NS>
+__global__ void __launch_bounds__(256) hop_block_kernel(const HopArgs a, Tile4 T)
+{
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
+    typedef typename Tr<P>::link_t link_t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ls = a.Ls;
+    const int LsN = Ls / NS;
+    const int x = threadIdx.x;
+    const int j = threadIdx.y;
+    const int SB = blockDim.y;
+    // block coordinates (lexicographic over the tiled half lattice) and local offsets
+    int b = blockIdx.x, l = j, c[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const int nb = a.ext[d] / T.tb[d];
+        const int bd = b % nb, ld = l % T.tb[d];
+        b /= nb;
+        l /= T.tb[d];
+        c[d] = bd * T.tb[d] + ld;
+    }
+    const int site = c[0] + a.ext[0] * (c[1] + a.ext[1] * (c[2] + a.ext[2] * c[3]));
+    const bool active = true;
+    const int tstride = Ls * 12 + 2;
+    T2 *tile = reinterpret_cast<T2 *>(smem_raw);
+    R *mtx = reinterpret_cast<R *>(tile + SB * tstride);
+    load_matrices<NS>(a, mtx);
+
+    T2 acc[NS][12];
+#pragma unroll
+    for (int n = 0; n < NS; ++n)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[n][k] = p_splat((R)0);
+    {
+        const int *nb = a.nbr + (size_t)site * 8;
+        const link_t *U = reinterpret_cast<const link_t *>(a.gauge) + (size_t)site * 8 * 18;
+        int n8[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) n8[d] = __ldg(nb + d);
+        hop_dir<P, DAG, 0, NS>(acc, a.in, n8[0], x, LsN, Ls, U);
+        hop_dir<P, DAG, 1, NS>(acc, a.in, n8[1], x, LsN, Ls, U);
+        hop_dir<P, DAG, 2, NS>(acc, a.in, n8[2], x, LsN, Ls, U);
+        hop_dir<P, DAG, 3, NS>(acc, a.in, n8[3], x, LsN, Ls, U);
+        hop_dir<P, DAG, 4, NS>(acc, a.in, n8[4], x, LsN, Ls, U);
+        hop_dir<P, DAG, 5, NS>(acc, a.in, n8[5], x, LsN, Ls, U);
+        hop_dir<P, DAG, 6, NS>(acc, a.in, n8[6], x, LsN, Ls, U);
+        hop_dir<P, DAG, 7, NS>(acc, a.in, n8[7], x, LsN, Ls, U);
+    }
+    hop_epilogue<P, NS>(a, acc, tile, j, mtx, site, x, LsN, active);
+}
+
+// ------------------------------------------ variant 3: persistent direct sweep
+// The direct kernel, persistent: CTA b handles the consecutive tiles
+// [b*tpc, (b+1)*tpc).  Consecutive tiles are consecutive x-rows, so an input
+// row fetched as the +y neighbour of one tile is fetched again (from L1) as
+// the x neighbour and the -y neighbour of the next two tiles.
+template <int P, bool DAG, int NS>
+__global__ void __launch_bounds__(256) hop_sweep_kernel(const HopArgs a, int tpc)
+{
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
+    typedef typename Tr<P>::link_t link_t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ls = a.Ls;
+    const int LsN = Ls / NS;
+    const int x = threadIdx.x;
+    const int j = threadIdx.y;
+    const int SB = blockDim.y;
+    const int tstride = Ls * 12 + 2;
+    T2 *tile = reinterpret_cast<T2 *>(smem_raw);
+    R *mtx = reinterpret_cast<R *>(tile + SB * tstride);
+    load_matrices<NS>(a, mtx);
+    const int ntiles = (a.Vh + SB - 1) / SB;
+    const int u0 = blockIdx.x * tpc;
+    const int u1 = min(u0 + tpc, ntiles);
+    double nrm = 0;
+    for (int u = u0; u < u1; ++u) {
+        const int site = u * SB + j;
+        const bool active = site < a.Vh;
+        T2 acc[NS][12];
+#pragma unroll
+        for (int n = 0; n < NS; ++n)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[n][k] = p_splat((R)0);
+        if (active) {
+            const int *nb = a.nbr + (size_t)site * 8;
+            const link_t *U = reinterpret_cast<const link_t *>(a.gauge) + (size_t)site * 8 * 18;
+            int n8[8];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) n8[d] = __ldg(nb + d);
+            hop_dir<P, DAG, 0, NS>(acc, a.in, n8[0], x, LsN, Ls, U);
+            hop_dir<P, DAG, 1, NS>(acc, a.in, n8[1], x, LsN, Ls, U);
+            hop_dir<P, DAG, 2, NS>(acc, a.in, n8[2], x, LsN, Ls, U);
+            hop_dir<P, DAG, 3, NS>(acc, a.in, n8[3], x, LsN, Ls, U);
+            hop_dir<P, DAG, 4, NS>(acc, a.in, n8[4], x, LsN, Ls, U);
+            hop_dir<P, DAG, 5, NS>(acc, a.in, n8[5], x, LsN, Ls, U);
+            hop_dir<P, DAG, 6, NS>(acc, a.in, n8[6], x, LsN, Ls, U);
+            hop_dir<P, DAG, 7, NS>(acc, a.in, n8[7], x, LsN, Ls, U);
+        }
+        __syncthreads();   // the previous tile's epilogue is done with `tile`
+        nrm += hop_epilogue_core<P, NS>(a, acc, cta_tile(tile, Ls), tile + j * tstride, mtx, site, x, LsN, active,
+                                        CtaBarrier());
+    }
+    if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
+}
+
+// ---------------------------------------------------------------- launch
+template <int P>
+size_t direct_smem(int Ls, int SB)
+{
+    typedef typename Tr<P>::real R;
+    typedef typename Tr<P>::pair T2;
+    return (size_t)SB * (Ls * 12 + 2) * sizeof(T2) + (size_t)3 * 2 * Ls * Ls * sizeof(R);
+}
+
+template <int P, bool DAG, int NS, int MIX = 0, bool H2 = false>
+cudaError_t launch_direct(const HopArgs &a, int SB, cudaStream_t st)
+{
+    if constexpr (NS == 1 && MIX == 0 && ((P == DWF_F16 && H2) || (P == DWF_F32 && !H2))) {
+        static unsigned long long optin_occ = 0;
+        cudaError_t e = smem_optin(hop_kernel_occ<P, DAG, MIX, H2>, 200 * 1024, optin_occ);
+        if (e != cudaSuccess) return e;
+        hop_kernel_occ<P, DAG, MIX, H2><<<(a.Vh + SB - 1) / SB, dim3(a.Ls, SB), direct_smem<P>(a.Ls, SB), st>>>(a);
+        return cudaGetLastError();
+    }
+    static unsigned long long optin = 0;
+    {
+        cudaError_t e = smem_optin(hop_kernel<P, DAG, NS, MIX, H2>, 200 * 1024, optin);
+        if (e != cudaSuccess) return e;
+    }
+    const int LsN = a.Ls / NS;
+    hop_kernel<P, DAG, NS, MIX, H2><<<(a.Vh + SB - 1) / SB, dim3(LsN, SB), direct_smem<P>(a.Ls, SB), st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int P, bool DAG, int NS, int MIX, bool H2 = false>
+cudaError_t launch_direct_batch(const HopArgs *tab, int nsys, const HopArgs &a0, int SB, cudaStream_t st)
+{
+    if constexpr (NS == 1 && MIX == 0 && ((P == DWF_F16 && H2) || (P == DWF_F32 && !H2))) {
+        static unsigned long long optin_occ = 0;
+        cudaError_t e = smem_optin(hop_batch_kernel_occ<P, DAG, MIX, H2>, 200 * 1024, optin_occ);
+        if (e != cudaSuccess) return e;
+        const long long g = (long long)((a0.Vh + SB - 1) / SB) * nsys;
+        if (g > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        hop_batch_kernel_occ<P, DAG, MIX, H2><<<(unsigned)g, dim3(a0.Ls, SB), direct_smem<P>(a0.Ls, SB), st>>>(tab, nsys);
+        return cudaGetLastError();
+    }
+    static unsigned long long optin = 0;
+    {
+        cudaError_t e = smem_optin(hop_batch_kernel<P, DAG, NS, MIX, H2>, 200 * 1024, optin);
+        if (e != cudaSuccess) return e;
+    }
+    const int LsN = a0.Ls / NS;
+    const long long grid = (long long)((a0.Vh + SB - 1) / SB) * nsys;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    hop_batch_kernel<P, DAG, NS, MIX, H2><<<(unsigned)grid, dim3(LsN, SB), direct_smem<P>(a0.Ls, SB), st>>>(tab, nsys);
+    return cudaGetLastError();
+}
+
+template <int P, bool DAG>
+cudaError_t launch_batch_pd(const HopArgs *tab, int nsys, const HopArgs &a0, int NS, int SB, cudaStream_t st)
+{
+    if constexpr (P == DWF_F16) {   // FP16 arithmetic (as hop variant 5) with dense mixing
+        if (a0.mixmode == 0)
+            return NS == 2 ? launch_direct_batch<P, DAG, 2, 0, true>(tab, nsys, a0, SB, st)
+                           : launch_direct_batch<P, DAG, 1, 0, true>(tab, nsys, a0, SB, st);
+    }
+    if (a0.mixmode == 1)
+        return NS == 2 ? launch_direct_batch<P, DAG, 2, 1>(tab, nsys, a0, SB, st)
+                       : launch_direct_batch<P, DAG, 1, 1>(tab, nsys, a0, SB, st);
+    if constexpr (P != DWF_F64) {
+        if (a0.mixmode == 2 && (a0.Ls / NS) * SB >= 32)
+            return NS == 2 ? launch_direct_batch<P, DAG, 2, 2>(tab, nsys, a0, SB, st)
+                           : launch_direct_batch<P, DAG, 1, 2>(tab, nsys, a0, SB, st);
+    }
+    return NS == 2 ? launch_direct_batch<P, DAG, 2, 0>(tab, nsys, a0, SB, st)
+                   : launch_direct_batch<P, DAG, 1, 0>(tab, nsys, a0, SB, st);
+}
+
+// The 4D block of SB sites with the smallest faces whose extents divide the
+// half-lattice extents; false if SB has no such factorisation.
+bool choose_tile4(const int ext[4], int SB, Tile4 &best)
+{
+    long bestcost = -1;
+    for (int t0 = 1; t0 <= ext[0] && t0 <= SB; ++t0) {
+        if (ext[0] % t0 || SB % t0) continue;
+        for (int t1 = 1; t1 <= ext[1] && t0 * t1 <= SB; ++t1) {
+            if (ext[1] % t1 || (SB / t0) % t1) continue;
+            for (int t2 = 1; t2 <= ext[2] && t0 * t1 * t2 <= SB; ++t2) {
+                if (ext[2] % t2 || (SB / (t0 * t1)) % t2) continue;
+                const int t3 = SB / (t0 * t1 * t2);
+                if (t3 < 1 || t3 > ext[3] || ext[3] % t3) continue;
+                // halo sites fetched besides the block's own: one face per direction
+                const long cost = 2L * SB / t0 + 2L * SB / t1 + 2L * SB / t2 + 2L * SB / t3;
+                if (bestcost < 0 || cost < bestcost) {
+                    bestcost = cost;
+                    best.tb[0] = t0;
+                    best.tb[1] = t1;
+                    best.tb[2] = t2;
+                    best.tb[3] = t3;
+                }
+            }
+        }
+    }
+    return bestcost >= 0;
+}
+
+template <int P, bool DAG, int NS>
+cudaError_t launch_block(const HopArgs &a, int SB, cudaStream_t st)
+{
+    static unsigned long long optin = 0;
+    {
+        cudaError_t e = smem_optin(hop_block_kernel<P, DAG, NS>, 200 * 1024, optin);
+        if (e != cudaSuccess) return e;
+    }
+    Tile4 T;
+    if (!choose_tile4(a.ext, SB, T)) return launch_direct<P, DAG, NS>(a, SB, st);
+    const int LsN = a.Ls / NS;
+    hop_block_kernel<P, DAG, NS><<<a.Vh / SB, dim3(LsN, SB), direct_smem<P>(a.Ls, SB), st>>>(a, T);
+    return cudaGetLastError();
+}
+
+template <int P, bool DAG, int NS>
+cudaError_t launch_sweep(const HopArgs &a, int SB, cudaStream_t st)
+{
+    static unsigned long long optin = 0;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = smem_optin(hop_sweep_kernel<P, DAG, NS>, 200 * 1024, optin)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int LsN = a.Ls / NS;
+    const size_t smem = direct_smem<P>(a.Ls, SB);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_sweep_kernel<P, DAG, NS>, LsN * SB, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int ntiles = (a.Vh + SB - 1) / SB;
+    int grid = nsm * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    const int tpc = (ntiles + grid - 1) / grid;
+    grid = (ntiles + tpc - 1) / tpc;
+    hop_sweep_kernel<P, DAG, NS><<<grid, dim3(LsN, SB), smem, st>>>(a, tpc);
+    return cudaGetLastError();
+}
+
+template <int P, bool DAG>
+cudaError_t launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
+{
+    // variant 5: FP16 fields with FP16 projection and SU(3) arithmetic (dense mixing)
+    if constexpr (P == DWF_F16) {
+        if (var == 5 && a.mixmode == 0) {
+            if (NS == 4) return launch_direct<P, DAG, 4, 0, true>(a, SB, st);
+            if (NS == 2) return launch_direct<P, DAG, 2, 0, true>(a, SB, st);
+            return launch_direct<P, DAG, 1, 0, true>(a, SB, st);
+        }
+    }
+    if (var == 5) var = 0;
+    if (NS == 4) NS = 2;
+    // the structured and tensor-core mixings are compiled for the direct variant only
+    if (a.mixmode == 1) {
+        if (NS == 2) return launch_direct<P, DAG, 2, 1>(a, SB, st);
+        return launch_direct<P, DAG, 1, 1>(a, SB, st);
+    }
+    if constexpr (P != DWF_F64) {
+        if (a.mixmode == 2 && (a.Ls / NS) * SB >= 32) {
+            if (NS == 2) return launch_direct<P, DAG, 2, 2>(a, SB, st);
+            return launch_direct<P, DAG, 1, 2>(a, SB, st);
+        }
+    }
+    if (var == 4) {
+        if (NS == 2) return launch_block<P, DAG, 2>(a, SB, st);
+        return launch_block<P, DAG, 1>(a, SB, st);
+    }
+    if (var == 3) {
+        if (NS == 2) return launch_sweep<P, DAG, 2>(a, SB, st);
+        return launch_sweep<P, DAG, 1>(a, SB, st);
+    }
+    if (NS == 2) return launch_direct<P, DAG, 2>(a, SB, st);
+    return launch_direct<P, DAG, 1>(a, SB, st);
+}
+
+}  // namespace
+
+// Launchers of one precision and direction, instantiated in hop_<prec>_<dir>.cu
+// (one translation unit each, compiled in parallel).
+template <int P, bool DAG>
+cudaError_t hop_launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
+{
+    return launch_pd<P, DAG>(a, var, NS, SB, st);
+}
+template <int P, bool DAG>
+cudaError_t hop_batch_launch_pd(const HopArgs *tab, int nsys, const HopArgs &a0, int NS, int SB, cudaStream_t st)
+{
+    return launch_batch_pd<P, DAG>(tab, nsys, a0, NS, SB, st);
+}
+
+}  // namespace dwf

@@ -95,6 +95,6 @@ extern "C" int dwf_apply_eo_noalloc(dwf_handle h, int prec, int dag, const void 
     if ((e = hop(h, prec, dag != 0, a2, st)) != cudaSuccess) return dwf_cuda_error(e, "hop");
     if ((e = launch_unpack_eo(prec, y, (double *)out, h->Vh, h->Ls, st)) != cudaSuccess)
         return dwf_cuda_error(e, "unpack");
-    h->launches += 2;
+    h->launches += 2;   // pack and unpack (mix and hop count their own launches)
     return DWF_OK;
 }

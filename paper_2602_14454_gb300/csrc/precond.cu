@@ -713,6 +713,32 @@ static int net_upload(dwf_ctx *h, const std::vector<double> &w)
     return DWF_OK;
 }
 
+// One Adam step (beta 0.9, 0.999, eps 1e-8; step count t from 1) from the
+// gradient accumulated in N->g, which the step clears.
+static cudaError_t net_adam(dwf_ctx *h, double lr, cudaStream_t st)
+{
+    NetState *N = h->net;
+    const size_t nall = N->nw * N->L;
+    N->t += 1;
+    const double c1 = 1 - std::pow(0.9, N->t), c2 = 1 - std::pow(0.999, N->t);
+    net_adam_kernel<<<(int)((nall + 255) / 256), 256, 0, st>>>(N->Wm, N->m, N->v, N->g, N->Wc, (int)nall, lr, 0.9,
+                                                               0.999, 1e-8, c1, c2);
+    h->launches += 1;
+    return cudaGetLastError();
+}
+
+// File format of dwf_precond_save / dwf_precond_load (little-endian host
+// binary): the header, then the FP64 master weights, Adam's first and second
+// moments, nall complex numbers each (nall = layers * 9 * 2 * C * C).
+struct NetFileHeader {
+    char magic[8];              // "DWFNET\0\0"
+    int32_t version;            // 1
+    int32_t layers, channels;   // L, C = Ls
+    int32_t adam_t;             // Adam steps taken
+    int64_t nall;               // complex numbers per array
+};
+static const char kNetMagic[8] = {'D', 'W', 'F', 'N', 'E', 'T', 0, 0};
+
 // which = 0: z = N r, 1: z = N^dag r, 2: z = M r = N N^dag r (FP32 even fields;
 // 2 is the preconditioner of flexible CG)
 int net_apply_f32(dwf_ctx *h, FieldRef r, FieldRef z, cudaStream_t st, int which)
@@ -980,7 +1006,6 @@ int dwf_precond_train(dwf_handle h, int nsrc, const void *const *b4, const dwf_t
     std::mt19937_64 gen(p->seed + 1);
     std::vector<int> order(nsrc);
     for (int k = 0; k < nsrc; ++k) order[k] = k;
-    const size_t nall = N->nw * N->L;
     S.pairs = nsrc;
     for (int ep = 0; ep < p->epochs; ++ep) {
         std::shuffle(order.begin(), order.end(), gen);
@@ -996,12 +1021,7 @@ int dwf_precond_train(dwf_handle h, int nsrc, const void *const *b4, const dwf_t
                 CK(cudaStreamSynchronize(st));
                 Lb += hs.last / N->pxn2[k] / nb;
             }
-            N->t += 1;
-            const double c1 = 1 - std::pow(0.9, N->t), c2 = 1 - std::pow(0.999, N->t);
-            net_adam_kernel<<<(int)((nall + 255) / 256), 256, 0, st>>>(N->Wm, N->m, N->v, N->g, N->Wc, (int)nall,
-                                                                       p->lr, 0.9, 0.999, 1e-8, c1, c2);
-            CK(cudaGetLastError());
-            h->launches += 1;
+            CK(net_adam(h, p->lr, st));
             S.steps += 1;
             Lep += Lb * nb / nsrc;
         }
@@ -1015,6 +1035,89 @@ int dwf_precond_train(dwf_handle h, int nsrc, const void *const *b4, const dwf_t
     S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     S.status = DWF_OK;
     if (stats) *stats = S;
+    return DWF_OK;
+}
+
+int dwf_precond_adam_step(dwf_handle h, int layers, const double *grad, double lr, void *stream)
+{
+    if (!h || !grad) return dwf_set_error(DWF_EINVAL, "NULL argument");
+    if (!h->net || h->net->L != layers) return dwf_set_error(DWF_EINVAL, "no preconditioner with that many layers");
+    if (!(lr > 0)) return dwf_set_error(DWF_EINVAL, "lr must be positive");
+    NetState *N = h->net;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nall = N->nw * N->L;
+    CK(cudaMemcpyAsync(N->g, grad, nall * sizeof(double2), cudaMemcpyHostToDevice, st));
+    CK(net_adam(h, lr, st));
+    CK(cudaStreamSynchronize(st));
+    return DWF_OK;
+}
+
+int dwf_precond_save(dwf_handle h, const char *path)
+{
+    if (!h || !path) return dwf_set_error(DWF_EINVAL, "NULL argument");
+    if (!h->net) return dwf_set_error(DWF_EINVAL, "no preconditioner to save");
+    NetState *N = h->net;
+    const size_t nall = N->nw * N->L;
+    std::vector<double2> buf(3 * nall);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(buf.data(), N->Wm, nall * sizeof(double2), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(buf.data() + nall, N->m, nall * sizeof(double2), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(buf.data() + 2 * nall, N->v, nall * sizeof(double2), cudaMemcpyDeviceToHost));
+    NetFileHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, kNetMagic, 8);
+    hd.version = 1;
+    hd.layers = N->L;
+    hd.channels = N->C;
+    hd.adam_t = N->t;
+    hd.nall = (int64_t)nall;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return dwf_set_error(DWF_EINVAL, std::string("cannot open ") + path + " for writing");
+    const bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 &&
+                    std::fwrite(buf.data(), sizeof(double2), buf.size(), f) == buf.size();
+    const bool closed = std::fclose(f) == 0;
+    if (!ok || !closed) return dwf_set_error(DWF_EINVAL, std::string("short write to ") + path);
+    return DWF_OK;
+}
+
+int dwf_precond_load(dwf_handle h, const char *path)
+{
+    if (!h || !path) return dwf_set_error(DWF_EINVAL, "NULL argument");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return dwf_set_error(DWF_EINVAL, std::string("cannot open ") + path);
+    NetFileHeader hd;
+    if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, kNetMagic, 8) != 0) {
+        std::fclose(f);
+        return dwf_set_error(DWF_EINVAL, std::string(path) + " is not a preconditioner file");
+    }
+    if (hd.version != 1) {
+        std::fclose(f);
+        return dwf_set_error(DWF_EINVAL, "unsupported preconditioner file version " + std::to_string(hd.version));
+    }
+    if (hd.channels != h->Ls || hd.layers < 1 || hd.layers > 8 ||
+        hd.nall != (int64_t)NHOP * 2 * hd.channels * hd.channels * hd.layers) {
+        std::fclose(f);
+        return dwf_set_error(DWF_EINVAL, "preconditioner file for " + std::to_string(hd.layers) + " layers and " +
+                                             std::to_string(hd.channels) + " channels does not fit this handle (Ls " +
+                                             std::to_string(h->Ls) + ")");
+    }
+    std::vector<double2> buf(3 * (size_t)hd.nall);
+    const bool ok = std::fread(buf.data(), sizeof(double2), buf.size(), f) == buf.size();
+    std::fclose(f);
+    if (!ok) return dwf_set_error(DWF_EINVAL, std::string(path) + " is truncated");
+    int rc = net_alloc(h, hd.layers);
+    if (rc) return rc;
+    NetState *N = h->net;
+    const size_t nall = (size_t)hd.nall;
+    CK(cudaMemcpy(N->Wm, buf.data(), nall * sizeof(double2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(N->m, buf.data() + nall, nall * sizeof(double2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(N->v, buf.data() + 2 * nall, nall * sizeof(double2), cudaMemcpyHostToDevice));
+    CK(cudaMemset(N->g, 0, nall * sizeof(double2)));
+    net_round_kernel<<<(int)((nall + 255) / 256), 256>>>(N->Wm, N->Wc, (int)nall);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    h->launches += 1;
+    N->t = hd.adam_t;
     return DWF_OK;
 }
 

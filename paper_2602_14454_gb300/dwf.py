@@ -34,7 +34,8 @@ EXPORTED = ["dwf_create", "dwf_create_s", "dwf_destroy", "dwf_strerror", "dwf_la
             "dwf_set_hop_config", "dwf_get_hop_config", "dwf_autotune", "dwf_device_status",
             "dwf_set_mix_mode", "dwf_get_mix_mode", "dwf_apply_eo_noalloc",
             "dwf_train_params_default", "dwf_precond_init", "dwf_precond_set_weights", "dwf_precond_get_weights",
-            "dwf_precond_apply", "dwf_precond_loss_grad", "dwf_precond_train"]
+            "dwf_precond_apply", "dwf_precond_loss_grad", "dwf_precond_train", "dwf_precond_adam_step",
+            "dwf_precond_save", "dwf_precond_load", "dwf_alu_peaks"]
 
 
 class SolveParams(ctypes.Structure):
@@ -136,6 +137,7 @@ def lib():
     L.dwf_autotune.argtypes = [vp, i, ctypes.c_char_p, vp]
     L.dwf_launch_count.argtypes = [vp]
     L.dwf_launch_count.restype = ctypes.c_longlong
+    L.dwf_alu_peaks.argtypes = [ctypes.POINTER(d), vp]
     dp = ctypes.POINTER(ctypes.c_double)
     L.dwf_train_params_default.argtypes = [ctypes.POINTER(TrainParams)]
     L.dwf_train_params_default.restype = None
@@ -144,6 +146,9 @@ def lib():
     L.dwf_precond_get_weights.argtypes = [vp, i, i, dp]
     L.dwf_precond_apply.argtypes = [vp, i, vp, vp, vp]
     L.dwf_precond_loss_grad.argtypes = [vp, i, ctypes.POINTER(vp), ctypes.POINTER(vp), dp, dp, vp]
+    L.dwf_precond_adam_step.argtypes = [vp, i, dp, d, vp]
+    L.dwf_precond_save.argtypes = [vp, ctypes.c_char_p]
+    L.dwf_precond_load.argtypes = [vp, ctypes.c_char_p]
     L.dwf_precond_train.argtypes = [vp, i, ctypes.POINTER(vp), ctypes.POINTER(TrainParams),
                                     ctypes.POINTER(TrainStats), vp]
     _lib = L
@@ -371,6 +376,18 @@ class Operator:
         check(lib().dwf_precond_train(self._h, n, B, ctypes.byref(p), ctypes.byref(st), _stream()))
         return st.as_dict()
 
+    def precond_adam_step(self, grad, lr, layers=3):
+        """One Adam step of the network from a host gradient (weight layout)."""
+        g = np.ascontiguousarray(np.asarray(grad, dtype=np.complex128))
+        check(lib().dwf_precond_adam_step(self._h, int(layers), g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          float(lr), _stream()))
+
+    def precond_save(self, path):
+        check(lib().dwf_precond_save(self._h, os.fsencode(path)))
+
+    def precond_load(self, path):
+        check(lib().dwf_precond_load(self._h, os.fsencode(path)))
+
     def time_hop(self, prec="f32", reps=20, flush_l2=True):
         us = ctypes.c_double()
         by = ctypes.c_double()
@@ -413,6 +430,15 @@ def fifth_matrix_host(Ls, M0, mf, b, c, form="standard", alpha=1.0, which=0, chi
     check(lib().dwf_fifth_matrix_host(int(Ls), float(M0), float(mf), ba, ca, FORM[form], float(alpha),
                                       int(w), int(chirality), out, ctypes.byref(band)))
     return np.array(out, dtype=np.float64).reshape(Ls, Ls), bool(band.value)
+
+
+def alu_peaks():
+    """Measured FP32 (scalar FMA, packed FP32x2 FMA) and FP64 FMA rates of the
+    current device in TFLOP/s, and its SM count."""
+    out = (ctypes.c_double * 4)()
+    check(lib().dwf_alu_peaks(out, _stream()))
+    return {"fp32_ffma_tflops": out[0], "fp32_ffma2_tflops": out[1], "fp64_dfma_tflops": out[2],
+            "sms": int(out[3])}
 
 
 def solve_batch(ops, b4s, x4s=None, allow_notconv=False, **kw):

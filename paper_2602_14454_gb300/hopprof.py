@@ -33,7 +33,7 @@ def main(argv=None):
     build.build()
     w = inputs.WORKLOADS[args.workload]
     op = dwf.Operator(w["dims"], w["Ls"], w["M0"], w["mf"], w["b"], w["c"], form=args.form, alpha=args.alpha)
-    op.set_gauge(torch.from_numpy(inputs.workload_links(w)).cuda())
+    op.set_gauge(torch.from_numpy(inputs.workload_links(w, device="cuda")).cuda())
     if args.config:
         v, ns, sb = (int(t) for t in args.config.split(","))
         op.set_hop_config(args.prec, v, ns, sb)

@@ -37,25 +37,88 @@ def _complex_normal(g: np.random.Generator, shape) -> np.ndarray:
     return g.normal(0.0, s, shape) + 1j * g.normal(0.0, s, shape)
 
 
-def _expi_hermitian(H: np.ndarray, eps: float) -> np.ndarray:
-    """exp(i*eps*H) for a batch of Hermitian 3x3 matrices (eigendecomposition)."""
-    w, v = np.linalg.eigh(H)
-    ph = np.exp(1j * eps * w)
-    return np.einsum("...ij,...j,...kj->...ik", v, ph, v.conj())
+# The link algebra below runs on torch tensors, on the CPU or (device="cuda")
+# on a GPU, so that the 32^3x64 fields are made in seconds; every function
+# returns numpy arrays.  The random numbers always come from numpy's PCG64
+# stream on the host, so a seed names the same field on every device (up to
+# the rounding of the device's arithmetic).
+def _torch():
+    import torch
+    return torch
 
 
-def random_links(dims, eps: float, seed: int) -> np.ndarray:
+def _dev(device):
+    return "cpu" if device is None else device
+
+
+def _tdag(A):
+    return A.conj().transpose(-1, -2)
+
+
+def _texpm(A):
+    """exp(A) for a batch of 3x3 complex matrices: scaling and squaring with a
+    Taylor polynomial of degree 16 (|A| / 2^k <= 1/2 for every matrix, so the
+    truncation error is below 1e-18 relative)."""
+    torch = _torch()
+    nrm = float(torch.linalg.matrix_norm(A, ord="fro").max()) if A.numel() else 0.0
+    k = 0
+    while nrm / (1 << k) > 0.5:
+        k += 1
+    X = A / float(1 << k)
+    eye = torch.eye(3, dtype=A.dtype, device=A.device)
+    E = eye.expand_as(X).clone()
+    T = eye.expand_as(X).clone()
+    for n in range(1, 17):
+        T = (T @ X) / float(n)
+        E = E + T
+    for _ in range(k):
+        E = E @ E
+    return E
+
+
+def _tdet(W):
+    return (W[..., 0, 0] * (W[..., 1, 1] * W[..., 2, 2] - W[..., 1, 2] * W[..., 2, 1])
+            - W[..., 0, 1] * (W[..., 1, 0] * W[..., 2, 2] - W[..., 1, 2] * W[..., 2, 0])
+            + W[..., 0, 2] * (W[..., 1, 0] * W[..., 2, 1] - W[..., 1, 1] * W[..., 2, 0]))
+
+
+def _treunitarise(U):
+    """Nearest SU(3) matrix of an almost unitary U: its polar factor by two
+    Newton-Schulz steps X <- X (3 - X^dag X) / 2 (quadratic convergence from
+    |1 - U^dag U| << 1), then the determinant phase removed."""
+    torch = _torch()
+    eye = torch.eye(3, dtype=U.dtype, device=U.device)
+    X = U
+    for _ in range(2):
+        X = X @ (3.0 * eye - _tdag(X) @ X) * 0.5
+    det = _tdet(X)
+    return X * (det ** (-1.0 / 3.0))[..., None, None]
+
+
+def _expi_hermitian(H: np.ndarray, eps: float, device=None) -> np.ndarray:
+    """exp(i*eps*H) for a batch of Hermitian 3x3 matrices."""
+    torch = _torch()
+    Ht = torch.from_numpy(np.ascontiguousarray(H, dtype=np.complex128)).to(_dev(device))
+    return _texpm(1j * eps * Ht).cpu().numpy()
+
+
+def _random_links_t(dims, eps: float, seed: int, device):
+    torch = _torch()
+    g = rng(seed)
+    shp = (4,) + site_shape(dims) + (3, 3)
+    G = torch.from_numpy(_complex_normal(g, shp)).to(_dev(device))
+    H = 0.5 * (G + _tdag(G))
+    tr = torch.diagonal(H, dim1=-2, dim2=-1).sum(-1)
+    H = H - (tr / 3.0)[..., None, None] * torch.eye(3, dtype=H.dtype, device=H.device)
+    return _treunitarise(_texpm(1j * eps * H))
+
+
+def random_links(dims, eps: float, seed: int, device=None) -> np.ndarray:
     """U = exp(i*eps*H), H = (G+G^dag)/2 - tr(...)/3 with G complex normal.
 
     The result is unitary with det 1 (H traceless), i.e. in SU(3).
     """
-    g = rng(seed)
-    shp = (4,) + site_shape(dims) + (3, 3)
-    G = _complex_normal(g, shp)
-    H = 0.5 * (G + np.swapaxes(G.conj(), -1, -2))
-    tr = np.trace(H, axis1=-2, axis2=-1)
-    H = H - (tr / 3.0)[..., None, None] * np.eye(3)
-    return np.ascontiguousarray(_expi_hermitian(H, eps))
+    return np.ascontiguousarray(_random_links_t(dims, eps, seed, device).cpu().numpy())
 
 
 def unit_links(dims) -> np.ndarray:
@@ -65,24 +128,44 @@ def unit_links(dims) -> np.ndarray:
     return U
 
 
-def _dag(A):
-    return np.swapaxes(A.conj(), -1, -2)
+def reunitarise(U: np.ndarray, device=None) -> np.ndarray:
+    """Nearest SU(3) matrix (polar factor with the determinant phase removed) of
+    an almost unitary U."""
+    torch = _torch()
+    Ut = torch.from_numpy(np.ascontiguousarray(U, dtype=np.complex128)).to(_dev(device))
+    return _treunitarise(Ut).cpu().numpy()
 
 
-def _shift(A, mu: int, k: int):
-    """B(x) = A(x + k*mu_hat), periodic; A has site axes (Lt,Lz,Ly,Lx) first."""
-    return np.roll(A, -k, axis=_AXIS[mu])
+def _smear_t(U, rho: float, nsteps: int, reunit: bool):
+    torch = _torch()
+    eye = torch.eye(3, dtype=U.dtype, device=U.device)
+
+    def shift(A, mu, k):
+        """B(x) = A(x + k*mu_hat), periodic; A has site axes (Lt,Lz,Ly,Lx) first."""
+        return torch.roll(A, shifts=-k, dims=_AXIS[mu])
+
+    for _ in range(nsteps):
+        Unew = torch.empty_like(U)
+        for mu in range(4):
+            C = torch.zeros_like(U[mu])
+            for nu in range(4):
+                if nu == mu:
+                    continue
+                up = U[nu] @ shift(U[mu], nu, 1) @ _tdag(shift(U[nu], mu, 1))
+                Unu_m = shift(U[nu], nu, -1)
+                dn = _tdag(Unu_m) @ shift(U[mu], nu, -1) @ shift(Unu_m, mu, 1)
+                C += up + dn
+            C *= rho
+            W = C @ _tdag(U[mu])
+            A = 0.5 * (W - _tdag(W))
+            tr = torch.diagonal(A, dim1=-2, dim2=-1).sum(-1)
+            A = A - (tr / 3.0)[..., None, None] * eye
+            Unew[mu] = _texpm(A) @ U[mu]
+        U = _treunitarise(Unew) if reunit else Unew
+    return U
 
 
-def reunitarise(U: np.ndarray) -> np.ndarray:
-    """Nearest SU(3) matrix: polar factor (SVD) with the determinant phase removed."""
-    u, _, vh = np.linalg.svd(U)
-    W = u @ vh
-    det = np.linalg.det(W)
-    return W * (det ** (-1.0 / 3.0))[..., None, None]
-
-
-def smear_stout(U: np.ndarray, rho: float, nsteps: int, reunit: bool = True) -> np.ndarray:
+def smear_stout(U: np.ndarray, rho: float, nsteps: int, reunit: bool = True, device=None) -> np.ndarray:
     """Stout projection of APE staples, eq. (stout_smearing) of Sec. 2.2, repeated.
 
     C_mu(x) = rho * sum_{nu != mu} [ U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
@@ -92,34 +175,15 @@ def smear_stout(U: np.ndarray, rho: float, nsteps: int, reunit: bool = True) -> 
     All directions are updated together from the previous step's links.  The
     optional re-unitarisation only removes rounding drift.
     """
-    U = np.array(U, dtype=np.complex128, copy=True)
-    for _ in range(nsteps):
-        Unew = np.empty_like(U)
-        for mu in range(4):
-            C = np.zeros_like(U[mu])
-            for nu in range(4):
-                if nu == mu:
-                    continue
-                up = U[nu] @ _shift(U[mu], nu, 1) @ _dag(_shift(U[nu], mu, 1))
-                Unu_m = _shift(U[nu], nu, -1)
-                dn = _dag(Unu_m) @ _shift(U[mu], nu, -1) @ _shift(_shift(U[nu], nu, -1), mu, 1)
-                C += up + dn
-            C *= rho
-            W = C @ _dag(U[mu])
-            A = 0.5 * (W - _dag(W))
-            tr = np.trace(A, axis1=-2, axis2=-1)
-            A = A - (tr / 3.0)[..., None, None] * np.eye(3)
-            # A is anti-Hermitian and traceless: A = i*Hm with Hm Hermitian
-            Hm = -1j * A
-            Hm = 0.5 * (Hm + _dag(Hm))
-            Unew[mu] = _expi_hermitian(Hm, 1.0) @ U[mu]
-        U = reunitarise(Unew) if reunit else Unew
-    return np.ascontiguousarray(U)
+    torch = _torch()
+    Ut = torch.from_numpy(np.array(U, dtype=np.complex128, copy=True)).to(_dev(device))
+    return np.ascontiguousarray(_smear_t(Ut, rho, nsteps, reunit).cpu().numpy())
 
 
-def smeared_links(dims, eps: float, rho: float, nsteps: int, seed: int) -> np.ndarray:
+def smeared_links(dims, eps: float, rho: float, nsteps: int, seed: int, device=None) -> np.ndarray:
     """Random SU(3) links followed by ``nsteps`` stout/APE smearing steps."""
-    return smear_stout(random_links(dims, eps, seed), rho, nsteps)
+    U = _random_links_t(dims, eps, seed, device)
+    return np.ascontiguousarray(_smear_t(U, rho, nsteps, True).cpu().numpy())
 
 
 def random_gauge_transform(dims, seed: int) -> np.ndarray:
@@ -175,7 +239,9 @@ WORKLOADS = {
 }
 
 
-def workload_links(w: dict) -> np.ndarray:
+def workload_links(w: dict, device=None) -> np.ndarray:
+    """The workload's link field; device selects where the link algebra runs
+    (None: the host; "cuda" for the large lattices)."""
     if w["smear"]:
-        return smeared_links(w["dims"], w["eps"], 0.1, w["smear"], w["gauge_seed"])
-    return random_links(w["dims"], w["eps"], w["gauge_seed"])
+        return smeared_links(w["dims"], w["eps"], 0.1, w["smear"], w["gauge_seed"], device=device)
+    return random_links(w["dims"], w["eps"], w["gauge_seed"], device=device)

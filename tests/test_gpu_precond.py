@@ -177,3 +177,66 @@ def test_trained_network_gain():
         assert t[2] <= 1e-10 and p[2] <= 1e-10
     print("iteration gain %.2f, time gain %.2f" % (sum(p[0] for p in plain) / sum(t[0] for t in trained),
                                                   sum(p[1] for p in plain) / sum(t[1] for t in trained)))
+
+
+def test_adam_step_matches_oracle():
+    """Three Adam steps of the library (the update of dwf_precond_train) from
+    given gradients against oracle.precond.adam_step, element by element: the
+    FP64 master weights after each step (the moments enter the later steps), and
+    the compute copy = the BF16 rounding of the master weights."""
+    from oracle import precond as pc
+    dims, Ls, L = (4, 4, 2, 4), 4, 2
+    op, ref = make_pair(dims, Ls, 1.8, 0.05, 1.5, 0.5, "neff", 0.5, seed=231)
+    w0 = random_weights(L, Ls, 232)
+    op.precond_set_weights(w0)
+    theta = op.precond_get_weights(L, compute_copy=False)
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    g = np.random.default_rng(233)
+    for t, lr in zip((1, 2, 3), (2e-3, 5e-3, 1e-3)):
+        grad = g.normal(size=theta.shape) + 1j * g.normal(size=theta.shape)
+        if t == 2:
+            grad[0, 0] *= 1e-6                                      # small gradients: eps matters
+        op.precond_adam_step(grad, lr, layers=L)
+        theta, m, v = pc.adam_step(theta, grad, m, v, t, lr)
+        got = op.precond_get_weights(L, compute_copy=False)
+        assert np.abs(got - theta).max() <= 1e-14 * np.abs(theta).max(), t
+        comp = op.precond_get_weights(L, compute_copy=True)
+        assert np.abs(comp - theta).max() <= 2.0 ** -8 * np.abs(theta).max()
+
+
+def test_save_load_round_trip(tmp_path):
+    """dwf_precond_save / dwf_precond_load: the weights, the compute copy and the
+    Adam state (the next step from the loaded state equals the next step from the
+    original) survive the round trip; files for another Ls, truncated files and
+    files of another format are refused."""
+    from paper_2602_14454_gb300 import dwf
+    dims, Ls, L = (4, 4, 2, 4), 4, 2
+    op, ref = make_pair(dims, Ls, 1.8, 0.05, 1.5, 0.5, "neff", 0.5, seed=241)
+    op.precond_set_weights(random_weights(L, Ls, 242))
+    g = np.random.default_rng(243)
+    shape = (L, 9, 2, Ls, Ls)
+    for _ in range(2):
+        op.precond_adam_step(g.normal(size=shape) + 1j * g.normal(size=shape), 3e-3, layers=L)
+    path = str(tmp_path / "net.bin")
+    op.precond_save(path)
+    op2, _ = make_pair(dims, Ls, 1.8, 0.05, 1.5, 0.5, "neff", 0.5, seed=241)
+    op2.precond_load(path)
+    for cc in (False, True):
+        assert np.array_equal(op2.precond_get_weights(L, cc), op.precond_get_weights(L, cc))
+    r = to_gpu(even_field(ref, 244))
+    assert np.array_equal(to_np(op2.precond_apply(r)), to_np(op.precond_apply(r)))
+    grad = g.normal(size=shape) + 1j * g.normal(size=shape)
+    op.precond_adam_step(grad, 3e-3, layers=L)
+    op2.precond_adam_step(grad, 3e-3, layers=L)
+    assert np.array_equal(op2.precond_get_weights(L, False), op.precond_get_weights(L, False))
+    op3, _ = make_pair(dims, 6, 1.8, 0.05, 1.5, 0.5, "neff", 0.5, seed=241)
+    with pytest.raises(dwf.DwfError):
+        op3.precond_load(path)                                       # another Ls
+    data = open(path, "rb").read()
+    open(path + ".cut", "wb").write(data[: len(data) // 2])
+    with pytest.raises(dwf.DwfError):
+        op2.precond_load(path + ".cut")
+    open(path + ".bad", "wb").write(b"X" + data[1:])
+    with pytest.raises(dwf.DwfError):
+        op2.precond_load(path + ".bad")

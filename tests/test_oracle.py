@@ -359,3 +359,40 @@ def test_links_are_su3():
     U = inputs.random_links((4, 4, 2, 2), 0.5, 1)
     assert np.abs(np.swapaxes(U.conj(), -1, -2) @ U - np.eye(3)).max() < 1e-13
     assert np.abs(np.linalg.det(U) - 1).max() < 1e-13
+
+
+def test_expi_hermitian_against_eigendecomposition():
+    """The link generator's exp(i eps H) (scaling and squaring of a Taylor
+    polynomial) against the closed form V diag(exp(i eps w)) V^dag from numpy's
+    eigendecomposition."""
+    g = np.random.default_rng(5)
+    G = g.normal(size=(500, 3, 3)) + 1j * g.normal(size=(500, 3, 3))
+    H = 0.5 * (G + np.swapaxes(G.conj(), -1, -2))
+    w, v = np.linalg.eigh(H)
+    for eps in (0.3, 0.5, 2.0):
+        want = np.einsum("...ij,...j,...kj->...ik", v, np.exp(1j * eps * w), v.conj())
+        assert np.abs(inputs._expi_hermitian(H, eps) - want).max() < 1e-13
+
+
+@pytest.mark.parametrize("form,alpha,b,c", [("standard", 1.0, 1.5, 0.5), ("neff", 0.5, 1.5, 0.5),
+                                            ("neff", 0.7, 1.0, 1.0)])
+def test_row_apply_and_residual_match_apply(form, alpha, b, c):
+    """apply_row (the large-lattice residual check) reproduces apply() row by row,
+    and residual_norm equals the norm of b5 - apply(x5)."""
+    dims, Ls = (4, 2, 2, 4), 6
+    U = inputs.random_links(dims, 0.5, 131)
+    ref = dwf.DWF(U, dims, Ls, 1.8, 0.03, b, c, form=form, alpha=alpha)
+    x = inputs.gaussian_5d(dims, Ls, 132)
+    y = ref.apply(x)
+    for s in range(Ls):
+        assert np.abs(ref.apply_row(x, s) - y[s]).max() < 1e-13
+    bvec = inputs.gaussian_5d(dims, Ls, 133)
+    want = np.linalg.norm((bvec - y).ravel()) / np.linalg.norm(bvec.ravel())
+    assert abs(ref.residual_norm(bvec, x) - want) < 1e-14 * want
+    # the source row by row, and the residual of a solve from a 4D source
+    b4 = inputs.gaussian_4d(dims, 134)
+    b5 = ref.source_5d(b4)
+    for s in range(Ls):
+        assert np.abs(ref.source_row(b4, s) - b5[s]).max() < 1e-14
+    want = np.linalg.norm((b5 - y).ravel()) / np.linalg.norm(b5.ravel())
+    assert abs(ref.residual_norm(lambda s: ref.source_row(b4, s), x) - want) < 1e-14 * want

@@ -49,12 +49,26 @@ def test_noalloc_matches_dwf_apply_twice(prec, form, alpha):
 
 
 def test_noalloc_allocates_nothing_in_the_handle():
+    import torch
     dims, Ls = (4, 4, 4, 4), 8
     op, ref = make_pair(dims, Ls, 1.8, 0.04, 1.0, 0.0, "standard", 1.0, seed=94)
     before = op.device_bytes()
     x = to_gpu(ref.to_eo(inputs.gaussian_5d(dims, Ls, 95), 0))
-    y1 = to_np(_noalloc(op, x, "f64", False))
-    y2 = to_np(_noalloc(op, x, "f64", False))
+    outs = [torch.empty_like(x) for _ in range(4)]
+    # the first call may load the device code that holds the array; after it,
+    # calls change neither the handle's buffers nor the device's free memory
+    _noalloc(op, x, "f64", False)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    from paper_2602_14454_gb300 import dwf
+    for k, o in enumerate(outs):
+        dwf.check(dwf.lib().dwf_apply_eo_noalloc(op.handle, dwf.PREC["f64"], k & 1, ctypes.c_void_p(x.data_ptr()),
+                                                 ctypes.c_void_p(o.data_ptr()),
+                                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0        # no device allocation during the calls
+    y1 = to_np(outs[0])
+    y2 = to_np(outs[2])
     assert op.device_bytes() == before                  # no work fields were created
     assert rel(y1, ref.d_pc(ref.to_eo(inputs.gaussian_5d(dims, Ls, 95), 0))) < TOL["f64"]
     assert np.array_equal(y1, y2)
