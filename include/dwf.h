@@ -155,6 +155,14 @@ typedef struct {
     int verbose;        /* 0 quiet                                              */
     int batch_wave;     /* dwf_solve_batch: at most this many systems per wave;
                            0 (default): as many as device memory allows        */
+    int eo_form;        /* the even-odd equation the inner CG iterates on:
+                           0 (default) eq. (even-odd_linear_equation),
+                           D x_e = b~_e with D = 1 - D_ee^-1 D_eo D_oo^-1 D_oe;
+                           1 eq. (another_even-odd_linear_equation),
+                           D' y_e = b'_e with D' = 1 - D_eo D_oo^-1 D_oe D_ee^-1,
+                           b'_e = D_ee b~_e, x_e = D_ee^-1 y_e (Sec. 2.3: Neff's
+                           factor cancels in D', so alpha does not change its
+                           convergence); dwf_solve only, not with precond   */
 } dwf_solve_params;
 
 typedef struct {
@@ -245,7 +253,7 @@ int dwf_fifth_matrix(dwf_handle h, int which, int chirality, double *out_host);
  *   k = 0 P = B R, 1 P^T, 2 Q = R^-1 A5^-1 (D_ee^-1), 3 Q^T, 4 M = B A5^-1,
  *   5 M^T, 6 A5 R (D_ee), 7 (A5 R)^T, 8 -1/2, 9 -1/2 R B^T, 10 -1/4 Q,
  *   11 -1/4 P^T, 12 1, 13 +1/2 Q, 14 c/2 (hop part of 1 - c D_W),
- *   15 1 - c (4 - M0) (its diagonal part).
+ *   15 1 - c (4 - M0) (its diagonal part), 16 -1/4, 17 -1/4 M^T.
  * *banded (if non-null): 1 when every nonzero of the matrix lies on the cyclic
  * tridiagonal, which the kernels then read as three coefficients per row
  * (always 0 for which 0..3).  Errors: DWF_EINVAL (Ls outside 2..32, form,

@@ -577,8 +577,16 @@ long long dwf_launch_count(dwf_handle h) { return h ? h->launches : 0; }
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb)
 {
     if (!h || prec < 0 || prec > 2) return dwf_set_error(DWF_EINVAL, "bad handle or precision");
-    if (variant < -1 || variant > 5 || variant == 1 || variant == 2)
-        return dwf_set_error(DWF_EINVAL, "variant must be -1, 0, 3, 4 or 5");
+    if (variant < -1 || variant > 6 || variant == 1 || variant == 2)
+        return dwf_set_error(DWF_EINVAL, "variant must be -1, 0, 3, 4, 5 or 6");
+    if (variant == 6) {   // sb counts warps per CTA
+        if (ns < 0 || ns > 1) return dwf_set_error(DWF_EINVAL, "variant 6 takes ns 0 or 1");
+        if (sb < 0 || sb > 8) return dwf_set_error(DWF_EINVAL, "variant 6 takes sb (warps per CTA) 0..8");
+        h->hop_var[prec] = variant;
+        h->hop_ns[prec] = ns;
+        h->hop_sb[prec] = sb;
+        return DWF_OK;
+    }
     if (ns < 0 || ns > 4 || ns == 3 || (ns && h->Ls % ns) || (ns == 4 && variant != 5))
         return dwf_set_error(DWF_EINVAL, "ns must be 0, 1, 2 or (variant 5) 4, and divide Ls");
     const int nsv = ns ? ns : hop_default_ns(prec, h->Ls);
@@ -651,18 +659,19 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
     double best = 1e30;
     int bvar = -1, bns = 0, bsb = 0, bmix = 0;
     for (int mix = 0; mix <= 2; ++mix)
-        for (int var = 0; var <= 5; ++var)
+        for (int var = 0; var <= 6; ++var)
             for (int ns = 1; ns <= 4; ns *= 2) {
                 if (mix == 1 && !h->fm.structured) continue;
                 if (mix == 2 && prec == DWF_F64) continue;
                 if (var == 1 || var == 2) continue;   // numbers of removed variants
                 if (mix != 0 && var != 0) continue;   // those mixings exist in the direct variant only
                 if (var == 5 && prec != DWF_F16) continue;
+                if (var == 6 && (prec == DWF_F64 || ns != 1 || 32 % h->Ls != 0)) continue;
                 if (ns == 4 && var != 5) continue;
                 if (h->Ls % ns) continue;
                 const int LsN = h->Ls / ns;
                 for (int threads = 64; threads <= 256; threads += 64) {
-                    const int sb = threads / LsN;
+                    const int sb = var == 6 ? threads / 32 : threads / LsN;   // variant 6: warps per CTA
                     if (sb < 1 || LsN * sb > 256) continue;
                     h->mixmode[prec] = mix;
                     h->hop_var[prec] = var;

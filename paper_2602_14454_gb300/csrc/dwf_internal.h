@@ -56,6 +56,8 @@ enum MatId {
     MAT_HALF_Q,      // +1/2 R^-1 A5^-1
     MAT_SRC_POST,    // c/2                 (hop part of 1 - c D_W, 5D source)
     MAT_SRC_Y,       // 1 - c (4 - M0)      (diagonal part of 1 - c D_W)
+    MAT_NQUARTER,    // -1/4                (second even-odd form)
+    MAT_NMT4,        // -1/4 (B A5^-1)^T    (its adjoint)
     MAT_COUNT
 };
 

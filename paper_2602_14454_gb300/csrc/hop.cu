@@ -56,8 +56,22 @@ cudaError_t launch_hop_batch(int prec, bool dag, const HopArgs *tab, int nsys, c
 
 cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
 {
-    if (var < 0 || var > 5 || var == 1 || var == 2) var = hop_default_variant(prec);
+    if (var < 0 || var > 6 || var == 1 || var == 2) var = hop_default_variant(prec);
     if (NS <= 0 || NS > 4 || NS == 3 || (a.Ls % NS) != 0 || (NS == 4 && var != 5)) NS = hop_default_ns(prec, a.Ls);
+    if (var == 6 && (prec == DWF_F64 || a.mixmode != 0 || a.Ls > 32 || 32 % a.Ls != 0)) {
+        var = prec == DWF_F16 ? 5 : 0;   // variant 6 needs FP32/FP16 fields, dense mixing, Ls dividing 32
+        SB = 0;
+        NS = hop_default_ns(prec, a.Ls);
+    }
+    if (var == 6) {   // one slice per thread; SB = warps per CTA (0: default)
+        NS = 1;
+        if (SB <= 0 || SB > 8) SB = 4;
+        switch (prec) {
+        case DWF_F32: return dag ? hop_launch_pd<DWF_F32, true>(a, 6, 1, SB, st) : hop_launch_pd<DWF_F32, false>(a, 6, 1, SB, st);
+        case DWF_F16: return dag ? hop_launch_pd<DWF_F16, true>(a, 6, 1, SB, st) : hop_launch_pd<DWF_F16, false>(a, 6, 1, SB, st);
+        default: var = 0; SB = 0; break;
+        }
+    }
     if (SB <= 0) SB = hop_default_sb(prec, a.Ls, NS);
     if ((a.Ls / NS) * SB > 256) SB = 256 / (a.Ls / NS);
     if (SB < 1) SB = 1;

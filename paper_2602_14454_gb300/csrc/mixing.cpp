@@ -212,6 +212,8 @@ bool build_fifth_matrices_s(int Ls, double M0, double mf, const double *bs, cons
         out.mats[MAT_HALF_Q][chi] = scale(Q, 0.5);
         out.mats[MAT_SRC_POST][chi] = diag(src_post.data(), n);
         out.mats[MAT_SRC_Y][chi] = diag(src_y.data(), n);
+        out.mats[MAT_NQUARTER][chi] = eye(n, -0.25);
+        out.mats[MAT_NMT4][chi] = scale(transpose(M, n), -0.25);
         dee = std::fmax(dee, spectral_norm(A5R, n));
     }
     out.dee_norm2 = dee;
@@ -288,6 +290,8 @@ void build_programs(int L, double alpha0, double beta0, double b, double c, doub
         {MAT_ID, ONE, 0, 0, 0, ONE, 1.0},       {MAT_HALF_Q, ONE, 1, 0, 0, RINV, 0.5},
         {MAT_SRC_POST, ONE, 0, 0, 0, ONE, 0.5 * c},
         {MAT_SRC_Y, ONE, 0, 0, 0, ONE, 1.0 - c * (4.0 - M0)},
+        {MAT_NQUARTER, ONE, 0, 0, 0, ONE, -0.25},
+        {MAT_NMT4, ONE, 1, 1, 1, ONE, -0.25},
     };
     for (const Spec &sp : specs) {
         FifthMatrices::Prog &p = out.prog[sp.id];

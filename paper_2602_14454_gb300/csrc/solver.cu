@@ -63,6 +63,7 @@ __global__ void reliable_fix_kernel(CgScalars *cg, const CgScalars *fresh, int f
 struct Bufs {
     int ps;   // inner precision
     int xp;   // accumulator precision
+    int form = 0;   // 0: CG on D_pc (eq. even-odd_linear_equation), 1: on D' (eq. another_even-odd_linear_equation)
     FieldRef be, bo, bt, x64, r64, t64, h64, xo64;
     FieldRef p, ph, t, wh, u, rs, xs;
     CgScalars *cg, *n64, *aux;
@@ -105,9 +106,14 @@ struct IterArgs {
     HopArgs k[4];   // K_a, K_b (operator), K_c, K_d (adjoint)
 };
 
+// B.form = 1: the operator is D' = D_ee D_pc D_ee^-1 = 1 - 1/4 H_eo M H_oe M and
+// D'^dag w = w - 1/4 M^T H^dag M^T H^dag w (the product P Q of the first form's
+// outer mixings is M, and D_ee Q = 1): p^ = M p, K_b without the Q^T mixing,
+// K_d with the identity in place of Q^-T and -1/4 M^T in place of -1/4 P^T.
 IterArgs iteration_args(dwf_ctx *h, const Bufs &B, const RedArgs &ra, const RedArgs &rb)
 {
     const int P = B.ps;
+    const bool f2 = B.form == 1;
     IterArgs I;
     CgUpdateArgs &ue = I.ue;
     ue.r = B.rs;
@@ -115,29 +121,30 @@ IterArgs iteration_args(dwf_ctx *h, const Bufs &B, const RedArgs &ra, const RedA
     ue.phat = B.ph;
     ue.Vh = h->Vh;
     ue.Ls = h->Ls;
-    ue.mat = h->mat(P, MAT_P);
+    const int pre = f2 ? MAT_M : MAT_P;
+    ue.mat = h->mat(P, pre);
     ue.mixmode = h->mix_mode(P);
-    ue.prog = h->prog(P, MAT_P);
-    ue.band = h->fm.band[MAT_P];
+    ue.prog = h->prog(P, pre);
+    ue.band = h->fm.band[pre];
     ue.scal = B.cg;
     ue.xacc = B.xs.v;   // x += alpha p of the previous iteration
 
     I.k[0] = hop_args(h, P, 1, B.ph, B.t, MAT_M);
 
     HopArgs &kb = I.k[1];
-    kb = hop_args(h, P, 0, B.t, B.wh, MAT_NQ4);
+    kb = hop_args(h, P, 0, B.t, B.wh, f2 ? MAT_NQUARTER : MAT_NQ4);
     kb.y = B.p;
     kb.ymode = 1;
-    kb.zmat = h->mat(P, MAT_QT);
+    kb.zmat = f2 ? nullptr : h->mat(P, MAT_QT);
     kb.red = ra;
 
     I.k[2] = hop_args(h, P, 1, B.wh, B.u, MAT_MT);
 
     HopArgs &kd = I.k[3];
-    kd = hop_args(h, P, 0, B.u, B.rs, MAT_NPT4);
+    kd = hop_args(h, P, 0, B.u, B.rs, f2 ? MAT_NMT4 : MAT_NPT4);
     kd.y = B.wh;
-    kd.ymode = 2;
-    kd.ymat = h->mat(P, MAT_RA5T);
+    kd.ymode = f2 ? 1 : 2;
+    kd.ymat = f2 ? nullptr : h->mat(P, MAT_RA5T);
     kd.rin = B.rs;
     kd.ralpha = &B.cg->alpha;
     kd.red = rb;
@@ -181,18 +188,20 @@ cudaError_t zero_iterate_residual(dwf_ctx *h, const Bufs &B, cudaStream_t st)
     return cudaMemcpyAsync(&B.n64->last, &B.aux->last, sizeof(double), cudaMemcpyDeviceToDevice, st);
 }
 
-// rs = D^dag r64 evaluated in the inner precision; |rs|^2 -> n64->last
+// rs = D^dag r64 evaluated in the inner precision; |rs|^2 -> n64->last.
+// B.form = 1: rs = D'^dag r' with r' = D_ee r64 = b' - D' y, the residual of the
+// second form's equation for y = D_ee x_e.
 cudaError_t normal_residual(dwf_ctx *h, const Bufs &B, cudaStream_t st)
 {
     const int P = B.ps;
     cudaError_t e;
     h->launches += 1;
     if ((e = launch_convert(DWF_F64, B.r64, P, B.rs, h->Vh, h->Ls, st)) != cudaSuccess) return e;
-    if ((e = mix(h, P, B.rs, B.ph, MAT_QT, st)) != cudaSuccess) return e;
+    if ((e = mix(h, P, B.rs, B.ph, B.form == 1 ? MAT_A5R : MAT_QT, st)) != cudaSuccess) return e;
     HopArgs a1 = hop_args(h, P, 1, B.ph, B.u, MAT_MT);
     if ((e = hop(h, P, true, a1, st)) != cudaSuccess) return e;
-    HopArgs a2 = hop_args(h, P, 0, B.u, B.rs, MAT_NPT4);
-    a2.y = B.rs;
+    HopArgs a2 = hop_args(h, P, 0, B.u, B.rs, B.form == 1 ? MAT_NMT4 : MAT_NPT4);
+    a2.y = B.form == 1 ? B.ph : B.rs;
     a2.ymode = 1;
     a2.red = red(h, RED_STORE, B.n64);
     return hop(h, P, true, a2, st);
@@ -327,9 +336,13 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
     if (p->precond && !h->net)
         return dwf_set_error(DWF_EINVAL, "precond = 1 needs a network (dwf_precond_init or dwf_precond_train)");
     if (p->precond && ps != DWF_F32) return dwf_set_error(DWF_EINVAL, "the FCG solve runs its inner cycles in FP32");
+    if (p->eo_form != 0 && p->eo_form != 1) return dwf_set_error(DWF_EINVAL, "eo_form must be 0 or 1");
+    if (p->eo_form == 1 && p->precond)
+        return dwf_set_error(DWF_EINVAL, "the learned preconditioner runs on the first even-odd form only");
     Bufs B;
     int rc = get_bufs(h, ps, B);
     if (rc) return rc;
+    B.form = p->eo_form;
     SolverExtra &X = solver_extra(h);
     if (!X.pinned) CK(cudaMallocHost(&X.pinned, sizeof(CgScalars) * 4));
     if (!X.cap) CK(cudaStreamCreateWithFlags(&X.cap, cudaStreamNonBlocking));
@@ -384,8 +397,8 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
     GraphCache &G = X.graph;
     char keybuf[256];
     // the captured kernels depend on the hop configuration and mixing mode too
-    std::snprintf(keybuf, sizeof keybuf, "%d/%d/%p/%p/%p/%d/%d/%d/%d/%d", ps, N, B.p.v, B.rs.v, B.xs.v, p->use_graph,
-                  h->hop_var[ps], h->hop_ns[ps], h->hop_sb[ps], h->mix_mode(ps));
+    std::snprintf(keybuf, sizeof keybuf, "%d/%d/%p/%p/%p/%d/%d/%d/%d/%d/%d", ps, N, B.p.v, B.rs.v, B.xs.v,
+                  p->use_graph, h->hop_var[ps], h->hop_ns[ps], h->hop_sb[ps], h->mix_mode(ps), B.form);
     if (p->use_graph && G.key != keybuf) {
         if (G.exec) cudaGraphExecDestroy(G.exec);
         G.exec = nullptr;
@@ -409,7 +422,14 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
     double q_rate = 0, rn_last = 0;   // per-iteration reduction of the inner residual, last inner residual
     // xzero: x64 is still zero (first update without an initial guess)
     auto reliable = [&](bool first, bool xzero) -> int {
-        if (!first) {
+        if (!first && B.form == 1) {
+            // the inner CG accumulated a correction f of y = D_ee x_e: x64 += D_ee^-1 f
+            CK(launch_zero(DWF_F64, B.h64, h->Vh, h->Ls, st));
+            CK(launch_accum_x((double *)B.h64.v, B.xs.v, B.xp, B.p, B.ps, &B.cg->alpha, h->Vh, h->Ls, st));
+            CK(mix(h, DWF_F64, B.h64, B.t64, MAT_Q, st));
+            CK(launch_accum_x((double *)B.x64.v, B.t64.v, DWF_F64, B.t64, DWF_F64, nullptr, h->Vh, h->Ls, st));
+            h->launches += 3;
+        } else if (!first) {
             CK(launch_accum_x((double *)B.x64.v, B.xs.v, B.xp, B.p, B.ps, &B.cg->alpha, h->Vh, h->Ls, st));
             h->launches += 1;
         }
@@ -779,6 +799,7 @@ int batch_impl(dwf_handle const *hs_in, const void *const *b4, void *const *x4, 
     if (!(p->tol > 0) || p->max_iter < 1 || !(p->delta > 0 && p->delta < 1) || p->check_every < 1 ||
         p->batch_wave < 0)
         return dwf_set_error(DWF_EINVAL, "bad solver parameters");
+    if (p->eo_form != 0) return dwf_set_error(DWF_EINVAL, "dwf_solve_batch iterates on the first even-odd form");
     dwf_ctx *h0 = hs_in[0];
     if (!h0) return dwf_set_error(DWF_EINVAL, "NULL handle in batch");
     int Lsmax = 0;

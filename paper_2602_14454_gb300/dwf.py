@@ -42,7 +42,7 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner_prec", ctypes.c_int),
                 ("delta", ctypes.c_double), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("precond", ctypes.c_int), ("use_initial_guess", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("batch_wave", ctypes.c_int)]
+                ("batch_wave", ctypes.c_int), ("eo_form", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -415,7 +415,7 @@ class Operator:
 
 
 KERNEL_MATRICES = ("P", "PT", "Q", "QT", "M", "MT", "A5R", "RA5T", "NHALF", "NHALF_RBT", "NQ4", "NPT4", "ID",
-                   "HALF_Q", "SRC_POST", "SRC_Y")
+                   "HALF_Q", "SRC_POST", "SRC_Y", "NQUARTER", "NMT4")
 
 
 def fifth_matrix_host(Ls, M0, mf, b, c, form="standard", alpha=1.0, which=0, chirality=0):

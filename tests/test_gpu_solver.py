@@ -170,3 +170,45 @@ def test_c2_mixed_precision_full_size(c2_setup, prec, form, alpha):
     for other in x4s.values():
         assert rel(x4, other) < 1e-8
     x4s[(prec, form)] = x4
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_c1_solve_with_async_gather_hop(c1_reference, prec):
+    """The solver with hop variant 6 (asynchronous gathers) in every inner launch,
+    including the reducing and residual epilogues."""
+    U, b4, b5, x5_ref, x4_ref = c1_reference
+    op, ref = make_pair(C1["dims"], C1["Ls"], C1["M0"], C1["mf"], C1["b"], C1["c"], "neff", 0.5, U=U)
+    op.set_hop_config(prec, 6, 1, 4)
+    x5, st = op.solve(to_gpu(b5), inner_prec=prec, tol=1e-10)
+    x5 = to_np(x5)
+    assert rel(ref.apply(x5), b5) <= 1e-10
+    assert rel(ref.project_4d(x5), x4_ref) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_second_even_odd_form_is_alpha_independent(prec):
+    """CG on eq. (another_even-odd_linear_equation), D' y_e = b'_e with
+    D' = 1 - D_eo D_oo^-1 D_oe D_ee^-1 and x_e = D_ee^-1 y_e (eo_form = 1): Neff's
+    factor cancels in D' (Sec. 2.3), so the iteration count is the same for every
+    alpha and for the standard form, while on the first form it changes with
+    alpha; every solve reaches the oracle-checked residual and the oracle's 4D
+    solution."""
+    dims, Ls = (4, 4, 4, 8), 8
+    U = inputs.random_links(dims, 0.5, 1011)
+    b4 = inputs.gaussian_4d(dims, 2011)
+    from oracle import dwf as orc
+    ref0 = orc.DWF(U, dims, Ls, 1.8, 0.02, 1.5, 0.5)
+    x4_ref = ref0.project_4d(ref0.solve(ref0.source_5d(b4), tol=1e-13)[0])
+    its = {0: [], 1: []}
+    for form, alpha in (("standard", 1.0), ("neff", 0.4), ("neff", 0.7), ("neff", 1.0)):
+        op, ref = make_pair(dims, Ls, 1.8, 0.02, 1.5, 0.5, form, alpha, U=U)
+        b5 = ref.source_5d(b4)
+        for eo in (0, 1):
+            x5, st = op.solve(to_gpu(b5), inner_prec=prec, tol=1e-10, eo_form=eo, check_every=1)
+            x5 = to_np(x5)
+            assert rel(ref.apply(x5), b5) <= 1e-10, (form, alpha, eo)
+            assert rel(ref.project_4d(x5), x4_ref) < 1e-9, (form, alpha, eo)
+            its[eo].append(st["iterations"])
+    print("iterations, first form %s, second form %s" % (its[0], its[1]))
+    assert max(its[1]) - min(its[1]) <= 1
+    assert max(its[0]) - min(its[0]) > 1
