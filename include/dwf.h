@@ -147,10 +147,11 @@ typedef struct {
     int check_every;    /* inner iterations between host convergence checks;
                            they are captured as one CUDA graph; default 16     */
     int use_graph;      /* 1: replay the inner iterations as a CUDA graph       */
-    int precond;        /* 0: CG with reliable updates; 1: CG on the normal
-                           equation left-preconditioned by the handle's learned
-                           network (FP32 cycles, FP64 defect correction;
-                           dwf_precond_*); needs inner_prec = DWF_F32         */
+    int precond;        /* 0: CG with reliable updates; 1: flexible CG on the
+                           normal equation preconditioned by M = N N^dag, N the
+                           handle's learned network (FP32 cycles, FP64 defect
+                           correction; dwf_precond_*); needs inner_prec =
+                           DWF_F32                                             */
     int use_initial_guess; /* 1: x5 holds the initial guess on entry; 0: zero   */
     int verbose;        /* 0 quiet                                              */
     int batch_wave;     /* dwf_solve_batch: at most this many systems per wave;
@@ -404,13 +405,12 @@ int dwf_spectrum_bounds(dwf_handle h, int eo_form, int max_steps, double rtol, u
 
 /* ------------------------------------------------ learned preconditioner
  * No counterpart in the paper (it solves with plain CG).  A gauge-covariant
- * linear stencil network N approximates D^-1 for the even-odd matrix D and
- * preconditions it from the left: dwf_solve with params.precond = 1 runs FP32
- * cycles of CG on (N D)^dag (N D) e = (N D)^dag N r, each closed by an FP64
- * defect correction (r the FP64 residual of the even-odd system); if the
- * preconditioned operator loses positivity the solve continues with N = 1.
- * N^dag N is Hermitian positive semi-definite (dwf_precond_apply, which = 2,
- * gives N N^dag).
+ * linear stencil network N approximates D^-1 for the even-odd matrix D, so
+ * that M = N N^dag approximates (D^dag D)^-1: dwf_solve with params.precond = 1
+ * runs FP32 cycles of flexible CG (Notay 2000) on D^dag D e = D^dag r
+ * preconditioned by M, each closed by an FP64 defect correction (r the FP64
+ * residual of the even-odd system); if M loses positivity the solve continues
+ * with M = 1 (plain CG).  dwf_precond_apply with which = 2 gives M.
  * Channels are the Ls fifth-direction slices (Ls <= 16).  Layer l maps a
  * field psi of Ls channels to
  *   out(x, c) = sum_p sum_c' W[l][p][chi][c][c'] T_p(x, c'),
@@ -499,6 +499,19 @@ int dwf_precond_adam_step(dwf_handle h, int layers, const double *grad, double l
  * DWF_ECUDA. */
 int dwf_precond_save(dwf_handle h, const char *path);
 int dwf_precond_load(dwf_handle h, const char *path);
+
+/* One FP32 flexible-CG solve of D^dag D x = b (D the even-odd matrix; b, x
+ * EO fields, device, complex double) preconditioned by M = N N^dag (plain != 0:
+ * M = 1), from x = 0, as the cycles of dwf_solve with precond = 1 run it:
+ * q = D^dag D p, alpha = (r, z)/(p, q), x += alpha p, r' = r - alpha q,
+ * z' = M r', beta = (z', r' - r)/(r, z), p = z' + beta p, until
+ * |r| <= tol |b| or max_iter steps.  history (host, max_iter + 1 doubles, may
+ * be NULL) receives |r_k| / |b| from k = 0; *iters (may be NULL) the steps.
+ * Errors: DWF_EINVAL (NULL or unaligned vector, tol <= 0, max_iter < 0, no
+ * network without plain), DWF_ENOGAUGE, DWF_EBREAKDOWN (M not positive on a
+ * residual), DWF_ENONFINITE, DWF_ECUDA. */
+int dwf_precond_fcg(dwf_handle h, const void *b, void *x, double tol, int max_iter, int plain, double *history,
+                    int *iters, void *stream);
 
 /* Make the pairs from nsrc 4D sources b4[k] (device) and train (above).
  * Errors: DWF_EINVAL (nsrc < 1, NULL pointers, bad parameters, Ls > 16),

@@ -577,8 +577,8 @@ long long dwf_launch_count(dwf_handle h) { return h ? h->launches : 0; }
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb)
 {
     if (!h || prec < 0 || prec > 2) return dwf_set_error(DWF_EINVAL, "bad handle or precision");
-    if (variant < -1 || variant > 6 || variant == 1 || variant == 2)
-        return dwf_set_error(DWF_EINVAL, "variant must be -1, 0, 3, 4, 5 or 6");
+    if (variant < -1 || variant > 8 || variant == 1 || variant == 2)
+        return dwf_set_error(DWF_EINVAL, "variant must be -1, 0, 3, 4, 5, 6, 7 or 8");
     if (variant == 6) {   // sb counts warps per CTA
         if (ns < 0 || ns > 1) return dwf_set_error(DWF_EINVAL, "variant 6 takes ns 0 or 1");
         if (sb < 0 || sb > 8) return dwf_set_error(DWF_EINVAL, "variant 6 takes sb (warps per CTA) 0..8");
@@ -587,6 +587,7 @@ int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb)
         h->hop_sb[prec] = sb;
         return DWF_OK;
     }
+    if ((variant == 7 || variant == 8) && ns > 1) return dwf_set_error(DWF_EINVAL, "variants 7 and 8 take ns 0 or 1");
     if (ns < 0 || ns > 4 || ns == 3 || (ns && h->Ls % ns) || (ns == 4 && variant != 5))
         return dwf_set_error(DWF_EINVAL, "ns must be 0, 1, 2 or (variant 5) 4, and divide Ls");
     const int nsv = ns ? ns : hop_default_ns(prec, h->Ls);
@@ -659,7 +660,7 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
     double best = 1e30;
     int bvar = -1, bns = 0, bsb = 0, bmix = 0;
     for (int mix = 0; mix <= 2; ++mix)
-        for (int var = 0; var <= 6; ++var)
+        for (int var = 0; var <= 8; ++var)
             for (int ns = 1; ns <= 4; ns *= 2) {
                 if (mix == 1 && !h->fm.structured) continue;
                 if (mix == 2 && prec == DWF_F64) continue;
@@ -667,6 +668,7 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
                 if (mix != 0 && var != 0) continue;   // those mixings exist in the direct variant only
                 if (var == 5 && prec != DWF_F16) continue;
                 if (var == 6 && (prec == DWF_F64 || ns != 1 || 32 % h->Ls != 0)) continue;
+                if (var >= 7 && (prec == DWF_F64 || ns != 1 || h->Ls % 4 != 0)) continue;
                 if (ns == 4 && var != 5) continue;
                 if (h->Ls % ns) continue;
                 const int LsN = h->Ls / ns;

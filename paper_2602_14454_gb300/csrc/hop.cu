@@ -56,7 +56,11 @@ cudaError_t launch_hop_batch(int prec, bool dag, const HopArgs *tab, int nsys, c
 
 cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
 {
-    if (var < 0 || var > 6 || var == 1 || var == 2) var = hop_default_variant(prec);
+    if (var < 0 || var > 8 || var == 1 || var == 2) var = hop_default_variant(prec);
+    if ((var == 7 || var == 8) && (prec == DWF_F64 || a.mixmode != 0 || a.Ls % 4 != 0)) {
+        var = prec == DWF_F16 ? 5 : 0;   // variant 7 needs FP32/FP16 fields, dense mixing, Ls a multiple of 4
+        SB = 0;
+    }
     if (NS <= 0 || NS > 4 || NS == 3 || (a.Ls % NS) != 0 || (NS == 4 && var != 5)) NS = hop_default_ns(prec, a.Ls);
     if (var == 6 && (prec == DWF_F64 || a.mixmode != 0 || a.Ls > 32 || 32 % a.Ls != 0)) {
         var = prec == DWF_F16 ? 5 : 0;   // variant 6 needs FP32/FP16 fields, dense mixing, Ls dividing 32

@@ -870,6 +870,373 @@ __global__ void __launch_bounds__(256) hop_async_kernel(const HopArgs a, int tpc
     if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
 }
 
+// ---------------------------------------- variants 7, 8: lean on the L1 path
+// The direct kernel, rebuilt around the L1/shared-memory data path, which
+// bounds the FP32 hop (every byte a thread loads from L1 or shared memory
+// crosses it; ncu: L1/TEX 79 % busy at 28 % of DRAM bandwidth):
+//  * persistent CTAs of SB sites x Ls slices (one slice per thread in the hop)
+//    walking the tiles b, b + grid, ...;
+//  * the tile's links (all 8 directions of its sites, contiguous in the link
+//    table) are copied into shared memory with 16-byte asynchronous copies one
+//    tile ahead; each thread reads its site's link as 16-byte vectors (5 loads
+//    per direction instead of 9, each serving every slice of the site);
+//  * the neighbour spinors are direct 16-byte loads (the cheapest way into
+//    registers);
+//  * the fifth-direction mixing runs on half of the CTA's threads, each
+//    forming two outputs (slices s and s + Ls/2) from one pass over the site's
+//    tile rows, so that every row read serves two outputs;
+//  * the tile rows (28 floats), the site stride (one extra 16 bytes) and the
+//    matrix rows are padded so that the 16-byte shared accesses of a warp hit
+//    distinct banks.
+// Dense mixing, Ls even and a multiple of 4.  Variant 7: two CTAs per SM
+// worth of registers, variant 8: three.
+constexpr int LEAN_ROW = 14;   // float2 per tile row (24 floats used)
+
+template <int P>
+struct LeanGeom {
+    static constexpr int LINK_BYTES = 8 * 18 * (P == DWF_F16 ? 2 : 4);
+};
+
+// float2 between consecutive sites of the tile; floats between matrix rows
+__host__ __device__ constexpr int lean_site_stride(int Ls) { return Ls * LEAN_ROW + 2; }
+__host__ __device__ constexpr int lean_mat_row(int Ls) { return ((Ls / 2) & 1) ? Ls : Ls + 2; }
+
+template <int P>
+__host__ __device__ constexpr size_t lean_smem_bytes(int Ls, int SB)
+{
+    return (size_t)3 * 2 * Ls * lean_mat_row(Ls) * sizeof(float)           // matrices
+           + (size_t)2 * SB * LeanGeom<P>::LINK_BYTES                    // links, double buffered
+           + (size_t)SB * lean_site_stride(Ls) * sizeof(float2);          // mixing tile
+}
+
+// u[9] <- link D of a site from shared memory (FP32: 72 bytes at 72 D)
+template <int P, int D>
+__device__ __forceinline__ void lean_link(const unsigned char *lk, float2 *u)
+{
+    if constexpr (P == DWF_F32) {
+        const unsigned char *b = lk + D * 72;
+        if constexpr ((D & 1) == 0) {   // 16-byte aligned: 4 x 16 + 8 bytes
+            const float4 *q = reinterpret_cast<const float4 *>(b);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 v = q[k];
+                u[2 * k] = make_float2(v.x, v.y);
+                u[2 * k + 1] = make_float2(v.z, v.w);
+            }
+            u[8] = *reinterpret_cast<const float2 *>(b + 64);
+        } else {                        // 8 + 4 x 16 bytes
+            u[0] = *reinterpret_cast<const float2 *>(b);
+            const float4 *q = reinterpret_cast<const float4 *>(b + 8);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 v = q[k];
+                u[2 * k + 1] = make_float2(v.x, v.y);
+                u[2 * k + 2] = make_float2(v.z, v.w);
+            }
+        }
+    } else {   // FP16: 36 bytes at 36 D, 4-byte aligned
+        const __half2 *q = reinterpret_cast<const __half2 *>(lk + D * 36);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) u[k] = __half22float2(q[k]);
+    }
+}
+
+template <int P, bool DAG, int D>
+__device__ __forceinline__ void lean_dir(float2 *acc, const FieldRef &in, int nb, int x, int Ls,
+                                         const unsigned char *lk)
+{
+    constexpr int MU = D & 3;
+    constexpr int SIG = (D < 4 ? 1 : -1) * (DAG ? -1 : 1);
+    float2 u[9];
+    lean_link<P, D>(lk, u);
+    if constexpr (P == DWF_F32) {
+        float2 v[12];
+        ld_pairs<P, true>(in, (size_t)nb, x, Ls, v);
+        hop_one<MU, SIG>(acc, u, v);
+    } else {
+        const uint4 *base = reinterpret_cast<const uint4 *>(in.v) + ((size_t)nb * 3) * Ls + x;
+        __half2 v[12];
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            const uint4 q = __ldg(base + (size_t)g * Ls);
+            v[4 * g] = *reinterpret_cast<const __half2 *>(&q.x);
+            v[4 * g + 1] = *reinterpret_cast<const __half2 *>(&q.y);
+            v[4 * g + 2] = *reinterpret_cast<const __half2 *>(&q.z);
+            v[4 * g + 3] = *reinterpret_cast<const __half2 *>(&q.w);
+        }
+        const float sc = __ldg(in.scale + (size_t)nb * ((Ls + 3) & ~3) + x);
+        __half2 hx[3], hy[3];
+        project_h2<MU, SIG>(v, hx, hy);
+        float2 Hx[3], Hy[3], Qx[3], Qy[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Hx[a] = __half22float2(hx[a]);
+            Hy[a] = __half22float2(hy[a]);
+        }
+        su3_pairs(u, Hx, Hy, Qx, Qy);
+        const float2 scp = make_float2(sc, sc);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Qx[a] = p_mul(Qx[a], scp);
+            Qy[a] = p_mul(Qy[a], scp);
+        }
+        reconstruct<MU, SIG>(acc, Qx, Qy);
+    }
+}
+
+__device__ __forceinline__ float2 *lean_row(float2 *tile, int j, int s, int Ls)
+{
+    return tile + (size_t)j * lean_site_stride(Ls) + (size_t)s * LEAN_ROW;
+}
+
+__device__ __forceinline__ void lean_put(float2 *row, const float2 *v)
+{
+    float4 *r4 = reinterpret_cast<float4 *>(row);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) r4[q] = make_float4(v[2 * q].x, v[2 * q].y, v[2 * q + 1].x, v[2 * q + 1].y);
+}
+
+// o[n] += sum_t M[chi][s_n][t] tile(j, t) for the two outputs s_0 = p, s_1 = p + Ls/2;
+// M: [chi][s][t] with rows of lean_mat_row(Ls) floats.  Each 16-byte chunk of a
+// tile row (one colour and re/im part: the P_+ pair and the P_- pair) is used
+// as soon as it is read, for both outputs.
+__device__ __forceinline__ void lean_mix2(const float *M, const float2 *tile, int j, int p, int Ls, float2 (*o)[12])
+{
+    const int MR = lean_mat_row(Ls), half = Ls / 2;
+    const float *m0u = M + (size_t)p * MR, *m1u = M + (size_t)(p + half) * MR;
+    const float *m0l = M + (size_t)(Ls + p) * MR, *m1l = M + (size_t)(Ls + p + half) * MR;
+    const float4 *base = reinterpret_cast<const float4 *>(tile + (size_t)j * lean_site_stride(Ls));
+#pragma unroll 1
+    for (int t = 0; t < Ls; t += 2) {
+        const float2 a0 = *reinterpret_cast<const float2 *>(m0u + t), a1 = *reinterpret_cast<const float2 *>(m1u + t);
+        const float2 b0 = *reinterpret_cast<const float2 *>(m0l + t), b1 = *reinterpret_cast<const float2 *>(m1l + t);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float2 u0 = p_splat(k ? a0.y : a0.x), u1 = p_splat(k ? a1.y : a1.x);
+            const float2 l0 = p_splat(k ? b0.y : b0.x), l1 = p_splat(k ? b1.y : b1.x);
+            const float4 *row = base + (size_t)(t + k) * (LEAN_ROW / 2);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const float4 v = row[q];
+                const float2 hp = make_float2(v.x, v.y), hm = make_float2(v.z, v.w);
+                o[0][2 * q] = p_fma(u0, hp, o[0][2 * q]);
+                o[0][2 * q + 1] = p_fma(l0, hm, o[0][2 * q + 1]);
+                o[1][2 * q] = p_fma(u1, hp, o[1][2 * q]);
+                o[1][2 * q + 1] = p_fma(l1, hm, o[1][2 * q + 1]);
+            }
+        }
+    }
+}
+
+// The same for a cyclic tridiagonal matrix: rows t = s - 1, s, s + 1 only.
+__device__ __forceinline__ void lean_mix2_band(const float *M, const float2 *tile, int j, int p, int Ls,
+                                               float2 (*o)[12])
+{
+    const int MR = lean_mat_row(Ls), half = Ls / 2;
+    const float4 *base = reinterpret_cast<const float4 *>(tile + (size_t)j * lean_site_stride(Ls));
+#pragma unroll
+    for (int n = 0; n < 2; ++n) {
+        const int sn = p + n * half;
+#pragma unroll
+        for (int dt = -1; dt <= 1; ++dt) {
+            int t = sn + dt;
+            t = t < 0 ? t + Ls : (t >= Ls ? t - Ls : t);
+            const float2 cu = p_splat(M[(size_t)sn * MR + t]), cl = p_splat(M[(size_t)(Ls + sn) * MR + t]);
+            const float4 *row = base + (size_t)t * (LEAN_ROW / 2);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const float4 v = row[q];
+                o[n][2 * q] = p_fma(cu, make_float2(v.x, v.y), o[n][2 * q]);
+                o[n][2 * q + 1] = p_fma(cl, make_float2(v.z, v.w), o[n][2 * q + 1]);
+            }
+        }
+    }
+}
+
+// The epilogue of hop_epilogue_core (dense mixing) on the lean tile.  Every
+// thread puts its hop result; threads tid < SB Ls / 2 (site j = tid / (Ls/2),
+// p = tid % (Ls/2)) then own the outputs s = p and p + Ls/2 of site j.
+template <int P>
+__device__ __forceinline__ float lean_epilogue(const HopArgs &a, const float2 *acc, float2 *tile, const float *mats,
+                                               int j0, int s0, int site0, bool active0, int u, int SB)
+{
+    const int Ls = a.Ls, half = Ls / 2;
+    const int msz = 2 * Ls * lean_mat_row(Ls);
+    if (active0) lean_put(lean_row(tile, j0, s0, Ls), acc);
+    __syncthreads();
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const bool mixer = tid < SB * half;
+    const int j = mixer ? tid / half : 0, p = mixer ? tid - (tid / half) * half : 0;
+    const int site = u * SB + j;
+    const bool active = mixer && site < a.Vh;
+    const int sl[2] = {p, p + half};
+    // the solution accumulator update xacc += xalpha xdir (independent of the
+    // hop) first, while no output is held in registers
+    if (active && a.rin.v && a.xacc) {
+        FieldRef xf;
+        xf.v = a.xacc;
+        const float2 xa = p_splat((float)(*a.xalpha));
+#pragma unroll 1
+        for (int n = 0; n < 2; ++n) {
+            float2 xv[12], dx[12];
+            ld_pairs<DWF_F32, false>(xf, (size_t)site, sl[n], Ls, xv);
+            ld_pairs<P, false>(a.xdir, (size_t)site, sl[n], Ls, dx);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) xv[k] = p_fma(xa, dx[k], xv[k]);
+            st_pairs<DWF_F32>(xf, (size_t)site, sl[n], Ls, xv);
+        }
+    }
+    float2 o[2][12];
+#pragma unroll
+    for (int n = 0; n < 2; ++n)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o[n][k] = make_float2(0.f, 0.f);
+    if (active) {
+        if (a.post_band) lean_mix2_band(mats, tile, j, p, Ls, o);
+        else lean_mix2(mats, tile, j, p, Ls, o);
+    }
+    if (a.ymode == 1) {
+        if (active) {
+#pragma unroll
+            for (int n = 0; n < 2; ++n) {
+                float2 y[12];
+                ld_pairs<P, false>(a.y, (size_t)site, sl[n], Ls, y);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) o[n][k] = p_add(o[n][k], y[k]);
+            }
+        }
+    } else if (a.ymode == 2) {
+        __syncthreads();
+        if (active) {
+#pragma unroll 1
+            for (int n = 0; n < 2; ++n) {
+                float2 y[12];
+                ld_pairs<P, false>(a.y, (size_t)site, sl[n], Ls, y);
+                lean_put(lean_row(tile, j, sl[n], Ls), y);
+            }
+        }
+        __syncthreads();
+        if (active) {
+            if (a.y_band) lean_mix2_band(mats + msz, tile, j, p, Ls, o);
+            else lean_mix2(mats + msz, tile, j, p, Ls, o);
+        }
+    }
+    // the rest output by output (each output's registers are free when it is done)
+    float nrm = 0.f;
+#pragma unroll
+    for (int n = 0; n < 2; ++n) {
+        if (active && a.rin.v) {
+            const float2 nal = p_splat((float)-(*a.ralpha));
+            float2 r[12];
+            ld_pairs<P, false>(a.rin, (size_t)site, sl[n], Ls, r);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) o[n][k] = p_fma(nal, o[n][k], r[k]);
+        }
+        if (active && a.red.op != RED_NONE) {
+            float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) s2 = p_fma(o[n][k], o[n][k], s2);
+            nrm += s2.x + s2.y;
+        }
+        if (active) {
+            if (a.zmat) lean_put(lean_row(tile, j, sl[n], Ls), o[n]);
+            else st_pairs<P>(a.out, (size_t)site, sl[n], Ls, o[n]);
+        }
+    }
+    if (a.zmat) {
+        __syncthreads();
+        float2 z[2][12];
+#pragma unroll
+        for (int n = 0; n < 2; ++n)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) z[n][k] = make_float2(0.f, 0.f);
+        if (active) {
+            if (a.z_band) lean_mix2_band(mats + 2 * msz, tile, j, p, Ls, z);
+            else lean_mix2(mats + 2 * msz, tile, j, p, Ls, z);
+#pragma unroll
+            for (int n = 0; n < 2; ++n) st_pairs<P>(a.out, (size_t)site, sl[n], Ls, z[n]);
+        }
+    }
+    return nrm;
+}
+
+// the CTA's share of the link copies of tile u (sites u SB .. u SB + n - 1)
+template <int P>
+__device__ __forceinline__ void lean_issue_links(const void *gauge, int site0, int n, unsigned char *dst)
+{
+    constexpr int CH = LeanGeom<P>::LINK_BYTES / 16;
+    const uint4 *src = reinterpret_cast<const uint4 *>(gauge) + (size_t)site0 * CH;
+    const uint32_t d = smem_addr(dst);
+    const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int c = tid; c < n * CH; c += nt) cp_async16(d + (uint32_t)c * 16, src + c);
+    cp_async_commit();
+}
+
+// blockDim = (Ls, SB); grid: persistent, CTA b takes tiles b, b + gridDim.x, ...
+template <int P, bool DAG, int MINB>
+__global__ void __launch_bounds__(256, MINB) hop_lean_kernel(const HopArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ls = a.Ls, SB = blockDim.y;
+    const int s = threadIdx.x, j = threadIdx.y;
+    const int nt = blockDim.x * blockDim.y, tid = j * Ls + s;
+    const int MR = lean_mat_row(Ls), msz = 2 * Ls * MR;
+    float *mats = reinterpret_cast<float *>(smem_raw);
+    unsigned char *links = smem_raw + (size_t)3 * msz * sizeof(float);
+    float2 *tile = reinterpret_cast<float2 *>(links + (size_t)2 * SB * LeanGeom<P>::LINK_BYTES);
+    // matrices: [chi][t][s] in, row-major [chi][s][t] (rows of MR floats) in shared memory
+    {
+        const float *src[3] = {reinterpret_cast<const float *>(a.post),
+                               a.ymode == 2 ? reinterpret_cast<const float *>(a.ymat) : nullptr,
+                               reinterpret_cast<const float *>(a.zmat)};
+        for (int m = 0; m < 3; ++m) {
+            if (!src[m]) continue;
+            for (int k = tid; k < 2 * Ls * Ls; k += nt) {
+                const int chi = k / (Ls * Ls), r = k - chi * Ls * Ls, t = r / Ls, ss = r - t * Ls;
+                mats[m * msz + (chi * Ls + ss) * MR + t] = src[m][k];
+            }
+        }
+    }
+    const int ntiles = (a.Vh + SB - 1) / SB;
+    int u = blockIdx.x;
+    if (u < ntiles) lean_issue_links<P>(a.gauge, u * SB, min(SB, a.Vh - u * SB), links);
+    float nrm = 0.f;
+    for (int k = 0; u < ntiles; ++k, u += gridDim.x) {
+        const int site = u * SB + j;
+        const bool active = site < a.Vh;
+        int n8[8];
+        if (active) {
+            const int4 *p = reinterpret_cast<const int4 *>(a.nbr + (size_t)site * 8);
+            const int4 q0 = __ldg(p), q1 = __ldg(p + 1);
+            n8[0] = q0.x; n8[1] = q0.y; n8[2] = q0.z; n8[3] = q0.w;
+            n8[4] = q1.x; n8[5] = q1.y; n8[6] = q1.z; n8[7] = q1.w;
+        }
+        cp_async_wait<0>();
+        __syncthreads();   // this tile's links are in; the previous tile's epilogue is done
+        const int un = u + gridDim.x;
+        if (un < ntiles)   // the next tile's links, into the other buffer
+            lean_issue_links<P>(a.gauge, un * SB, min(SB, a.Vh - un * SB),
+                                links + (size_t)((k + 1) & 1) * SB * LeanGeom<P>::LINK_BYTES);
+        float2 acc[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) acc[q] = make_float2(0.f, 0.f);
+        if (active) {
+            const unsigned char *lk = links + ((size_t)(k & 1) * SB + j) * LeanGeom<P>::LINK_BYTES;
+            lean_dir<P, DAG, 0>(acc, a.in, n8[0], s, Ls, lk);
+            lean_dir<P, DAG, 1>(acc, a.in, n8[1], s, Ls, lk);
+            lean_dir<P, DAG, 2>(acc, a.in, n8[2], s, Ls, lk);
+            lean_dir<P, DAG, 3>(acc, a.in, n8[3], s, Ls, lk);
+            lean_dir<P, DAG, 4>(acc, a.in, n8[4], s, Ls, lk);
+            lean_dir<P, DAG, 5>(acc, a.in, n8[5], s, Ls, lk);
+            lean_dir<P, DAG, 6>(acc, a.in, n8[6], s, Ls, lk);
+            lean_dir<P, DAG, 7>(acc, a.in, n8[7], s, Ls, lk);
+        }
+        nrm += lean_epilogue<P>(a, acc, tile, mats, j, s, site, active, u, SB);
+    }
+    cp_async_wait<0>();
+    if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
+}
+
 // ---------------------------------------------------------------- launch
 template <int P>
 size_t direct_smem(int Ls, int SB)
@@ -1018,13 +1385,13 @@ cudaError_t launch_async(const HopArgs &a, int nw, cudaStream_t st)
     int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if ((e = smem_optin(hop_async_kernel<P, DAG, 0>, 227 * 1024, optin)) != cudaSuccess) return e;
+    if ((e = smem_optin(hop_async_kernel<P, DAG, 0>, 200 * 1024, optin)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if (nw < 1) nw = 4;
     if (nw > 8) nw = 8;
     size_t smem = async_cta_bytes<P>(a.Ls, nw);
-    while (nw > 1 && smem > 227 * 1024) smem = async_cta_bytes<P>(a.Ls, --nw);
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    while (nw > 1 && smem > 200 * 1024) smem = async_cta_bytes<P>(a.Ls, --nw);
+    if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_async_kernel<P, DAG, 0>, 32 * nw, smem);
     if (e != cudaSuccess) return e;
@@ -1039,9 +1406,39 @@ cudaError_t launch_async(const HopArgs &a, int nw, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Variant 7: persistent CTAs of SB sites, as many per SM as fit.
+template <int P, bool DAG, int MINB>
+cudaError_t launch_lean(const HopArgs &a, int SB, cudaStream_t st)
+{
+    static unsigned long long optin = 0;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = smem_optin(hop_lean_kernel<P, DAG, MINB>, 200 * 1024, optin)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (SB < 1) SB = 1;
+    while (SB > 1 && a.Ls * SB > 256) --SB;
+    const size_t smem = lean_smem_bytes<P>(a.Ls, SB);
+    if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_lean_kernel<P, DAG, MINB>, a.Ls * SB, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int ntiles = (a.Vh + SB - 1) / SB;
+    int grid = nsm * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    hop_lean_kernel<P, DAG, MINB><<<grid, dim3(a.Ls, SB), smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int P, bool DAG>
 cudaError_t launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
 {
+    if constexpr (P != DWF_F64) {
+        if (var == 7 && a.mixmode == 0 && a.Ls % 4 == 0) return launch_lean<P, DAG, 2>(a, SB, st);
+        if (var == 8 && a.mixmode == 0 && a.Ls % 4 == 0) return launch_lean<P, DAG, 3>(a, SB, st);
+    }
+    if (var == 7 || var == 8) var = P == DWF_F16 ? 5 : 0;
     // variant 6: asynchronous gathers (FP32 and FP16 fields, dense mixing, Ls dividing 32);
     // SB is read as warps per CTA
     if constexpr (P != DWF_F64) {

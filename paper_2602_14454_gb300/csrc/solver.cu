@@ -207,23 +207,25 @@ cudaError_t normal_residual(dwf_ctx *h, const Bufs &B, cudaStream_t st)
     return hop(h, P, true, a2, st);
 }
 
-// One FP32 cycle of CG on the normal equation of the left-preconditioned
-// system N D e = N r (N the handle's network, trained so that N D ~ 1):
-//     (N D)^dag (N D) e = (N D)^dag N r,
-// from e = 0 until the residual of this equation fell below eta times its
-// initial norm, or kmax iterations; e is added into B.xs.  With plain = true
-// N is the identity (CG on D^dag D).  A non-positive or non-finite curvature
-// (p, B p) of the preconditioned operator ends the cycle and sets `plain` for
-// the rest of the solve (the caller's FP64 defect correction continues from
-// the iterate reached).
-int lpcg_cycle(dwf_ctx *h, const Bufs &B, FieldRef r32, double eta, int kmax, bool &plain, int &iters, int &napp,
-               int &fallbacks, int &dapp, cudaStream_t st)
+// One FP32 cycle of flexible CG (Notay 2000) on the normal equation
+//     A x = b,  A = D^dag D (D the even-odd matrix),
+// preconditioned by M = N N^dag (N the handle's network, trained so that
+// N D ~ 1, hence M ~ A^-1), from x = 0: r = b, z = M r, p = z; then per step
+// q = A p, alpha = (r, z) / (p, q), x += alpha p, r' = r - alpha q, z' = M r',
+// beta = (z', r' - r) / (r, z) (Polak-Ribiere), p = z' + beta p.  It stops when
+// |r| <= eta |b| or after kmax steps; x is added into `xacc`.  With plain =
+// true M is the identity (CG on D^dag D).  A non-positive (p, q) or (r, z)
+// ends the cycle and sets `plain` for the rest of the solve (the caller's FP64
+// defect correction continues from the iterate reached).  hist (if not null)
+// receives |r_k| / |b| for k = 0, 1, ... (at most kmax + 1 values).
+int fcg_cycle(dwf_ctx *h, FieldRef b, FieldRef xacc, double eta, int kmax, bool &plain, int &iters, int &napp,
+              int &fallbacks, int &dapp, double *hist, cudaStream_t st)
 {
     cudaError_t e = cudaSuccess;
-    FieldRef rr = h->field("lp_r", DWF_F32, &e), pp = h->field("lp_p", DWF_F32, &e);
-    FieldRef q = h->field("lp_q", DWF_F32, &e), t1 = h->field("lp_t1", DWF_F32, &e);
-    FieldRef t2 = h->field("lp_t2", DWF_F32, &e);
-    if (!rr.v || !pp.v || !q.v || !t1.v || !t2.v) return dwf_cuda_error(e, "workspace");
+    FieldRef ra = h->field("fc_ra", DWF_F32, &e), rb = h->field("fc_rb", DWF_F32, &e);
+    FieldRef z = h->field("fc_z", DWF_F32, &e), pp = h->field("fc_p", DWF_F32, &e);
+    FieldRef q = h->field("fc_q", DWF_F32, &e), t1 = h->field("fc_t1", DWF_F32, &e);
+    if (!ra.v || !rb.v || !z.v || !pp.v || !q.v || !t1.v) return dwf_cuda_error(e, "workspace");
     const int Vh = h->Vh, Ls = h->Ls;
     CgScalars *sc = h->scal + 4;
     CgScalars hs[2];
@@ -236,26 +238,37 @@ int lpcg_cycle(dwf_ctx *h, const Bufs &B, FieldRef r32, double eta, int kmax, bo
         out = hs[0].last;
         return DWF_OK;
     };
-    // y = (N D)^dag N v (learned) or D^dag v (plain), from v (destroys t1, t2)
-    auto lhs_of = [&](FieldRef v, FieldRef y) -> int {
-        int r2;
-        if (plain) return eo_dag_apply_f32(h, v, y, st);
-        if ((r2 = net_apply_f32(h, v, t2, st, 0))) return r2;
-        if ((r2 = net_apply_f32(h, t2, t1, st, 1))) return r2;
-        napp += 2;
-        return eo_dag_apply_f32(h, t1, y, st);
+    auto precondition = [&](FieldRef v, FieldRef out) -> int {
+        if (plain) {
+            CK(launch_vaxpby(1.f, v, 0.f, out, Vh, Ls, st));
+            h->launches += 1;
+            return DWF_OK;
+        }
+        napp += 1;
+        return net_apply_f32(h, v, out, st, 2);
     };
-    if ((rc = lhs_of(r32, rr))) return rc;
-    dapp += 1;
-    CK(launch_vaxpby(1.f, rr, 0.f, pp, Vh, Ls, st));
+    FieldRef r = ra, rn = rb;
+    CK(launch_vaxpby(1.f, b, 0.f, r, Vh, Ls, st));   // r = b - A 0
+    h->launches += 1;
+    double bn2;
+    if ((rc = dot(b, b, bn2))) return rc;
+    const double bn = std::sqrt(bn2);
+    if (hist) hist[0] = 1.0;
+    if (!(bn > 0) || !std::isfinite(bn)) return DWF_OK;
+    if ((rc = precondition(r, z))) return rc;
+    CK(launch_vaxpby(1.f, z, 0.f, pp, Vh, Ls, st));
     h->launches += 1;
     double rz;
-    if ((rc = dot(rr, rr, rz))) return rc;
-    const double r0 = std::sqrt(rz);
-    if (!(r0 > 0) || !std::isfinite(r0)) return DWF_OK;
+    if ((rc = dot(r, z, rz))) return rc;
+    if (!(rz > 0) || !std::isfinite(rz)) {
+        if (plain) return dwf_set_error(DWF_EBREAKDOWN, "CG breakdown");
+        plain = true;
+        fallbacks += 1;
+        return DWF_OK;
+    }
     for (int k = 0; k < kmax; ++k) {
-        if ((rc = eo_apply_f32(h, pp, q, st))) return rc;   // q = D p
-        if ((rc = lhs_of(q, q))) return rc;                  // q = (N D)^dag N D p
+        if ((rc = eo_apply_f32(h, pp, t1, st))) return rc;     // D p
+        if ((rc = eo_dag_apply_f32(h, t1, q, st))) return rc;  // q = D^dag D p
         dapp += 2;
         double pq;
         if ((rc = dot(pp, q, pq))) return rc;
@@ -265,18 +278,34 @@ int lpcg_cycle(dwf_ctx *h, const Bufs &B, FieldRef r32, double eta, int kmax, bo
             fallbacks += 1;
             return DWF_OK;
         }
-        const float alpha = (float)(rz / pq);
-        CK(launch_vaxpby(alpha, pp, 1.f, B.xs, Vh, Ls, st));
-        CK(launch_vaxpby(-alpha, q, 1.f, rr, Vh, Ls, st));
-        h->launches += 2;
-        double rn2;
-        if ((rc = dot(rr, rr, rn2))) return rc;
+        const double alpha = rz / pq;
+        CK(launch_vaxpby((float)alpha, pp, 1.f, xacc, Vh, Ls, st));        // x += alpha p
+        CK(launch_vaxpby(1.f, r, 0.f, rn, Vh, Ls, st));                    // r' = r - alpha q
+        CK(launch_vaxpby((float)-alpha, q, 1.f, rn, Vh, Ls, st));
+        h->launches += 3;
         iters += 1;
-        if (!std::isfinite(rn2)) return dwf_set_error(DWF_ENONFINITE, "non-finite residual in the CG cycle");
-        if (std::sqrt(rn2) <= eta * r0) break;
-        CK(launch_vaxpby(1.f, rr, (float)(rn2 / rz), pp, Vh, Ls, st));
+        double rn2;
+        if ((rc = dot(rn, rn, rn2))) return rc;
+        if (!std::isfinite(rn2)) return dwf_set_error(DWF_ENONFINITE, "non-finite residual in the FCG cycle");
+        if (hist) hist[k + 1] = std::sqrt(rn2) / bn;
+        if (std::sqrt(rn2) <= eta * bn) break;
+        if ((rc = precondition(rn, z))) return rc;                          // z' = M r'
+        double zrn, zr;
+        if ((rc = dot(z, rn, zrn))) return rc;
+        if ((rc = dot(z, r, zr))) return rc;
+        if (!(zrn > 0) || !std::isfinite(zrn)) {
+            if (plain) return dwf_set_error(DWF_EBREAKDOWN, "CG breakdown");
+            plain = true;
+            fallbacks += 1;
+            return DWF_OK;
+        }
+        const double beta = (zrn - zr) / rz;
+        CK(launch_vaxpby(1.f, z, (float)beta, pp, Vh, Ls, st));            // p = z' + beta p
         h->launches += 1;
-        rz = rn2;
+        rz = zrn;
+        FieldRef tmp = r;
+        r = rn;
+        rn = tmp;
     }
     return DWF_OK;
 }
@@ -386,7 +415,11 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
     CK(launch_zero(ps, B.p, h->Vh, h->Ls, st));
     CK(cudaMemsetAsync(B.cg, 0, sizeof(CgScalars), st));
 
-    double target = p->tol * b5n / h->fm.dee_norm2 * 0.5;
+    // stop when the even part of the full 5D residual is below tol |b5| / 2 (the
+    // odd part vanishes after the exact reconstruction of x_o): first form,
+    // r_full,e = D_ee r64, bounded by |D_ee| |r64|; second form, r_full,e = r'
+    // itself, the residual of its own equation (D_ee r64)
+    double target = B.form == 1 ? p->tol * b5n * 0.5 : p->tol * b5n / h->fm.dee_norm2 * 0.5;
     const int N = p->check_every;
     int iters = 0, nru = 0, dapp = 0;
     double rtrue = 0, rho = 1, rmax = 0;
@@ -443,6 +476,11 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
             CK(true_residual(h, B, st));
             dapp += 1;
         }
+        if (B.form == 1) {   // |r'| = |D_ee r64|, the second form's residual
+            CK(mix(h, DWF_F64, B.r64, B.t64, MAT_A5R, st));
+            CK(launch_norm2(DWF_F64, B.t64, h->Vh, h->Ls, red(h, RED_STORE, B.n64), st));
+            h->launches += 1;
+        }
         CgScalars n64;
         CK(cudaMemcpyAsync(&hs[1], B.n64, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -476,19 +514,23 @@ static int solve_impl(dwf_handle h, const void *b5, void *x5, const dwf_solve_pa
         converged = false;
         const bool fresh = round == 0 && !p->use_initial_guess;
         if ((rc = reliable(fresh, fresh))) return rc;
-        // learned preconditioner: FP32 cycles of left-preconditioned CGNR, each
-        // closed by an FP64 defect correction (x64 += e, r64 = b~ - D x64)
+        // learned preconditioner: FP32 cycles of flexible CG on the correction's
+        // normal equation D^dag D e = D^dag r64 with M = N N^dag, each closed by an
+        // FP64 defect correction (x64 += e, r64 = b~ - D x64)
         while (p->precond && !converged) {
             if (iters >= p->max_iter) {
                 status = DWF_ENOTCONV;
                 break;
             }
-            FieldRef r32 = h->field("lp_r32", DWF_F32, &ce);
-            if (!r32.v) return dwf_cuda_error(ce, "workspace");
+            // the right side of the correction's normal equation: D^dag r64 in FP32
+            FieldRef r32 = h->field("lp_r32", DWF_F32, &ce), b32 = h->field("lp_b32", DWF_F32, &ce);
+            if (!r32.v || !b32.v) return dwf_cuda_error(ce, "workspace");
             CK(launch_convert(DWF_F64, B.r64, DWF_F32, r32, h->Vh, h->Ls, st));
             h->launches += 1;
-            if ((rc = lpcg_cycle(h, B, r32, 0.01 * p->delta, p->max_iter - iters, lp_plain, iters, napp, nfall, dapp,
-                                 st)))
+            if ((rc = eo_dag_apply_f32(h, r32, b32, st))) return rc;
+            dapp += 1;
+            if ((rc = fcg_cycle(h, b32, B.xs, 0.01 * p->delta, p->max_iter - iters, lp_plain, iters, napp, nfall,
+                                dapp, nullptr, st)))
                 return rc;
             if ((rc = reliable(false, false))) return rc;
         }
@@ -1216,6 +1258,35 @@ int dwf_solve(dwf_handle h, const void *b5, void *x5, const dwf_solve_params *p,
     dwf_solve_params def;
     dwf_solve_params_default(&def);
     return solve_impl(h, b5, x5, p ? p : &def, stats, (cudaStream_t)stream);
+}
+
+int dwf_precond_fcg(dwf_handle h, const void *b, void *x, double tol, int max_iter, int plain, double *history,
+                    int *iters, void *stream)
+{
+    if (!h || !b || !x) return dwf_set_error(DWF_EINVAL, "NULL argument");
+    if (!h->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
+    if (!(tol > 0) || max_iter < 0) return dwf_set_error(DWF_EINVAL, "bad tol or max_iter");
+    if (!plain && !h->net) return dwf_set_error(DWF_EINVAL, "no preconditioner (dwf_precond_init or dwf_precond_train)");
+    if (((uintptr_t)b & 15u) || ((uintptr_t)x & 15u)) return dwf_set_error(DWF_EINVAL, "vectors must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    FieldRef b32 = h->field("pf_b32", DWF_F32, &e), x32 = h->field("pf_x32", DWF_F32, &e);
+    FieldRef x64 = h->field("pf_x64", DWF_F64, &e);
+    if (!b32.v || !x32.v || !x64.v) return dwf_cuda_error(e, "workspace");
+    CK(launch_pack_eo(DWF_F32, (const double *)b, b32, h->Vh, h->Ls, st));
+    CK(launch_zero(DWF_F32, x32, h->Vh, h->Ls, st));
+    h->launches += 2;
+    bool pl = plain != 0;
+    int it = 0, napp = 0, nfall = 0, dapp = 0;
+    int rc = fcg_cycle(h, b32, x32, tol, max_iter, pl, it, napp, nfall, dapp, history, st);
+    if (rc) return rc;
+    CK(launch_convert(DWF_F32, x32, DWF_F64, x64, h->Vh, h->Ls, st));
+    CK(launch_unpack_eo(DWF_F64, x64, (double *)x, h->Vh, h->Ls, st));
+    h->launches += 2;
+    CK(cudaStreamSynchronize(st));
+    if (iters) *iters = it;
+    if (nfall) return dwf_set_error(DWF_EBREAKDOWN, "the preconditioner lost positivity");
+    return DWF_OK;
 }
 
 int dwf_propagator_host(dwf_handle h, const double *b4_host, double *x4_host, const dwf_solve_params *p,

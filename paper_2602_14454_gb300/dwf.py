@@ -35,7 +35,7 @@ EXPORTED = ["dwf_create", "dwf_create_s", "dwf_destroy", "dwf_strerror", "dwf_la
             "dwf_set_mix_mode", "dwf_get_mix_mode", "dwf_apply_eo_noalloc",
             "dwf_train_params_default", "dwf_precond_init", "dwf_precond_set_weights", "dwf_precond_get_weights",
             "dwf_precond_apply", "dwf_precond_loss_grad", "dwf_precond_train", "dwf_precond_adam_step",
-            "dwf_precond_save", "dwf_precond_load", "dwf_alu_peaks"]
+            "dwf_precond_save", "dwf_precond_load", "dwf_alu_peaks", "dwf_precond_fcg"]
 
 
 class SolveParams(ctypes.Structure):
@@ -147,6 +147,7 @@ def lib():
     L.dwf_precond_apply.argtypes = [vp, i, vp, vp, vp]
     L.dwf_precond_loss_grad.argtypes = [vp, i, ctypes.POINTER(vp), ctypes.POINTER(vp), dp, dp, vp]
     L.dwf_precond_adam_step.argtypes = [vp, i, dp, d, vp]
+    L.dwf_precond_fcg.argtypes = [vp, vp, vp, d, i, i, dp, ip, vp]
     L.dwf_precond_save.argtypes = [vp, ctypes.c_char_p]
     L.dwf_precond_load.argtypes = [vp, ctypes.c_char_p]
     L.dwf_precond_train.argtypes = [vp, i, ctypes.POINTER(vp), ctypes.POINTER(TrainParams),
@@ -381,6 +382,17 @@ class Operator:
         g = np.ascontiguousarray(np.asarray(grad, dtype=np.complex128))
         check(lib().dwf_precond_adam_step(self._h, int(layers), g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                           float(lr), _stream()))
+
+    def precond_fcg(self, b, tol=1e-6, max_iter=200, plain=False, out=None):
+        """FP32 flexible CG on D^dag D x = b (EO fields) preconditioned by N N^dag
+        (or by 1 when plain); returns (x, residual history)."""
+        x = out if out is not None else self._new(self.shape_eo())
+        hist = np.zeros(int(max_iter) + 1)
+        n = ctypes.c_int()
+        check(lib().dwf_precond_fcg(self._h, _ptr(b), _ptr(x), float(tol), int(max_iter), int(bool(plain)),
+                                    hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(n),
+                                    _stream()))
+        return x, hist[: n.value + 1]
 
     def precond_save(self, path):
         check(lib().dwf_precond_save(self._h, os.fsencode(path)))

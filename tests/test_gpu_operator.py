@@ -135,7 +135,7 @@ def test_full_size_eo_parity():
 
 HOP_CONFIGS = [(4, 1, 4), (4, 2, 6), (4, 1, 12), (4, 2, 16), (4, 1, 5), (3, 1, 3), (3, 2, 8), (3, 1, 8), (0, 1, 3),
                (0, 2, 5), (0, 1, 16), (0, 2, 1), (5, 1, 8), (5, 2, 5), (5, 4, 3), (5, 4, 16), (6, 1, 1), (6, 1, 4),
-               (6, 0, 8)]
+               (6, 0, 8), (7, 1, 1), (7, 1, 5), (7, 0, 16), (8, 1, 3), (8, 0, 8)]
 
 
 @pytest.mark.parametrize("cfg", HOP_CONFIGS, ids=lambda c: "var%d_ns%d_sb%d" % c)
@@ -147,8 +147,8 @@ def test_hop_configurations_ragged_tiles(cfg, prec, Ls):
     var, ns, sb = cfg
     dims = (6, 2, 2, 4)
     op, ref = make_pair(dims, Ls, 1.8, 0.02, 1.5, 0.5, "neff", 0.6, seed=51)
-    if var == 6 and prec == "f64":
-        return                      # variant 6 has no FP64 form (FP64 falls back to variant 0)
+    if var >= 6 and prec == "f64":
+        return                      # variants 6-8 have no FP64 form (FP64 falls back to variant 0)
     op.set_hop_config(prec, var, ns, sb)
     assert op.hop_config(prec)[0] == var
     x = ref.to_eo(inputs.gaussian_5d(dims, Ls, 52), 0)
@@ -268,16 +268,19 @@ def test_errors():
     assert e.value.status == 8
 
 
-@pytest.mark.parametrize("Ls,dims", [(16, (4, 2, 6, 4)), (4, (2, 4, 4, 6)), (32, (2, 2, 2, 4)), (8, (8, 4, 4, 4))])
+@pytest.mark.parametrize("Ls,dims", [(16, (4, 2, 6, 4)), (4, (2, 4, 4, 6)), (32, (2, 2, 2, 4)), (8, (8, 4, 4, 4)),
+                                     (12, (4, 2, 2, 6))])
 @pytest.mark.parametrize("prec", ["f32", "f16"])
-@pytest.mark.parametrize("warps", [1, 3, 8])
-def test_async_gather_hop(Ls, dims, prec, warps):
-    """Variant 6 (asynchronous neighbour gathers, links staged per warp tile, one
-    to eight warps per persistent CTA) gives the even-odd operator, its adjoint
-    and the full 5D operator of the oracle; Ls = 4, 8, 16 and 32 put 8, 4, 2 and
-    1 sites in a warp tile."""
+@pytest.mark.parametrize("var,sb", [(6, 1), (6, 3), (6, 8), (7, 1), (7, 3), (8, 8), (8, 5)])
+def test_persistent_hop_variants(Ls, dims, prec, var, sb):
+    """Variant 6 (asynchronous neighbour gathers, links staged per warp tile; sb
+    warps per persistent CTA) and variants 7 and 8 (links staged per CTA tile of
+    sb sites, padded mixing tile, two or three CTAs per SM) give the even-odd
+    operator, its adjoint and the full 5D operator of the oracle; Ls = 4, 8, 16
+    and 32 put 8, 4, 2 and 1 sites in a warp tile (Ls 12 takes the fallback of
+    variant 6)."""
     op, ref = make_pair(dims, Ls, 1.8, 0.02, 1.5, 0.5, "neff", 0.5, seed=81)
-    op.set_hop_config(prec, 6, 1, warps)
+    op.set_hop_config(prec, var, 1, sb)
     x = ref.to_eo(inputs.gaussian_5d(dims, Ls, 82), 0)
     for dag in (False, True):
         got = to_np(op.apply(to_gpu(x), op="eo", prec=prec, dag=dag))
@@ -289,9 +292,10 @@ def test_async_gather_hop(Ls, dims, prec, warps):
     op.device_status()
 
 
-def test_async_gather_hop_full_size():
-    """16^3x32, Ls 16: variant 6 against variant 0 (FP32) and variant 5 (FP16) on the
-    same input: the same operator to the precision's rounding."""
+@pytest.mark.parametrize("var", [6, 7, 8])
+def test_persistent_hop_variants_full_size(var):
+    """16^3x32, Ls 16: variants 6-8 against variant 0 (FP32) and variant 5 (FP16)
+    on the same input: the same operator to the precision's rounding."""
     dims, Ls = (16, 16, 16, 32), 16
     U = inputs.random_links(dims, 0.3, 1002)
     op, ref = make_pair(dims, Ls, 1.8, 0.01, 1.5, 0.5, "neff", 0.5, seed=84, U=U)
@@ -300,7 +304,7 @@ def test_async_gather_hop_full_size():
         for dag in (False, True):
             op.set_hop_config(prec, base, 1, 0)
             want = to_np(op.apply(x, op="eo", prec=prec, dag=dag))
-            op.set_hop_config(prec, 6, 1, 0)
+            op.set_hop_config(prec, var, 1, 0)
             got = to_np(op.apply(x, op="eo", prec=prec, dag=dag))
             assert rel(got, want) < tol, (prec, dag, rel(got, want))
     op.device_status()

@@ -240,3 +240,37 @@ def test_save_load_round_trip(tmp_path):
     open(path + ".bad", "wb").write(b"X" + data[1:])
     with pytest.raises(dwf.DwfError):
         op2.precond_load(path + ".bad")
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_fcg_cycle_matches_the_oracle_fcg(plain):
+    """The library's flexible-CG cycle (the inner solve of dwf_solve with
+    precond = 1, run alone by dwf_precond_fcg in FP32) against oracle.precond.fcg
+    in FP64 on the same normal equation D^dag D x = b with the same
+    preconditioner M = N N^dag (the oracle fed the kernels' BF16-rounded
+    weights), step by step: the residual histories agree to FP32 accuracy, and
+    so do the solutions.  plain: M = 1, the FCG of the oracle is then plain CG."""
+    from oracle import precond as pc
+    dims, Ls, L = (4, 4, 2, 4), 6, 2
+    op, ref = make_pair(dims, Ls, 1.8, 0.1, 1.5, 0.5, "neff", 0.5, seed=251)
+    op.precond_set_weights(random_weights(L, Ls, 252, scale=0.05))
+    W = op.precond_get_weights(L, compute_copy=True)
+    net = pc.Net(ref.U, dims, BC, W)
+    b = even_field(ref, 253)
+    x, hist = op.precond_fcg(to_gpu(b), tol=1e-5, max_iter=60, plain=plain)
+
+    def A(v):
+        return ref.d_pc(ref.d_pc(v), dag=True)
+    M = (lambda v: v) if plain else net.precondition
+    x_ref, info = pc.fcg(A, M, b, tol=1e-5, maxiter=60)
+    want = np.array(info["history"])
+    # the same recurrence: FP32 and FP64 agree step by step at first (finite
+    # precision then lets the two drift apart slowly), and both stop after about
+    # the same number of steps; the FP32 iterate's true residual (recomputed in
+    # FP64) stalls near the FP32 rounding times the condition number of D^dag D
+    # (about 1e-7 x 1e3 here), which the solver's FP64 defect corrections remove
+    assert np.all(np.abs(np.log(hist[:16] / want[:16])) < 1e-4), (hist[:16], want[:16])
+    assert abs(len(hist) - len(want)) <= 3
+    xg = to_np(x)
+    assert rel(A(xg), b) <= 1e-3
+    assert rel(xg, x_ref) < 1e-2
