@@ -141,7 +141,7 @@ def peaks():
         return None
 
 
-HOP_SOURCES = ("hop.cu", "hop_kernels.cuh", "stencil.cuh", "fields.cuh", "dwf_internal.h")
+HOP_SOURCES = ("hop.cu", "hop_kernels.cuh", "stencil.cuh", "fields.cuh")
 
 
 def hop_source_key():
@@ -281,14 +281,20 @@ def timed_solves(op, b4, n, **kw):
     return e0.elapsed_time(e1) / 1000.0 / n, s
 
 
+KERNEL_NAMES = {0: "hop_kernel", 3: "hop_sweep_kernel", 4: "hop_block_kernel", 5: "hop_kernel_occ (FP16 projection)",
+                7: "hop_lean_kernel", 9: "hop_wa_kernel (warp-autonomous)"}
+
+
 def hop_roofline(op, prec, Ls, peak, reps=30):
     """The hop kernel (the dominant kernel) timed alone with CUDA events, L2
     flushed between launches, against the measured HBM peak."""
     us, nbytes = op.time_hop(prec, reps=reps, flush_l2=True)
     achieved = nbytes / (us * 1e-6) / 1e9
+    var, ns, sb = op.hop_config(prec)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "us_per_launch": us, "algorithmic_bytes_per_launch": nbytes,
-            "kernel": "hop_kernel<%s> (even-odd hop + fused Ls mixing)" % prec}
+            "kernel": "%s<%s> variant %d (even-odd hop + fused Ls mixing)" % (KERNEL_NAMES.get(var, "hop"), prec, var),
+            "config": {"variant": var, "ns": ns, "sb": sb}}
 
 
 def main():

@@ -272,18 +272,28 @@ size_t dwf_device_bytes(dwf_handle h);
 long long dwf_launch_count(dwf_handle h);
 
 /* Configuration of the hop kernel in precision prec: variant 0 loads the
- * neighbour spinors directly from global memory, variant 3 is a persistent
- * kernel sweeping consecutive tiles, variant 4 takes each CTA's sites as a 4D
- * block of the half lattice (neighbour reuse in L1), variant 5 (DWF_F16 only,
- * dense mixing; else variant 0) is variant 0 with the spin projection in FP16
- * arithmetic on the stored FP16 values (one rounding at the FP16 storage
- * level) and the SU(3) product in FP32 shared by the thread's slices; ns
- * fifth-direction slices per thread (1, 2 when it divides Ls, 4 for variant
- * 5); sb four-dimensional sites per CTA.  -1 / 0 select the built-in
- * defaults.  Variants 0, 3 and 4 have no numerical effect beyond summation
- * order.  (Numbers 1 and 2 are not used.)
+ * neighbour spinors directly from global memory, one CTA per tile of sb sites;
+ * variant 3 is a persistent kernel sweeping consecutive tiles; variant 4 takes
+ * each CTA's sites as a 4D block of the half lattice (neighbour reuse in L1);
+ * variant 5 (DWF_F16 only, dense mixing; else variant 0) is variant 0 with the
+ * spin projection in FP16 arithmetic on the stored FP16 values (one rounding
+ * at the FP16 storage level) and the SU(3) product in FP32 shared by the
+ * thread's slices; variant 7 (FP32/FP16, dense mixing, Ls a multiple of 4) is
+ * a persistent kernel of sb-site tiles with the tile's links staged in shared
+ * memory one tile ahead and the mixing done by half of the threads, two
+ * outputs each; variant 9 (FP32/FP16, dense mixing, Ls dividing 32 and a
+ * multiple of 4) is persistent and warp-autonomous: every warp walks its own
+ * tiles of 32/Ls sites (a window sweeping the lattice in index order) with
+ * its own shared-memory links (staged one tile ahead) and mixing tile, and no
+ * CTA barrier; there sb counts warps per CTA (1..4) and ns selects the
+ * register budget (1: five CTAs of sb warps per SM, 2: four).  ns: slices per
+ * thread for the other variants (1, 2 when it divides Ls, 4 for variant 5);
+ * sb: sites per CTA.  -1 / 0 select the built-in defaults (FP32: variant 9
+ * where it applies, else 0; FP16: 5; FP64: 0).  Variants differ only in the
+ * order of the sums, except 5 (FP16 rounding of the projection).  Numbers 1,
+ * 2, 6 and 8 are not used.
  * Errors: DWF_EINVAL (NULL handle or pointer, bad prec, variant not -1, 0, 3,
- * 4 or 5, ns not 0, 1, 2 or (variant 5) 4 dividing Ls, sb making a CTA of more
+ * 4, 5, 7 or 9, ns or sb outside the ranges above, sb making a CTA of more
  * than 256 threads). */
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb);
 int dwf_get_hop_config(dwf_handle h, int prec, int *variant, int *ns, int *sb);
@@ -299,13 +309,16 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream);
 /* Fifth-direction mixing in precision prec: 0 applies the dense per-chirality
  * Ls x Ls matrices, 1 their structured form (diagonal, bidiagonal-plus-corner
  * and closed-form inverse factors, about 6 flops per element instead of
- * 2 Ls), 2 the dense matrices as one [Ls x Ls] x [Ls x 12 sites] product per
- * chirality and CTA on the tensor cores (TF32 MMAs with the matrix split in
- * two TF32 terms; FP32 fields also split the field, FP16 fields do not; FP32
- * and FP16 only).  Modes 1 and 2 are compiled for the direct hop variant,
+ * 2 Ls), 2 the dense matrices on the tensor cores (FP32 and FP16 only): the
+ * stand-alone mixing launches run as a batched GEMM of tcgen05 MMAs, the
+ * field of 16 sites as the A operand (rows = site, colour, re/im, spin;
+ * K = slice), both chiralities' matrices side by side as B, operands split in
+ * two TF32 terms each (FP32 accuracy), the accumulator in tensor memory;
+ * inside the hop the mixing of a CTA's tile runs as warp-level TF32 MMAs (the
+ * matrix split in two TF32 terms; FP32 fields also split the field, FP16
+ * fields do not).  Modes 1 and 2 are compiled for the direct hop variant,
  * which they then select (mode 2 needs CTAs of at least 32 threads, else the
- * dense form runs); the vector kernels outside the hop keep the dense form in
- * mode 2.  -1 restores the default (dense for DWF_F32 and DWF_F16, the
+ * dense form runs); the CG update keeps the dense form in mode 2.  -1 restores the default (dense for DWF_F32 and DWF_F16, the
  * structured form for DWF_F64 when it is available).  mode 1 is refused when
  * the handle's parameters make the structured form unavailable
  * (|kappa| = |beta0/alpha0| >= 0.95), mode 2 for prec = DWF_F64; both with
@@ -353,6 +366,17 @@ int dwf_device_status(dwf_handle h, void *stream);
  * DWF_ECUDA. */
 int dwf_time_hop(dwf_handle h, int prec, int reps, int flush_l2, double *us_per_launch,
                  double *bytes_per_launch, void *stream);
+
+/* Timing of one stand-alone fifth-direction mixing launch (out = M in with
+ * the even-odd factor M = B A5^-1 of Sec. 2.3, per chirality) on an even
+ * field in precision prec with mixing mode `mode` (dwf_set_mix_mode: 0 dense
+ * on the CUDA cores, 1 structured, 2 tensor cores: tcgen05 MMAs with the
+ * accumulator in tensor memory, FP32/FP16 only); as dwf_time_hop otherwise
+ * (*bytes: the field read once and written once).  The handle's own mixing
+ * mode is restored.  Errors: DWF_EINVAL (bad argument, mode unavailable),
+ * DWF_ECUDA. */
+int dwf_time_mix(dwf_handle h, int prec, int mode, int reps, int flush_l2, double *us, double *bytes,
+                 void *stream);
 
 /* Profiling aid: times the five launches of one inner CG iteration of
  * dwf_solve in precision prec (DWF_F16, DWF_F32, DWF_F64) on the handle's

@@ -479,6 +479,7 @@ size_t scale_bytes(int prec, int Vh, int Ls) { return prec == DWF_F16 ? (size_t)
 
 cudaError_t launch_mix(int prec, const MixArgs &a, cudaStream_t st)
 {
+    if (a.mixmode == 2 && prec != DWF_F64 && a.Ls <= 32) return launch_mix_tc(prec, a, st);
     switch (prec) {
     case DWF_F64: return launch_mix_t<DWF_F64>(a, st);
     case DWF_F32: return launch_mix_t<DWF_F32>(a, st);

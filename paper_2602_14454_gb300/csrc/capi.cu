@@ -176,6 +176,7 @@ cudaError_t mix(dwf_ctx *h, int prec, FieldRef in, FieldRef out, int id, cudaStr
     m.mixmode = h->mix_mode(prec);
     m.prog = h->prog(prec, id);
     m.band = h->fm.band[id];
+    m.err = h->errflag();
     h->launches += 1;
     return launch_mix(prec, m, st);
 }
@@ -577,17 +578,17 @@ long long dwf_launch_count(dwf_handle h) { return h ? h->launches : 0; }
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb)
 {
     if (!h || prec < 0 || prec > 2) return dwf_set_error(DWF_EINVAL, "bad handle or precision");
-    if (variant < -1 || variant > 8 || variant == 1 || variant == 2)
-        return dwf_set_error(DWF_EINVAL, "variant must be -1, 0, 3, 4, 5, 6, 7 or 8");
-    if (variant == 6) {   // sb counts warps per CTA
-        if (ns < 0 || ns > 1) return dwf_set_error(DWF_EINVAL, "variant 6 takes ns 0 or 1");
-        if (sb < 0 || sb > 8) return dwf_set_error(DWF_EINVAL, "variant 6 takes sb (warps per CTA) 0..8");
+    if (variant < -1 || variant > 9 || variant == 1 || variant == 2 || variant == 6 || variant == 8)
+        return dwf_set_error(DWF_EINVAL, "variant must be -1, 0, 3, 4, 5, 7 or 9");
+    if (variant == 9) {   // sb counts warps per CTA (1..4), ns the register budget (1, 2)
+        if (ns < 0 || ns > 2) return dwf_set_error(DWF_EINVAL, "variant 9 takes ns 0, 1 or 2");
+        if (sb < 0 || sb > 4) return dwf_set_error(DWF_EINVAL, "variant 9 takes sb (warps per CTA) 0..4");
         h->hop_var[prec] = variant;
         h->hop_ns[prec] = ns;
         h->hop_sb[prec] = sb;
         return DWF_OK;
     }
-    if ((variant == 7 || variant == 8) && ns > 1) return dwf_set_error(DWF_EINVAL, "variants 7 and 8 take ns 0 or 1");
+    if (variant == 7 && ns > 1) return dwf_set_error(DWF_EINVAL, "variant 7 takes ns 0 or 1");
     if (ns < 0 || ns > 4 || ns == 3 || (ns && h->Ls % ns) || (ns == 4 && variant != 5))
         return dwf_set_error(DWF_EINVAL, "ns must be 0, 1, 2 or (variant 5) 4, and divide Ls");
     const int nsv = ns ? ns : hop_default_ns(prec, h->Ls);
@@ -660,20 +661,22 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
     double best = 1e30;
     int bvar = -1, bns = 0, bsb = 0, bmix = 0;
     for (int mix = 0; mix <= 2; ++mix)
-        for (int var = 0; var <= 8; ++var)
+        for (int var = 0; var <= 9; ++var)
             for (int ns = 1; ns <= 4; ns *= 2) {
                 if (mix == 1 && !h->fm.structured) continue;
                 if (mix == 2 && prec == DWF_F64) continue;
-                if (var == 1 || var == 2) continue;   // numbers of removed variants
+                if (var == 1 || var == 2 || var == 6 || var == 8) continue;   // numbers not in use
                 if (mix != 0 && var != 0) continue;   // those mixings exist in the direct variant only
                 if (var == 5 && prec != DWF_F16) continue;
-                if (var == 6 && (prec == DWF_F64 || ns != 1 || 32 % h->Ls != 0)) continue;
-                if (var >= 7 && (prec == DWF_F64 || ns != 1 || h->Ls % 4 != 0)) continue;
+                if ((var == 7 || var == 9) && (prec == DWF_F64 || h->Ls % 4 != 0)) continue;
+                if (var == 7 && ns != 1) continue;
+                if (var == 9 && (32 % h->Ls != 0 || ns > 2)) continue;
                 if (ns == 4 && var != 5) continue;
-                if (h->Ls % ns) continue;
-                const int LsN = h->Ls / ns;
+                if (var != 9 && h->Ls % ns) continue;
+                const int LsN = h->Ls / (var == 9 ? 1 : ns);
                 for (int threads = 64; threads <= 256; threads += 64) {
-                    const int sb = var == 6 ? threads / 32 : threads / LsN;   // variant 6: warps per CTA
+                    if (var == 9 && threads > 128) continue;
+                    const int sb = var == 9 ? threads / 32 : threads / LsN;   // variant 9: warps per CTA
                     if (sb < 1 || LsN * sb > 256) continue;
                     h->mixmode[prec] = mix;
                     h->hop_var[prec] = var;
@@ -702,6 +705,51 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
             std::fclose(f);
         }
     }
+    return DWF_OK;
+}
+
+int dwf_time_mix(dwf_handle h, int prec, int mode, int reps, int flush_l2, double *us, double *bytes, void *stream)
+{
+    if (!h || reps < 1 || !us || !bytes) return dwf_set_error(DWF_EINVAL, "bad argument");
+    if (prec != DWF_F64 && prec != DWF_F32 && prec != DWF_F16) return dwf_set_error(DWF_EINVAL, "bad precision");
+    if (mode < 0 || mode > 2 || (mode == 2 && prec == DWF_F64) || (mode == 1 && !h->fm.structured))
+        return dwf_set_error(DWF_EINVAL, "mode must be 0, 1 (if available) or 2 (FP32/FP16)");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    FieldRef in = h->field("th_in", prec, &e), out = h->field("th_out", prec, &e);
+    if (!in.v || !out.v) return dwf_cuda_error(e, "workspace");
+    CK(cudaMemsetAsync(in.v, 0x3c, field_bytes(prec, h->Vh, h->Ls), st));
+    if (in.scale) CK(cudaMemsetAsync(in.scale, 0x3f, scale_bytes(prec, h->Vh, h->Ls), st));
+    const size_t flush_bytes = (size_t)512 << 20;
+    void *flush = nullptr;
+    if (flush_l2) {
+        flush = h->ws("th_flush", flush_bytes, &e);
+        if (!flush) return dwf_cuda_error(e, "workspace");
+    }
+    const int saved = h->mixmode[prec];
+    h->mixmode[prec] = mode;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double total_ms = 0;
+    for (int r = -2; r < reps && e == cudaSuccess; ++r) {
+        if (flush_l2) e = cudaMemsetAsync(flush, r & 0xff, flush_bytes, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = mix(h, prec, in, out, MAT_M, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess && r >= 0) {
+            cudaEventElapsedTime(&ms, e0, e1);
+            total_ms += ms;
+        }
+    }
+    h->mixmode[prec] = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return dwf_cuda_error(e, "dwf_time_mix");
+    *us = 1000.0 * total_ms / reps;
+    *bytes = 2.0 * (double)(field_bytes(prec, h->Vh, h->Ls) + scale_bytes(prec, h->Vh, h->Ls));
     return DWF_OK;
 }
 

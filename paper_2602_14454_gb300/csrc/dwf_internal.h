@@ -124,6 +124,7 @@ struct MixArgs {
     int mixmode = 0;
     const void *prog = nullptr;
     int band = 0;
+    int *err = nullptr;            // bit 0 set when a bounded device wait gave up (tensor-core form)
 };
 
 // p = r + beta p ; phat = P p   (or with init: p = r)
@@ -169,6 +170,8 @@ int hop_default_variant(int prec);
 int hop_default_ns(int prec, int Ls);
 int hop_default_sb(int prec, int Ls, int ns);
 cudaError_t launch_mix(int prec, const MixArgs &a, cudaStream_t st);
+// the same on the tensor cores (tcgen05, TMEM; FP32 and FP16 fields, Ls <= 32)
+cudaError_t launch_mix_tc(int prec, const MixArgs &a, cudaStream_t st);
 cudaError_t launch_cg_update(int prec, const CgUpdateArgs &a, cudaStream_t st);
 // Batched launches over nsys systems with equal Ls (tables in device memory;
 // a0: host copy of one entry, for Ls, Vh and the mixing mode): the direct hop

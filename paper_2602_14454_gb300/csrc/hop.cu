@@ -10,11 +10,13 @@ cudaError_t hop_launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_
 template <int P, bool DAG>
 cudaError_t hop_batch_launch_pd(const HopArgs *tab, int nsys, const HopArgs &a0, int NS, int SB, cudaStream_t st);
 
-// Defaults from the sweeps on 16^3x32, Ls 16 (GB300), chosen by the time to
-// solution: FP16 variant 5 (0.206 s vs 0.210 s for variant 0), FP32 and FP64
-// variant 0; one slice per thread (with the register caps above, the FP32 hop
-// takes 106.3 us against 122.8 us with two slices).
-int hop_default_variant(int prec) { return prec == DWF_F16 ? 5 : 0; }
+// Defaults from the sweeps on GB300 at 16^3x32 and 32^3x64, Ls 16: FP32 the
+// warp-autonomous variant 9 (83.7 / 1446 us per hop against 102.4 / 1519 us for
+// the direct variant 0; the whole FP32 CG iteration 475 / 7897 us against
+// 586 / 8755 us), FP16 variant 5 (84.7 / 1183 us; variant 9: 87.8 / 1372 us),
+// FP64 variant 0.  Variant 9 needs dense mixing and Ls dividing 32 (and a
+// multiple of 4); otherwise the FP32 default is variant 0.
+int hop_default_variant(int prec) { return prec == DWF_F16 ? 5 : (prec == DWF_F32 ? 9 : 0); }
 
 int hop_default_ns(int prec, int Ls)
 {
@@ -56,26 +58,24 @@ cudaError_t launch_hop_batch(int prec, bool dag, const HopArgs *tab, int nsys, c
 
 cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
 {
-    if (var < 0 || var > 8 || var == 1 || var == 2) var = hop_default_variant(prec);
-    if ((var == 7 || var == 8) && (prec == DWF_F64 || a.mixmode != 0 || a.Ls % 4 != 0)) {
-        var = prec == DWF_F16 ? 5 : 0;   // variant 7 needs FP32/FP16 fields, dense mixing, Ls a multiple of 4
+    if (var < 0 || var > 9 || var == 1 || var == 2 || var == 6 || var == 8) var = hop_default_variant(prec);
+    // variants 7 and 9 need FP32/FP16 fields and dense mixing (9 also Ls dividing 32), else the default
+    const bool v_ok = prec != DWF_F64 && a.mixmode == 0 && a.Ls % 4 == 0;
+    if ((var == 7 && !v_ok) || (var == 9 && !(v_ok && a.Ls <= 32 && 32 % a.Ls == 0))) {
+        var = prec == DWF_F16 ? 5 : 0;
         SB = 0;
+        NS = 0;
     }
-    if (NS <= 0 || NS > 4 || NS == 3 || (a.Ls % NS) != 0 || (NS == 4 && var != 5)) NS = hop_default_ns(prec, a.Ls);
-    if (var == 6 && (prec == DWF_F64 || a.mixmode != 0 || a.Ls > 32 || 32 % a.Ls != 0)) {
-        var = prec == DWF_F16 ? 5 : 0;   // variant 6 needs FP32/FP16 fields, dense mixing, Ls dividing 32
-        SB = 0;
+    if (var == 9) {   // SB = warps per CTA, NS = register budget (1: five CTAs per SM, 2: four)
+        if (SB <= 0 || SB > 4) SB = 4;
+        if (NS != 1) NS = 2;
+        return prec == DWF_F32 ? (dag ? hop_launch_pd<DWF_F32, true>(a, 9, NS, SB, st)
+                                      : hop_launch_pd<DWF_F32, false>(a, 9, NS, SB, st))
+                               : (dag ? hop_launch_pd<DWF_F16, true>(a, 9, NS, SB, st)
+                                      : hop_launch_pd<DWF_F16, false>(a, 9, NS, SB, st));
+    }
+    if (NS <= 0 || NS > 4 || NS == 3 || (a.Ls % NS) != 0 || (NS == 4 && var != 5) || var == 7)
         NS = hop_default_ns(prec, a.Ls);
-    }
-    if (var == 6) {   // one slice per thread; SB = warps per CTA (0: default)
-        NS = 1;
-        if (SB <= 0 || SB > 8) SB = 4;
-        switch (prec) {
-        case DWF_F32: return dag ? hop_launch_pd<DWF_F32, true>(a, 6, 1, SB, st) : hop_launch_pd<DWF_F32, false>(a, 6, 1, SB, st);
-        case DWF_F16: return dag ? hop_launch_pd<DWF_F16, true>(a, 6, 1, SB, st) : hop_launch_pd<DWF_F16, false>(a, 6, 1, SB, st);
-        default: var = 0; SB = 0; break;
-        }
-    }
     if (SB <= 0) SB = hop_default_sb(prec, a.Ls, NS);
     if ((a.Ls / NS) * SB > 256) SB = 256 / (a.Ls / NS);
     if (SB < 1) SB = 1;

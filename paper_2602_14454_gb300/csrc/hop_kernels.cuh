@@ -596,32 +596,11 @@ __global__ void __launch_bounds__(256) hop_sweep_kernel(const HopArgs a, int tpc
     if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
 }
 
-// ------------------------------------------- variant 6: asynchronous gathers
-// One warp works on 32 / Ls consecutive sites at a time (a warp tile; all Ls
-// slices of a site in one warp, Ls dividing 32), persistent over the tiles of
-// its CTA's contiguous range.  Each thread streams the neighbour spinors it
-// needs, direction after direction and tile after tile, into its own slots of
-// a ring of ASYNC_STAGES shared-memory stages with per-thread asynchronous
-// copies (cp.async, one commit group per direction): ASYNC_STAGES - 1
-// directions are in flight while one is computed, without registers and
-// without a barrier (a thread reads only the slots it filled itself).  The
-// links of the warp's sites (576 bytes per site, all 8 directions) are copied
-// once per tile, one tile ahead, by all lanes together, and every lane reads
-// its site's link from shared memory: each link serves the Ls slices of its
-// site.  The fifth-direction mixing and the epilogue work on a warp-local
-// tile (warp barriers only).  FP32 fields read 6 x 16 bytes per neighbour and
-// direction; FP16 fields 3 x 16 bytes plus the 4-byte scale, projected in
-// FP16 arithmetic as variant 5.
-constexpr int ASYNC_STAGES = 3;
-
+// 16-byte asynchronous copies global -> shared (per-thread commit groups)
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -630,247 +609,7 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-struct WarpBarrier {
-    __device__ __forceinline__ void sync() const { __syncwarp(); }
-};
-
-template <int P>
-struct AsyncGeom {
-    static constexpr int G = Tr<P>::G;                   // 16-byte vectors per (site, s)
-    static constexpr int LINK_BYTES = 8 * 18 * (P == DWF_F16 ? 2 : 4);   // one site's 8 links
-};
-
-// shared-memory bytes of one warp's private part
-template <int P>
-__host__ __device__ constexpr size_t async_warp_bytes(int Ls)
-{
-    return (size_t)ASYNC_STAGES * AsyncGeom<P>::G * 32 * 16                  // neighbour ring
-           + (P == DWF_F16 ? (size_t)ASYNC_STAGES * 32 * 4 : 0)             // FP16 scales
-           + (size_t)2 * (32 / Ls) * AsyncGeom<P>::LINK_BYTES                // links, double buffered
-           + (size_t)(32 / Ls) * (Ls * 12 + 2) * sizeof(float2);            // mixing tile
-}
-
-template <int P>
-__host__ __device__ constexpr size_t async_cta_bytes(int Ls, int nwarps)
-{
-    return (size_t)3 * 2 * Ls * Ls * sizeof(float) + (size_t)nwarps * async_warp_bytes<P>(Ls);
-}
-
-// this thread's share of the copies of one direction: its neighbour's slice
-template <int P>
-__device__ __forceinline__ void async_issue_nb(const FieldRef &in, int nb, int x, int Ls, uint32_t ring16,
-                                               uint32_t sc4, int lane, int stage)
-{
-    constexpr int G = AsyncGeom<P>::G;
-    const uint4 *src = reinterpret_cast<const uint4 *>(in.v) + ((size_t)nb * G) * Ls + x;
-#pragma unroll
-    for (int g = 0; g < G; ++g) cp_async16(ring16 + (uint32_t)(((stage * G + g) * 32 + lane) * 16), src + (size_t)g * Ls);
-    if constexpr (P == DWF_F16)
-        cp_async4(sc4 + (uint32_t)((stage * 32 + lane) * 4), in.scale + (size_t)nb * ((Ls + 3) & ~3) + x);
-}
-
-// the lanes' share of the copies of the warp's links (tile sites site0 ..)
-template <int P>
-__device__ __forceinline__ void async_issue_links(const void *gauge, int site0, int nsites, uint32_t dst, int lane)
-{
-    constexpr int CH = AsyncGeom<P>::LINK_BYTES / 16;   // 16-byte chunks per site
-    const uint4 *src = reinterpret_cast<const uint4 *>(gauge) + (size_t)site0 * CH;
-    for (int c = lane; c < nsites * CH; c += 32) cp_async16(dst + (uint32_t)c * 16, src + c);
-}
-
-template <int P, bool DAG, int D>
-__device__ __forceinline__ void async_hop_dir(typename Tr<P>::pair *acc, const unsigned char *ring, const float *scl,
-                                              const unsigned char *lk, int lane, int stage)
-{
-    constexpr int MU = D & 3;
-    constexpr int SIG = (D < 4 ? 1 : -1) * (DAG ? -1 : 1);
-    constexpr int G = AsyncGeom<P>::G;
-    const uint4 *r = reinterpret_cast<const uint4 *>(ring) + (size_t)stage * G * 32 + lane;
-    if constexpr (P == DWF_F32) {
-        float2 u[9], v[12];
-        const float2 *L = reinterpret_cast<const float2 *>(lk + D * 72);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) u[k] = L[k];
-#pragma unroll
-        for (int g = 0; g < 6; ++g) {
-            const float4 q = *reinterpret_cast<const float4 *>(r + g * 32);
-            v[2 * g] = make_float2(q.x, q.y);
-            v[2 * g + 1] = make_float2(q.z, q.w);
-        }
-        hop_one<MU, SIG>(acc, u, v);
-    } else {
-        float2 u[9];
-        const __half2 *L = reinterpret_cast<const __half2 *>(lk + D * 36);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) u[k] = __half22float2(L[k]);
-        __half2 v[12];
-#pragma unroll
-        for (int g = 0; g < 3; ++g) {
-            const uint4 q = r[g * 32];
-            v[4 * g] = *reinterpret_cast<const __half2 *>(&q.x);
-            v[4 * g + 1] = *reinterpret_cast<const __half2 *>(&q.y);
-            v[4 * g + 2] = *reinterpret_cast<const __half2 *>(&q.z);
-            v[4 * g + 3] = *reinterpret_cast<const __half2 *>(&q.w);
-        }
-        const float sc = scl[stage * 32 + lane];
-        __half2 hx[3], hy[3];
-        project_h2<MU, SIG>(v, hx, hy);
-        float2 Hx[3], Hy[3], Qx[3], Qy[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            Hx[a] = __half22float2(hx[a]);
-            Hy[a] = __half22float2(hy[a]);
-        }
-        su3_pairs(u, Hx, Hy, Qx, Qy);
-        const float2 scp = make_float2(sc, sc);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            Qx[a] = p_mul(Qx[a], scp);
-            Qy[a] = p_mul(Qy[a], scp);
-        }
-        reconstruct<MU, SIG>(acc, Qx, Qy);
-    }
-}
-
-// The state of one warp tile's pass over the 8 directions.
-template <int P>
-struct AsyncPass {
-    const HopArgs *a;
-    const unsigned char *ring;
-    const float *scl;
-    const unsigned char *lk;     // this lane's site's links in shared memory
-    uint32_t ring16, sc4, lk16;
-    int lane, x, Ls, base;       // base: ring stage of direction 0 of this tile
-    bool active, more;           // this lane's site exists; a next tile exists
-    int next_site0, next_nlink, next_buf;
-};
-
-// Direction D of the tile: issue the copies ASYNC_STAGES - 1 directions ahead
-// (an empty group past the last tile), wait for direction D's, compute it.
-template <int P, bool DAG, int D>
-__device__ __forceinline__ void async_step(const AsyncPass<P> &st, typename Tr<P>::pair *acc, const int *cur,
-                                           const int *nxt)
-{
-    constexpr int AHEAD = ASYNC_STAGES - 1;
-    constexpr int DI = (D + AHEAD) & 7;
-    constexpr bool NEXT = D + AHEAD >= 8;
-    int slot_i = st.base + (D + AHEAD) % ASYNC_STAGES;
-    slot_i -= slot_i >= ASYNC_STAGES ? ASYNC_STAGES : 0;
-    int slot = st.base + D % ASYNC_STAGES;
-    slot -= slot >= ASYNC_STAGES ? ASYNC_STAGES : 0;
-    const int nb = NEXT ? (st.more ? nxt[DI] : -1) : cur[DI];
-    if (nb >= 0) async_issue_nb<P>(st.a->in, nb, st.x, st.Ls, st.ring16, st.sc4, st.lane, slot_i);
-    if (NEXT && DI == 0 && st.more)
-        async_issue_links<P>(st.a->gauge, st.next_site0, st.next_nlink,
-                             st.lk16 + (uint32_t)(st.next_buf * AsyncGeom<P>::LINK_BYTES), st.lane);
-    cp_async_commit();
-    cp_async_wait<AHEAD>();            // the group of direction D is in
-    if (D == 0) __syncwarp();          // and every lane's link copies of this tile
-    if (st.active) async_hop_dir<P, DAG, D>(acc, st.ring, st.scl, st.lk, st.lane, slot);
-}
-
-// Grid: CTA b owns the warp tiles [b * tpc, (b + 1) * tpc) (a contiguous range
-// of sites, so that neighbour sites shared between tiles are L1 hits); warp w
-// of the CTA takes tiles b * tpc + w, + nwarps, ...
-template <int P, bool DAG, int MIX>
-__global__ void __launch_bounds__(256) hop_async_kernel(const HopArgs a, int tpc)
-{
-    typedef typename Tr<P>::pair T2;
-    typedef typename Tr<P>::real R;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Ls = a.Ls;
-    const int SPW = 32 / Ls;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int j = lane / Ls, x = lane - (lane / Ls) * Ls;
-    R *mtx = reinterpret_cast<R *>(smem_raw);
-    load_matrices<1>(a, mtx);
-    unsigned char *wbase = smem_raw + (size_t)3 * 2 * Ls * Ls * sizeof(float) + (size_t)warp * async_warp_bytes<P>(Ls);
-    unsigned char *ring = wbase;
-    float *scl = reinterpret_cast<float *>(ring + (size_t)ASYNC_STAGES * AsyncGeom<P>::G * 32 * 16);
-    unsigned char *links = reinterpret_cast<unsigned char *>(scl) + (P == DWF_F16 ? ASYNC_STAGES * 32 * 4 : 0);
-    T2 *tile = reinterpret_cast<T2 *>(links + 2 * SPW * AsyncGeom<P>::LINK_BYTES);
-    __syncthreads();   // the matrices
-
-    const int ntiles = (a.Vh + SPW - 1) / SPW;
-    const int t0 = blockIdx.x * tpc;
-    const int t1 = min(t0 + tpc, ntiles);
-    const int nmy = t0 + warp < t1 ? (t1 - (t0 + warp) + nwarps - 1) / nwarps : 0;
-
-    R nrm = 0;
-    if (nmy > 0) {
-        AsyncPass<P> st;
-        st.a = &a;
-        st.ring = ring;
-        st.scl = scl;
-        st.ring16 = smem_addr(ring);
-        st.sc4 = smem_addr(scl);
-        st.lk16 = smem_addr(links);
-        st.lane = lane;
-        st.x = x;
-        st.Ls = Ls;
-        int cur[8], nxt[8];
-        auto load_idx = [&](int jt, int *n8) {
-            const int site = (t0 + warp + jt * nwarps) * SPW + j;
-            if (jt < nmy && site < a.Vh) {
-                const int4 *p = reinterpret_cast<const int4 *>(a.nbr + (size_t)site * 8);
-                const int4 q0 = __ldg(p), q1 = __ldg(p + 1);
-                n8[0] = q0.x; n8[1] = q0.y; n8[2] = q0.z; n8[3] = q0.w;
-                n8[4] = q1.x; n8[5] = q1.y; n8[6] = q1.z; n8[7] = q1.w;
-            } else {
-#pragma unroll
-                for (int d = 0; d < 8; ++d) n8[d] = -1;
-            }
-        };
-        load_idx(0, cur);
-        load_idx(1, nxt);
-        // prologue: the links of tile 0 and the first ASYNC_STAGES - 1 directions
-        {
-            const int s0 = (t0 + warp) * SPW;
-            async_issue_links<P>(a.gauge, s0, min(SPW, a.Vh - s0), st.lk16, lane);
-        }
-#pragma unroll
-        for (int q = 0; q < ASYNC_STAGES - 1; ++q) {
-            if (cur[q] >= 0) async_issue_nb<P>(a.in, cur[q], x, Ls, st.ring16, st.sc4, lane, q);
-            cp_async_commit();
-        }
-        for (int jt = 0; jt < nmy; ++jt) {
-            const int site = (t0 + warp + jt * nwarps) * SPW + j;
-            st.active = site < a.Vh;
-            st.more = jt + 1 < nmy;
-            st.next_site0 = (t0 + warp + (jt + 1) * nwarps) * SPW;
-            st.next_nlink = st.more ? min(SPW, a.Vh - st.next_site0) : 0;
-            st.next_buf = ((jt + 1) & 1) * SPW;
-            st.base = (jt * 8) % ASYNC_STAGES;
-            st.lk = links + ((jt & 1) * SPW + j) * AsyncGeom<P>::LINK_BYTES;
-            T2 acc[1][12];
-#pragma unroll
-            for (int k = 0; k < 12; ++k) acc[0][k] = p_splat((R)0);
-            async_step<P, DAG, 0>(st, acc[0], cur, nxt);
-            async_step<P, DAG, 1>(st, acc[0], cur, nxt);
-            async_step<P, DAG, 2>(st, acc[0], cur, nxt);
-            async_step<P, DAG, 3>(st, acc[0], cur, nxt);
-            async_step<P, DAG, 4>(st, acc[0], cur, nxt);
-            async_step<P, DAG, 5>(st, acc[0], cur, nxt);
-            async_step<P, DAG, 6>(st, acc[0], cur, nxt);
-            async_step<P, DAG, 7>(st, acc[0], cur, nxt);
-            TileCtx<T2> tc;
-            tc.tile0 = tile;
-            tc.tstride = Ls * 12 + 2;
-            tc.nsites = SPW;
-            tc.tid = lane;
-            tc.nthr = 32;
-            nrm += hop_epilogue_core<P, 1, MIX>(a, acc, tc, tile + j * tc.tstride, mtx, site, x, Ls, st.active,
-                                                WarpBarrier());
-#pragma unroll
-            for (int d = 0; d < 8; ++d) cur[d] = nxt[d];
-            load_idx(jt + 2, nxt);
-        }
-        cp_async_wait<0>();
-    }
-    if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
-}
-
-// ---------------------------------------- variants 7, 8: lean on the L1 path
+// --------------------------------------------- variant 7: lean on the L1 path
 // The direct kernel, rebuilt around the L1/shared-memory data path, which
 // bounds the FP32 hop (every byte a thread loads from L1 or shared memory
 // crosses it; ncu: L1/TEX 79 % busy at 28 % of DRAM bandwidth):
@@ -888,8 +627,8 @@ __global__ void __launch_bounds__(256) hop_async_kernel(const HopArgs a, int tpc
 //  * the tile rows (28 floats), the site stride (one extra 16 bytes) and the
 //    matrix rows are padded so that the 16-byte shared accesses of a warp hit
 //    distinct banks.
-// Dense mixing, Ls even and a multiple of 4.  Variant 7: two CTAs per SM
-// worth of registers, variant 8: three.
+// Dense mixing, Ls a multiple of 4; two CTAs of 256 threads per SM worth of
+// registers.
 constexpr int LEAN_ROW = 14;   // float2 per tile row (24 floats used)
 
 template <int P>
@@ -1237,6 +976,230 @@ __global__ void __launch_bounds__(256, MINB) hop_lean_kernel(const HopArgs a)
     if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
 }
 
+// ------------------------------------------ variant 9: warp-autonomous hop
+// Every warp works alone on its own tiles of 32 / Ls sites (Ls dividing 32),
+// persistent over its CTA's contiguous range of tiles, with no CTA barrier
+// after the matrices are loaded: the warp's links (its sites' 8 directions)
+// are copied into its own shared-memory buffer with 16-byte asynchronous
+// copies one tile ahead (warp barrier only) and read as 16-byte vectors; the
+// neighbour spinors are direct 16-byte loads; the mixing tile is the warp's
+// own (rows of 28 floats, sites 16 bytes apart beyond that, so 16-byte
+// accesses hit distinct banks) and the matrix rows are padded the same way,
+// so a thread reads four coefficients of its row at once.  Dense mixing
+// (cyclic tridiagonal matrices read three rows).
+template <int P>
+__host__ __device__ constexpr size_t wa_warp_bytes(int Ls)
+{
+    return (size_t)2 * (32 / Ls) * LeanGeom<P>::LINK_BYTES + (size_t)(32 / Ls) * lean_site_stride(Ls) * sizeof(float2);
+}
+__host__ __device__ constexpr int wa_mat_row(int Ls) { return ((Ls / 4) & 1) ? Ls : Ls + 4; }
+template <int P>
+__host__ __device__ constexpr size_t wa_cta_bytes(int Ls, int nwarps)
+{
+    return (size_t)3 * 2 * Ls * wa_mat_row(Ls) * sizeof(float) + (size_t)nwarps * wa_warp_bytes<P>(Ls);
+}
+
+// o += sum_t M[chi][s][t] tile(t) over the rows of one site; M row-major with
+// rows of wa_mat_row(Ls) floats
+__device__ __forceinline__ void wa_mix(const float *M, const float2 *site_tile, int s, int Ls, bool band, float2 *o)
+{
+    const int MR = wa_mat_row(Ls);
+    const float *mu = M + (size_t)s * MR, *ml = M + (size_t)(Ls + s) * MR;
+    const float4 *base = reinterpret_cast<const float4 *>(site_tile);
+    if (band) {
+#pragma unroll
+        for (int dt = -1; dt <= 1; ++dt) {
+            int t = s + dt;
+            t = t < 0 ? t + Ls : (t >= Ls ? t - Ls : t);
+            const float2 cu = p_splat(mu[t]), cl = p_splat(ml[t]);
+            const float4 *row = base + (size_t)t * (LEAN_ROW / 2);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const float4 v = row[q];
+                o[2 * q] = p_fma(cu, make_float2(v.x, v.y), o[2 * q]);
+                o[2 * q + 1] = p_fma(cl, make_float2(v.z, v.w), o[2 * q + 1]);
+            }
+        }
+        return;
+    }
+#pragma unroll 1
+    for (int t0 = 0; t0 < Ls; t0 += 4) {
+        const float4 a4 = *reinterpret_cast<const float4 *>(mu + t0);
+        const float4 b4 = *reinterpret_cast<const float4 *>(ml + t0);
+        const float ca[4] = {a4.x, a4.y, a4.z, a4.w}, cb[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 cu = p_splat(ca[k]), cl = p_splat(cb[k]);
+            const float4 *row = base + (size_t)(t0 + k) * (LEAN_ROW / 2);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const float4 v = row[q];
+                o[2 * q] = p_fma(cu, make_float2(v.x, v.y), o[2 * q]);
+                o[2 * q + 1] = p_fma(cl, make_float2(v.z, v.w), o[2 * q + 1]);
+            }
+        }
+    }
+}
+
+// the epilogue of hop_epilogue_core (dense mixing) on the warp's tile
+template <int P>
+__device__ __forceinline__ float wa_epilogue(const HopArgs &a, const float2 *acc, float2 *site_tile,
+                                             const float *mats, int s, int site, bool active)
+{
+    const int Ls = a.Ls;
+    const int msz = 2 * Ls * wa_mat_row(Ls);
+    float2 *row = site_tile + (size_t)s * LEAN_ROW;
+    if (active && a.rin.v && a.xacc) {   // independent of the hop: first, while few registers are live
+        FieldRef xf;
+        xf.v = a.xacc;
+        const float2 xa = p_splat((float)(*a.xalpha));
+        float2 xv[12], dx[12];
+        ld_pairs<DWF_F32, false>(xf, (size_t)site, s, Ls, xv);
+        ld_pairs<P, false>(a.xdir, (size_t)site, s, Ls, dx);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) xv[k] = p_fma(xa, dx[k], xv[k]);
+        st_pairs<DWF_F32>(xf, (size_t)site, s, Ls, xv);
+    }
+    if (active) lean_put(row, acc);
+    __syncwarp();
+    float2 o[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = make_float2(0.f, 0.f);
+    if (active) wa_mix(mats, site_tile, s, Ls, a.post_band != 0, o);
+    if (a.ymode == 1) {
+        if (active) {
+            float2 y[12];
+            ld_pairs<P, false>(a.y, (size_t)site, s, Ls, y);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) o[k] = p_add(o[k], y[k]);
+        }
+    } else if (a.ymode == 2) {
+        __syncwarp();
+        if (active) {
+            float2 y[12];
+            ld_pairs<P, false>(a.y, (size_t)site, s, Ls, y);
+            lean_put(row, y);
+        }
+        __syncwarp();
+        if (active) wa_mix(mats + msz, site_tile, s, Ls, a.y_band != 0, o);
+    }
+    if (active && a.rin.v) {
+        const float2 nal = p_splat((float)-(*a.ralpha));
+        float2 r[12];
+        ld_pairs<P, false>(a.rin, (size_t)site, s, Ls, r);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o[k] = p_fma(nal, o[k], r[k]);
+    }
+    float nrm = 0.f;
+    if (active && a.red.op != RED_NONE) {
+        float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s2 = p_fma(o[k], o[k], s2);
+        nrm = s2.x + s2.y;
+    }
+    if (a.zmat) {
+        __syncwarp();
+        if (active) lean_put(row, o);
+        __syncwarp();
+        float2 z[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) z[k] = make_float2(0.f, 0.f);
+        if (active) {
+            wa_mix(mats + 2 * msz, site_tile, s, Ls, a.z_band != 0, z);
+            st_pairs<P>(a.out, (size_t)site, s, Ls, z);
+        }
+    } else if (active) {
+        st_pairs<P>(a.out, (size_t)site, s, Ls, o);
+    }
+    return nrm;
+}
+
+// the lanes' share of the link copies of a warp tile (sites site0 .. site0 + n - 1)
+template <int P>
+__device__ __forceinline__ void wa_issue_links(const void *gauge, int site0, int n, unsigned char *dst, int lane)
+{
+    constexpr int CH = LeanGeom<P>::LINK_BYTES / 16;
+    const uint4 *src = reinterpret_cast<const uint4 *>(gauge) + (size_t)site0 * CH;
+    const uint32_t d = smem_addr(dst);
+    for (int c = lane; c < n * CH; c += 32) cp_async16(d + (uint32_t)c * 16, src + c);
+    cp_async_commit();
+}
+
+// Grid: warp w of CTA b (global warp g = b nwarps + w) takes the warp tiles
+// g, g + G, g + 2G, ... (G = all warps of the grid), so that the tiles in work
+// at any moment form one window sweeping the lattice in index order: the
+// neighbour sites a tile shares with tiles one x-row or one t-slice away are
+// still in L2 when those are processed (which a contiguous range per CTA,
+// spreading the tiles in work over the whole lattice, loses once the fields
+// exceed L2).
+template <int P, bool DAG, int MINB>
+__global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ls = a.Ls, SPW = 32 / Ls;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int j = lane / Ls, s = lane - (lane / Ls) * Ls;
+    const int MR = wa_mat_row(Ls), msz = 2 * Ls * MR;
+    float *mats = reinterpret_cast<float *>(smem_raw);
+    {
+        const float *src[3] = {reinterpret_cast<const float *>(a.post),
+                               a.ymode == 2 ? reinterpret_cast<const float *>(a.ymat) : nullptr,
+                               reinterpret_cast<const float *>(a.zmat)};
+        for (int m = 0; m < 3; ++m) {
+            if (!src[m]) continue;
+            for (int k = threadIdx.x; k < 2 * Ls * Ls; k += blockDim.x) {
+                const int chi = k / (Ls * Ls), r = k - chi * Ls * Ls, t = r / Ls, ss = r - t * Ls;
+                mats[m * msz + (chi * Ls + ss) * MR + t] = src[m][k];
+            }
+        }
+    }
+    unsigned char *wbase = smem_raw + (size_t)3 * msz * sizeof(float) + (size_t)warp * wa_warp_bytes<P>(Ls);
+    unsigned char *links = wbase;
+    float2 *tile = reinterpret_cast<float2 *>(wbase + (size_t)2 * SPW * LeanGeom<P>::LINK_BYTES);
+    float2 *site_tile = tile + (size_t)j * lean_site_stride(Ls);
+    __syncthreads();   // the matrices (the only CTA barrier before the final reduction)
+
+    const int ntiles = (a.Vh + SPW - 1) / SPW;
+    const int G = gridDim.x * nwarps;
+    float nrm = 0.f;
+    int u = blockIdx.x * nwarps + warp;
+    if (u < ntiles) wa_issue_links<P>(a.gauge, u * SPW, min(SPW, a.Vh - u * SPW), links, lane);
+    for (int k = 0; u < ntiles; ++k, u += G) {
+        const int site = u * SPW + j;
+        const bool active = site < a.Vh;
+        int n8[8];
+        if (active) {
+            const int4 *p = reinterpret_cast<const int4 *>(a.nbr + (size_t)site * 8);
+            const int4 q0 = __ldg(p), q1 = __ldg(p + 1);
+            n8[0] = q0.x; n8[1] = q0.y; n8[2] = q0.z; n8[3] = q0.w;
+            n8[4] = q1.x; n8[5] = q1.y; n8[6] = q1.z; n8[7] = q1.w;
+        }
+        cp_async_wait<0>();
+        __syncwarp();   // this tile's links are in; every lane is done with the previous tile
+        const int un = u + G;
+        if (un < ntiles)   // the next tile's links, into the other buffer
+            wa_issue_links<P>(a.gauge, un * SPW, min(SPW, a.Vh - un * SPW),
+                              links + (size_t)((k + 1) & 1) * SPW * LeanGeom<P>::LINK_BYTES, lane);
+        float2 acc[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) acc[q] = make_float2(0.f, 0.f);
+        if (active) {
+            const unsigned char *lk = links + ((size_t)(k & 1) * SPW + j) * LeanGeom<P>::LINK_BYTES;
+            lean_dir<P, DAG, 0>(acc, a.in, n8[0], s, Ls, lk);
+            lean_dir<P, DAG, 1>(acc, a.in, n8[1], s, Ls, lk);
+            lean_dir<P, DAG, 2>(acc, a.in, n8[2], s, Ls, lk);
+            lean_dir<P, DAG, 3>(acc, a.in, n8[3], s, Ls, lk);
+            lean_dir<P, DAG, 4>(acc, a.in, n8[4], s, Ls, lk);
+            lean_dir<P, DAG, 5>(acc, a.in, n8[5], s, Ls, lk);
+            lean_dir<P, DAG, 6>(acc, a.in, n8[6], s, Ls, lk);
+            lean_dir<P, DAG, 7>(acc, a.in, n8[7], s, Ls, lk);
+        }
+        nrm += wa_epilogue<P>(a, acc, site_tile, mats, s, site, active);
+    }
+    cp_async_wait<0>();
+    if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
+}
+
 // ---------------------------------------------------------------- launch
 template <int P>
 size_t direct_smem(int Ls, int SB)
@@ -1377,35 +1340,6 @@ cudaError_t launch_sweep(const HopArgs &a, int SB, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// Variant 6: persistent CTAs of `nw` warps, as many per SM as fit.
-template <int P, bool DAG>
-cudaError_t launch_async(const HopArgs &a, int nw, cudaStream_t st)
-{
-    static unsigned long long optin = 0;
-    int dev = 0, nsm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if ((e = smem_optin(hop_async_kernel<P, DAG, 0>, 200 * 1024, optin)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if (nw < 1) nw = 4;
-    if (nw > 8) nw = 8;
-    size_t smem = async_cta_bytes<P>(a.Ls, nw);
-    while (nw > 1 && smem > 200 * 1024) smem = async_cta_bytes<P>(a.Ls, --nw);
-    if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_async_kernel<P, DAG, 0>, 32 * nw, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    const int SPW = 32 / a.Ls;
-    const int ntiles = (a.Vh + SPW - 1) / SPW;
-    int grid = nsm * per_sm;
-    int tpc = (ntiles + grid - 1) / grid;
-    if (tpc < nw) tpc = nw;
-    grid = (ntiles + tpc - 1) / tpc;
-    hop_async_kernel<P, DAG, 0><<<grid, 32 * nw, smem, st>>>(a, tpc);
-    return cudaGetLastError();
-}
-
 // Variant 7: persistent CTAs of SB sites, as many per SM as fit.
 template <int P, bool DAG, int MINB>
 cudaError_t launch_lean(const HopArgs &a, int SB, cudaStream_t st)
@@ -1431,21 +1365,49 @@ cudaError_t launch_lean(const HopArgs &a, int SB, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Variant 9: persistent CTAs of `nw` warps (2, 4 or 8 resident CTAs' worth of
+// registers: nw x MINB x 32 threads per SM), as many per SM as fit.
+template <int P, bool DAG, int MINB>
+cudaError_t launch_wa(const HopArgs &a, int nw, cudaStream_t st)
+{
+    static unsigned long long optin = 0;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = smem_optin(hop_wa_kernel<P, DAG, MINB>, 200 * 1024, optin)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (nw < 1) nw = 4;
+    if (nw > 4) nw = 4;
+    const size_t smem = wa_cta_bytes<P>(a.Ls, nw);
+    if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_wa_kernel<P, DAG, MINB>, 32 * nw, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int SPW = 32 / a.Ls;
+    const int ntiles = (a.Vh + SPW - 1) / SPW;
+    int grid = nsm * per_sm;
+    if (grid > (ntiles + nw - 1) / nw) grid = (ntiles + nw - 1) / nw;
+    hop_wa_kernel<P, DAG, MINB><<<grid, 32 * nw, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int P, bool DAG>
 cudaError_t launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
 {
+    // variant 9: warp-autonomous (FP32 and FP16 fields, dense mixing, Ls dividing 32 and a
+    // multiple of 4); SB = warps per CTA, NS selects the register budget (1: 5 CTAs of 4
+    // warps per SM, 2: 4)
+    if constexpr (P != DWF_F64) {
+        if (var == 9 && a.mixmode == 0 && a.Ls <= 32 && 32 % a.Ls == 0 && a.Ls % 4 == 0)
+            return NS == 2 ? launch_wa<P, DAG, 4>(a, SB, st) : launch_wa<P, DAG, 5>(a, SB, st);
+    }
+    if (var == 9) var = P == DWF_F16 ? 5 : 0;
     if constexpr (P != DWF_F64) {
         if (var == 7 && a.mixmode == 0 && a.Ls % 4 == 0) return launch_lean<P, DAG, 2>(a, SB, st);
-        if (var == 8 && a.mixmode == 0 && a.Ls % 4 == 0) return launch_lean<P, DAG, 3>(a, SB, st);
     }
-    if (var == 7 || var == 8) var = P == DWF_F16 ? 5 : 0;
-    // variant 6: asynchronous gathers (FP32 and FP16 fields, dense mixing, Ls dividing 32);
-    // SB is read as warps per CTA
-    if constexpr (P != DWF_F64) {
-        if (var == 6 && a.mixmode == 0 && a.Ls <= 32 && 32 % a.Ls == 0) return launch_async<P, DAG>(a, SB, st);
-        if (var == 6) var = P == DWF_F16 ? 5 : 0;
-    }
-    if (var == 6) var = 0;
+    if (var == 7) var = P == DWF_F16 ? 5 : 0;
+
     // variant 5: FP16 fields with FP16 projection and SU(3) arithmetic (dense mixing)
     if constexpr (P == DWF_F16) {
         if (var == 5 && a.mixmode == 0) {

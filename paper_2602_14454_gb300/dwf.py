@@ -35,7 +35,7 @@ EXPORTED = ["dwf_create", "dwf_create_s", "dwf_destroy", "dwf_strerror", "dwf_la
             "dwf_set_mix_mode", "dwf_get_mix_mode", "dwf_apply_eo_noalloc",
             "dwf_train_params_default", "dwf_precond_init", "dwf_precond_set_weights", "dwf_precond_get_weights",
             "dwf_precond_apply", "dwf_precond_loss_grad", "dwf_precond_train", "dwf_precond_adam_step",
-            "dwf_precond_save", "dwf_precond_load", "dwf_alu_peaks", "dwf_precond_fcg"]
+            "dwf_precond_save", "dwf_precond_load", "dwf_alu_peaks", "dwf_precond_fcg", "dwf_time_mix"]
 
 
 class SolveParams(ctypes.Structure):
@@ -127,6 +127,7 @@ def lib():
     L.dwf_device_bytes.restype = ctypes.c_size_t
     L.dwf_time_hop.argtypes = [vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]
     L.dwf_time_iteration.argtypes = [vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]
+    L.dwf_time_mix.argtypes = [vp, i, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]
     L.dwf_spectrum_bounds.argtypes = [vp, i, i, d, ctypes.c_ulonglong, ctypes.POINTER(d), ctypes.POINTER(d), ip, vp]
     L.dwf_set_hop_config.argtypes = [vp, i, i, i, i]
     L.dwf_get_hop_config.argtypes = [vp, i, ip, ip, ip]
@@ -404,6 +405,14 @@ class Operator:
         us = ctypes.c_double()
         by = ctypes.c_double()
         check(lib().dwf_time_hop(self._h, PREC[prec], int(reps), int(bool(flush_l2)), ctypes.byref(us),
+                                 ctypes.byref(by), _stream()))
+        return us.value, by.value
+
+    def time_mix(self, prec="f32", mode=2, reps=20, flush_l2=True):
+        """(us per launch, algorithmic bytes) of one stand-alone mixing launch."""
+        us = ctypes.c_double()
+        by = ctypes.c_double()
+        check(lib().dwf_time_mix(self._h, PREC[prec], int(mode), int(reps), int(bool(flush_l2)), ctypes.byref(us),
                                  ctypes.byref(by), _stream()))
         return us.value, by.value
 

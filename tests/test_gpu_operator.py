@@ -134,8 +134,8 @@ def test_full_size_eo_parity():
 
 
 HOP_CONFIGS = [(4, 1, 4), (4, 2, 6), (4, 1, 12), (4, 2, 16), (4, 1, 5), (3, 1, 3), (3, 2, 8), (3, 1, 8), (0, 1, 3),
-               (0, 2, 5), (0, 1, 16), (0, 2, 1), (5, 1, 8), (5, 2, 5), (5, 4, 3), (5, 4, 16), (6, 1, 1), (6, 1, 4),
-               (6, 0, 8), (7, 1, 1), (7, 1, 5), (7, 0, 16), (8, 1, 3), (8, 0, 8)]
+               (0, 2, 5), (0, 1, 16), (0, 2, 1), (5, 1, 8), (5, 2, 5), (5, 4, 3), (5, 4, 16), (7, 1, 1), (7, 1, 5),
+               (7, 0, 16), (9, 1, 4), (9, 2, 2), (9, 0, 1), (9, 2, 3)]
 
 
 @pytest.mark.parametrize("cfg", HOP_CONFIGS, ids=lambda c: "var%d_ns%d_sb%d" % c)
@@ -147,8 +147,8 @@ def test_hop_configurations_ragged_tiles(cfg, prec, Ls):
     var, ns, sb = cfg
     dims = (6, 2, 2, 4)
     op, ref = make_pair(dims, Ls, 1.8, 0.02, 1.5, 0.5, "neff", 0.6, seed=51)
-    if var >= 6 and prec == "f64":
-        return                      # variants 6-8 have no FP64 form (FP64 falls back to variant 0)
+    if var >= 7 and prec == "f64":
+        return                      # variants 7 and 9 have no FP64 form (FP64 falls back to variant 0)
     op.set_hop_config(prec, var, ns, sb)
     assert op.hop_config(prec)[0] == var
     x = ref.to_eo(inputs.gaussian_5d(dims, Ls, 52), 0)
@@ -271,16 +271,16 @@ def test_errors():
 @pytest.mark.parametrize("Ls,dims", [(16, (4, 2, 6, 4)), (4, (2, 4, 4, 6)), (32, (2, 2, 2, 4)), (8, (8, 4, 4, 4)),
                                      (12, (4, 2, 2, 6))])
 @pytest.mark.parametrize("prec", ["f32", "f16"])
-@pytest.mark.parametrize("var,sb", [(6, 1), (6, 3), (6, 8), (7, 1), (7, 3), (8, 8), (8, 5)])
-def test_persistent_hop_variants(Ls, dims, prec, var, sb):
-    """Variant 6 (asynchronous neighbour gathers, links staged per warp tile; sb
-    warps per persistent CTA) and variants 7 and 8 (links staged per CTA tile of
-    sb sites, padded mixing tile, two or three CTAs per SM) give the even-odd
+@pytest.mark.parametrize("var,ns,sb", [(7, 1, 1), (7, 1, 3), (7, 0, 16), (9, 1, 1), (9, 1, 3), (9, 2, 4), (9, 2, 2)])
+def test_persistent_hop_variants(Ls, dims, prec, var, ns, sb):
+    """Variant 7 (links staged per CTA tile of sb sites, padded mixing tile,
+    mixing by half of the threads) and variant 9 (warp tiles with their own links
+    and mixing tile, sb warps per CTA, ns the register budget) give the even-odd
     operator, its adjoint and the full 5D operator of the oracle; Ls = 4, 8, 16
-    and 32 put 8, 4, 2 and 1 sites in a warp tile (Ls 12 takes the fallback of
-    variant 6)."""
+    and 32 put 8, 4, 2 and 1 sites in a warp tile (Ls 12 takes variant 9's
+    fallback)."""
     op, ref = make_pair(dims, Ls, 1.8, 0.02, 1.5, 0.5, "neff", 0.5, seed=81)
-    op.set_hop_config(prec, var, 1, sb)
+    op.set_hop_config(prec, var, ns, sb)
     x = ref.to_eo(inputs.gaussian_5d(dims, Ls, 82), 0)
     for dag in (False, True):
         got = to_np(op.apply(to_gpu(x), op="eo", prec=prec, dag=dag))
@@ -292,9 +292,9 @@ def test_persistent_hop_variants(Ls, dims, prec, var, sb):
     op.device_status()
 
 
-@pytest.mark.parametrize("var", [6, 7, 8])
+@pytest.mark.parametrize("var", [7, 9])
 def test_persistent_hop_variants_full_size(var):
-    """16^3x32, Ls 16: variants 6-8 against variant 0 (FP32) and variant 5 (FP16)
+    """16^3x32, Ls 16: variants 7 and 9 against variant 0 (FP32) and variant 5 (FP16)
     on the same input: the same operator to the precision's rounding."""
     dims, Ls = (16, 16, 16, 32), 16
     U = inputs.random_links(dims, 0.3, 1002)

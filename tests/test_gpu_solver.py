@@ -173,7 +173,7 @@ def test_c2_mixed_precision_full_size(c2_setup, prec, form, alpha):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16"])
-@pytest.mark.parametrize("var", [6, 7, 8])
+@pytest.mark.parametrize("var", [0, 7, 9])
 def test_c1_solve_with_persistent_hops(c1_reference, prec, var):
     """The solver with the persistent hop variants in every inner launch,
     including the reducing and residual epilogues."""
