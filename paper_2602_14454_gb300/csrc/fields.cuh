@@ -135,6 +135,78 @@ __device__ __forceinline__ void st_pairs(const FieldRef &f, size_t site, int s, 
     }
 }
 
+// The same with streaming stores (st.global.cs: evict first), for outputs no
+// later load of the same launch reads: they then leave L2 to the data that is
+// read again (the neighbour spinors of the hop).
+template <int P, typename T2>
+__device__ __forceinline__ void st_pairs_cs(const FieldRef &f, size_t site, int s, int Ls, const T2 *v)
+{
+    if constexpr (P == DWF_F64) {
+        double2 *p = reinterpret_cast<double2 *>(f.v) + (site * 12) * Ls + s;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) __stcs(p + (size_t)k * Ls, make_double2((double)v[k].x, (double)v[k].y));
+    } else if constexpr (P == DWF_F32) {
+        float4 *p = reinterpret_cast<float4 *>(f.v) + (site * 6) * Ls + s;
+#pragma unroll
+        for (int g = 0; g < 6; ++g)
+            __stcs(p + (size_t)g * Ls, make_float4((float)v[2 * g].x, (float)v[2 * g].y, (float)v[2 * g + 1].x,
+                                                   (float)v[2 * g + 1].y));
+    } else {
+        float mx = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) mx = fmaxf(mx, fmaxf(fabsf((float)v[k].x), fabsf((float)v[k].y)));
+        const float inv = mx > 0.f ? 1.0f / mx : 0.f;
+        uint4 *p = reinterpret_cast<uint4 *>(f.v) + (site * 3) * Ls + s;
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            unsigned w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                __half2 h2 = __floats2half2_rn((float)v[4 * g + k].x * inv, (float)v[4 * g + k].y * inv);
+                w[k] = *reinterpret_cast<unsigned *>(&h2);
+            }
+            __stcs(p + (size_t)g * Ls, make_uint4(w[0], w[1], w[2], w[3]));
+        }
+        __stcs(f.scale + site * (size_t)((Ls + 3) & ~3) + s, mx);
+    }
+}
+
+// v[12] <- field(site, s) with streaming loads (ld.global.cs), for inputs read once
+template <int P, typename T2>
+__device__ __forceinline__ void ld_pairs_cs(const FieldRef &f, size_t site, int s, int Ls, T2 *v)
+{
+    typedef typename PairReal<T2>::R R;
+    if constexpr (P == DWF_F64) {
+        const double2 *p = reinterpret_cast<const double2 *>(f.v) + (site * 12) * Ls + s;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const double2 q = __ldcs(p + (size_t)k * Ls);
+            v[k] = p_make((R)q.x, (R)q.y);
+        }
+    } else if constexpr (P == DWF_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>(f.v) + (site * 6) * Ls + s;
+#pragma unroll
+        for (int g = 0; g < 6; ++g) {
+            const float4 q = __ldcs(p + (size_t)g * Ls);
+            v[2 * g] = p_make((R)q.x, (R)q.y);
+            v[2 * g + 1] = p_make((R)q.z, (R)q.w);
+        }
+    } else {
+        const uint4 *p = reinterpret_cast<const uint4 *>(f.v) + (site * 3) * Ls + s;
+        const float sc = __ldcs(f.scale + site * (size_t)((Ls + 3) & ~3) + s);
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            const uint4 q = __ldcs(p + (size_t)g * Ls);
+            const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
+                v[4 * g + k] = p_make((R)(f2.x * sc), (R)(f2.y * sc));
+            }
+        }
+    }
+}
+
 // internal real index (4g + spin, g = 2a + c) <-> canonical (spin*3 + a)*2 + c
 __host__ __device__ __forceinline__ int canon_of_internal(int k)
 {

@@ -1054,11 +1054,11 @@ __device__ __forceinline__ float wa_epilogue(const HopArgs &a, const float2 *acc
         xf.v = a.xacc;
         const float2 xa = p_splat((float)(*a.xalpha));
         float2 xv[12], dx[12];
-        ld_pairs<DWF_F32, false>(xf, (size_t)site, s, Ls, xv);
-        ld_pairs<P, false>(a.xdir, (size_t)site, s, Ls, dx);
+        ld_pairs_cs<DWF_F32>(xf, (size_t)site, s, Ls, xv);
+        ld_pairs_cs<P>(a.xdir, (size_t)site, s, Ls, dx);
 #pragma unroll
         for (int k = 0; k < 12; ++k) xv[k] = p_fma(xa, dx[k], xv[k]);
-        st_pairs<DWF_F32>(xf, (size_t)site, s, Ls, xv);
+        st_pairs_cs<DWF_F32>(xf, (size_t)site, s, Ls, xv);
     }
     if (active) lean_put(row, acc);
     __syncwarp();
@@ -1069,7 +1069,7 @@ __device__ __forceinline__ float wa_epilogue(const HopArgs &a, const float2 *acc
     if (a.ymode == 1) {
         if (active) {
             float2 y[12];
-            ld_pairs<P, false>(a.y, (size_t)site, s, Ls, y);
+            ld_pairs_cs<P>(a.y, (size_t)site, s, Ls, y);
 #pragma unroll
             for (int k = 0; k < 12; ++k) o[k] = p_add(o[k], y[k]);
         }
@@ -1077,7 +1077,7 @@ __device__ __forceinline__ float wa_epilogue(const HopArgs &a, const float2 *acc
         __syncwarp();
         if (active) {
             float2 y[12];
-            ld_pairs<P, false>(a.y, (size_t)site, s, Ls, y);
+            ld_pairs_cs<P>(a.y, (size_t)site, s, Ls, y);
             lean_put(row, y);
         }
         __syncwarp();
@@ -1086,7 +1086,7 @@ __device__ __forceinline__ float wa_epilogue(const HopArgs &a, const float2 *acc
     if (active && a.rin.v) {
         const float2 nal = p_splat((float)-(*a.ralpha));
         float2 r[12];
-        ld_pairs<P, false>(a.rin, (size_t)site, s, Ls, r);
+        ld_pairs_cs<P>(a.rin, (size_t)site, s, Ls, r);
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[k] = p_fma(nal, o[k], r[k]);
     }
@@ -1106,10 +1106,10 @@ __device__ __forceinline__ float wa_epilogue(const HopArgs &a, const float2 *acc
         for (int k = 0; k < 12; ++k) z[k] = make_float2(0.f, 0.f);
         if (active) {
             wa_mix(mats + 2 * msz, site_tile, s, Ls, a.z_band != 0, z);
-            st_pairs<P>(a.out, (size_t)site, s, Ls, z);
+            st_pairs_cs<P>(a.out, (size_t)site, s, Ls, z);
         }
     } else if (active) {
-        st_pairs<P>(a.out, (size_t)site, s, Ls, o);
+        st_pairs_cs<P>(a.out, (size_t)site, s, Ls, o);
     }
     return nrm;
 }

@@ -23,7 +23,7 @@ def _sync():
 def _links(w):
     import torch
     from . import inputs
-    return torch.from_numpy(inputs.workload_links(w)).cuda()
+    return torch.from_numpy(inputs.workload_links(w, device="cuda")).cuda()
 
 
 def run_batch(args):
@@ -59,6 +59,21 @@ def run_batch(args):
            "iterations": {"min": min(s["iterations"] for s in st), "max": max(s["iterations"] for s in st)},
            "true_residual_max": max(s["true_residual"] for s in st),
            "status": sorted({s["status"] for s in st}), "kernel_launches": st[0]["kernel_launches"]}
+    if args.sequential:
+        # the same systems one at a time through dwf_solve (5D source, solve, 4D projection)
+        n = len(hs) if args.sequential < 0 else min(args.sequential, len(hs))
+        worst = 0.0
+        _sync()
+        t0 = time.perf_counter()
+        for h, b4, xb in zip(hs[:n], b4s[:n], x4s[:n]):
+            x5, s1 = h.solve(h.source_5d(b4), inner_prec=args.inner, tol=1e-10)
+            x4 = h.project_4d(x5)
+            worst = max(worst, float(torch.linalg.vector_norm(x4 - xb) / torch.linalg.vector_norm(x4)))
+        _sync()
+        ds = time.perf_counter() - t0
+        out["sequential"] = {"systems": n, "seconds": ds, "systems_per_s": n / ds,
+                             "batched_over_sequential": (len(hs) / dt) / (n / ds),
+                             "max_rel_diff_x4_batched_vs_sequential": worst}
     print(json.dumps(out), flush=True)
 
 
@@ -177,6 +192,8 @@ def main(argv=None):
     ap.add_argument("--inner", default="f32", choices=["f16", "f32", "f64"])
     ap.add_argument("--wave", type=int, default=0)
     ap.add_argument("--small", action="store_true", help="batch: 8^3x16 instead of 24^3x48")
+    ap.add_argument("--sequential", type=int, default=0,
+                    help="batch: also solve this many of the systems one by one (-1: all) and compare")
     ap.add_argument("--ntrain", type=int, default=256)
     ap.add_argument("--ntest", type=int, default=4)
     ap.add_argument("--epochs", type=int, default=20)

@@ -240,9 +240,9 @@ def test_autotuner_picks_a_valid_configuration(tmp_path):
     op, ref = make_pair(dims, 16, 1.8, 0.01, 1.5, 0.5, "standard", 1.0, seed=61)
     cache = str(tmp_path / "tune.txt")
     cfg = op.autotune("f32", cache)
-    assert cfg[0] in range(5) and cfg[1] in (1, 2) and cfg[2] >= 1
+    assert cfg[0] in (0, 3, 4, 7, 9) and cfg[1] in (1, 2) and cfg[2] >= 1
     c16 = op.autotune("f16")
-    assert c16[0] in range(6) and c16[1] in (1, 2, 4) and c16[2] >= 1
+    assert c16[0] in (0, 3, 4, 5, 7, 9) and c16[1] in (1, 2, 4) and c16[2] >= 1
     x = ref.to_eo(inputs.gaussian_5d(dims, 16, 63), 0)
     assert rel(to_np(op.apply(to_gpu(x), op="eo", prec="f16")), ref.d_pc(x)) < TOL["f16"]
     op2, _ = make_pair(dims, 16, 1.8, 0.01, 1.5, 0.5, "standard", 1.0, seed=61)
@@ -271,7 +271,7 @@ def test_errors():
 @pytest.mark.parametrize("Ls,dims", [(16, (4, 2, 6, 4)), (4, (2, 4, 4, 6)), (32, (2, 2, 2, 4)), (8, (8, 4, 4, 4)),
                                      (12, (4, 2, 2, 6))])
 @pytest.mark.parametrize("prec", ["f32", "f16"])
-@pytest.mark.parametrize("var,ns,sb", [(7, 1, 1), (7, 1, 3), (7, 0, 16), (9, 1, 1), (9, 1, 3), (9, 2, 4), (9, 2, 2)])
+@pytest.mark.parametrize("var,ns,sb", [(7, 1, 1), (7, 1, 3), (7, 0, 8), (9, 1, 1), (9, 1, 3), (9, 2, 4), (9, 2, 2)])
 def test_persistent_hop_variants(Ls, dims, prec, var, ns, sb):
     """Variant 7 (links staged per CTA tile of sb sites, padded mixing tile,
     mixing by half of the threads) and variant 9 (warp tiles with their own links
