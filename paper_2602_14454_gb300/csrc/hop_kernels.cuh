@@ -1041,6 +1041,118 @@ __device__ __forceinline__ void wa_mix(const float *M, const float2 *site_tile, 
     }
 }
 
+// Structured fifth-direction mixing (MixProg, dwf_internal.h) in registers:
+// the Ls slices of a site sit on Ls consecutive lanes, so the chain along s
+// is a warp segment of width Ls.  x <- d1 x; A5^-1 by its recurrence
+// x_u = w_u + kappa x_{u-1} (w = x / alpha0, x_{-1} = -m x_last) written as a
+// decaying inclusive prefix scan y_u = sum_{t<=u} kappa^(u-t) w_t (log2 Ls
+// shuffle steps) followed by x_u = y_u - m kappa^(u+1) corner y_last; the
+// shift (s0 + s1 K) x with one indexed shuffle (the corner -m at the chain's
+// start); x <- d2 x.  u is the position along the chain (s, or Ls - 1 - s
+// when K reads s + 1).  Pairs k even are the P_+ chirality, odd the P_-.
+__device__ __forceinline__ void scan_mix(const MixProg<float> *pg, float2 *o, int s, int Ls)
+{
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi) {
+        const bool up = pg->up[chi] != 0;
+        const int u = up ? Ls - 1 - s : s;
+        const float d1 = pg->d1[chi][s], d2 = pg->d2[chi][s];
+#pragma unroll
+        for (int k = chi; k < 12; k += 2) o[k] = p_mul(o[k], p_splat(d1));
+        if (pg->inv) {
+            const float a0inv = pg->a0inv;
+#pragma unroll
+            for (int k = chi; k < 12; k += 2) o[k] = p_mul(o[k], p_splat(a0inv));
+            float kd = pg->kappa;
+            for (int d = 1; d < Ls; d <<= 1) {
+                const float2 kk = p_splat(u >= d ? kd : 0.f);
+#pragma unroll
+                for (int k = chi; k < 12; k += 2) {
+                    float2 t;
+                    t.x = up ? __shfl_down_sync(full, o[k].x, d, Ls) : __shfl_up_sync(full, o[k].x, d, Ls);
+                    t.y = up ? __shfl_down_sync(full, o[k].y, d, Ls) : __shfl_up_sync(full, o[k].y, d, Ls);
+                    o[k] = p_fma(kk, t, o[k]);
+                }
+                kd *= kd;
+            }
+            float kp = pg->kappa;   // kappa^(u+1)
+            for (int e = 0; e < u; ++e) kp *= pg->kappa;
+            const float2 c = p_splat(pg->mneg * pg->corner * kp);
+            const int last = up ? 0 : Ls - 1;
+#pragma unroll
+            for (int k = chi; k < 12; k += 2) {
+                float2 yl;
+                yl.x = __shfl_sync(full, o[k].x, last, Ls);
+                yl.y = __shfl_sync(full, o[k].y, last, Ls);
+                o[k] = p_fma(c, yl, o[k]);
+            }
+        }
+        if (pg->shift) {
+            const int src = up ? (s + 1 == Ls ? 0 : s + 1) : (s == 0 ? Ls - 1 : s - 1);
+            const float2 a = p_splat(pg->s0), b = p_splat(pg->s1 * (u == 0 ? pg->mneg : 1.f));
+#pragma unroll
+            for (int k = chi; k < 12; k += 2) {
+                float2 t;
+                t.x = __shfl_sync(full, o[k].x, src, Ls);
+                t.y = __shfl_sync(full, o[k].y, src, Ls);
+                o[k] = p_fma(b, t, p_mul(a, o[k]));
+            }
+        }
+#pragma unroll
+        for (int k = chi; k < 12; k += 2) o[k] = p_mul(o[k], p_splat(d2));
+    }
+}
+
+// the epilogue with the structured mixings in registers (every lane of the warp calls it)
+template <int P>
+__device__ __forceinline__ float wa_epilogue_scan(const HopArgs &a, const float2 *acc, int s, int site, bool active)
+{
+    const int Ls = a.Ls;
+    const MixProg<float> *pp = reinterpret_cast<const MixProg<float> *>(a.post_prog);
+    if (active && a.rin.v && a.xacc) {
+        FieldRef xf;
+        xf.v = a.xacc;
+        const float2 xa = p_splat((float)(*a.xalpha));
+        float2 xv[12], dx[12];
+        ld_pairs_cs<DWF_F32>(xf, (size_t)site, s, Ls, xv);
+        ld_pairs_cs<P>(a.xdir, (size_t)site, s, Ls, dx);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) xv[k] = p_fma(xa, dx[k], xv[k]);
+        st_pairs_cs<DWF_F32>(xf, (size_t)site, s, Ls, xv);
+    }
+    float2 o[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = acc[k];
+    scan_mix(pp, o, s, Ls);
+    if (a.ymode != 0) {
+        float2 y[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) y[k] = make_float2(0.f, 0.f);
+        if (active) ld_pairs_cs<P>(a.y, (size_t)site, s, Ls, y);
+        if (a.ymode == 2) scan_mix(reinterpret_cast<const MixProg<float> *>(a.y_prog), y, s, Ls);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o[k] = p_add(o[k], y[k]);
+    }
+    if (active && a.rin.v) {
+        const float2 nal = p_splat((float)-(*a.ralpha));
+        float2 r[12];
+        ld_pairs_cs<P>(a.rin, (size_t)site, s, Ls, r);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o[k] = p_fma(nal, o[k], r[k]);
+    }
+    float nrm = 0.f;
+    if (active && a.red.op != RED_NONE) {
+        float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s2 = p_fma(o[k], o[k], s2);
+        nrm = s2.x + s2.y;
+    }
+    if (a.zmat) scan_mix(reinterpret_cast<const MixProg<float> *>(a.z_prog), o, s, Ls);
+    if (active) st_pairs_cs<P>(a.out, (size_t)site, s, Ls, o);
+    return nrm;
+}
+
 // the epilogue of hop_epilogue_core (dense mixing) on the warp's tile
 template <int P>
 __device__ __forceinline__ float wa_epilogue(const HopArgs &a, const float2 *acc, float2 *site_tile,
@@ -1132,7 +1244,7 @@ __device__ __forceinline__ void wa_issue_links(const void *gauge, int site0, int
 // still in L2 when those are processed (which a contiguous range per CTA,
 // spreading the tiles in work over the whole lattice, loses once the fields
 // exceed L2).
-template <int P, bool DAG, int MINB>
+template <int P, bool DAG, int MINB, int MIX>
 __global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1194,7 +1306,10 @@ __global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
             lean_dir<P, DAG, 6>(acc, a.in, n8[6], s, Ls, lk);
             lean_dir<P, DAG, 7>(acc, a.in, n8[7], s, Ls, lk);
         }
-        nrm += wa_epilogue<P>(a, acc, site_tile, mats, s, site, active);
+        if constexpr (MIX == 1)
+            nrm += wa_epilogue_scan<P>(a, acc, s, site, active);
+        else
+            nrm += wa_epilogue<P>(a, acc, site_tile, mats, s, site, active);
     }
     cp_async_wait<0>();
     if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
@@ -1367,28 +1482,28 @@ cudaError_t launch_lean(const HopArgs &a, int SB, cudaStream_t st)
 
 // Variant 9: persistent CTAs of `nw` warps (2, 4 or 8 resident CTAs' worth of
 // registers: nw x MINB x 32 threads per SM), as many per SM as fit.
-template <int P, bool DAG, int MINB>
+template <int P, bool DAG, int MINB, int MIX>
 cudaError_t launch_wa(const HopArgs &a, int nw, cudaStream_t st)
 {
     static unsigned long long optin = 0;
     int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if ((e = smem_optin(hop_wa_kernel<P, DAG, MINB>, 200 * 1024, optin)) != cudaSuccess) return e;
+    if ((e = smem_optin(hop_wa_kernel<P, DAG, MINB, MIX>, 200 * 1024, optin)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if (nw < 1) nw = 4;
     if (nw > 4) nw = 4;
     const size_t smem = wa_cta_bytes<P>(a.Ls, nw);
     if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_wa_kernel<P, DAG, MINB>, 32 * nw, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_wa_kernel<P, DAG, MINB, MIX>, 32 * nw, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     const int SPW = 32 / a.Ls;
     const int ntiles = (a.Vh + SPW - 1) / SPW;
     int grid = nsm * per_sm;
     if (grid > (ntiles + nw - 1) / nw) grid = (ntiles + nw - 1) / nw;
-    hop_wa_kernel<P, DAG, MINB><<<grid, 32 * nw, smem, st>>>(a);
+    hop_wa_kernel<P, DAG, MINB, MIX><<<grid, 32 * nw, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1400,7 +1515,10 @@ cudaError_t launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st
     // warps per SM, 2: 4)
     if constexpr (P != DWF_F64) {
         if (var == 9 && a.mixmode == 0 && a.Ls <= 32 && 32 % a.Ls == 0 && a.Ls % 4 == 0)
-            return NS == 2 ? launch_wa<P, DAG, 4>(a, SB, st) : launch_wa<P, DAG, 5>(a, SB, st);
+            return NS == 2 ? launch_wa<P, DAG, 4, 0>(a, SB, st) : launch_wa<P, DAG, 5, 0>(a, SB, st);
+        // structured mixing by warp shuffles (no mixing tile)
+        if (var == 9 && a.mixmode == 1 && a.Ls <= 32 && 32 % a.Ls == 0 && a.Ls % 4 == 0)
+            return NS == 2 ? launch_wa<P, DAG, 4, 1>(a, SB, st) : launch_wa<P, DAG, 5, 1>(a, SB, st);
     }
     if (var == 9) var = P == DWF_F16 ? 5 : 0;
     if constexpr (P != DWF_F64) {

@@ -3,13 +3,16 @@
     python -m paper_2602_14454_gb300.hopprof --prec f16 --reps 4
     python -m paper_2602_14454_gb300.hopprof --workload c1_4^4_ls8_shamir --prec f32
     python -m paper_2602_14454_gb300.hopprof --prec f16 --iteration   # the 5 launches of one CG iteration
+    python -m paper_2602_14454_gb300.hopprof --prec f32 --time-mix --mix 2   # one stand-alone mixing launch
 
 Builds the operator of the named workload (links from the seeded generator of
 ``inputs``), optionally pins a hop configuration or a mixing mode, and times
 ``reps`` hop launches with CUDA events, L2 flushed between them.  Prints one
 JSON line: microseconds per launch, algorithmic bytes per launch and GB/s.
 With ``--iteration`` it times the five launches of one inner CG iteration of
-the solver instead (p update and the four hops with their fused epilogues).
+the solver instead (p update and the four hops with their fused epilogues);
+with ``--time-mix`` one stand-alone fifth-direction mixing launch in the mode
+given by ``--mix`` (0 CUDA cores, 2 tensor cores).
 """
 
 import argparse
@@ -26,6 +29,7 @@ def main(argv=None):
     ap.add_argument("--config", default=None, help="variant,ns,sb (default: the library's choice)")
     ap.add_argument("--mix", type=int, default=None, help="fifth-direction mixing mode")
     ap.add_argument("--iteration", action="store_true", help="time the launches of one CG iteration")
+    ap.add_argument("--time-mix", action="store_true", help="time one stand-alone mixing launch (mode --mix)")
     args = ap.parse_args(argv)
 
     import torch
@@ -37,6 +41,13 @@ def main(argv=None):
     if args.config:
         v, ns, sb = (int(t) for t in args.config.split(","))
         op.set_hop_config(args.prec, v, ns, sb)
+    if args.time_mix:
+        mode = 0 if args.mix is None else args.mix
+        us, nbytes = op.time_mix(args.prec, mode, reps=args.reps, flush_l2=True)
+        op.device_status()
+        print(json.dumps({"workload": args.workload, "prec": args.prec, "mix_mode": mode, "us_per_launch": us,
+                          "algorithmic_bytes": nbytes, "gbs": nbytes / (us * 1e-6) / 1e9}))
+        return 0
     if args.mix is not None:
         op.set_mix_mode(args.prec, args.mix)
     if args.iteration:
