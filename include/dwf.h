@@ -283,7 +283,7 @@ long long dwf_launch_count(dwf_handle h);
  * memory one tile ahead and the mixing done by half of the threads, two
  * outputs each; variant 9 (FP32/FP16, dense mixing, Ls dividing 32 and a
  * multiple of 4) is persistent and warp-autonomous: every warp walks its own
- * tiles of 32/Ls sites (a window sweeping the lattice in index order) with
+ * tiles of 32/Ls sites (a window sweeping the lattice, see dwf_set_sweep) with
  * its own shared-memory links (staged one tile ahead) and mixing tile, and no
  * CTA barrier; there sb counts warps per CTA (1..4) and ns selects the
  * register budget (1: five CTAs of sb warps per SM, 2: four).  ns: slices per
@@ -297,6 +297,20 @@ long long dwf_launch_count(dwf_handle h);
  * than 256 threads). */
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb);
 int dwf_get_hop_config(dwf_handle h, int prec, int *variant, int *ns, int *sb);
+
+/* Sweep order of the hop kernels in precision prec (variants 0, 5 and 9): the
+ * sites of one parity are taken in columns of zblock z-planes, each column
+ * t-slice by t-slice, so that the two reads of a site as the -t and +t
+ * neighbour of others lie 2 zblock (Lx/2) Ly sites apart and the field between
+ * them stays in L2 on lattices whose t-slices exceed it; the z-planes at a
+ * column's border are read twice.  zblock: -1 automatic (the default: the
+ * largest divisor of Lz whose column band of input, output and links of one
+ * parity stays within 16 MiB; index order when a whole t-slice does), 0 index
+ * order, else a divisor of Lz below Lz with zblock (Lx/2) Ly a multiple of 32.
+ * The order changes only the order of the fused norms' partial sums.
+ * Errors: DWF_EINVAL (NULL handle or pointer, bad prec or zblock). */
+int dwf_set_sweep(dwf_handle h, int prec, int zblock);
+int dwf_get_sweep(dwf_handle h, int prec, int *zblock);
 
 /* Autotuner: times every hop configuration (all variants, ns in {1, 2, 4},
  * CTAs of 64 to 256 threads, every available mixing mode) on this handle's lattice with CUDA events on

@@ -117,6 +117,25 @@ FieldRef dwf_ctx::field(const std::string &name, int prec, cudaError_t *err)
 // --------------------------------------------------------------- helpers
 namespace dwf_detail {
 
+// Columns of z-planes for the hop's sweep order (HopArgs::zblock): the largest
+// divisor Bz of Lz whose column band of Bz z-planes (input and output spinors of
+// one parity and their links) stays within 16 MiB, so that the 2 Bz planes read
+// between a site's two t-neighbour reads fit in L2 with room to spare; 0 (index
+// order) while a whole t-slice fits.  Runs of Bz A sites are kept multiples of 32
+// so that no hop tile straddles two of them.
+static int sweep_zblock(const dwf_ctx *h, int prec)
+{
+    if (h->sweep_zb[prec] >= 0) return h->sweep_zb[prec];
+    const long long A = (long long)(h->dims[0] / 2) * h->dims[1];
+    const long long w = prec == DWF_F64 ? 8 : prec == DWF_F32 ? 4 : 2;
+    const long long plane = A * ((long long)h->Ls * 24 * w * 2 + 8 * 18 * w);
+    const long long budget = 16ll << 20;
+    if (plane * h->dims[2] <= budget) return 0;
+    for (int bz = h->dims[2] - 1; bz >= 1; --bz)
+        if (h->dims[2] % bz == 0 && bz * plane <= budget && (bz * A) % 32 == 0) return bz;
+    return 0;
+}
+
 HopArgs hop_args(dwf_ctx *h, int prec, int out_par, FieldRef in, FieldRef out, int post)
 {
     HopArgs a;
@@ -132,6 +151,7 @@ HopArgs hop_args(dwf_ctx *h, int prec, int out_par, FieldRef in, FieldRef out, i
     a.ext[1] = h->dims[1];
     a.ext[2] = h->dims[2];
     a.ext[3] = h->dims[3];
+    a.zblock = sweep_zblock(h, prec);
     return a;
 }
 
@@ -596,6 +616,23 @@ int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb)
     h->hop_var[prec] = variant;
     h->hop_ns[prec] = ns;
     h->hop_sb[prec] = sb;
+    return DWF_OK;
+}
+
+int dwf_set_sweep(dwf_handle h, int prec, int zblock)
+{
+    if (!h || prec < 0 || prec > 2) return dwf_set_error(DWF_EINVAL, "bad handle or precision");
+    const long long A = (long long)(h->dims[0] / 2) * h->dims[1];
+    if (zblock < -1 || (zblock > 0 && (zblock >= h->dims[2] || h->dims[2] % zblock || (zblock * A) % 32)))
+        return dwf_set_error(DWF_EINVAL, "zblock must be -1, 0 or a divisor of Lz below Lz with zblock Lx/2 Ly a multiple of 32");
+    h->sweep_zb[prec] = zblock;
+    return DWF_OK;
+}
+
+int dwf_get_sweep(dwf_handle h, int prec, int *zblock)
+{
+    if (!h || prec < 0 || prec > 2 || !zblock) return dwf_set_error(DWF_EINVAL, "bad argument");
+    *zblock = sweep_zblock(h, prec);
     return DWF_OK;
 }
 

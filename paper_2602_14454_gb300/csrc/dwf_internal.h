@@ -115,6 +115,7 @@ struct HopArgs {
     const void *post_prog = nullptr, *y_prog = nullptr, *z_prog = nullptr;
     const int *skip = nullptr;     // batched launches: the system is left untouched while *skip != 0
     int post_band = 0, y_band = 0, z_band = 0;   // the matrix is cyclic tridiagonal (dense mode reads 3 per row)
+    int zblock = 0;                // sweep the lattice in columns of zblock z-planes (0: index order)
 };
 
 struct MixArgs {
@@ -291,6 +292,7 @@ struct dwf_ctx {
     int hop_var[3] = {-1, -1, -1};    // hop variant per precision (-1 = default), set by the autotuner
     int hop_ns[3] = {0, 0, 0};        // hop tiling per precision (0 = default)
     int hop_sb[3] = {0, 0, 0};
+    int sweep_zb[3] = {-1, -1, -1};   // hop sweep columns per precision (dwf_set_sweep; -1 automatic)
     dwf::NetState *net = nullptr;     // learned preconditioner (dwf_precond_*)
     int *errflag() const { return &scal[7].flags; }
 

@@ -389,7 +389,25 @@ __device__ __forceinline__ void gather8(typename Tr<P>::pair (*acc)[12], const H
     }
 }
 
-// One tile of SB sites: blockDim = (Ls/NS, SB), site = u SB + threadIdx.y.
+// Sweep order: sweep position p -> site index.  With a.zblock = Bz (0 < Bz <
+// Lz) the lattice is swept in columns of Bz z-planes, each column t-slice by
+// t-slice: site = r + A (z + Lz t), A = (Lx/2) Ly sites of one parity per
+// z-plane, z = column Bz + zl, p = column (Lt Bz A) + t (Bz A) + zl A + r.  A
+// site's -t and +t neighbours are then read 2 Bz A positions apart instead of
+// 2 Lz A, which keeps the field between the two reads within L2 once a whole
+// t-slice no longer fits; only the z-planes bordering a column are read twice
+// from DRAM.  Consecutive positions stay consecutive sites inside a run of Bz A.
+__device__ __forceinline__ int sweep_site(const HopArgs &a, int p)
+{
+    const int Bz = a.zblock;
+    if (Bz <= 0) return p;
+    const int A = a.ext[0] * a.ext[1], plane = Bz * A, col = plane * a.ext[3];
+    const int c = p / col, q = p - c * col, t = q / plane;
+    return q - t * plane + A * (c * Bz + a.ext[2] * t);
+}
+
+// One tile of SB sites: blockDim = (Ls/NS, SB), site = u SB + threadIdx.y
+// (in the sweep order above when a tile never straddles a run of Bz A sites).
 // The norm reduction runs over the nb_red tiles that share a.red.
 template <int P, bool DAG, int NS, int MIX, bool H2 = false>
 __device__ __forceinline__ void hop_direct_tile(const HopArgs &a, int u, unsigned nb_red)
@@ -403,8 +421,8 @@ __device__ __forceinline__ void hop_direct_tile(const HopArgs &a, int u, unsigne
     const int x = threadIdx.x;
     const int j = threadIdx.y;
     const int SB = blockDim.y;
-    const int site = u * SB + j;
-    const bool active = site < a.Vh;
+    const bool active = u * SB + j < a.Vh;
+    const int site = (a.zblock > 0 && (a.zblock * a.ext[0] * a.ext[1]) % SB == 0 ? sweep_site(a, u * SB) : u * SB) + j;
     const int tstride = Ls * 12 + 2;
     T2 *tile = reinterpret_cast<T2 *>(smem_raw);
     R *mtx = reinterpret_cast<R *>(tile + SB * tstride);
@@ -1239,11 +1257,11 @@ __device__ __forceinline__ void wa_issue_links(const void *gauge, int site0, int
 
 // Grid: warp w of CTA b (global warp g = b nwarps + w) takes the warp tiles
 // g, g + G, g + 2G, ... (G = all warps of the grid), so that the tiles in work
-// at any moment form one window sweeping the lattice in index order: the
-// neighbour sites a tile shares with tiles one x-row or one t-slice away are
-// still in L2 when those are processed (which a contiguous range per CTA,
-// spreading the tiles in work over the whole lattice, loses once the fields
-// exceed L2).
+// at any moment form one window sweeping the lattice in the sweep order of
+// sweep_site: the neighbour sites a tile shares with tiles one x-row or one
+// t-slice away are still in L2 when those are processed (which a contiguous
+// range per CTA, spreading the tiles in work over the whole lattice, loses once
+// the fields exceed L2).
 template <int P, bool DAG, int MINB, int MIX>
 __global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
 {
@@ -1275,10 +1293,10 @@ __global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
     const int G = gridDim.x * nwarps;
     float nrm = 0.f;
     int u = blockIdx.x * nwarps + warp;
-    if (u < ntiles) wa_issue_links<P>(a.gauge, u * SPW, min(SPW, a.Vh - u * SPW), links, lane);
+    if (u < ntiles) wa_issue_links<P>(a.gauge, sweep_site(a, u * SPW), min(SPW, a.Vh - u * SPW), links, lane);
     for (int k = 0; u < ntiles; ++k, u += G) {
-        const int site = u * SPW + j;
-        const bool active = site < a.Vh;
+        const int site = sweep_site(a, u * SPW) + j;
+        const bool active = u * SPW + j < a.Vh;
         int n8[8];
         if (active) {
             const int4 *p = reinterpret_cast<const int4 *>(a.nbr + (size_t)site * 8);
@@ -1290,7 +1308,7 @@ __global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
         __syncwarp();   // this tile's links are in; every lane is done with the previous tile
         const int un = u + G;
         if (un < ntiles)   // the next tile's links, into the other buffer
-            wa_issue_links<P>(a.gauge, un * SPW, min(SPW, a.Vh - un * SPW),
+            wa_issue_links<P>(a.gauge, sweep_site(a, un * SPW), min(SPW, a.Vh - un * SPW),
                               links + (size_t)((k + 1) & 1) * SPW * LeanGeom<P>::LINK_BYTES, lane);
         float2 acc[12];
 #pragma unroll

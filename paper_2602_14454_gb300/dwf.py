@@ -31,7 +31,7 @@ EXPORTED = ["dwf_create", "dwf_create_s", "dwf_destroy", "dwf_strerror", "dwf_la
             "dwf_apply", "dwf_apply_dag", "dwf_source_5d", "dwf_project_4d",
             "dwf_solve_params_default", "dwf_solve", "dwf_propagator_host", "dwf_solve_batch",
             "dwf_fifth_matrix", "dwf_fifth_matrix_host", "dwf_device_bytes", "dwf_time_hop", "dwf_time_iteration", "dwf_spectrum_bounds", "dwf_launch_count",
-            "dwf_set_hop_config", "dwf_get_hop_config", "dwf_autotune", "dwf_device_status",
+            "dwf_set_hop_config", "dwf_get_hop_config", "dwf_set_sweep", "dwf_get_sweep", "dwf_autotune", "dwf_device_status",
             "dwf_set_mix_mode", "dwf_get_mix_mode", "dwf_apply_eo_noalloc",
             "dwf_train_params_default", "dwf_precond_init", "dwf_precond_set_weights", "dwf_precond_get_weights",
             "dwf_precond_apply", "dwf_precond_loss_grad", "dwf_precond_train", "dwf_precond_adam_step",
@@ -131,6 +131,8 @@ def lib():
     L.dwf_spectrum_bounds.argtypes = [vp, i, i, d, ctypes.c_ulonglong, ctypes.POINTER(d), ctypes.POINTER(d), ip, vp]
     L.dwf_set_hop_config.argtypes = [vp, i, i, i, i]
     L.dwf_get_hop_config.argtypes = [vp, i, ip, ip, ip]
+    L.dwf_set_sweep.argtypes = [vp, i, i]
+    L.dwf_get_sweep.argtypes = [vp, i, ip]
     L.dwf_device_status.argtypes = [vp, vp]
     L.dwf_set_mix_mode.argtypes = [vp, i, i]
     L.dwf_get_mix_mode.argtypes = [vp, i, ip]
@@ -306,6 +308,14 @@ class Operator:
         check(lib().dwf_get_hop_config(self._h, PREC[prec], ctypes.byref(var), ctypes.byref(ns),
                                        ctypes.byref(sb)))
         return var.value, ns.value, sb.value
+
+    def set_sweep(self, prec, zblock):
+        check(lib().dwf_set_sweep(self._h, PREC[prec], int(zblock)))
+
+    def sweep(self, prec):
+        zb = ctypes.c_int()
+        check(lib().dwf_get_sweep(self._h, PREC[prec], ctypes.byref(zb)))
+        return zb.value
 
     def set_mix_mode(self, prec, mode):
         check(lib().dwf_set_mix_mode(self._h, PREC[prec], int(mode)))

@@ -4,6 +4,7 @@
     python -m paper_2602_14454_gb300.hopprof --workload c1_4^4_ls8_shamir --prec f32
     python -m paper_2602_14454_gb300.hopprof --prec f16 --iteration   # the 5 launches of one CG iteration
     python -m paper_2602_14454_gb300.hopprof --prec f32 --time-mix --mix 2   # one stand-alone mixing launch
+    python -m paper_2602_14454_gb300.hopprof --workload c5_32^3x64_ls16_mobius --prec f32 --sweep 0   # index order
 
 Builds the operator of the named workload (links from the seeded generator of
 ``inputs``), optionally pins a hop configuration or a mixing mode, and times
@@ -28,6 +29,7 @@ def main(argv=None):
     ap.add_argument("--alpha", type=float, default=0.5)
     ap.add_argument("--config", default=None, help="variant,ns,sb (default: the library's choice)")
     ap.add_argument("--mix", type=int, default=None, help="fifth-direction mixing mode")
+    ap.add_argument("--sweep", type=int, default=None, help="z-planes per sweep column (0: index order)")
     ap.add_argument("--iteration", action="store_true", help="time the launches of one CG iteration")
     ap.add_argument("--time-mix", action="store_true", help="time one stand-alone mixing launch (mode --mix)")
     args = ap.parse_args(argv)
@@ -41,6 +43,8 @@ def main(argv=None):
     if args.config:
         v, ns, sb = (int(t) for t in args.config.split(","))
         op.set_hop_config(args.prec, v, ns, sb)
+    if args.sweep is not None:
+        op.set_sweep(args.prec, args.sweep)
     if args.time_mix:
         mode = 0 if args.mix is None else args.mix
         us, nbytes = op.time_mix(args.prec, mode, reps=args.reps, flush_l2=True)
@@ -56,7 +60,7 @@ def main(argv=None):
         tot_us = sum(v[0] for v in t.values())
         tot_by = sum(v[1] for v in t.values())
         print(json.dumps({"workload": args.workload, "prec": args.prec, "config": op.hop_config(args.prec),
-                          "mix": op.mix_mode(args.prec),
+                          "mix": op.mix_mode(args.prec), "sweep": op.sweep(args.prec),
                           "kernels": {k: {"us": v[0], "algorithmic_bytes": v[1], "gbs": v[1] / (v[0] * 1e-6) / 1e9}
                                       for k, v in t.items()},
                           "iteration_us": tot_us, "iteration_bytes": tot_by,
@@ -65,7 +69,7 @@ def main(argv=None):
     us, nbytes = op.time_hop(args.prec, reps=args.reps, flush_l2=True)
     op.device_status()
     print(json.dumps({"workload": args.workload, "prec": args.prec, "config": op.hop_config(args.prec),
-                      "mix": op.mix_mode(args.prec), "us_per_launch": us, "algorithmic_bytes": nbytes,
+                      "mix": op.mix_mode(args.prec), "sweep": op.sweep(args.prec), "us_per_launch": us, "algorithmic_bytes": nbytes,
                       "gbs": nbytes / (us * 1e-6) / 1e9}))
     return 0
 

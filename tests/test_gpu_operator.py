@@ -308,3 +308,37 @@ def test_persistent_hop_variants_full_size(var):
             got = to_np(op.apply(x, op="eo", prec=prec, dag=dag))
             assert rel(got, want) < tol, (prec, dag, rel(got, want))
     op.device_status()
+
+
+@pytest.mark.parametrize("prec,var,ns,sb", [("f32", 9, 2, 4), ("f32", 0, 1, 0), ("f16", 5, 1, 0), ("f16", 9, 1, 3),
+                                            ("f64", 0, 1, 0)])
+@pytest.mark.parametrize("zblock", [1, 2, 4])
+def test_sweep_order_columns(prec, var, ns, sb, zblock):
+    """The hops swept in columns of zblock z-planes (dwf_set_sweep) give the
+    oracle's even-odd operator and adjoint."""
+    dims, Ls = (8, 8, 8, 6), 8     # A = 32 sites of one parity per z-plane
+    op, ref = make_pair(dims, Ls, 1.8, 0.02, 1.5, 0.5, "neff", 0.5, seed=86)
+    op.set_hop_config(prec, var, ns, sb)
+    op.set_sweep(prec, zblock)
+    assert op.sweep(prec) == zblock
+    x = ref.to_eo(inputs.gaussian_5d(dims, Ls, 87), 0)
+    for dag in (False, True):
+        got = to_np(op.apply(to_gpu(x), op="eo", prec=prec, dag=dag))
+        want = ref.d_pc(x, dag=dag)
+        assert rel(got, want) < TOL[prec], (dag, rel(got, want))
+        assert maxrel(got, want) < 10 * TOL[prec]
+    op.device_status()
+
+
+def test_sweep_argument_checks():
+    from paper_2602_14454_gb300 import dwf
+    op = dwf.Operator((8, 8, 8, 6), 8, 1.8, 0.02, 1.5, 0.5)
+    assert op.sweep("f32") == 0           # a whole t-slice fits the column budget: index order
+    for bad in (-2, 3, 8, 16):            # 3 does not divide Lz, 8 is Lz
+        with pytest.raises(dwf.DwfError):
+            op.set_sweep("f32", bad)
+    op2 = dwf.Operator((4, 2, 4, 4), 4, 1.8, 0.02, 1.5, 0.5)
+    with pytest.raises(dwf.DwfError):     # 1 z-plane = 4 sites: not a multiple of 32
+        op2.set_sweep("f32", 1)
+    op.set_sweep("f32", -1)
+    assert op.sweep("f32") == 0
