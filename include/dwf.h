@@ -286,14 +286,20 @@ long long dwf_launch_count(dwf_handle h);
  * tiles of 32/Ls sites (a window sweeping the lattice, see dwf_set_sweep) with
  * its own shared-memory links (staged one tile ahead) and mixing tile, and no
  * CTA barrier; there sb counts warps per CTA (1..4) and ns selects the
- * register budget (1: five CTAs of sb warps per SM, 2: four).  ns: slices per
- * thread for the other variants (1, 2 when it divides Ls, 4 for variant 5);
- * sb: sites per CTA.  -1 / 0 select the built-in defaults (FP32: variant 9
- * where it applies, else 0; FP16: 5; FP64: 0).  Variants differ only in the
- * order of the sums, except 5 (FP16 rounding of the projection).  Numbers 1,
- * 2, 6 and 8 are not used.
+ * register budget (1: five CTAs of sb warps per SM, 2: four); variant 10
+ * (FP32, dense mixing, Ls 8 or 16, no mixed y term; else variant 9) is
+ * variant 9 in CTAs of eight warps whose dense fifth-direction mixings run on
+ * the tensor cores: the CTA's hop results are the A operand of tcgen05 TF32
+ * products (rows = site and spinor component, K = slice; both operands split
+ * in two TF32 terms, FP32 accumulators in tensor memory), the epilogue reads
+ * them back row by row (ns and sb must be 0).  ns: slices per thread for the
+ * other variants (1, 2 when it divides Ls, 4 for variant 5); sb: sites per
+ * CTA.  -1 / 0 select the built-in defaults (FP32: variant 9 where it
+ * applies, else 0; FP16: 5; FP64: 0).  Variants differ only in the order of
+ * the sums, except 5 (FP16 rounding of the projection) and 10 (products of
+ * the TF32 terms).  Numbers 1, 2, 6 and 8 are not used.
  * Errors: DWF_EINVAL (NULL handle or pointer, bad prec, variant not -1, 0, 3,
- * 4, 5, 7 or 9, ns or sb outside the ranges above, sb making a CTA of more
+ * 4, 5, 7, 9 or 10, ns or sb outside the ranges above, sb making a CTA of more
  * than 256 threads). */
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb);
 int dwf_get_hop_config(dwf_handle h, int prec, int *variant, int *ns, int *sb);

@@ -598,8 +598,15 @@ long long dwf_launch_count(dwf_handle h) { return h ? h->launches : 0; }
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb)
 {
     if (!h || prec < 0 || prec > 2) return dwf_set_error(DWF_EINVAL, "bad handle or precision");
-    if (variant < -1 || variant > 9 || variant == 1 || variant == 2 || variant == 6 || variant == 8)
-        return dwf_set_error(DWF_EINVAL, "variant must be -1, 0, 3, 4, 5, 7 or 9");
+    if (variant < -1 || variant > 10 || variant == 1 || variant == 2 || variant == 6 || variant == 8)
+        return dwf_set_error(DWF_EINVAL, "variant must be -1, 0, 3, 4, 5, 7, 9 or 10");
+    if (variant == 10) {   // no tiling parameters
+        if (ns != 0 || sb != 0) return dwf_set_error(DWF_EINVAL, "variant 10 takes ns 0 and sb 0");
+        h->hop_var[prec] = variant;
+        h->hop_ns[prec] = 0;
+        h->hop_sb[prec] = 0;
+        return DWF_OK;
+    }
     if (variant == 9) {   // sb counts warps per CTA (1..4), ns the register budget (1, 2)
         if (ns < 0 || ns > 2) return dwf_set_error(DWF_EINVAL, "variant 9 takes ns 0, 1 or 2");
         if (sb < 0 || sb > 4) return dwf_set_error(DWF_EINVAL, "variant 9 takes sb (warps per CTA) 0..4");
@@ -698,8 +705,9 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
     double best = 1e30;
     int bvar = -1, bns = 0, bsb = 0, bmix = 0;
     for (int mix = 0; mix <= 2; ++mix)
-        for (int var = 0; var <= 9; ++var)
+        for (int var = 0; var <= 10; ++var)
             for (int ns = 1; ns <= 4; ns *= 2) {
+                if (var == 10 && (prec != DWF_F32 || mix != 0 || (h->Ls != 8 && h->Ls != 16) || ns != 1)) continue;
                 if (mix == 1 && !h->fm.structured) continue;
                 if (mix == 2 && prec == DWF_F64) continue;
                 if (var == 1 || var == 2 || var == 6 || var == 8) continue;   // numbers not in use
@@ -713,11 +721,12 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
                 const int LsN = h->Ls / (var == 9 ? 1 : ns);
                 for (int threads = 64; threads <= 256; threads += 64) {
                     if (var == 9 && threads > 128) continue;
-                    const int sb = var == 9 ? threads / 32 : threads / LsN;   // variant 9: warps per CTA
-                    if (sb < 1 || LsN * sb > 256) continue;
+                    if (var == 10 && threads != 256) continue;   // fixed CTA of 8 warps
+                    const int sb = var == 10 ? 0 : var == 9 ? threads / 32 : threads / LsN;   // variant 9: warps per CTA
+                    if (var != 10 && (sb < 1 || LsN * sb > 256)) continue;
                     h->mixmode[prec] = mix;
                     h->hop_var[prec] = var;
-                    h->hop_ns[prec] = ns;
+                    h->hop_ns[prec] = var == 10 ? 0 : ns;
                     h->hop_sb[prec] = sb;
                     double us = 0, by = 0;
                     int rc = dwf_time_hop(h, prec, 10, 0, &us, &by, stream);
@@ -725,7 +734,7 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream)
                     if (us < best) {
                         best = us;
                         bvar = var;
-                        bns = ns;
+                        bns = var == 10 ? 0 : ns;
                         bsb = sb;
                         bmix = mix;
                     }

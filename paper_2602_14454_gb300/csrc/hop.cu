@@ -58,7 +58,16 @@ cudaError_t launch_hop_batch(int prec, bool dag, const HopArgs *tab, int nsys, c
 
 cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
 {
-    if (var < 0 || var > 9 || var == 1 || var == 2 || var == 6 || var == 8) var = hop_default_variant(prec);
+    if (var < 0 || var > 10 || var == 1 || var == 2 || var == 6 || var == 8) var = hop_default_variant(prec);
+    // variant 10 (variant 9 with the dense mixings on the tensor cores): FP32 fields, dense mixing,
+    // Ls 8 or 16, no mixed y term; else variant 9
+    if (var == 10) {
+        if (prec == DWF_F32 && a.mixmode == 0 && a.ymode != 2 && (a.Ls == 8 || a.Ls == 16))
+            return dag ? hop_launch_pd<DWF_F32, true>(a, 10, 0, 0, st) : hop_launch_pd<DWF_F32, false>(a, 10, 0, 0, st);
+        var = 9;
+        NS = 2;
+        SB = 4;
+    }
     // variants 7 and 9 need FP32/FP16 fields and dense mixing (9 also Ls dividing 32), else the default
     const bool v_ok = prec != DWF_F64 && a.mixmode == 0 && a.Ls % 4 == 0;
     const bool v9_ok = prec != DWF_F64 && (a.mixmode == 0 || a.mixmode == 1) && a.Ls % 4 == 0 && a.Ls <= 32 &&

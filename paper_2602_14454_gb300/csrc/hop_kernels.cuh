@@ -28,6 +28,7 @@
 #include <cstdint>
 
 #include "stencil.cuh"
+#include "tcgen05.cuh"
 
 namespace dwf {
 namespace {
@@ -1333,6 +1334,320 @@ __global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
     if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
 }
 
+
+// ---------------------------------------------------------------- variant 10
+// The hop of variant 9 (warp tiles of 32/Ls sites, each warp's links staged
+// in its own shared buffer one tile ahead) with the dense fifth-direction
+// mixings of the epilogue on the tensor cores.  Eight warps make a CTA step of
+// S = 8 (32/Ls) sites; their hop results become the A operand of a tcgen05
+// product, rows r = (site, component) (24 per site, 24 S = 384 rows = three
+// M = 128 blocks for Ls 16, six for Ls 8), K = slice t; B = [M_+ | M_-]
+// (N = 2 Ls) holds both chiralities' matrices, so D[r][chi Ls + s] =
+// sum_t M_chi[s][t] A[r][t] and each row keeps the half of its chirality.
+// Operands in two TF32 terms (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 level),
+// FP32 accumulators in tensor memory.  The epilogue reads D row by row
+// (tcgen05.ld: TMEM lane = row, so each thread holds one component of one site
+// for all Ls slices): the y addition, the r update, the norm and the stores
+// run in that transposed form with scalar loads and stores, which stay
+// coalesced because consecutive rows are consecutive components of a site.  A
+// second mixing (zmat, applied after the norm) stages the rows, now contiguous
+// along K (16-byte stores), as a new A operand for a second product.
+//
+// Against variant 9 the mixing leaves the SM's load/store path (variant 9
+// reads Ls rows of the site tile and of the matrix per output from shared
+// memory) for 24 scalar 4-byte shared stores per thread and tensor-memory
+// reads.  The staging stores are free of bank conflicts: K-groups are LBO =
+// 16 (rows/8) 8 + 16 bytes apart (4 banks), and the rows of the sites of one
+// warp are rotated within 8-row groups by 8/(32/Ls) per site (a permutation of
+// the site's 24 components, undone in the epilogue), so the sites of a warp
+// store into disjoint banks.
+//
+// Every mbarrier wait is bounded by %globaltimer (1 s) and its outcome made
+// uniform over the CTA; a CTA that gives up sets the error flag, waits
+// (bounded) for its committed MMAs, frees its tensor memory and leaves.
+constexpr int HT_WARPS = 8;
+
+struct HtGeom {
+    int Ls, spw, sites, rows, mblk, np, shift;
+    uint32_t lbo, a_bytes, b_lbo, b_bytes, tmem_cols;
+    uint32_t link_off, bar_off, smem;
+};
+
+__host__ __device__ inline HtGeom ht_geom(int Ls)
+{
+    HtGeom g;
+    g.Ls = Ls;
+    g.spw = 32 / Ls;
+    g.sites = HT_WARPS * g.spw;
+    g.rows = 24 * g.sites;
+    g.mblk = g.rows / 128;
+    g.np = 2 * Ls;
+    g.shift = 8 / g.spw;
+    g.lbo = (uint32_t)(g.rows / 8) * 128 + 16;
+    g.a_bytes = (uint32_t)(Ls / 4) * g.lbo;
+    g.b_lbo = (uint32_t)(g.np / 8) * 128;
+    g.b_bytes = (uint32_t)(Ls / 4) * g.b_lbo;
+    uint32_t c = 32;
+    while (c < (uint32_t)(g.mblk * g.np)) c *= 2;
+    g.tmem_cols = c;
+    g.link_off = 2 * g.a_bytes + 4 * g.b_bytes;   // A hi, A lo, B post hi / lo, B z hi / lo
+    g.bar_off = g.link_off + (uint32_t)(HT_WARPS * 2 * g.spw * LeanGeom<DWF_F32>::LINK_BYTES);
+    g.smem = g.bar_off + 16;
+    return g;
+}
+
+// variant 10 applies: FP32 fields, dense mixing mode, no mixed y term, Ls 8 or 16
+__host__ __device__ inline bool ht_applies(const HopArgs &a)
+{
+    return a.mixmode == 0 && a.ymode != 2 && (a.Ls == 8 || a.Ls == 16);
+}
+
+// the MMAs of one product: D = A B^T over every M block, committed to the mbarrier
+__device__ __forceinline__ void ht_issue(const HtGeom &g, uint32_t tbase, uint32_t sA, uint32_t sB, uint64_t *bar)
+{
+    const uint32_t idesc = idesc_tf32(g.np);
+    for (int mb = 0; mb < g.mblk; ++mb) {
+        const uint32_t d = tbase + (uint32_t)(mb * g.np);
+        for (int ks = 0; ks < g.Ls / 8; ++ks) {
+            const uint32_t ao = (uint32_t)ks * 2 * g.lbo + (uint32_t)mb * 16 * 128;
+            const uint32_t bo = (uint32_t)ks * 2 * g.b_lbo;
+            const uint64_t ah = smem_desc(sA + ao, g.lbo, 128), al = smem_desc(sA + g.a_bytes + ao, g.lbo, 128);
+            const uint64_t bh = smem_desc(sB + bo, g.b_lbo, 128), bl = smem_desc(sB + g.b_bytes + bo, g.b_lbo, 128);
+            mma_tf32(d, ah, bh, idesc, ks > 0);
+            mma_tf32(d, ah, bl, idesc, 1);
+            mma_tf32(d, al, bh, idesc, 1);
+        }
+    }
+    tc_commit(bar);
+}
+
+// every thread waits for the product; false on the whole CTA if any thread gave up
+__device__ __forceinline__ bool ht_wait(uint64_t *bar, uint32_t &phase)
+{
+    const bool ok = mbar_wait_bounded(smem_u32addr(bar), phase, 1000000000ull);
+    phase ^= 1u;
+    const bool all = !__syncthreads_or(!ok);
+    tc_fence_after();
+    return all;
+}
+
+// the row this thread reads in M block mb: site (CTA-local), component c, chirality
+struct HtRow {
+    int site, c, chi, wt, j;
+};
+__device__ __forceinline__ HtRow ht_row(const HtGeom &g, int mb, int warp, int lane)
+{
+    HtRow h;
+    const int R = mb * 128 + (warp & 3) * 32 + lane;
+    h.site = R / 24;
+    const int cp = R - h.site * 24;
+    h.wt = h.site / g.spw;
+    h.j = h.site - h.wt * g.spw;
+    h.c = (cp & ~7) | ((cp - g.shift * h.j) & 7);
+    h.chi = (h.c >> 1) & 1;
+    return h;
+}
+
+template <bool DAG, int LS>
+__global__ void __launch_bounds__(256, 2) hop_tc_kernel(const HopArgs a, const HtGeom g)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int LB = LeanGeom<DWF_F32>::LINK_BYTES;
+    constexpr int SPW = 32 / LS;
+    unsigned char *Ahi = smem_raw, *Alo = smem_raw + g.a_bytes;
+    unsigned char *Bm = smem_raw + 2 * g.a_bytes;   // post hi, post lo, z hi, z lo
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + g.bar_off);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j = lane / LS, s = lane - j * LS;
+    unsigned char *links = smem_raw + g.link_off + (size_t)warp * 2 * SPW * LB;
+
+    // B operands, B[n][t] = M_chi[n - chi Ls][t] (n = chi Ls + s), in two TF32 terms
+    {
+        const float *src[2] = {reinterpret_cast<const float *>(a.post), reinterpret_cast<const float *>(a.zmat)};
+        for (int m = 0; m < 2; ++m) {
+            if (!src[m]) continue;
+            for (int e = tid; e < g.np * LS; e += blockDim.x) {
+                const int n = e / LS, k = e - n * LS, chi = n / LS, so = n - chi * LS;
+                const float v = src[m][(chi * LS + k) * LS + so];
+                const float hi = tf32_hi(v);
+                const uint32_t off = kmaj_off(n, k, g.b_lbo);
+                *reinterpret_cast<float *>(Bm + (2 * m) * g.b_bytes + off) = hi;
+                *reinterpret_cast<float *>(Bm + (2 * m + 1) * g.b_bytes + off) = tf32_hi(v - hi);
+            }
+        }
+    }
+    if (warp == 0) tmem_alloc(tslot, g.tmem_cols);
+    if (tid == 0) mbar_init(bar, 1);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    const uint32_t sA = smem_u32addr(Ahi), sB = smem_u32addr(Bm);
+
+    const int nsteps = (a.Vh + g.sites - 1) / g.sites;
+    const int nwt = (a.Vh + SPW - 1) / SPW;
+    float nrm = 0.f;
+    uint32_t phase = 0;
+    bool failed = false;
+    int st = blockIdx.x;
+    {
+        const int wt = st * HT_WARPS + warp;
+        if (st < nsteps && wt < nwt) wa_issue_links<DWF_F32>(a.gauge, sweep_site(a, wt * SPW), min(SPW, a.Vh - wt * SPW), links, lane);
+    }
+    for (int k = 0; st < nsteps; ++k, st += gridDim.x) {
+        // ---- the hop of this warp's tile
+        const int wt = st * HT_WARPS + warp;
+        const bool active = wt * SPW + j < a.Vh;
+        const int site = active ? sweep_site(a, wt * SPW) + j : 0;
+        int n8[8];
+        if (active) {
+            const int4 *p = reinterpret_cast<const int4 *>(a.nbr + (size_t)site * 8);
+            const int4 q0 = __ldg(p), q1 = __ldg(p + 1);
+            n8[0] = q0.x; n8[1] = q0.y; n8[2] = q0.z; n8[3] = q0.w;
+            n8[4] = q1.x; n8[5] = q1.y; n8[6] = q1.z; n8[7] = q1.w;
+        }
+        cp_async_wait<0>();
+        __syncwarp();
+        {
+            const int sn = st + gridDim.x, wn = sn * HT_WARPS + warp;
+            if (sn < nsteps && wn < nwt)
+                wa_issue_links<DWF_F32>(a.gauge, sweep_site(a, wn * SPW), min(SPW, a.Vh - wn * SPW),
+                                        links + (size_t)((k + 1) & 1) * SPW * LB, lane);
+        }
+        float2 acc[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) acc[q] = make_float2(0.f, 0.f);
+        if (active) {
+            const unsigned char *lk = links + ((size_t)(k & 1) * SPW + j) * LB;
+            lean_dir<DWF_F32, DAG, 0>(acc, a.in, n8[0], s, LS, lk);
+            lean_dir<DWF_F32, DAG, 1>(acc, a.in, n8[1], s, LS, lk);
+            lean_dir<DWF_F32, DAG, 2>(acc, a.in, n8[2], s, LS, lk);
+            lean_dir<DWF_F32, DAG, 3>(acc, a.in, n8[3], s, LS, lk);
+            lean_dir<DWF_F32, DAG, 4>(acc, a.in, n8[4], s, LS, lk);
+            lean_dir<DWF_F32, DAG, 5>(acc, a.in, n8[5], s, LS, lk);
+            lean_dir<DWF_F32, DAG, 6>(acc, a.in, n8[6], s, LS, lk);
+            lean_dir<DWF_F32, DAG, 7>(acc, a.in, n8[7], s, LS, lk);
+        }
+        if (active && a.rin.v && a.xacc) {   // x += xalpha xdir, in the field layout
+            FieldRef xf;
+            xf.v = a.xacc;
+            const float2 xa = p_splat((float)(*a.xalpha));
+            float2 xv[12], dx[12];
+            ld_pairs_cs<DWF_F32>(xf, (size_t)site, s, LS, xv);
+            ld_pairs_cs<DWF_F32>(a.xdir, (size_t)site, s, LS, dx);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) xv[q] = p_fma(xa, dx[q], xv[q]);
+            st_pairs_cs<DWF_F32>(xf, (size_t)site, s, LS, xv);
+        }
+        // ---- stage: row (warp SPW + j) 24 + rotated component, K = s (inactive lanes: zeros)
+        {
+            const int rbase = (warp * SPW + j) * 24, sh = g.shift * j;
+            const uint32_t kofs = (uint32_t)(s >> 2) * g.lbo + (uint32_t)(s & 3) * 4;
+#pragma unroll
+            for (int c = 0; c < 24; ++c) {
+                const float v = (c & 1) ? acc[c >> 1].y : acc[c >> 1].x;
+                const int row = rbase + ((c & ~7) | ((c + sh) & 7));
+                const uint32_t off = kofs + (uint32_t)row * 16;
+                const float hi = tf32_hi(v);
+                *reinterpret_cast<float *>(Ahi + off) = hi;
+                *reinterpret_cast<float *>(Alo + off) = tf32_hi(v - hi);
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) ht_issue(g, tbase, sA, sB, bar);
+        if (!ht_wait(bar, phase)) {
+            failed = true;
+            break;
+        }
+        // ---- epilogue: this warp's rows of the product
+        const float *yv = reinterpret_cast<const float *>(a.y.v);
+        const float *rv = reinterpret_cast<const float *>(a.rin.v);
+        float *ov = reinterpret_cast<float *>(a.out.v);
+        const float nal = a.rin.v ? -(float)(*a.ralpha) : 0.f;
+        for (int mb = warp >> 2; mb < g.mblk; mb += 2) {
+            const HtRow h = ht_row(g, mb, warp, lane);
+            const int wt2 = st * HT_WARPS + h.wt;
+            const bool act = wt2 * SPW + h.j < a.Vh;
+            const size_t base = act ? ((size_t)(sweep_site(a, wt2 * SPW) + h.j) * LS) * 24 + h.c : 0;
+            uint32_t r[2 * LS];
+            tmem_ld<2 * LS>(tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mb * g.np), r);
+            float o[LS];
+#pragma unroll
+            for (int t = 0; t < LS; ++t) o[t] = __uint_as_float(h.chi ? r[LS + t] : r[t]);
+            if (act) {
+                if (a.ymode == 1)
+#pragma unroll
+                    for (int t = 0; t < LS; ++t) o[t] += __ldcs(yv + base + 24 * t);
+                if (rv)
+#pragma unroll
+                    for (int t = 0; t < LS; ++t) o[t] = fmaf(nal, o[t], __ldcs(rv + base + 24 * t));
+                if (a.red.op != RED_NONE)
+#pragma unroll
+                    for (int t = 0; t < LS; ++t) nrm = fmaf(o[t], o[t], nrm);
+            } else {
+#pragma unroll
+                for (int t = 0; t < LS; ++t) o[t] = 0.f;
+            }
+            if (a.zmat) {   // the row, now contiguous along K, as the next A operand
+                const int R = mb * 128 + (warp & 3) * 32 + lane;
+#pragma unroll
+                for (int q = 0; q < LS / 4; ++q) {
+                    float4 hi, lo;
+                    hi.x = tf32_hi(o[4 * q]);     lo.x = tf32_hi(o[4 * q] - hi.x);
+                    hi.y = tf32_hi(o[4 * q + 1]); lo.y = tf32_hi(o[4 * q + 1] - hi.y);
+                    hi.z = tf32_hi(o[4 * q + 2]); lo.z = tf32_hi(o[4 * q + 2] - hi.z);
+                    hi.w = tf32_hi(o[4 * q + 3]); lo.w = tf32_hi(o[4 * q + 3] - hi.w);
+                    const uint32_t off = (uint32_t)q * g.lbo + (uint32_t)R * 16;
+                    *reinterpret_cast<float4 *>(Ahi + off) = hi;
+                    *reinterpret_cast<float4 *>(Alo + off) = lo;
+                }
+            } else if (act) {
+#pragma unroll
+                for (int t = 0; t < LS; ++t) __stcs(ov + base + 24 * t, o[t]);
+            }
+        }
+        if (a.zmat) {
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) ht_issue(g, tbase, sA, sB + 2 * g.b_bytes, bar);
+            if (!ht_wait(bar, phase)) {
+                failed = true;
+                break;
+            }
+            for (int mb = warp >> 2; mb < g.mblk; mb += 2) {
+                const HtRow h = ht_row(g, mb, warp, lane);
+                const int wt2 = st * HT_WARPS + h.wt;
+                const bool act = wt2 * SPW + h.j < a.Vh;
+                uint32_t r[2 * LS];
+                tmem_ld<2 * LS>(tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mb * g.np), r);
+                if (act) {
+                    const size_t base = ((size_t)(sweep_site(a, wt2 * SPW) + h.j) * LS) * 24 + h.c;
+#pragma unroll
+                    for (int t = 0; t < LS; ++t) __stcs(ov + base + 24 * t, __uint_as_float(h.chi ? r[LS + t] : r[t]));
+                }
+            }
+        }
+        tc_fence_before();   // this step's tensor-memory reads before the next step's MMAs
+    }
+    cp_async_wait<0>();
+    if (failed) {
+        if (tid == 0 && a.err) atomicOr(a.err, 1);
+        // the last committed product may still run: let it finish before the memory is freed (bounded)
+        mbar_wait_bounded(smem_u32addr(bar), phase ^ 1u, 1000000000ull);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tbase, g.tmem_cols);
+    if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
+}
+
 // ---------------------------------------------------------------- launch
 template <int P>
 size_t direct_smem(int Ls, int SB)
@@ -1525,9 +1840,42 @@ cudaError_t launch_wa(const HopArgs &a, int nw, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <bool DAG, int LS>
+cudaError_t launch_tc(const HopArgs &a, cudaStream_t st)
+{
+    static unsigned long long optin = 0;
+    const HtGeom g = ht_geom(LS);
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = smem_optin(hop_tc_kernel<DAG, LS>, 200 * 1024, optin)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_tc_kernel<DAG, LS>, 32 * HT_WARPS, g.smem)) !=
+        cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // tensor memory: 512 columns per SM
+    if (per_sm * (int)g.tmem_cols > 512) per_sm = 512 / (int)g.tmem_cols;
+    const int nsteps = (a.Vh + g.sites - 1) / g.sites;
+    int grid = nsm * per_sm;
+    if (grid > nsteps) grid = nsteps;
+    hop_tc_kernel<DAG, LS><<<grid, 32 * HT_WARPS, g.smem, st>>>(a, g);
+    return cudaGetLastError();
+}
+
 template <int P, bool DAG>
 cudaError_t launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
 {
+    // variant 10: variant 9 with the dense mixings on the tensor cores (FP32 fields, Ls 8 or 16,
+    // no mixed y term; else variant 9)
+    if constexpr (P == DWF_F32) {
+        if (var == 10 && ht_applies(a)) return a.Ls == 16 ? launch_tc<DAG, 16>(a, st) : launch_tc<DAG, 8>(a, st);
+    }
+    if (var == 10) {
+        var = 9;
+        NS = 2;
+        SB = 4;
+    }
     // variant 9: warp-autonomous (FP32 and FP16 fields, dense mixing, Ls dividing 32 and a
     // multiple of 4); SB = warps per CTA, NS selects the register budget (1: 5 CTAs of 4
     // warps per SM, 2: 4)

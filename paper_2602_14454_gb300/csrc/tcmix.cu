@@ -29,6 +29,7 @@
 #include <cstdint>
 
 #include "fields.cuh"
+#include "tcgen05.cuh"
 
 namespace dwf {
 namespace {
@@ -37,8 +38,6 @@ constexpr int TC_SITES = 16;            // sites per tile
 constexpr int TC_ROWS = TC_SITES * 24;  // A rows per tile (3 x 128)
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_A_LBO = (TC_ROWS / 8) * 128 + 16;   // padded: the K-groups start 4 banks apart
-
-__host__ __device__ constexpr int tc_pad8(int x) { return (x + 7) & ~7; }
 
 struct TcGeom {
     int Ls, Lsp, Kp, Np;     // Lsp = pad8(Ls) = K extent, Np = 2 Lsp = N
@@ -64,73 +63,6 @@ __host__ __device__ inline TcGeom tc_geom(int Ls)
     // A hi, A lo, B hi, B lo, then 16 bytes for the mbarrier and the TMEM address
     g.smem = (size_t)2 * g.a_bytes + (size_t)2 * g.b_bytes + 16;
     return g;
-}
-
-// byte offset of element (row, k) in a canonical no-swizzle K-major operand
-__device__ __forceinline__ uint32_t kmaj_off(int row, int k, uint32_t lbo)
-{
-    return (uint32_t)(k >> 2) * lbo + (uint32_t)(row >> 3) * 128u + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 3) * 4u;
-}
-
-__device__ __forceinline__ uint32_t smem_u32addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ float tf32_hi(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-// shared memory matrix descriptor of tcgen05 (no swizzle)
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
-{
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// instruction descriptor: D FP32, A and B TF32, both K-major, M = 128, N = n
-__device__ __forceinline__ uint32_t idesc_tf32(int n)
-{
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int accum)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t globaltimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// wait for phase `parity` of the mbarrier, at most `ns` nanoseconds
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t ns)
-{
-    const uint64_t t0 = globaltimer();
-    while (!mbar_try(bar, parity))
-        if (globaltimer() - t0 > ns) return false;
-    return true;
 }
 
 template <int P>

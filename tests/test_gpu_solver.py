@@ -173,13 +173,13 @@ def test_c2_mixed_precision_full_size(c2_setup, prec, form, alpha):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16"])
-@pytest.mark.parametrize("var", [0, 7, 9])
+@pytest.mark.parametrize("var", [0, 7, 9, 10])
 def test_c1_solve_with_persistent_hops(c1_reference, prec, var):
     """The solver with the persistent hop variants in every inner launch,
     including the reducing and residual epilogues."""
     U, b4, b5, x5_ref, x4_ref = c1_reference
     op, ref = make_pair(C1["dims"], C1["Ls"], C1["M0"], C1["mf"], C1["b"], C1["c"], "neff", 0.5, U=U)
-    op.set_hop_config(prec, var, 1, 0)
+    op.set_hop_config(prec, var, 0 if var == 10 else 1, 0)
     x5, st = op.solve(to_gpu(b5), inner_prec=prec, tol=1e-10)
     x5 = to_np(x5)
     assert rel(ref.apply(x5), b5) <= 1e-10
