@@ -1345,22 +1345,23 @@ __global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
 // (N = 2 Ls) holds both chiralities' matrices, so D[r][chi Ls + s] =
 // sum_t M_chi[s][t] A[r][t] and each row keeps the half of its chirality.
 // Operands in two TF32 terms (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 level),
-// FP32 accumulators in tensor memory.  The epilogue reads D row by row
-// (tcgen05.ld: TMEM lane = row, so each thread holds one component of one site
-// for all Ls slices): the y addition, the r update, the norm and the stores
-// run in that transposed form with scalar loads and stores, which stay
-// coalesced because consecutive rows are consecutive components of a site.  A
-// second mixing (zmat, applied after the norm) stages the rows, now contiguous
-// along K (16-byte stores), as a new A operand for a second product.
+// FP32 accumulators in tensor memory.  Each warp reads its rows back
+// (tcgen05.ld: TMEM lane = row) into a shared tile in the field's own order
+// (site, colour-re/im group g, slice, spin; rows of one (site, g) 4 Ls + 4
+// floats apart, so the 32 rows of a warp write 32 distinct banks); the
+// epilogue then runs per (site, s) as in variant 9 (16-byte field loads and
+// stores, the y addition, the r update, the fused norm).  A second mixing
+// (zmat, after the norm) stages the result again as an A operand for a second
+// product.
 //
 // Against variant 9 the mixing leaves the SM's load/store path (variant 9
 // reads Ls rows of the site tile and of the matrix per output from shared
-// memory) for 24 scalar 4-byte shared stores per thread and tensor-memory
-// reads.  The staging stores are free of bank conflicts: K-groups are LBO =
-// 16 (rows/8) 8 + 16 bytes apart (4 banks), and the rows of the sites of one
-// warp are rotated within 8-row groups by 8/(32/Ls) per site (a permutation of
-// the site's 24 components, undone in the epilogue), so the sites of a warp
-// store into disjoint banks.
+// memory) for 48 scalar 4-byte shared stores per thread (A hi and lo), 24 per
+// row read back and six 16-byte reads.  The A stores are free of bank
+// conflicts: K-groups are LBO = 16 (rows/8) 8 + 16 bytes apart (4 banks), and
+// the rows of the sites of one warp are rotated within 8-row groups by
+// 8/(32/Ls) per site (a permutation of the site's 24 components, undone when
+// the rows are read back), so the sites of a warp store into disjoint banks.
 //
 // Every mbarrier wait is bounded by %globaltimer (1 s) and its outcome made
 // uniform over the CTA; a CTA that gives up sets the error flag, waits
@@ -1368,9 +1369,9 @@ __global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
 constexpr int HT_WARPS = 8;
 
 struct HtGeom {
-    int Ls, spw, sites, rows, mblk, np, shift;
+    int Ls, spw, sites, rows, mblk, np, shift, dstride;
     uint32_t lbo, a_bytes, b_lbo, b_bytes, tmem_cols;
-    uint32_t link_off, bar_off, smem;
+    uint32_t d_off, link_off, bar_off, smem;
 };
 
 __host__ __device__ inline HtGeom ht_geom(int Ls)
@@ -1383,6 +1384,7 @@ __host__ __device__ inline HtGeom ht_geom(int Ls)
     g.mblk = g.rows / 128;
     g.np = 2 * Ls;
     g.shift = 8 / g.spw;
+    g.dstride = 4 * Ls + 4;   // floats between the (site, g) rows of the read-back tile
     g.lbo = (uint32_t)(g.rows / 8) * 128 + 16;
     g.a_bytes = (uint32_t)(Ls / 4) * g.lbo;
     g.b_lbo = (uint32_t)(g.np / 8) * 128;
@@ -1390,7 +1392,8 @@ __host__ __device__ inline HtGeom ht_geom(int Ls)
     uint32_t c = 32;
     while (c < (uint32_t)(g.mblk * g.np)) c *= 2;
     g.tmem_cols = c;
-    g.link_off = 2 * g.a_bytes + 4 * g.b_bytes;   // A hi, A lo, B post hi / lo, B z hi / lo
+    g.d_off = 2 * g.a_bytes + 4 * g.b_bytes;   // A hi, A lo, B post hi / lo, B z hi / lo, read-back tile
+    g.link_off = g.d_off + (uint32_t)(g.sites * 6 * g.dstride * 4);
     g.bar_off = g.link_off + (uint32_t)(HT_WARPS * 2 * g.spw * LeanGeom<DWF_F32>::LINK_BYTES);
     g.smem = g.bar_off + 16;
     return g;
@@ -1431,21 +1434,53 @@ __device__ __forceinline__ bool ht_wait(uint64_t *bar, uint32_t &phase)
     return all;
 }
 
-// the row this thread reads in M block mb: site (CTA-local), component c, chirality
-struct HtRow {
-    int site, c, chi, wt, j;
-};
-__device__ __forceinline__ HtRow ht_row(const HtGeom &g, int mb, int warp, int lane)
+// A operand rows of one (site, s) thread: row (local site) 24 + rotated component, K = s
+template <int LS>
+__device__ __forceinline__ void ht_stage_a(const HtGeom &g, unsigned char *Ahi, int lsite, int j, int s,
+                                           const float2 *v)
 {
-    HtRow h;
-    const int R = mb * 128 + (warp & 3) * 32 + lane;
-    h.site = R / 24;
-    const int cp = R - h.site * 24;
-    h.wt = h.site / g.spw;
-    h.j = h.site - h.wt * g.spw;
-    h.c = (cp & ~7) | ((cp - g.shift * h.j) & 7);
-    h.chi = (h.c >> 1) & 1;
-    return h;
+    const int rbase = lsite * 24, sh = g.shift * j;
+    const uint32_t kofs = (uint32_t)(s >> 2) * g.lbo + (uint32_t)(s & 3) * 4;
+    unsigned char *Alo = Ahi + g.a_bytes;
+#pragma unroll
+    for (int c = 0; c < 24; ++c) {
+        const float x = (c & 1) ? v[c >> 1].y : v[c >> 1].x;
+        const int row = rbase + ((c & ~7) | ((c + sh) & 7));
+        const uint32_t off = kofs + (uint32_t)row * 16;   // 8-row groups 128 bytes apart: 16 bytes per row
+        const float hi = tf32_hi(x);
+        *reinterpret_cast<float *>(Ahi + off) = hi;
+        *reinterpret_cast<float *>(Alo + off) = tf32_hi(x - hi);
+    }
+}
+
+// this warp's rows of the product -> the read-back tile D[(site 6 + g) dstride + 4 s + spin]
+template <int LS>
+__device__ __forceinline__ void ht_read_back(const HtGeom &g, uint32_t tbase, float *D, int warp, int lane)
+{
+    for (int mb = warp >> 2; mb < g.mblk; mb += 2) {
+        const int R = mb * 128 + (warp & 3) * 32 + lane;
+        const int site = R / 24, cp = R - site * 24, j = site % g.spw;
+        const int c = (cp & ~7) | ((cp - g.shift * j) & 7);
+        const int chi = (c >> 1) & 1;
+        uint32_t r[2 * LS];
+        tmem_ld<2 * LS>(tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mb * g.np), r);
+        float *row = D + (size_t)(site * 6 + (c >> 2)) * g.dstride + (c & 3);
+#pragma unroll
+        for (int t = 0; t < LS; ++t) row[4 * t] = __uint_as_float(chi ? r[LS + t] : r[t]);
+    }
+}
+
+// the (site, s) thread's 24 components from the read-back tile
+template <int LS>
+__device__ __forceinline__ void ht_take(const HtGeom &g, const float *D, int lsite, int s, float2 *o)
+{
+    const float4 *p = reinterpret_cast<const float4 *>(D + (size_t)lsite * 6 * g.dstride) + s;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float4 q = p[(size_t)k * (g.dstride / 4)];
+        o[2 * k] = make_float2(q.x, q.y);
+        o[2 * k + 1] = make_float2(q.z, q.w);
+    }
 }
 
 template <bool DAG, int LS>
@@ -1454,12 +1489,14 @@ __global__ void __launch_bounds__(256, 2) hop_tc_kernel(const HopArgs a, const H
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int LB = LeanGeom<DWF_F32>::LINK_BYTES;
     constexpr int SPW = 32 / LS;
-    unsigned char *Ahi = smem_raw, *Alo = smem_raw + g.a_bytes;
+    unsigned char *Ahi = smem_raw;
     unsigned char *Bm = smem_raw + 2 * g.a_bytes;   // post hi, post lo, z hi, z lo
+    float *D = reinterpret_cast<float *>(smem_raw + g.d_off);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + g.bar_off);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j = lane / LS, s = lane - j * LS;
+    const int lsite = warp * SPW + j;
     unsigned char *links = smem_raw + g.link_off + (size_t)warp * 2 * SPW * LB;
 
     // B operands, B[n][t] = M_chi[n - chi Ls][t] (n = chi Ls + s), in two TF32 terms
@@ -1494,7 +1531,8 @@ __global__ void __launch_bounds__(256, 2) hop_tc_kernel(const HopArgs a, const H
     int st = blockIdx.x;
     {
         const int wt = st * HT_WARPS + warp;
-        if (st < nsteps && wt < nwt) wa_issue_links<DWF_F32>(a.gauge, sweep_site(a, wt * SPW), min(SPW, a.Vh - wt * SPW), links, lane);
+        if (st < nsteps && wt < nwt)
+            wa_issue_links<DWF_F32>(a.gauge, sweep_site(a, wt * SPW), min(SPW, a.Vh - wt * SPW), links, lane);
     }
     for (int k = 0; st < nsteps; ++k, st += gridDim.x) {
         // ---- the hop of this warp's tile
@@ -1530,7 +1568,7 @@ __global__ void __launch_bounds__(256, 2) hop_tc_kernel(const HopArgs a, const H
             lean_dir<DWF_F32, DAG, 6>(acc, a.in, n8[6], s, LS, lk);
             lean_dir<DWF_F32, DAG, 7>(acc, a.in, n8[7], s, LS, lk);
         }
-        if (active && a.rin.v && a.xacc) {   // x += xalpha xdir, in the field layout
+        if (active && a.rin.v && a.xacc) {   // x += xalpha xdir (independent of the hop)
             FieldRef xf;
             xf.v = a.xacc;
             const float2 xa = p_splat((float)(*a.xalpha));
@@ -1541,20 +1579,8 @@ __global__ void __launch_bounds__(256, 2) hop_tc_kernel(const HopArgs a, const H
             for (int q = 0; q < 12; ++q) xv[q] = p_fma(xa, dx[q], xv[q]);
             st_pairs_cs<DWF_F32>(xf, (size_t)site, s, LS, xv);
         }
-        // ---- stage: row (warp SPW + j) 24 + rotated component, K = s (inactive lanes: zeros)
-        {
-            const int rbase = (warp * SPW + j) * 24, sh = g.shift * j;
-            const uint32_t kofs = (uint32_t)(s >> 2) * g.lbo + (uint32_t)(s & 3) * 4;
-#pragma unroll
-            for (int c = 0; c < 24; ++c) {
-                const float v = (c & 1) ? acc[c >> 1].y : acc[c >> 1].x;
-                const int row = rbase + ((c & ~7) | ((c + sh) & 7));
-                const uint32_t off = kofs + (uint32_t)row * 16;
-                const float hi = tf32_hi(v);
-                *reinterpret_cast<float *>(Ahi + off) = hi;
-                *reinterpret_cast<float *>(Alo + off) = tf32_hi(v - hi);
-            }
-        }
+        // ---- o = post . acc on the tensor cores (inactive lanes stage zeros)
+        ht_stage_a<LS>(g, Ahi, lsite, j, s, acc);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -1564,54 +1590,36 @@ __global__ void __launch_bounds__(256, 2) hop_tc_kernel(const HopArgs a, const H
             failed = true;
             break;
         }
-        // ---- epilogue: this warp's rows of the product
-        const float *yv = reinterpret_cast<const float *>(a.y.v);
-        const float *rv = reinterpret_cast<const float *>(a.rin.v);
-        float *ov = reinterpret_cast<float *>(a.out.v);
-        const float nal = a.rin.v ? -(float)(*a.ralpha) : 0.f;
-        for (int mb = warp >> 2; mb < g.mblk; mb += 2) {
-            const HtRow h = ht_row(g, mb, warp, lane);
-            const int wt2 = st * HT_WARPS + h.wt;
-            const bool act = wt2 * SPW + h.j < a.Vh;
-            const size_t base = act ? ((size_t)(sweep_site(a, wt2 * SPW) + h.j) * LS) * 24 + h.c : 0;
-            uint32_t r[2 * LS];
-            tmem_ld<2 * LS>(tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mb * g.np), r);
-            float o[LS];
+        ht_read_back<LS>(g, tbase, D, warp, lane);
+        tc_fence_before();
+        __syncthreads();
+        float2 o[12];
+        ht_take<LS>(g, D, lsite, s, o);
+        // ---- the epilogue of variant 9 without its mixings
+        if (active && a.ymode == 1) {
+            float2 y[12];
+            ld_pairs_cs<DWF_F32>(a.y, (size_t)site, s, LS, y);
 #pragma unroll
-            for (int t = 0; t < LS; ++t) o[t] = __uint_as_float(h.chi ? r[LS + t] : r[t]);
-            if (act) {
-                if (a.ymode == 1)
-#pragma unroll
-                    for (int t = 0; t < LS; ++t) o[t] += __ldcs(yv + base + 24 * t);
-                if (rv)
-#pragma unroll
-                    for (int t = 0; t < LS; ++t) o[t] = fmaf(nal, o[t], __ldcs(rv + base + 24 * t));
-                if (a.red.op != RED_NONE)
-#pragma unroll
-                    for (int t = 0; t < LS; ++t) nrm = fmaf(o[t], o[t], nrm);
-            } else {
-#pragma unroll
-                for (int t = 0; t < LS; ++t) o[t] = 0.f;
-            }
-            if (a.zmat) {   // the row, now contiguous along K, as the next A operand
-                const int R = mb * 128 + (warp & 3) * 32 + lane;
-#pragma unroll
-                for (int q = 0; q < LS / 4; ++q) {
-                    float4 hi, lo;
-                    hi.x = tf32_hi(o[4 * q]);     lo.x = tf32_hi(o[4 * q] - hi.x);
-                    hi.y = tf32_hi(o[4 * q + 1]); lo.y = tf32_hi(o[4 * q + 1] - hi.y);
-                    hi.z = tf32_hi(o[4 * q + 2]); lo.z = tf32_hi(o[4 * q + 2] - hi.z);
-                    hi.w = tf32_hi(o[4 * q + 3]); lo.w = tf32_hi(o[4 * q + 3] - hi.w);
-                    const uint32_t off = (uint32_t)q * g.lbo + (uint32_t)R * 16;
-                    *reinterpret_cast<float4 *>(Ahi + off) = hi;
-                    *reinterpret_cast<float4 *>(Alo + off) = lo;
-                }
-            } else if (act) {
-#pragma unroll
-                for (int t = 0; t < LS; ++t) __stcs(ov + base + 24 * t, o[t]);
-            }
+            for (int q = 0; q < 12; ++q) o[q] = p_add(o[q], y[q]);
         }
-        if (a.zmat) {
+        if (active && a.rin.v) {
+            const float2 nal = p_splat((float)-(*a.ralpha));
+            float2 r[12];
+            ld_pairs_cs<DWF_F32>(a.rin, (size_t)site, s, LS, r);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) o[q] = p_fma(nal, o[q], r[q]);
+        }
+        if (active && a.red.op != RED_NONE) {
+            float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) s2 = p_fma(o[q], o[q], s2);
+            nrm += s2.x + s2.y;
+        }
+        if (a.zmat) {   // out = zmat . o, a second product
+            if (!active)
+#pragma unroll
+                for (int q = 0; q < 12; ++q) o[q] = make_float2(0.f, 0.f);
+            ht_stage_a<LS>(g, Ahi, lsite, j, s, o);
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
@@ -1621,20 +1629,12 @@ __global__ void __launch_bounds__(256, 2) hop_tc_kernel(const HopArgs a, const H
                 failed = true;
                 break;
             }
-            for (int mb = warp >> 2; mb < g.mblk; mb += 2) {
-                const HtRow h = ht_row(g, mb, warp, lane);
-                const int wt2 = st * HT_WARPS + h.wt;
-                const bool act = wt2 * SPW + h.j < a.Vh;
-                uint32_t r[2 * LS];
-                tmem_ld<2 * LS>(tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mb * g.np), r);
-                if (act) {
-                    const size_t base = ((size_t)(sweep_site(a, wt2 * SPW) + h.j) * LS) * 24 + h.c;
-#pragma unroll
-                    for (int t = 0; t < LS; ++t) __stcs(ov + base + 24 * t, __uint_as_float(h.chi ? r[LS + t] : r[t]));
-                }
-            }
+            ht_read_back<LS>(g, tbase, D, warp, lane);
+            tc_fence_before();
+            __syncthreads();
+            ht_take<LS>(g, D, lsite, s, o);
         }
-        tc_fence_before();   // this step's tensor-memory reads before the next step's MMAs
+        if (active) st_pairs_cs<DWF_F32>(a.out, (size_t)site, s, LS, o);
     }
     cp_async_wait<0>();
     if (failed) {

@@ -5,6 +5,7 @@
     python -m paper_2602_14454_gb300.workloads large      # 32^3x64, Ls 16: mixed precision vs FP64 CG
     python -m paper_2602_14454_gb300.workloads alpha      # 16^3x32, Ls 16: iterations against alpha
     python -m paper_2602_14454_gb300.workloads alpha --spectrum   # ... and the condition number
+    python -m paper_2602_14454_gb300.workloads delta      # 32^3x64: reliable-update threshold against time
 
 Every run uses the seeded generators of ``inputs``; times are wall clock
 around the library call after a synchronisation (device work included).
@@ -186,12 +187,38 @@ def run_alpha(args):
                       "check_every": args.check, "scan": rows}), flush=True)
 
 
+def run_delta(args):
+    """Time to solution against the reliable-update threshold delta (the inner
+    residual falls by delta between two FP64 true-residual recomputations): a
+    smaller delta means fewer FP64 hops and more drift of the iterated residual."""
+    import torch
+    from . import dwf, inputs
+    name = "c2_16^3x32_ls16_mobius" if args.small else "c5_32^3x64_ls16_mobius"
+    w = inputs.WORKLOADS[name]
+    op = dwf.Operator(w["dims"], w["Ls"], w["M0"], w["mf"], w["b"], w["c"], form="neff", alpha=w["alpha"])
+    op.set_gauge(_links(w))
+    b4 = torch.from_numpy(inputs.gaussian_4d(w["dims"], w["src_seed"])).cuda()
+    b5 = op.source_5d(b4)
+    rows = []
+    for delta in (0.3, 0.1, 0.03, 0.01, 0.003, 0.001):
+        op.solve(b5, inner_prec=args.inner, delta=delta)
+        _sync()
+        t0 = time.perf_counter()
+        _, s = op.solve(b5, inner_prec=args.inner, delta=delta)
+        _sync()
+        rows.append({"delta": delta, "seconds": time.perf_counter() - t0, "iterations": s["iterations"],
+                     "reliable_updates": s["reliable_updates"], "d_applications": s["d_applications"],
+                     "true_residual": s["true_residual"]})
+    print(json.dumps({"workload": name, "inner_precision": args.inner, "scan": rows}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["batch", "learned", "large", "alpha"])
+    ap.add_argument("what", choices=["batch", "learned", "large", "alpha", "delta"])
     ap.add_argument("--inner", default="f32", choices=["f16", "f32", "f64"])
     ap.add_argument("--wave", type=int, default=0)
-    ap.add_argument("--small", action="store_true", help="batch: 8^3x16 instead of 24^3x48")
+    ap.add_argument("--small", action="store_true",
+                    help="batch: 8^3x16 instead of 24^3x48; delta: 16^3x32 instead of 32^3x64")
     ap.add_argument("--sequential", type=int, default=0,
                     help="batch: also solve this many of the systems one by one (-1: all) and compare")
     ap.add_argument("--ntrain", type=int, default=256)
@@ -205,7 +232,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     from . import build
     build.build()
-    {"batch": run_batch, "learned": run_learned, "large": run_large, "alpha": run_alpha}[args.what](args)
+    {"batch": run_batch, "learned": run_learned, "large": run_large, "alpha": run_alpha,
+     "delta": run_delta}[args.what](args)
     return 0
 
 
