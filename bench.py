@@ -141,7 +141,7 @@ def peaks():
         return None
 
 
-HOP_SOURCES = ("hop.cu", "hop_kernels.cuh", "stencil.cuh", "fields.cuh")
+HOP_SOURCES = ("hop.cu", "hop_kernels.cuh", "stencil.cuh", "fields.cuh", "tcgen05.cuh", "dwf_internal.h")
 
 
 def hop_source_key():
@@ -152,9 +152,10 @@ def hop_source_key():
     return h.hexdigest()[:16]
 
 
-def hop_traffic(prec, workload):
+def hop_traffic(prec, workload, variant, sweep):
     """DRAM bytes per hop launch from the committed ncu summary, if it was taken
-    from the current hop kernel sources on this workload (else null)."""
+    from the current hop kernel sources on this workload with the same variant
+    and sweep order (else null)."""
     path = os.path.join(ROOT, "profiles", "hop_traffic.json")
     try:
         d = json.load(open(path))
@@ -162,6 +163,8 @@ def hop_traffic(prec, workload):
         return None
     e = d.get(workload, {}).get(prec)
     if not e or e.get("hop_sources_sha256_16") != hop_source_key():
+        return None
+    if e.get("variant") != variant or e.get("sweep_zblock") != sweep:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -282,7 +285,8 @@ def timed_solves(op, b4, n, **kw):
 
 
 KERNEL_NAMES = {0: "hop_kernel", 3: "hop_sweep_kernel", 4: "hop_block_kernel", 5: "hop_kernel_occ (FP16 projection)",
-                7: "hop_lean_kernel", 9: "hop_wa_kernel (warp-autonomous)"}
+                7: "hop_lean_kernel", 9: "hop_wa_kernel (warp-autonomous)",
+                10: "hop_tc_kernel (warp tiles, tcgen05 mixing)"}
 
 
 def hop_roofline(op, prec, Ls, peak, reps=30):
@@ -294,7 +298,7 @@ def hop_roofline(op, prec, Ls, peak, reps=30):
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "us_per_launch": us, "algorithmic_bytes_per_launch": nbytes,
             "kernel": "%s<%s> variant %d (even-odd hop + fused Ls mixing)" % (KERNEL_NAMES.get(var, "hop"), prec, var),
-            "config": {"variant": var, "ns": ns, "sb": sb}}
+            "config": {"variant": var, "ns": ns, "sb": sb, "sweep_zblock": op.sweep(prec)}}
 
 
 def main():
@@ -367,7 +371,7 @@ def main():
     pk = peaks()
     peak = pk["hbm_gbs"] if pk else 6800.0
     roof = hop_roofline(op, args.inner, w["Ls"], peak)
-    roof["traffic"] = hop_traffic(args.inner, args.workload)
+    roof["traffic"] = hop_traffic(args.inner, args.workload, roof["config"]["variant"], roof["config"]["sweep_zblock"])
     roof["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs (burst copy), of measured" if pk
                            else "fallback 6.8 TB/s")
     iteration = op.time_iteration(args.inner, reps=10, flush_l2=True) if args.inner != "f64" else None

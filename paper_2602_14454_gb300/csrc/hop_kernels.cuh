@@ -1849,6 +1849,15 @@ cudaError_t launch_tc(const HopArgs &a, cudaStream_t st)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = smem_optin(hop_tc_kernel<DAG, LS>, 200 * 1024, optin)) != cudaSuccess) return e;
+    // two CTAs of about 100 KB per SM: ask for the largest shared-memory carveout (the
+    // driver's default split admitted one)
+    static bool carve = false;
+    if (!carve) {
+        if ((e = cudaFuncSetAttribute(hop_tc_kernel<DAG, LS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+            return e;
+        carve = true;
+    }
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_tc_kernel<DAG, LS>, 32 * HT_WARPS, g.smem)) !=
         cudaSuccess)
