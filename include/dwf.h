@@ -304,16 +304,18 @@ long long dwf_launch_count(dwf_handle h);
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb);
 int dwf_get_hop_config(dwf_handle h, int prec, int *variant, int *ns, int *sb);
 
-/* Sweep order of the hop kernels in precision prec (variants 0, 5 and 9): the
- * sites of one parity are taken in columns of zblock z-planes, each column
+/* Sweep order of the hop kernels in precision prec (variants 0, 5, 9 and 10):
+ * the sites of one parity are taken in columns of zblock z-planes, each column
  * t-slice by t-slice, so that the two reads of a site as the -t and +t
  * neighbour of others lie 2 zblock (Lx/2) Ly sites apart and the field between
  * them stays in L2 on lattices whose t-slices exceed it; the z-planes at a
- * column's border are read twice.  zblock: -1 automatic (the default: the
- * largest divisor of Lz whose column band of input, output and links of one
- * parity stays within 16 MiB; index order when a whole t-slice does), 0 index
- * order, else a divisor of Lz below Lz with zblock (Lx/2) Ly a multiple of 32.
- * The order changes only the order of the fused norms' partial sums.
+ * column's border are read twice.  zblock: -1 or 0 index order (the default),
+ * -2 the largest divisor of Lz whose column band of input, output and links of
+ * one parity stays within 16 MiB (index order when a whole t-slice does), else
+ * a divisor of Lz below Lz with zblock (Lx/2) Ly a multiple of 32.  On
+ * 32^3x64, Ls 16, columns of 8 planes cut the FP32 hop's DRAM reads by a fifth
+ * but not its time (it is bound by the SMs' load/store path).  The order
+ * changes only the order of the fused norms' partial sums.
  * Errors: DWF_EINVAL (NULL handle or pointer, bad prec or zblock). */
 int dwf_set_sweep(dwf_handle h, int prec, int zblock);
 int dwf_get_sweep(dwf_handle h, int prec, int *zblock);

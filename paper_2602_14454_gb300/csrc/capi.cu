@@ -117,15 +117,24 @@ FieldRef dwf_ctx::field(const std::string &name, int prec, cudaError_t *err)
 // --------------------------------------------------------------- helpers
 namespace dwf_detail {
 
-// Columns of z-planes for the hop's sweep order (HopArgs::zblock): the largest
-// divisor Bz of Lz whose column band of Bz z-planes (input and output spinors of
-// one parity and their links) stays within 16 MiB, so that the 2 Bz planes read
-// between a site's two t-neighbour reads fit in L2 with room to spare; 0 (index
-// order) while a whole t-slice fits.  Runs of Bz A sites are kept multiples of 32
-// so that no hop tile straddles two of them.
+// Columns of z-planes for the hop's sweep order (HopArgs::zblock): index order
+// unless dwf_set_sweep chose columns.  Measured at 32^3x64, Ls 16 (FP32 variant 9):
+// columns of 8 z-planes cut the hop's DRAM reads from 5.11 to 4.02 GB per launch but
+// made it 2-5 % slower, since the kernel is bound by the SMs' load/store path, not by
+// DRAM; the FP16 direct hop lost 4.6 %.
 static int sweep_zblock(const dwf_ctx *h, int prec)
 {
-    if (h->sweep_zb[prec] >= 0) return h->sweep_zb[prec];
+    return h->sweep_zb[prec] > 0 ? h->sweep_zb[prec] : 0;
+}
+
+// The automatic choice of dwf_set_sweep(h, prec, -2): the largest divisor Bz of Lz
+// whose column band of Bz z-planes (input and output spinors of one parity and their
+// links) stays within 16 MiB, so that the 2 Bz planes read between a site's two
+// t-neighbour reads fit in L2 with room to spare; 0 (index order) while a whole
+// t-slice fits.  Runs of Bz A sites are kept multiples of 32 so that no hop tile
+// straddles two of them.
+static int sweep_zblock_auto(const dwf_ctx *h, int prec)
+{
     const long long A = (long long)(h->dims[0] / 2) * h->dims[1];
     const long long w = prec == DWF_F64 ? 8 : prec == DWF_F32 ? 4 : 2;
     const long long plane = A * ((long long)h->Ls * 24 * w * 2 + 8 * 18 * w);
@@ -630,9 +639,10 @@ int dwf_set_sweep(dwf_handle h, int prec, int zblock)
 {
     if (!h || prec < 0 || prec > 2) return dwf_set_error(DWF_EINVAL, "bad handle or precision");
     const long long A = (long long)(h->dims[0] / 2) * h->dims[1];
-    if (zblock < -1 || (zblock > 0 && (zblock >= h->dims[2] || h->dims[2] % zblock || (zblock * A) % 32)))
-        return dwf_set_error(DWF_EINVAL, "zblock must be -1, 0 or a divisor of Lz below Lz with zblock Lx/2 Ly a multiple of 32");
-    h->sweep_zb[prec] = zblock;
+    if (zblock < -2 || (zblock > 0 && (zblock >= h->dims[2] || h->dims[2] % zblock || (zblock * A) % 32)))
+        return dwf_set_error(DWF_EINVAL,
+                             "zblock must be -2, -1, 0 or a divisor of Lz below Lz with zblock Lx/2 Ly a multiple of 32");
+    h->sweep_zb[prec] = zblock == -2 ? sweep_zblock_auto(h, prec) : zblock;
     return DWF_OK;
 }
 

@@ -1859,12 +1859,24 @@ cudaError_t launch_tc(const HopArgs &a, cudaStream_t st)
         carve = true;
     }
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_tc_kernel<DAG, LS>, 32 * HT_WARPS, g.smem)) !=
-        cudaSuccess)
-        return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    // tensor memory: 512 columns per SM
-    if (per_sm * (int)g.tmem_cols > 512) per_sm = 512 / (int)g.tmem_cols;
+    // CTAs per SM from the shared memory and the register file (the occupancy query answered
+    // one CTA where two fit); more CTAs than fit would only wait for a slot (no CTA waits on
+    // another), and two take 256 of the 512 tensor-memory columns
+    {
+        cudaFuncAttributes fa;
+        int smem_sm = 0, resv = 0, regs_sm = 0;
+        if ((e = cudaFuncGetAttributes(&fa, hop_tc_kernel<DAG, LS>)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+            return e;
+        if ((e = cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess)
+            return e;
+        const int by_smem = smem_sm / (int)(g.smem + fa.sharedSizeBytes + resv);
+        const int by_regs = regs_sm / (fa.numRegs * 32 * HT_WARPS);
+        per_sm = by_smem < by_regs ? by_smem : by_regs;
+        if (per_sm > 2) per_sm = 2;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    }
     const int nsteps = (a.Vh + g.sites - 1) / g.sites;
     int grid = nsm * per_sm;
     if (grid > nsteps) grid = nsteps;

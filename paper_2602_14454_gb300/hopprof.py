@@ -29,7 +29,7 @@ def main(argv=None):
     ap.add_argument("--alpha", type=float, default=0.5)
     ap.add_argument("--config", default=None, help="variant,ns,sb (default: the library's choice)")
     ap.add_argument("--mix", type=int, default=None, help="fifth-direction mixing mode")
-    ap.add_argument("--sweep", type=int, default=None, help="z-planes per sweep column (0: index order)")
+    ap.add_argument("--sweep", type=int, default=None, help="z-planes per sweep column (0: index order, -2: automatic)")
     ap.add_argument("--iteration", action="store_true", help="time the launches of one CG iteration")
     ap.add_argument("--time-mix", action="store_true", help="time one stand-alone mixing launch (mode --mix)")
     args = ap.parse_args(argv)

@@ -344,3 +344,10 @@ def test_sweep_argument_checks():
         op2.set_sweep("f32", 1)
     op.set_sweep("f32", -1)
     assert op.sweep("f32") == 0
+    op.set_sweep("f32", -2)               # automatic: a t-slice of this lattice fits the budget
+    assert op.sweep("f32") == 0
+    w = (32, 32, 32, 8)
+    op3 = dwf.Operator(w, 16, 1.8, 0.02, 1.5, 0.5)
+    op3.set_sweep("f32", -2)              # a z-plane pair of 32x32 at Ls 16 in FP32: 1.9 MB
+    assert op3.sweep("f32") == 8
+    assert op3.sweep("f16") == 0
