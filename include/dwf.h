@@ -143,7 +143,9 @@ typedef struct {
     int inner_prec;     /* DWF_F64 (plain FP64 CG), DWF_F32 or DWF_F16; the
                            outer residuals and corrections are always FP64     */
     double delta;       /* reliable-update trigger: recompute the FP64 residual
-                           when the inner residual fell by this factor; 0.1    */
+                           when the inner residual fell by this factor; 0 (the
+                           default) takes 1e-3 for FP32 and 0.1 for FP16 and
+                           FP64 inner iterations                               */
     int check_every;    /* inner iterations between host convergence checks;
                            they are captured as one CUDA graph; default 16     */
     int use_graph;      /* 1: replay the inner iterations as a CUDA graph       */

@@ -336,7 +336,7 @@ def test_sweep_argument_checks():
     from paper_2602_14454_gb300 import dwf
     op = dwf.Operator((8, 8, 8, 6), 8, 1.8, 0.02, 1.5, 0.5)
     assert op.sweep("f32") == 0           # a whole t-slice fits the column budget: index order
-    for bad in (-2, 3, 8, 16):            # 3 does not divide Lz, 8 is Lz
+    for bad in (-3, 3, 8, 16):            # 3 does not divide Lz, 8 is Lz
         with pytest.raises(dwf.DwfError):
             op.set_sweep("f32", bad)
     op2 = dwf.Operator((4, 2, 4, 4), 4, 1.8, 0.02, 1.5, 0.5)

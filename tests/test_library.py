@@ -57,7 +57,7 @@ def test_param_struct_layout_matches_header(libpath):
     from paper_2602_14454_gb300 import dwf
     p = dwf.default_params()
     assert p.tol == 1e-10 and p.max_iter == 20000 and p.inner_prec == dwf.F32
-    assert p.check_every == 16 and p.use_graph == 1 and abs(p.delta - 0.1) < 1e-15
+    assert p.check_every == 16 and p.use_graph == 1 and p.delta == 0.0   # 0: by the inner precision
 
 
 def test_product_path_does_not_import_oracle():
