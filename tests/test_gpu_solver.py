@@ -186,6 +186,26 @@ def test_c1_solve_with_persistent_hops(c1_reference, prec, var):
     assert rel(ref.project_4d(x5), x4_ref) < 1e-9
 
 
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("var", [9, 10, 11])
+def test_ls16_solve_with_warp_tile_hops(prec, var):
+    """Ls 16 (variants 10 and 11 run there; FP16 takes variant 9 for 10): the
+    solve reaches the oracle-checked residual and the oracle's 4D solution."""
+    dims, Ls = (4, 4, 4, 8), 16
+    U = inputs.random_links(dims, 0.5, 1012)
+    op, ref = make_pair(dims, Ls, 1.8, 0.05, 1.5, 0.5, "neff", 0.5, U=U)
+    b4 = inputs.gaussian_4d(dims, 2012)
+    b5 = ref.source_5d(b4)
+    op.set_hop_config(prec, var, 0 if var == 10 else 2, 0)
+    x5, st = op.solve(to_gpu(b5), inner_prec=prec, tol=1e-10)
+    x5 = to_np(x5)
+    assert rel(ref.apply(x5), b5) <= 1e-10
+    op2, _ = make_pair(dims, Ls, 1.8, 0.05, 1.5, 0.5, "standard", 1.0, U=U)
+    x5s, _ = op2.solve(op2.source_5d(to_gpu(b4)), inner_prec="f64", tol=1e-11)
+    assert rel(ref.project_4d(x5), to_np(op2.project_4d(x5s))) < 1e-9
+    op.device_status()
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_second_even_odd_form_is_alpha_independent(prec):
     """CG on eq. (another_even-odd_linear_equation), D' y_e = b'_e with
