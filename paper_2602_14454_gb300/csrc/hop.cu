@@ -82,8 +82,9 @@ cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int var, int NS, in
     }
     // variants 7 and 9 need FP32/FP16 fields and dense mixing (9 also Ls dividing 32), else the default
     const bool v_ok = prec != DWF_F64 && a.mixmode == 0 && a.Ls % 4 == 0;
-    const bool v9_ok = prec != DWF_F64 && (a.mixmode == 0 || a.mixmode == 1) && a.Ls % 4 == 0 && a.Ls <= 32 &&
-                       32 % a.Ls == 0;   // variant 9 also runs the structured mixing (by warp shuffles)
+    const bool v9_ok = prec != DWF_F64 &&
+                       ((a.mixmode == 0 && a.Ls % 4 == 0 && a.Ls <= 32 && 32 % a.Ls == 0) ||
+                        (a.mixmode == 1 && (a.Ls == 8 || a.Ls == 16)));   // structured mixing: chains in registers
     if ((var == 7 && !v_ok) || (var == 9 && !v9_ok)) {
         var = prec == DWF_F16 ? 5 : 0;
         SB = 0;

@@ -1009,13 +1009,20 @@ __global__ void __launch_bounds__(256, MINB) hop_lean_kernel(const HopArgs a)
 template <int P>
 __host__ __device__ constexpr size_t wa_warp_bytes(int Ls)
 {
-    return (size_t)2 * (32 / Ls) * LeanGeom<P>::LINK_BYTES + (size_t)(32 / Ls) * lean_site_stride(Ls) * sizeof(float2);
+    return (size_t)2 * (32 / Ls) * LeanGeom<P>::LINK_BYTES + (size_t)(32 / Ls) * (Ls * 14 + 12) * sizeof(float2);
 }
 __host__ __device__ constexpr int wa_mat_row(int Ls) { return ((Ls / 4) & 1) ? Ls : Ls + 4; }
+// the CTA's front area: the three dense matrices, or the three structured programs
+// (at most 2048 bytes, checked where they are defined)
+__host__ __device__ constexpr size_t wa_front_bytes(int Ls)
+{
+    return (size_t)3 * 2 * Ls * wa_mat_row(Ls) * sizeof(float) > 2048 ? (size_t)3 * 2 * Ls * wa_mat_row(Ls) * sizeof(float)
+                                                                      : 2048;
+}
 template <int P>
 __host__ __device__ constexpr size_t wa_cta_bytes(int Ls, int nwarps)
 {
-    return (size_t)3 * 2 * Ls * wa_mat_row(Ls) * sizeof(float) + (size_t)nwarps * wa_warp_bytes<P>(Ls);
+    return wa_front_bytes(Ls) + (size_t)nwarps * wa_warp_bytes<P>(Ls);
 }
 
 // o += sum_t M[chi][s][t] tile(t) over the rows of one site; M row-major with
@@ -1060,103 +1067,175 @@ __device__ __forceinline__ void wa_mix(const float *M, const float2 *site_tile, 
     }
 }
 
-// Structured fifth-direction mixing (MixProg, dwf_internal.h) in registers:
-// the Ls slices of a site sit on Ls consecutive lanes, so the chain along s
-// is a warp segment of width Ls.  x <- d1 x; A5^-1 by its recurrence
-// x_u = w_u + kappa x_{u-1} (w = x / alpha0, x_{-1} = -m x_last) written as a
-// decaying inclusive prefix scan y_u = sum_{t<=u} kappa^(u-t) w_t (log2 Ls
-// shuffle steps) followed by x_u = y_u - m kappa^(u+1) corner y_last; the
-// shift (s0 + s1 K) x with one indexed shuffle (the corner -m at the chain's
-// start); x <- d2 x.  u is the position along the chain (s, or Ls - 1 - s
-// when K reads s + 1).  Pairs k even are the P_+ chirality, odd the P_-.
-__device__ __forceinline__ void scan_mix(const MixProg<float> *pg, float2 *o, int s, int Ls)
+// Structured fifth-direction mixing (MixProg, dwf_internal.h) by chains: one
+// chain = one real component of one site over its Ls slices.  The warp's hop
+// results sit in its tile (rows of 28 floats per slice); each lane takes whole
+// chains (the 24 (32/Ls) chains of a warp tile, 32 at a time) into registers,
+// applies x <- d1 x, A5^-1 by its recurrence x_u = w_u + kappa x_{u-1}
+// (w = x / alpha0, x_{-1} = -m x_last: a backward sum for x_last, then one
+// forward pass), the shift (s0 + s1 K) x (the corner -m at the chain's start)
+// and x <- d2 x, and writes the chain back; u is the position along the chain
+// (s, or Ls - 1 - s when K reads s + 1).  Per chain element that is one 4-byte
+// shared load and one store, against Ls 16-byte broadcast reads per output for
+// the dense form.  Chains c = lane + 32 r all have component k = c mod 24 of
+// the same chirality, (lane >> 1) & 1, since 24 and 32 are multiples of 4.
+// The sites of a warp tile lie wc_site_stride floats apart: 24 banks on, so
+// the 32 chains a warp loads at once (24 components of one site, 8 of the
+// next) hit distinct banks.
+__host__ __device__ constexpr int wc_site_stride(int Ls) { return Ls * 14 + 12; }   // float2
+
+// a program in shared memory with the chirality-interleaved d vectors
+struct WcProg {
+    int inv, shift, up[2], d1one, d2one;
+    float s0, s1, a0inv, kappa, mneg, corner;
+    float d1[LS_MAX][2], d2[LS_MAX][2];
+};
+static_assert(3 * sizeof(WcProg) <= 2048, "the programs exceed the CTA's front area");
+
+__device__ __forceinline__ void wc_load_prog(WcProg *dst, const MixProg<float> *src, int Ls, int tid, int nt)
 {
-    const unsigned full = 0xffffffffu;
-#pragma unroll
-    for (int chi = 0; chi < 2; ++chi) {
-        const bool up = pg->up[chi] != 0;
-        const int u = up ? Ls - 1 - s : s;
-        const float d1 = pg->d1[chi][s], d2 = pg->d2[chi][s];
-#pragma unroll
-        for (int k = chi; k < 12; k += 2) o[k] = p_mul(o[k], p_splat(d1));
-        if (pg->inv) {
-            const float a0inv = pg->a0inv;
-#pragma unroll
-            for (int k = chi; k < 12; k += 2) o[k] = p_mul(o[k], p_splat(a0inv));
-            float kd = pg->kappa;
-            for (int d = 1; d < Ls; d <<= 1) {
-                const float2 kk = p_splat(u >= d ? kd : 0.f);
-#pragma unroll
-                for (int k = chi; k < 12; k += 2) {
-                    float2 t;
-                    t.x = up ? __shfl_down_sync(full, o[k].x, d, Ls) : __shfl_up_sync(full, o[k].x, d, Ls);
-                    t.y = up ? __shfl_down_sync(full, o[k].y, d, Ls) : __shfl_up_sync(full, o[k].y, d, Ls);
-                    o[k] = p_fma(kk, t, o[k]);
-                }
-                kd *= kd;
+    if (tid == 0) {
+        dst->inv = src->inv;
+        dst->shift = src->shift;
+        dst->up[0] = src->up[0];
+        dst->up[1] = src->up[1];
+        dst->s0 = src->s0;
+        dst->s1 = src->s1;
+        dst->a0inv = src->a0inv;
+        dst->kappa = src->kappa;
+        dst->mneg = src->mneg;
+        dst->corner = src->corner;
+        int o1 = 1, o2 = 1;
+        for (int c = 0; c < 2; ++c)
+            for (int s = 0; s < Ls; ++s) {
+                o1 &= src->d1[c][s] == 1.f;
+                o2 &= src->d2[c][s] == 1.f;
             }
-            float kp = pg->kappa;   // kappa^(u+1)
-            for (int e = 0; e < u; ++e) kp *= pg->kappa;
-            const float2 c = p_splat(pg->mneg * pg->corner * kp);
-            const int last = up ? 0 : Ls - 1;
-#pragma unroll
-            for (int k = chi; k < 12; k += 2) {
-                float2 yl;
-                yl.x = __shfl_sync(full, o[k].x, last, Ls);
-                yl.y = __shfl_sync(full, o[k].y, last, Ls);
-                o[k] = p_fma(c, yl, o[k]);
-            }
-        }
-        if (pg->shift) {
-            const int src = up ? (s + 1 == Ls ? 0 : s + 1) : (s == 0 ? Ls - 1 : s - 1);
-            const float2 a = p_splat(pg->s0), b = p_splat(pg->s1 * (u == 0 ? pg->mneg : 1.f));
-#pragma unroll
-            for (int k = chi; k < 12; k += 2) {
-                float2 t;
-                t.x = __shfl_sync(full, o[k].x, src, Ls);
-                t.y = __shfl_sync(full, o[k].y, src, Ls);
-                o[k] = p_fma(b, t, p_mul(a, o[k]));
-            }
-        }
-#pragma unroll
-        for (int k = chi; k < 12; k += 2) o[k] = p_mul(o[k], p_splat(d2));
+        dst->d1one = o1;
+        dst->d2one = o2;
+    }
+    for (int e = tid; e < 2 * Ls; e += nt) {
+        const int c = e / Ls, s = e - c * Ls;
+        dst->d1[s][c] = src->d1[c][s];
+        dst->d2[s][c] = src->d2[c][s];
     }
 }
 
-// the epilogue with the structured mixings in registers (every lane of the warp calls it)
-template <int P>
-__device__ __forceinline__ float wa_epilogue_scan(const HopArgs &a, const float2 *acc, int s, int site, bool active)
+// the program applied to every chain of the warp's tile, in place (d1 is
+// applied as the chain is loaded, d2 as it is stored)
+template <int LS>
+__device__ __forceinline__ void wc_chains(const WcProg *pg, float *tile, int lane)
 {
-    const int Ls = a.Ls;
-    const MixProg<float> *pp = reinterpret_cast<const MixProg<float> *>(a.post_prog);
-    if (active && a.rin.v && a.xacc) {
+    constexpr int NCH = (32 / LS) * 24;
+    constexpr int RS = 2 * LEAN_ROW;   // floats between slices
+    const int chi = (lane >> 1) & 1;
+    const bool up = pg->up[chi] != 0;
+    const bool o1 = pg->d1one != 0, o2 = pg->d2one != 0;
+    const float kappa = pg->kappa, a0inv = pg->a0inv, mneg = pg->mneg, s0 = pg->s0, s1 = pg->s1;
+#pragma unroll 1
+    for (int c = lane; c < NCH; c += 32) {
+        const int jj = c / 24, k = c - jj * 24;
+        float *b = tile + (size_t)jj * 2 * wc_site_stride(LS) + k;
+        float v[LS];
+#pragma unroll
+        for (int u = 0; u < LS; ++u) {
+            const int sl = up ? LS - 1 - u : u;
+            v[u] = b[sl * RS];
+            if (!o1) v[u] *= pg->d1[sl][chi];
+        }
+        if (pg->inv) {
+            float acc = 0.f;
+#pragma unroll
+            for (int u = 0; u < LS; ++u) acc = fmaf(kappa, acc, v[u]);
+            float prev = mneg * (acc * a0inv * pg->corner);
+#pragma unroll
+            for (int u = 0; u < LS; ++u) {
+                const float w = fmaf(v[u], a0inv, kappa * prev);
+                prev = w;
+                v[u] = w;
+            }
+            if (pg->shift) {
+                float prevs = mneg * v[LS - 1];
+#pragma unroll
+                for (int u = 0; u < LS; ++u) {
+                    const float tt = v[u];
+                    v[u] = fmaf(s0, tt, s1 * prevs);
+                    prevs = tt;
+                }
+            }
+        } else if (pg->shift) {
+            float prevs = mneg * v[LS - 1];
+#pragma unroll
+            for (int u = 0; u < LS; ++u) {
+                const float tt = v[u];
+                v[u] = fmaf(s0, tt, s1 * prevs);
+                prevs = tt;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < LS; ++u) {
+            const int sl = up ? LS - 1 - u : u;
+            b[sl * RS] = o2 ? v[u] : v[u] * pg->d2[sl][chi];
+        }
+    }
+}
+
+__device__ __forceinline__ void wc_take(const float2 *row, float2 *o)
+{
+    const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const float4 v = r4[q];
+        o[2 * q] = make_float2(v.x, v.y);
+        o[2 * q + 1] = make_float2(v.z, v.w);
+    }
+}
+
+// the epilogue of hop_epilogue_core with the structured mixings by chains
+// (every lane of the warp calls it; progs: post, y, z)
+template <int P, int LS>
+__device__ __forceinline__ float wc_epilogue(const HopArgs &a, const float2 *acc, float2 *tile, const WcProg *progs,
+                                             int j, int s, int site, bool active, int lane)
+{
+    float2 *row = tile + (size_t)j * wc_site_stride(LS) + (size_t)s * LEAN_ROW;
+    float *tf = reinterpret_cast<float *>(tile);
+    if (active && a.rin.v && a.xacc) {   // independent of the hop: first, while few registers are live
         FieldRef xf;
         xf.v = a.xacc;
         const float2 xa = p_splat((float)(*a.xalpha));
         float2 xv[12], dx[12];
-        ld_pairs_cs<DWF_F32>(xf, (size_t)site, s, Ls, xv);
-        ld_pairs_cs<P>(a.xdir, (size_t)site, s, Ls, dx);
+        ld_pairs_cs<DWF_F32>(xf, (size_t)site, s, LS, xv);
+        ld_pairs_cs<P>(a.xdir, (size_t)site, s, LS, dx);
 #pragma unroll
         for (int k = 0; k < 12; ++k) xv[k] = p_fma(xa, dx[k], xv[k]);
-        st_pairs_cs<DWF_F32>(xf, (size_t)site, s, Ls, xv);
+        st_pairs_cs<DWF_F32>(xf, (size_t)site, s, LS, xv);
     }
+    lean_put(row, acc);   // inactive lanes put zeros
+    __syncwarp();
+    wc_chains<LS>(progs, tf, lane);
+    __syncwarp();
     float2 o[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) o[k] = acc[k];
-    scan_mix(pp, o, s, Ls);
+    wc_take(row, o);
     if (a.ymode != 0) {
         float2 y[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) y[k] = make_float2(0.f, 0.f);
-        if (active) ld_pairs_cs<P>(a.y, (size_t)site, s, Ls, y);
-        if (a.ymode == 2) scan_mix(reinterpret_cast<const MixProg<float> *>(a.y_prog), y, s, Ls);
+        if (active) ld_pairs_cs<P>(a.y, (size_t)site, s, LS, y);
+        if (a.ymode == 2) {
+            __syncwarp();
+            lean_put(row, y);
+            __syncwarp();
+            wc_chains<LS>(progs + 1, tf, lane);
+            __syncwarp();
+            wc_take(row, y);
+        }
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[k] = p_add(o[k], y[k]);
     }
     if (active && a.rin.v) {
         const float2 nal = p_splat((float)-(*a.ralpha));
         float2 r[12];
-        ld_pairs_cs<P>(a.rin, (size_t)site, s, Ls, r);
+        ld_pairs_cs<P>(a.rin, (size_t)site, s, LS, r);
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[k] = p_fma(nal, o[k], r[k]);
     }
@@ -1167,8 +1246,15 @@ __device__ __forceinline__ float wa_epilogue_scan(const HopArgs &a, const float2
         for (int k = 0; k < 12; ++k) s2 = p_fma(o[k], o[k], s2);
         nrm = s2.x + s2.y;
     }
-    if (a.zmat) scan_mix(reinterpret_cast<const MixProg<float> *>(a.z_prog), o, s, Ls);
-    if (active) st_pairs_cs<P>(a.out, (size_t)site, s, Ls, o);
+    if (a.zmat) {
+        __syncwarp();
+        lean_put(row, o);
+        __syncwarp();
+        wc_chains<LS>(progs + 2, tf, lane);
+        __syncwarp();
+        wc_take(row, o);
+    }
+    if (active) st_pairs_cs<P>(a.out, (size_t)site, s, LS, o);
     return nrm;
 }
 
@@ -1272,7 +1358,16 @@ __global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
     const int j = lane / Ls, s = lane - (lane / Ls) * Ls;
     const int MR = wa_mat_row(Ls), msz = 2 * Ls * MR;
     float *mats = reinterpret_cast<float *>(smem_raw);
-    {
+    WcProg *progs = reinterpret_cast<WcProg *>(smem_raw);   // the structured programs (MIX 1) in the same place
+
+    if constexpr (MIX == 1) {
+        const MixProg<float> *src[3] = {reinterpret_cast<const MixProg<float> *>(a.post_prog),
+                                        reinterpret_cast<const MixProg<float> *>(a.y_prog),
+                                        reinterpret_cast<const MixProg<float> *>(a.z_prog)};
+        for (int m = 0; m < 3; ++m)
+            if (src[m] && (m != 1 || a.ymode == 2) && (m != 2 || a.zmat))
+                wc_load_prog(progs + m, src[m], Ls, threadIdx.x, blockDim.x);
+    } else {
         const float *src[3] = {reinterpret_cast<const float *>(a.post),
                                a.ymode == 2 ? reinterpret_cast<const float *>(a.ymat) : nullptr,
                                reinterpret_cast<const float *>(a.zmat)};
@@ -1284,7 +1379,7 @@ __global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
             }
         }
     }
-    unsigned char *wbase = smem_raw + (size_t)3 * msz * sizeof(float) + (size_t)warp * wa_warp_bytes<P>(Ls);
+    unsigned char *wbase = smem_raw + wa_front_bytes(Ls) + (size_t)warp * wa_warp_bytes<P>(Ls);
     unsigned char *links = wbase;
     float2 *tile = reinterpret_cast<float2 *>(wbase + (size_t)2 * SPW * LeanGeom<P>::LINK_BYTES);
     float2 *site_tile = tile + (size_t)j * lean_site_stride(Ls);
@@ -1325,10 +1420,12 @@ __global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
             lean_dir<P, DAG, 6>(acc, a.in, n8[6], s, Ls, lk);
             lean_dir<P, DAG, 7>(acc, a.in, n8[7], s, Ls, lk);
         }
-        if constexpr (MIX == 1)
-            nrm += wa_epilogue_scan<P>(a, acc, s, site, active);
-        else
+        if constexpr (MIX == 1) {
+            if (Ls == 16) nrm += wc_epilogue<P, 16>(a, acc, tile, progs, j, s, site, active, lane);
+            else nrm += wc_epilogue<P, 8>(a, acc, tile, progs, j, s, site, active, lane);   // Ls 8 (launch_pd)
+        } else {
             nrm += wa_epilogue<P>(a, acc, site_tile, mats, s, site, active);
+        }
     }
     cp_async_wait<0>();
     if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
@@ -2156,8 +2253,8 @@ cudaError_t launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st
     if constexpr (P != DWF_F64) {
         if (var == 9 && a.mixmode == 0 && a.Ls <= 32 && 32 % a.Ls == 0 && a.Ls % 4 == 0)
             return NS == 2 ? launch_wa<P, DAG, 4, 0>(a, SB, st) : launch_wa<P, DAG, 5, 0>(a, SB, st);
-        // structured mixing by warp shuffles (no mixing tile)
-        if (var == 9 && a.mixmode == 1 && a.Ls <= 32 && 32 % a.Ls == 0 && a.Ls % 4 == 0)
+        // structured mixing by chains in registers (Ls 8 and 16)
+        if (var == 9 && a.mixmode == 1 && (a.Ls == 8 || a.Ls == 16))
             return NS == 2 ? launch_wa<P, DAG, 4, 1>(a, SB, st) : launch_wa<P, DAG, 5, 1>(a, SB, st);
     }
     if (var == 9) var = P == DWF_F16 ? 5 : 0;
