@@ -174,7 +174,8 @@ cudaError_t launch_mix_m(const MixArgs &a, cudaStream_t st)
 template <int P>
 cudaError_t launch_mix_t(const MixArgs &a, cudaStream_t st)
 {
-    return a.mixmode == 1 ? launch_mix_m<P, 1>(a, st) : launch_mix_m<P, 0>(a, st);
+    // FP32/FP16: a banded matrix takes the dense form's three-row path (faster than its program)
+    return a.mixmode == 1 && (P == DWF_F64 || !a.band) ? launch_mix_m<P, 1>(a, st) : launch_mix_m<P, 0>(a, st);
 }
 
 template <int P, int MIX>
@@ -193,7 +194,8 @@ cudaError_t launch_cg_update_m(const CgUpdateArgs &a, cudaStream_t st)
 template <int P>
 cudaError_t launch_cg_update_t(const CgUpdateArgs &a, cudaStream_t st)
 {
-    return a.mixmode == 1 ? launch_cg_update_m<P, 1>(a, st) : launch_cg_update_m<P, 0>(a, st);
+    return a.mixmode == 1 && (P == DWF_F64 || !a.band) ? launch_cg_update_m<P, 1>(a, st)
+                                                       : launch_cg_update_m<P, 0>(a, st);
 }
 
 template <int P, int MIX>
@@ -214,8 +216,8 @@ cudaError_t launch_cg_update_batch_m(const CgUpdateArgs *tab, int nsys, const Cg
 template <int P>
 cudaError_t launch_cg_update_batch_t(const CgUpdateArgs *tab, int nsys, const CgUpdateArgs &a0, cudaStream_t st)
 {
-    return a0.mixmode == 1 ? launch_cg_update_batch_m<P, 1>(tab, nsys, a0, st)
-                           : launch_cg_update_batch_m<P, 0>(tab, nsys, a0, st);
+    return a0.mixmode == 1 && (P == DWF_F64 || !a0.band) ? launch_cg_update_batch_m<P, 1>(tab, nsys, a0, st)
+                                                         : launch_cg_update_batch_m<P, 0>(tab, nsys, a0, st);
 }
 
 // ------------------------------------------------------------------ packing
