@@ -611,8 +611,8 @@ long long dwf_launch_count(dwf_handle h) { return h ? h->launches : 0; }
 int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb)
 {
     if (!h || prec < 0 || prec > 2) return dwf_set_error(DWF_EINVAL, "bad handle or precision");
-    if (variant < -1 || variant > 11 || variant == 1 || variant == 2 || variant == 6 || variant == 8)
-        return dwf_set_error(DWF_EINVAL, "variant must be -1, 0, 3, 4, 5, 7, 9, 10 or 11");
+    if (variant < -1 || variant > 10 || variant == 1 || variant == 2 || variant == 6 || variant == 8)
+        return dwf_set_error(DWF_EINVAL, "variant must be -1, 0, 3, 4, 5, 7, 9 or 10");
     if (variant == 10) {   // no tiling parameters
         if (ns != 0 || sb != 0) return dwf_set_error(DWF_EINVAL, "variant 10 takes ns 0 and sb 0");
         h->hop_var[prec] = variant;
@@ -620,9 +620,9 @@ int dwf_set_hop_config(dwf_handle h, int prec, int variant, int ns, int sb)
         h->hop_sb[prec] = 0;
         return DWF_OK;
     }
-    if (variant == 9 || variant == 11) {   // sb counts warps per CTA (1..4), ns the register budget (1, 2)
-        if (ns < 0 || ns > 2) return dwf_set_error(DWF_EINVAL, "variants 9 and 11 take ns 0, 1 or 2");
-        if (sb < 0 || sb > 4) return dwf_set_error(DWF_EINVAL, "variants 9 and 11 take sb (warps per CTA) 0..4");
+    if (variant == 9) {   // sb counts warps per CTA (1..4), ns the register budget (1, 2)
+        if (ns < 0 || ns > 2) return dwf_set_error(DWF_EINVAL, "variant 9 takes ns 0, 1 or 2");
+        if (sb < 0 || sb > 4) return dwf_set_error(DWF_EINVAL, "variant 9 takes sb (warps per CTA) 0..4");
         h->hop_var[prec] = variant;
         h->hop_ns[prec] = ns;
         h->hop_sb[prec] = sb;

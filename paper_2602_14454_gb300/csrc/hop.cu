@@ -58,19 +58,7 @@ cudaError_t launch_hop_batch(int prec, bool dag, const HopArgs *tab, int nsys, c
 
 cudaError_t launch_hop(int prec, bool dag, const HopArgs &a, int var, int NS, int SB, cudaStream_t st)
 {
-    if (var < 0 || var > 11 || var == 1 || var == 2 || var == 6 || var == 8) var = hop_default_variant(prec);
-    // variant 11 (variant 9 with two warp tiles per step): FP32/FP16 fields, dense mixing, Ls 16 or 32
-    if (var == 11) {
-        if (prec != DWF_F64 && a.mixmode == 0 && (a.Ls == 16 || a.Ls == 32)) {
-            if (SB <= 0 || SB > 4) SB = 4;
-            if (NS != 1) NS = 2;
-            return prec == DWF_F32 ? (dag ? hop_launch_pd<DWF_F32, true>(a, 11, NS, SB, st)
-                                          : hop_launch_pd<DWF_F32, false>(a, 11, NS, SB, st))
-                                   : (dag ? hop_launch_pd<DWF_F16, true>(a, 11, NS, SB, st)
-                                          : hop_launch_pd<DWF_F16, false>(a, 11, NS, SB, st));
-        }
-        var = 9;
-    }
+    if (var < 0 || var > 10 || var == 1 || var == 2 || var == 6 || var == 8) var = hop_default_variant(prec);
     // variant 10 (variant 9 with the dense mixings on the tensor cores): FP32 fields, dense mixing,
     // Ls 8 or 16, no mixed y term; else variant 9
     if (var == 10) {

@@ -1453,252 +1453,6 @@ __global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
 }
 
 
-// ---------------------------------------------------------------- variant 11
-// Variant 9 with two warp tiles per step: the warp gathers the hops of 2 (32/Ls)
-// sites in two passes, puts both into its tile, and then every thread mixes two
-// outputs (slices p and p + Ls/2) of one of the 2 (32/Ls) sites.  Each 16-byte
-// broadcast read of the tile and the matrix then serves two outputs instead of
-// one; the lanes reading one address are Ls/2 consecutive lanes.
-
-// o[n] += sum_t M[chi][s_n][t] tile(t), s_0 = p, s_1 = p + Ls/2; rows of wa_mat_row(Ls) floats
-__device__ __forceinline__ void wa_mix2(const float *M, const float2 *site_tile, int p, int Ls, bool band,
-                                        float2 (*o)[12])
-{
-    const int MR = wa_mat_row(Ls), half = Ls / 2;
-    const float *mu0 = M + (size_t)p * MR, *ml0 = M + (size_t)(Ls + p) * MR;
-    const float *mu1 = mu0 + (size_t)half * MR, *ml1 = ml0 + (size_t)half * MR;
-    const float4 *base = reinterpret_cast<const float4 *>(site_tile);
-    if (band) {   // cyclic tridiagonal: rows s - 1, s, s + 1 for each output
-#pragma unroll
-        for (int n = 0; n < 2; ++n) {
-            const int sn = p + n * half;
-            const float *mu = n ? mu1 : mu0, *ml = n ? ml1 : ml0;
-#pragma unroll
-            for (int dt = -1; dt <= 1; ++dt) {
-                int t = sn + dt;
-                t = t < 0 ? t + Ls : (t >= Ls ? t - Ls : t);
-                const float2 cu = p_splat(mu[t]), cl = p_splat(ml[t]);
-                const float4 *row = base + (size_t)t * (LEAN_ROW / 2);
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    const float4 v = row[q];
-                    o[n][2 * q] = p_fma(cu, make_float2(v.x, v.y), o[n][2 * q]);
-                    o[n][2 * q + 1] = p_fma(cl, make_float2(v.z, v.w), o[n][2 * q + 1]);
-                }
-            }
-        }
-        return;
-    }
-#pragma unroll 1
-    for (int t0 = 0; t0 < Ls; t0 += 4) {
-        const float4 a0 = *reinterpret_cast<const float4 *>(mu0 + t0), b0 = *reinterpret_cast<const float4 *>(ml0 + t0);
-        const float4 a1 = *reinterpret_cast<const float4 *>(mu1 + t0), b1 = *reinterpret_cast<const float4 *>(ml1 + t0);
-        const float ca0[4] = {a0.x, a0.y, a0.z, a0.w}, cb0[4] = {b0.x, b0.y, b0.z, b0.w};
-        const float ca1[4] = {a1.x, a1.y, a1.z, a1.w}, cb1[4] = {b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float2 cu0 = p_splat(ca0[k]), cl0 = p_splat(cb0[k]);
-            const float2 cu1 = p_splat(ca1[k]), cl1 = p_splat(cb1[k]);
-            const float4 *row = base + (size_t)(t0 + k) * (LEAN_ROW / 2);
-#pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                const float4 v = row[q];
-                const float2 hp = make_float2(v.x, v.y), hm = make_float2(v.z, v.w);
-                o[0][2 * q] = p_fma(cu0, hp, o[0][2 * q]);
-                o[0][2 * q + 1] = p_fma(cl0, hm, o[0][2 * q + 1]);
-                o[1][2 * q] = p_fma(cu1, hp, o[1][2 * q]);
-                o[1][2 * q + 1] = p_fma(cl1, hm, o[1][2 * q + 1]);
-            }
-        }
-    }
-}
-
-template <int P>
-__host__ __device__ constexpr size_t wa2_warp_bytes(int Ls)
-{
-    return (size_t)2 * (64 / Ls) * LeanGeom<P>::LINK_BYTES + (size_t)(64 / Ls) * lean_site_stride(Ls) * sizeof(float2);
-}
-template <int P>
-__host__ __device__ constexpr size_t wa2_cta_bytes(int Ls, int nwarps)
-{
-    return (size_t)3 * 2 * Ls * wa_mat_row(Ls) * sizeof(float) + (size_t)nwarps * wa2_warp_bytes<P>(Ls);
-}
-
-template <int P, bool DAG, int MINB>
-__global__ void __launch_bounds__(128, MINB) hop_wa2_kernel(const HopArgs a)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int LB = LeanGeom<P>::LINK_BYTES;
-    const int Ls = a.Ls, SPW = 32 / Ls, SPS = 2 * SPW, half = Ls / 2;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int j = lane / Ls, s = lane - (lane / Ls) * Ls;           // the hop passes: site j (+ SPW), slice s
-    const int qm = lane / half, pm = lane - (lane / half) * half;   // the mixing: site qm, slices pm, pm + Ls/2
-    const int MR = wa_mat_row(Ls), msz = 2 * Ls * MR;
-    float *mats = reinterpret_cast<float *>(smem_raw);
-    {
-        const float *src[3] = {reinterpret_cast<const float *>(a.post),
-                               a.ymode == 2 ? reinterpret_cast<const float *>(a.ymat) : nullptr,
-                               reinterpret_cast<const float *>(a.zmat)};
-        for (int m = 0; m < 3; ++m) {
-            if (!src[m]) continue;
-            for (int k = threadIdx.x; k < 2 * Ls * Ls; k += blockDim.x) {
-                const int chi = k / (Ls * Ls), r = k - chi * Ls * Ls, t = r / Ls, ss = r - t * Ls;
-                mats[m * msz + (chi * Ls + ss) * MR + t] = src[m][k];
-            }
-        }
-    }
-    unsigned char *wbase = smem_raw + (size_t)3 * msz * sizeof(float) + (size_t)warp * wa2_warp_bytes<P>(Ls);
-    unsigned char *links = wbase;
-    float2 *tile = reinterpret_cast<float2 *>(wbase + (size_t)2 * SPS * LB);
-    const int sst = lean_site_stride(Ls);
-    __syncthreads();   // the matrices (the only CTA barrier before the final reduction)
-
-    const int nst = (a.Vh + SPS - 1) / SPS;
-    const int G = gridDim.x * nwarps;
-    float nrm = 0.f;
-    int u = blockIdx.x * nwarps + warp;
-    if (u < nst) wa_issue_links<P>(a.gauge, sweep_site(a, u * SPS), min(SPS, a.Vh - u * SPS), links, lane);
-    for (int k = 0; u < nst; ++k, u += G) {
-        const int site0 = sweep_site(a, u * SPS);
-        cp_async_wait<0>();
-        __syncwarp();   // this step's links are in; every lane is done with the previous step's tile
-        const int un = u + G;
-        if (un < nst)
-            wa_issue_links<P>(a.gauge, sweep_site(a, un * SPS), min(SPS, a.Vh - un * SPS),
-                              links + (size_t)((k + 1) & 1) * SPS * LB, lane);
-#pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
-            const int jj = pass * SPW + j;
-            const bool active = u * SPS + jj < a.Vh;
-            const int site = site0 + jj;
-            float2 acc[12];
-#pragma unroll
-            for (int q = 0; q < 12; ++q) acc[q] = make_float2(0.f, 0.f);
-            if (active) {
-                int n8[8];
-                const int4 *pn = reinterpret_cast<const int4 *>(a.nbr + (size_t)site * 8);
-                const int4 q0 = __ldg(pn), q1 = __ldg(pn + 1);
-                n8[0] = q0.x; n8[1] = q0.y; n8[2] = q0.z; n8[3] = q0.w;
-                n8[4] = q1.x; n8[5] = q1.y; n8[6] = q1.z; n8[7] = q1.w;
-                const unsigned char *lk = links + ((size_t)(k & 1) * SPS + jj) * LB;
-                lean_dir<P, DAG, 0>(acc, a.in, n8[0], s, Ls, lk);
-                lean_dir<P, DAG, 1>(acc, a.in, n8[1], s, Ls, lk);
-                lean_dir<P, DAG, 2>(acc, a.in, n8[2], s, Ls, lk);
-                lean_dir<P, DAG, 3>(acc, a.in, n8[3], s, Ls, lk);
-                lean_dir<P, DAG, 4>(acc, a.in, n8[4], s, Ls, lk);
-                lean_dir<P, DAG, 5>(acc, a.in, n8[5], s, Ls, lk);
-                lean_dir<P, DAG, 6>(acc, a.in, n8[6], s, Ls, lk);
-                lean_dir<P, DAG, 7>(acc, a.in, n8[7], s, Ls, lk);
-                lean_put(tile + (size_t)jj * sst + (size_t)s * LEAN_ROW, acc);
-                if (a.rin.v && a.xacc) {   // x += xalpha xdir, independent of the hop
-                    FieldRef xf;
-                    xf.v = a.xacc;
-                    const float2 xa = p_splat((float)(*a.xalpha));
-                    float2 xv[12], dx[12];
-                    ld_pairs_cs<DWF_F32>(xf, (size_t)site, s, Ls, xv);
-                    ld_pairs_cs<P>(a.xdir, (size_t)site, s, Ls, dx);
-#pragma unroll
-                    for (int q = 0; q < 12; ++q) xv[q] = p_fma(xa, dx[q], xv[q]);
-                    st_pairs_cs<DWF_F32>(xf, (size_t)site, s, Ls, xv);
-                }
-            }
-        }
-        __syncwarp();
-        // ---- the epilogue, two outputs per thread
-        const bool act = u * SPS + qm < a.Vh;
-        const int site = site0 + qm;
-        float2 *stile = tile + (size_t)qm * sst;
-        float2 o[2][12];
-#pragma unroll
-        for (int n = 0; n < 2; ++n)
-#pragma unroll
-            for (int q = 0; q < 12; ++q) o[n][q] = make_float2(0.f, 0.f);
-        if (act) wa_mix2(mats, stile, pm, Ls, a.post_band != 0, o);
-        if (a.ymode == 1) {
-            if (act)
-#pragma unroll
-                for (int n = 0; n < 2; ++n) {
-                    float2 y[12];
-                    ld_pairs_cs<P>(a.y, (size_t)site, pm + n * half, Ls, y);
-#pragma unroll
-                    for (int q = 0; q < 12; ++q) o[n][q] = p_add(o[n][q], y[q]);
-                }
-        } else if (a.ymode == 2) {
-            __syncwarp();
-            if (act)
-#pragma unroll
-                for (int n = 0; n < 2; ++n) {
-                    float2 y[12];
-                    ld_pairs_cs<P>(a.y, (size_t)site, pm + n * half, Ls, y);
-                    lean_put(stile + (size_t)(pm + n * half) * LEAN_ROW, y);
-                }
-            __syncwarp();
-            if (act) wa_mix2(mats + msz, stile, pm, Ls, a.y_band != 0, o);
-        }
-        if (act && a.rin.v) {
-            const float2 nal = p_splat((float)-(*a.ralpha));
-#pragma unroll
-            for (int n = 0; n < 2; ++n) {
-                float2 r[12];
-                ld_pairs_cs<P>(a.rin, (size_t)site, pm + n * half, Ls, r);
-#pragma unroll
-                for (int q = 0; q < 12; ++q) o[n][q] = p_fma(nal, o[n][q], r[q]);
-            }
-        }
-        if (act && a.red.op != RED_NONE) {
-            float2 s2 = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int n = 0; n < 2; ++n)
-#pragma unroll
-                for (int q = 0; q < 12; ++q) s2 = p_fma(o[n][q], o[n][q], s2);
-            nrm += s2.x + s2.y;
-        }
-        if (a.zmat) {
-            __syncwarp();
-            if (act) {
-                lean_put(stile + (size_t)pm * LEAN_ROW, o[0]);
-                lean_put(stile + (size_t)(pm + half) * LEAN_ROW, o[1]);
-            }
-            __syncwarp();
-#pragma unroll
-            for (int n = 0; n < 2; ++n)
-#pragma unroll
-                for (int q = 0; q < 12; ++q) o[n][q] = make_float2(0.f, 0.f);
-            if (act) wa_mix2(mats + 2 * msz, stile, pm, Ls, a.z_band != 0, o);
-        }
-        if (act) {
-            st_pairs_cs<P>(a.out, (size_t)site, pm, Ls, o[0]);
-            st_pairs_cs<P>(a.out, (size_t)site, pm + half, Ls, o[1]);
-        }
-    }
-    cp_async_wait<0>();
-    if (a.red.op != RED_NONE) grid_reduce(nrm, a.red);
-}
-
-template <int P, bool DAG, int MINB>
-cudaError_t launch_wa2(const HopArgs &a, int nw, cudaStream_t st)
-{
-    static unsigned long long optin = 0;
-    int dev = 0, nsm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if ((e = smem_optin(hop_wa2_kernel<P, DAG, MINB>, 200 * 1024, optin)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if (nw < 1 || nw > 4) nw = 4;
-    const size_t smem = wa2_cta_bytes<P>(a.Ls, nw);
-    if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_wa2_kernel<P, DAG, MINB>, 32 * nw, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    const int SPS = 64 / a.Ls;
-    const int nst = (a.Vh + SPS - 1) / SPS;
-    int grid = nsm * per_sm;
-    if (grid > (nst + nw - 1) / nw) grid = (nst + nw - 1) / nw;
-    hop_wa2_kernel<P, DAG, MINB><<<grid, 32 * nw, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------- variant 10
 // The hop of variant 9 (warp tiles of 32/Ls sites, each warp's links staged
 // in its own shared buffer one tile ahead) with the dense fifth-direction
@@ -2261,13 +2015,7 @@ cudaError_t launch_pd(const HopArgs &a, int var, int NS, int SB, cudaStream_t st
         NS = 2;
         SB = 4;
     }
-    // variant 11: variant 9 with two warp tiles per step and two mixing outputs per thread
-    // (dense mixing, Ls 16 or 32; else variant 9)
-    if constexpr (P != DWF_F64) {
-        if (var == 11 && a.mixmode == 0 && (a.Ls == 16 || a.Ls == 32))
-            return NS == 1 ? launch_wa2<P, DAG, 5>(a, SB, st) : launch_wa2<P, DAG, 4>(a, SB, st);
-    }
-    if (var == 11) var = 9;
+
     // variant 9: warp-autonomous (FP32 and FP16 fields, dense mixing, Ls dividing 32 and a
     // multiple of 4); SB = warps per CTA, NS selects the register budget (1: 5 CTAs of 4
     // warps per SM, 2: 4)

@@ -135,7 +135,7 @@ def test_full_size_eo_parity():
 
 HOP_CONFIGS = [(4, 1, 4), (4, 2, 6), (4, 1, 12), (4, 2, 16), (4, 1, 5), (3, 1, 3), (3, 2, 8), (3, 1, 8), (0, 1, 3),
                (0, 2, 5), (0, 1, 16), (0, 2, 1), (5, 1, 8), (5, 2, 5), (5, 4, 3), (5, 4, 16), (7, 1, 1), (7, 1, 5),
-               (7, 0, 16), (9, 1, 4), (9, 2, 2), (9, 0, 1), (9, 2, 3), (10, 0, 0), (11, 2, 4)]
+               (7, 0, 16), (9, 1, 4), (9, 2, 2), (9, 0, 1), (9, 2, 3), (10, 0, 0)]
 
 
 @pytest.mark.parametrize("cfg", HOP_CONFIGS, ids=lambda c: "var%d_ns%d_sb%d" % c)
@@ -272,7 +272,7 @@ def test_errors():
                                      (12, (4, 2, 2, 6))])
 @pytest.mark.parametrize("prec", ["f32", "f16"])
 @pytest.mark.parametrize("var,ns,sb", [(7, 1, 1), (7, 1, 3), (7, 0, 8), (9, 1, 1), (9, 1, 3), (9, 2, 4), (9, 2, 2),
-                                       (10, 0, 0), (11, 2, 4), (11, 1, 3), (11, 2, 1)])
+                                       (10, 0, 0)])
 def test_persistent_hop_variants(Ls, dims, prec, var, ns, sb):
     """Variant 7 (links staged per CTA tile of sb sites, padded mixing tile,
     mixing by half of the threads) and variant 9 (warp tiles with their own links
@@ -280,8 +280,7 @@ def test_persistent_hop_variants(Ls, dims, prec, var, ns, sb):
     operator, its adjoint and the full 5D operator of the oracle; Ls = 4, 8, 16
     and 32 put 8, 4, 2 and 1 sites in a warp tile (Ls 12 takes variant 9's
     fallback).  Variant 10 (variant 9 with the mixings on the tensor cores) runs
-    for FP32 at Ls 8 and 16, variant 11 (two warp tiles per step, two mixing
-    outputs per thread) at Ls 16 and 32; both fall back to variant 9 elsewhere."""
+    for FP32 at Ls 8 and 16 and falls back to variant 9 elsewhere."""
     op, ref = make_pair(dims, Ls, 1.8, 0.02, 1.5, 0.5, "neff", 0.5, seed=81)
     op.set_hop_config(prec, var, ns, sb)
     x = ref.to_eo(inputs.gaussian_5d(dims, Ls, 82), 0)
@@ -295,7 +294,7 @@ def test_persistent_hop_variants(Ls, dims, prec, var, ns, sb):
     op.device_status()
 
 
-@pytest.mark.parametrize("var", [7, 9, 10, 11])
+@pytest.mark.parametrize("var", [7, 9, 10])
 def test_persistent_hop_variants_full_size(var):
     """16^3x32, Ls 16: variants 7 and 9 against variant 0 (FP32) and variant 5 (FP16)
     on the same input: the same operator to the precision's rounding."""

@@ -187,9 +187,11 @@ def test_c1_solve_with_persistent_hops(c1_reference, prec, var):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16"])
-@pytest.mark.parametrize("var", [9, 10, 11])
-def test_ls16_solve_with_warp_tile_hops(prec, var):
-    """Ls 16 (variants 10 and 11 run there; FP16 takes variant 9 for 10): the
+@pytest.mark.parametrize("var", [9, 10])
+@pytest.mark.parametrize("mix", [0, 1])
+def test_ls16_solve_with_warp_tile_hops(prec, var, mix):
+    """Ls 16 (variant 10 runs there for FP32, FP16 takes variant 9), with the
+    dense and the structured mixing (chains in registers in variant 9): the
     solve reaches the oracle-checked residual and the oracle's 4D solution."""
     dims, Ls = (4, 4, 4, 8), 16
     U = inputs.random_links(dims, 0.5, 1012)
@@ -197,6 +199,7 @@ def test_ls16_solve_with_warp_tile_hops(prec, var):
     b4 = inputs.gaussian_4d(dims, 2012)
     b5 = ref.source_5d(b4)
     op.set_hop_config(prec, var, 0 if var == 10 else 2, 0)
+    op.set_mix_mode(prec, mix)
     x5, st = op.solve(to_gpu(b5), inner_prec=prec, tol=1e-10)
     x5 = to_np(x5)
     assert rel(ref.apply(x5), b5) <= 1e-10
