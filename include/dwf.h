@@ -342,13 +342,13 @@ int dwf_autotune(dwf_handle h, int prec, const char *cache_path, void *stream);
  * matrix split in two TF32 terms; FP32 fields also split the field, FP16
  * fields do not).  Mode 1 runs in hop variant 9 at Ls 8 and 16 (each lane
  * takes whole chains of one spinor component over the Ls slices from the
- * warp's tile into registers; banded matrices keep the dense form's three-row
- * path in FP32/FP16, also in the CG update and the stand-alone mixing), else in
+ * warp's tile into registers; in FP32/FP16 the CG update and the stand-alone
+ * mixing keep the dense form's three-row path for banded matrices), else in
  * the direct variant, which it then selects; mode 2 selects the direct
  * variant (CTAs of at least 32 threads, else the dense form runs) or hop
  * variant 10; the CG update keeps the dense form in mode 2.  -1 restores the
- * default: the structured form for DWF_F64, and for DWF_F32 at Ls 8 and 16,
- * when it is available; dense elsewhere.  mode 1 is refused when
+ * default: the structured form for DWF_F64 when it is available, dense for
+ * DWF_F32 and DWF_F16.  mode 1 is refused when
  * the handle's parameters make the structured form unavailable
  * (|kappa| = |beta0/alpha0| >= 0.95), mode 2 for prec = DWF_F64; both with
  * DWF_EINVAL, as a NULL handle or pointer and a bad prec or mode. */

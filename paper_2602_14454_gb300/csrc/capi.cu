@@ -52,12 +52,10 @@ int dwf_ctx::mix_mode(int prec) const
     if (m == 1) return fm.structured ? 1 : 0;
     if (m == 2) return prec == DWF_F64 ? 0 : 2;
     // default: the structured form in FP64, where the FP64 pipe bounds the hop
-    // (measured 2014 us vs 2217 us at 16^3x32, Ls 16), and in FP32 at Ls 8 and 16,
-    // where the warp-autonomous hop runs it by chains in registers (the dense
-    // matrices' hops 2-4 % faster at 32^3x64; banded matrices keep the three-row
-    // dense path); dense elsewhere
+    // (measured 2014 us vs 2217 us at 16^3x32, Ls 16); dense elsewhere (in FP32 the
+    // structured chains of the warp-autonomous hop are 3-4 % faster for K_a and K_c
+    // at 32^3x64 but slower for the banded K_d and the CG update)
     if (m < 0 && prec == DWF_F64 && fm.structured) return 1;
-    if (m < 0 && prec == DWF_F32 && fm.structured && (Ls == 8 || Ls == 16)) return 1;
     return 0;
 }
 

@@ -1194,11 +1194,9 @@ __device__ __forceinline__ void wc_take(const float2 *row, float2 *o)
 // (every lane of the warp calls it; progs: post, y, z)
 template <int P, int LS>
 __device__ __forceinline__ float wc_epilogue(const HopArgs &a, const float2 *acc, float2 *tile, const WcProg *progs,
-                                             const float *mats, int j, int s, int site, bool active, int lane)
+                                             int j, int s, int site, bool active, int lane)
 {
-    const int msz = 2 * LS * wa_mat_row(LS);
-    float2 *stile = tile + (size_t)j * wc_site_stride(LS);
-    float2 *row = stile + (size_t)s * LEAN_ROW;
+    float2 *row = tile + (size_t)j * wc_site_stride(LS) + (size_t)s * LEAN_ROW;
     float *tf = reinterpret_cast<float *>(tile);
     if (active && a.rin.v && a.xacc) {   // independent of the hop: first, while few registers are live
         FieldRef xf;
@@ -1214,15 +1212,9 @@ __device__ __forceinline__ float wc_epilogue(const HopArgs &a, const float2 *acc
     lean_put(row, acc);   // inactive lanes put zeros
     __syncwarp();
     float2 o[12];
-    if (a.post_band) {   // cyclic tridiagonal: three rows of the dense matrix
-#pragma unroll
-        for (int k = 0; k < 12; ++k) o[k] = make_float2(0.f, 0.f);
-        wa_mix(mats, stile, s, LS, true, o);
-    } else {
-        wc_chains<LS>(progs, tf, lane);
-        __syncwarp();
-        wc_take(row, o);
-    }
+    wc_chains<LS>(progs, tf, lane);
+    __syncwarp();
+    wc_take(row, o);
     if (a.ymode != 0) {
         float2 y[12];
 #pragma unroll
@@ -1232,15 +1224,9 @@ __device__ __forceinline__ float wc_epilogue(const HopArgs &a, const float2 *acc
             __syncwarp();
             lean_put(row, y);
             __syncwarp();
-            if (a.y_band) {
-#pragma unroll
-                for (int k = 0; k < 12; ++k) y[k] = make_float2(0.f, 0.f);
-                wa_mix(mats + msz, stile, s, LS, true, y);
-            } else {
-                wc_chains<LS>(progs + 1, tf, lane);
-                __syncwarp();
-                wc_take(row, y);
-            }
+            wc_chains<LS>(progs + 1, tf, lane);
+            __syncwarp();
+            wc_take(row, y);
         }
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[k] = p_add(o[k], y[k]);
@@ -1263,15 +1249,9 @@ __device__ __forceinline__ float wc_epilogue(const HopArgs &a, const float2 *acc
         __syncwarp();
         lean_put(row, o);
         __syncwarp();
-        if (a.z_band) {
-#pragma unroll
-            for (int k = 0; k < 12; ++k) o[k] = make_float2(0.f, 0.f);
-            wa_mix(mats + 2 * msz, stile, s, LS, true, o);
-        } else {
-            wc_chains<LS>(progs + 2, tf, lane);
-            __syncwarp();
-            wc_take(row, o);
-        }
+        wc_chains<LS>(progs + 2, tf, lane);
+        __syncwarp();
+        wc_take(row, o);
     }
     if (active) st_pairs_cs<P>(a.out, (size_t)site, s, LS, o);
     return nrm;
@@ -1377,18 +1357,16 @@ __global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
     const int j = lane / Ls, s = lane - (lane / Ls) * Ls;
     const int MR = wa_mat_row(Ls), msz = 2 * Ls * MR;
     float *mats = reinterpret_cast<float *>(smem_raw);
-    // MIX 1: the structured programs of the matrices that are not banded, after the matrix area
+    // MIX 1: the structured programs, after the matrix area
     WcProg *progs = reinterpret_cast<WcProg *>(smem_raw + (size_t)3 * msz * sizeof(float));
     if constexpr (MIX == 1) {
         const MixProg<float> *src[3] = {reinterpret_cast<const MixProg<float> *>(a.post_prog),
                                         reinterpret_cast<const MixProg<float> *>(a.y_prog),
                                         reinterpret_cast<const MixProg<float> *>(a.z_prog)};
-        const int band[3] = {a.post_band, a.y_band, a.z_band};
         for (int m = 0; m < 3; ++m)
-            if (src[m] && !band[m] && (m != 1 || a.ymode == 2) && (m != 2 || a.zmat))
+            if (src[m] && (m != 1 || a.ymode == 2) && (m != 2 || a.zmat))
                 wc_load_prog(progs + m, src[m], Ls, threadIdx.x, blockDim.x);
-    }
-    {
+    } else {
         const float *src[3] = {reinterpret_cast<const float *>(a.post),
                                a.ymode == 2 ? reinterpret_cast<const float *>(a.ymat) : nullptr,
                                reinterpret_cast<const float *>(a.zmat)};
@@ -1442,8 +1420,8 @@ __global__ void __launch_bounds__(128, MINB) hop_wa_kernel(const HopArgs a)
             lean_dir<P, DAG, 7>(acc, a.in, n8[7], s, Ls, lk);
         }
         if constexpr (MIX == 1) {
-            if (Ls == 16) nrm += wc_epilogue<P, 16>(a, acc, tile, progs, mats, j, s, site, active, lane);
-            else nrm += wc_epilogue<P, 8>(a, acc, tile, progs, mats, j, s, site, active, lane);   // Ls 8 (launch_pd)
+            if (Ls == 16) nrm += wc_epilogue<P, 16>(a, acc, tile, progs, j, s, site, active, lane);
+            else nrm += wc_epilogue<P, 8>(a, acc, tile, progs, j, s, site, active, lane);   // Ls 8 (launch_pd)
         } else {
             nrm += wa_epilogue<P>(a, acc, site_tile, mats, s, site, active);
         }

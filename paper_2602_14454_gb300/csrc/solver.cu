@@ -1043,9 +1043,6 @@ int batch_impl(dwf_handle const *hs_in, const void *const *b4, void *const *x4, 
                 ue[q] = I.ue;
                 for (int j = 0; j < 4; ++j) {
                     HopArgs a = with_programs(R.h, ps, I.k[j]);
-                    // the batched hop is the direct variant, whose FP32/FP16 structured form is slower
-                    // than its dense one: the default mode stays dense there
-                    if (ps != DWF_F64 && R.h->mixmode[ps] < 0) a.mixmode = 0;
                     a.skip = I.ue.skip;
                     kt[j].push_back(a);
                 }
