@@ -16,7 +16,7 @@ def pytest_configure(config):
 # Files whose tests run after every other test, in this order: the
 # allocation-free entry point's test comes last, so that a run stopping at the
 # first failure has run everything else when it fails.
-RUN_LAST = ("test_zz_no_alloc.py",)
+RUN_LAST = ("test_gpu_noalloc.py",)
 
 
 def pytest_collection_modifyitems(session, config, items):
