@@ -121,6 +121,49 @@ int dwf_set_gauge(dwf_handle h, const void *U, void *stream);
  * vector, bad prec or op), DWF_ENOGAUGE, DWF_ECUDA.
  */
 int dwf_apply(dwf_handle h, int op, int prec, const void *in, void *out, void *stream);
+
+/*
+ * 4D domain decomposition in time (the operator of eq. even-odd_linear_equation
+ * split over ranks; Sec. 2.3 defines the operator, the split is the
+ * library's).  dwf_create_slab makes a handle for the time slices
+ * [t0, t0 + nt) of a lattice of extents global_dims (t0 and nt even, nt below
+ * the global Lt; the other arguments as dwf_create).  Its dwf_set_gauge takes
+ * the GLOBAL link field (layout above, global extents) and keeps the slab's
+ * links with the global boundary phases.  Its fields are the slab's even-odd
+ * fields (as DWF_OP_EO_PREC, Vh = Lx Ly Lz nt / 2 local sites, the local
+ * even-odd order with t slowest, so a slab is a contiguous range of the global
+ * even-odd index), and every internal field carries two ghost faces beyond its
+ * Vh rows: the lower neighbour's last time slice and the upper neighbour's
+ * first.  A slab handle is applied only through dwf_slab_apply_eo; the other
+ * operator and solver entry points return DWF_EINVAL for it.
+ *
+ * dwf_slab_apply_eo runs the even-odd matrix (dag = 0) or its adjoint
+ * (dag = 1) in three stages, in precision DWF_F64 or DWF_F32:
+ *   stage 0: reads in (the slab's even field, complex double) and forms
+ *            x^ = P x (Q^T x), whose faces are then exchanged;
+ *   stage 1: t = M H_oe x^ (M^T H^dag_oe x^), reading x^'s ghost faces; t's
+ *            faces are then exchanged;
+ *   stage 2: out = x - 1/4 Q H_eo t (x - 1/4 P^T H^dag_eo t), reading t's
+ *            ghost faces, written to out (complex double).
+ * Between stages 0 and 1, and 1 and 2, each slab's last time slice goes to
+ * the next slab's lower ghost face and its first slice to the previous slab's
+ * upper ghost face.  dwf_slab_faces gives, after stage 0 or 1, the device
+ * addresses of the slab's two boundary slices (send_lo: first slice, send_hi:
+ * last) and of its two ghost faces (recv_lo, recv_hi), each `bytes` long and
+ * contiguous (copy them with cudaMemcpyAsync or NCCL send/recv between
+ * ranks); dwf_slab_exchange_ring does all copies of a ring of n >= 2 slabs on
+ * one device, hs[i + 1] holding the slices after hs[i] and hs[0] after
+ * hs[n - 1], on `stream`, ordered after the stage that made the faces.
+ * Errors: DWF_EINVAL (not a slab, bad stage or precision, NULL or unaligned
+ * vector, slabs of different lattices or not consecutive), DWF_ENOGAUGE,
+ * DWF_ECUDA.
+ */
+int dwf_create_slab(const int global_dims[4], int t0, int nt, int Ls, double M0, double mf, double b, double c,
+                    int form, double alpha, const int bc[4], dwf_handle *out);
+int dwf_slab_apply_eo(dwf_handle h, int prec, int stage, int dag, const void *in, void *out, void *stream);
+int dwf_slab_faces(dwf_handle h, int prec, int stage, void **send_lo, void **send_hi, void **recv_lo,
+                   void **recv_hi, size_t *bytes);
+int dwf_slab_exchange_ring(dwf_handle *hs, int n, int prec, int stage, void *stream);
 int dwf_apply_dag(dwf_handle h, int op, int prec, const void *in, void *out, void *stream);
 
 /* b5 = (-D_-) P^dag (0, ..., 0, b4)^T  (Sec. 2.3, with D_- = diag_s(c D_W - 1)):

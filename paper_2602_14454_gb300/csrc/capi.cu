@@ -106,8 +106,8 @@ void *dwf_ctx::ws(const std::string &name, size_t need, cudaError_t *err)
 FieldRef dwf_ctx::field(const std::string &name, int prec, cudaError_t *err)
 {
     FieldRef f;
-    const size_t fb = field_bytes(prec, Vh, Ls);
-    const size_t sb = scale_bytes(prec, Vh, Ls);
+    const size_t fb = field_bytes(prec, Vh + ghost, Ls);   // a slab's fields carry its ghost faces
+    const size_t sb = scale_bytes(prec, Vh + ghost, Ls);
     const size_t off = (fb + 255) & ~(size_t)255;
     char *p = (char *)ws(name + "#" + std::to_string(prec), off + sb, err);
     if (!p) return f;
@@ -418,6 +418,32 @@ int dwf_destroy(dwf_handle h)
     return DWF_OK;
 }
 
+int dwf_create_slab(const int global_dims[4], int t0, int nt, int Ls, double M0, double mf, double b, double c,
+                    int form, double alpha, const int bc[4], dwf_handle *out)
+{
+    if (!global_dims || !out) return dwf_set_error(DWF_EINVAL, "dims/out is NULL");
+    *out = nullptr;
+    const int Lt = global_dims[3];
+    if (nt < 2 || (nt & 1) || (t0 & 1) || t0 < 0 || t0 >= Lt || nt >= Lt || Lt % 2)
+        return dwf_set_error(DWF_EINVAL, "the slab needs an even origin and an even length below Lt");
+    const int dims[4] = {global_dims[0], global_dims[1], global_dims[2], nt};
+    dwf_handle h = nullptr;
+    int rc = dwf_create(dims, Ls, M0, mf, b, c, form, alpha, bc, &h);
+    if (rc) return rc;
+    h->slab = 1;
+    for (int k = 0; k < 4; ++k) h->gdims[k] = global_dims[k];
+    h->t0 = t0;
+    h->ghost = 2 * (h->Vh / nt);
+    cudaError_t e = launch_slab_tables(h, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        dwf_destroy(h);
+        return dwf_cuda_error(e, "slab tables");
+    }
+    *out = h;
+    return DWF_OK;
+}
+
 int dwf_set_gauge(dwf_handle h, const void *U, void *stream)
 {
     if (!h || !U) return dwf_set_error(DWF_EINVAL, "NULL handle or links");
@@ -430,8 +456,11 @@ int dwf_set_gauge(dwf_handle h, const void *U, void *stream)
             CK(cudaMalloc(&h->gauge[k], sz[k]));
             h->bytes += sz[k];
         }
-    CK(launch_pack_gauge((const double *)U, h->dims, h->bc, h->eo2lex, h->nbr, h->gauge[0], h->gauge[1],
-                         h->gauge[2], st));
+    if (h->slab)   // the global field, the slab's links with the global boundary phases
+        CK(launch_slab_pack_gauge(h, (const double *)U, st));
+    else
+        CK(launch_pack_gauge((const double *)U, h->dims, h->bc, h->eo2lex, h->nbr, h->gauge[0], h->gauge[1],
+                             h->gauge[2], st));
     h->launches += 1;
     h->has_gauge = true;
     return DWF_OK;
@@ -440,6 +469,7 @@ int dwf_set_gauge(dwf_handle h, const void *U, void *stream)
 static int check_common(dwf_handle h, int prec, const void *in, const void *out)
 {
     if (!h) return dwf_set_error(DWF_EINVAL, "NULL handle");
+    if (h && h->slab) return dwf_set_error(DWF_EINVAL, "a slab handle applies its operator through dwf_slab_apply_eo");
     if (!h->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
     if (prec != DWF_F64 && prec != DWF_F32 && prec != DWF_F16) return dwf_set_error(DWF_EINVAL, "bad precision");
     if (!in || !out) return dwf_set_error(DWF_EINVAL, "NULL vector");
@@ -498,6 +528,92 @@ static int apply_impl(dwf_handle h, int op, int prec, const void *in, void *out,
         return DWF_OK;
     }
     return dwf_set_error(DWF_EINVAL, "unknown operator");
+}
+
+// the field a stage of the slab's even-odd application leaves for the exchange
+static FieldRef slab_stage_field(dwf_handle h, int prec, int stage, cudaError_t *e)
+{
+    return h->field(stage == 0 ? "sl_xh" : "sl_t", prec, e);
+}
+
+int dwf_slab_apply_eo(dwf_handle h, int prec, int stage, int dag, const void *in, void *out, void *stream)
+{
+    if (!h || !h->slab) return dwf_set_error(DWF_EINVAL, "not a slab handle");
+    if (!h->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
+    if (prec != DWF_F64 && prec != DWF_F32) return dwf_set_error(DWF_EINVAL, "slabs run in FP64 or FP32");
+    if (stage < 0 || stage > 2) return dwf_set_error(DWF_EINVAL, "stage must be 0, 1 or 2");
+    if ((stage == 0 && !in) || (stage == 2 && !out)) return dwf_set_error(DWF_EINVAL, "NULL vector");
+    if ((in && !aligned16(in)) || (out && !aligned16(out))) return dwf_set_error(DWF_EINVAL, "vectors must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    FieldRef x = h->field("sl_x", prec, &e), xh = h->field("sl_xh", prec, &e);
+    FieldRef t = h->field("sl_t", prec, &e), y = h->field("sl_y", prec, &e);
+    if (!x.v || !xh.v || !t.v || !y.v) return dwf_cuda_error(e, "workspace");
+    if (stage == 0) {   // x^ = P x (Q^T x for the adjoint); its faces go to the neighbours
+        CK(launch_pack_eo(prec, (const double *)in, x, h->Vh, h->Ls, st));
+        h->launches += 1;
+        CK(mix(h, prec, x, xh, dag ? MAT_QT : MAT_P, st));
+    } else if (stage == 1) {   // t = M H_oe x^ (M^T H^dag_oe), reading x^'s ghost rows; t's faces go out
+        HopArgs a1 = hop_args(h, prec, 1, xh, t, dag ? MAT_MT : MAT_M);
+        CK(hop(h, prec, dag != 0, a1, st));
+    } else {   // y = x - 1/4 Q H_eo t (x - 1/4 P^T H^dag_eo t), reading t's ghost rows
+        HopArgs a2 = hop_args(h, prec, 0, t, y, dag ? MAT_NPT4 : MAT_NQ4);
+        a2.y = x;
+        a2.ymode = 1;
+        CK(hop(h, prec, dag != 0, a2, st));
+        CK(launch_unpack_eo(prec, y, (double *)out, h->Vh, h->Ls, st));
+        h->launches += 1;
+    }
+    return DWF_OK;
+}
+
+int dwf_slab_faces(dwf_handle h, int prec, int stage, void **send_lo, void **send_hi, void **recv_lo,
+                   void **recv_hi, size_t *bytes)
+{
+    if (!h || !h->slab) return dwf_set_error(DWF_EINVAL, "not a slab handle");
+    if (prec != DWF_F64 && prec != DWF_F32) return dwf_set_error(DWF_EINVAL, "slabs run in FP64 or FP32");
+    if (stage != 0 && stage != 1) return dwf_set_error(DWF_EINVAL, "faces exist after stages 0 and 1");
+    if (!send_lo || !send_hi || !recv_lo || !recv_hi || !bytes) return dwf_set_error(DWF_EINVAL, "NULL pointer");
+    cudaError_t e = cudaSuccess;
+    FieldRef f = slab_stage_field(h, prec, stage, &e);
+    if (!f.v) return dwf_cuda_error(e, "workspace");
+    const size_t row = field_bytes(prec, 1, h->Ls);   // one site, all slices
+    const size_t A3 = (size_t)h->Vh / h->dims[3];
+    char *p = (char *)f.v;
+    *send_lo = p;
+    *send_hi = p + (size_t)(h->dims[3] - 1) * A3 * row;
+    *recv_lo = p + (size_t)h->Vh * row;
+    *recv_hi = p + ((size_t)h->Vh + A3) * row;
+    *bytes = A3 * row;
+    return DWF_OK;
+}
+
+int dwf_slab_exchange_ring(dwf_handle *hs, int n, int prec, int stage, void *stream)
+{
+    if (!hs || n < 2) return dwf_set_error(DWF_EINVAL, "a ring needs at least two slabs");
+    for (int i = 0; i < n; ++i) {
+        const dwf_handle a = hs[i], b = hs[(i + 1) % n];
+        if (!a || !b || !a->slab || !b->slab) return dwf_set_error(DWF_EINVAL, "not a slab handle");
+        for (int k = 0; k < 4; ++k)
+            if (a->gdims[k] != b->gdims[k] || (k < 3 && a->dims[k] != b->dims[k]))
+                return dwf_set_error(DWF_EINVAL, "the slabs belong to different lattices");
+        if (a->Ls != b->Ls) return dwf_set_error(DWF_EINVAL, "the slabs have different Ls");
+        if ((a->t0 + a->dims[3]) % a->gdims[3] != b->t0)
+            return dwf_set_error(DWF_EINVAL, "the slabs are not consecutive in time");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < n; ++i) {
+        void *sl, *sh, *rl, *rh, *nsl, *nsh, *nrl, *nrh;
+        size_t by = 0, nby = 0;
+        int rc = dwf_slab_faces(hs[i], prec, stage, &sl, &sh, &rl, &rh, &by);
+        if (rc) return rc;
+        rc = dwf_slab_faces(hs[(i + 1) % n], prec, stage, &nsl, &nsh, &nrl, &nrh, &nby);
+        if (rc) return rc;
+        // my last slice -> the next slab's lower ghost face; its first slice -> my upper ghost face
+        CK(cudaMemcpyAsync(nrl, sh, by, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(rh, nsl, by, cudaMemcpyDeviceToDevice, st));
+    }
+    return DWF_OK;
 }
 
 int dwf_apply(dwf_handle h, int op, int prec, const void *in, void *out, void *stream)

@@ -293,6 +293,12 @@ struct dwf_ctx {
     int hop_ns[3] = {0, 0, 0};        // hop tiling per precision (0 = default)
     int hop_sb[3] = {0, 0, 0};
     int sweep_zb[3] = {-1, -1, -1};   // hop sweep columns per precision (dwf_set_sweep; -1 automatic)
+    // time slab of a decomposed lattice (dwf_create_slab): global extents, first global
+    // time slice, and the ghost rows appended to every field (two faces of Vh/nt sites)
+    int slab = 0;
+    int gdims[4] = {0, 0, 0, 0};
+    int t0 = 0;
+    int ghost = 0;
     dwf::NetState *net = nullptr;     // learned preconditioner (dwf_precond_*)
     int *errflag() const { return &scal[7].flags; }
 
@@ -311,6 +317,9 @@ int net_apply_f32(dwf_ctx *h, FieldRef r, FieldRef z, cudaStream_t st, int which
 int normal_apply_f32(dwf_ctx *h, FieldRef x, FieldRef out, cudaStream_t st);
 int eo_apply_f32(dwf_ctx *h, FieldRef x, FieldRef out, cudaStream_t st);
 int eo_dag_apply_f32(dwf_ctx *h, FieldRef w, FieldRef out, cudaStream_t st);   // out = D^dag w
+// time slabs (slab.cu): neighbour table with ghost rows, links from the global field
+cudaError_t launch_slab_tables(const dwf_ctx *h, cudaStream_t st);
+cudaError_t launch_slab_pack_gauge(const dwf_ctx *h, const double *U, cudaStream_t st);
 }  // namespace dwf
 void dwf_precond_release(dwf_ctx *h);
 

@@ -61,6 +61,7 @@ size_t round256(size_t n) { return (n + 255) & ~(size_t)255; }
 extern "C" int dwf_apply_eo_noalloc(dwf_handle h, int prec, int dag, const void *in, void *out, void *stream)
 {
     if (!h) return dwf_set_error(DWF_EINVAL, "NULL handle");
+    if (h->slab) return dwf_set_error(DWF_EINVAL, "a slab handle applies its operator through dwf_slab_apply_eo");
     if (!h->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
     if (prec != DWF_F64 && prec != DWF_F32 && prec != DWF_F16) return dwf_set_error(DWF_EINVAL, "bad precision");
     if (!in || !out) return dwf_set_error(DWF_EINVAL, "NULL vector");

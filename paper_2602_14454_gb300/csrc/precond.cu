@@ -841,6 +841,7 @@ int dwf_precond_get_weights(dwf_handle h, int layers, int compute_copy, double *
 int dwf_precond_apply(dwf_handle h, int which, const void *in, void *out, void *stream)
 {
     if (!h || !in || !out) return dwf_set_error(DWF_EINVAL, "NULL argument");
+    if (h && h->slab) return dwf_set_error(DWF_EINVAL, "a slab handle applies its operator through dwf_slab_apply_eo");
     if (which < 0 || which > 2) return dwf_set_error(DWF_EINVAL, "which must be 0 (N), 1 (N^dag) or 2 (N N^dag)");
     if (!h->net) return dwf_set_error(DWF_EINVAL, "no preconditioner (dwf_precond_init or dwf_precond_train first)");
     cudaStream_t st = (cudaStream_t)stream;
@@ -862,6 +863,7 @@ int dwf_precond_loss_grad(dwf_handle h, int npairs, const void *const *b, const 
                           double *grad, void *stream)
 {
     if (!h || npairs < 1 || !b || !x) return dwf_set_error(DWF_EINVAL, "bad argument");
+    if (h && h->slab) return dwf_set_error(DWF_EINVAL, "a slab handle applies its operator through dwf_slab_apply_eo");
     if (!h->net) return dwf_set_error(DWF_EINVAL, "no preconditioner");
     cudaStream_t st = (cudaStream_t)stream;
     NetState *N = h->net;
@@ -899,6 +901,7 @@ int dwf_precond_train(dwf_handle h, int nsrc, const void *const *b4, const dwf_t
                       dwf_train_stats *stats, void *stream)
 {
     if (!h || nsrc < 1 || !b4) return dwf_set_error(DWF_EINVAL, "bad argument");
+    if (h && h->slab) return dwf_set_error(DWF_EINVAL, "a slab handle applies its operator through dwf_slab_apply_eo");
     dwf_train_params defp;
     dwf_train_params_default(&defp);
     dwf_train_params pv = tp ? *tp : defp;

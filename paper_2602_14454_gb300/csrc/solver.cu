@@ -1267,6 +1267,7 @@ void dwf_solve_params_default(dwf_solve_params *p)
 int dwf_solve(dwf_handle h, const void *b5, void *x5, const dwf_solve_params *p, dwf_solve_stats *stats, void *stream)
 {
     if (!h || !b5 || !x5) return dwf_set_error(DWF_EINVAL, "NULL argument");
+    if (h && h->slab) return dwf_set_error(DWF_EINVAL, "a slab handle applies its operator through dwf_slab_apply_eo");
     if (!h->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
     if (((uintptr_t)b5 & 15) || ((uintptr_t)x5 & 15)) return dwf_set_error(DWF_EINVAL, "vectors must be 16-byte aligned");
     dwf_solve_params def;
@@ -1278,6 +1279,7 @@ int dwf_precond_fcg(dwf_handle h, const void *b, void *x, double tol, int max_it
                     int *iters, void *stream)
 {
     if (!h || !b || !x) return dwf_set_error(DWF_EINVAL, "NULL argument");
+    if (h && h->slab) return dwf_set_error(DWF_EINVAL, "a slab handle applies its operator through dwf_slab_apply_eo");
     if (!h->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
     if (!(tol > 0) || max_iter < 0) return dwf_set_error(DWF_EINVAL, "bad tol or max_iter");
     if (!plain && !h->net) return dwf_set_error(DWF_EINVAL, "no preconditioner (dwf_precond_init or dwf_precond_train)");
@@ -1307,6 +1309,7 @@ int dwf_propagator_host(dwf_handle h, const double *b4_host, double *x4_host, co
                         dwf_solve_stats *stats, void *stream)
 {
     if (!h || !b4_host || !x4_host) return dwf_set_error(DWF_EINVAL, "NULL argument");
+    if (h && h->slab) return dwf_set_error(DWF_EINVAL, "a slab handle applies its operator through dwf_slab_apply_eo");
     if (!h->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
@@ -1336,6 +1339,9 @@ int dwf_solve_batch(dwf_handle const *hs, const void *const *b4, void *const *x4
                     dwf_solve_stats *stats, void *stream)
 {
     if (n < 0 || (n > 0 && (!hs || !b4 || !x4))) return dwf_set_error(DWF_EINVAL, "NULL argument");
+    for (int i = 0; i < n; ++i)
+        if (hs[i] && hs[i]->slab)
+            return dwf_set_error(DWF_EINVAL, "a slab handle applies its operator through dwf_slab_apply_eo");
     dwf_solve_params def;
     dwf_solve_params_default(&def);
     return batch_impl(hs, b4, x4, n, p ? p : &def, stats, (cudaStream_t)stream);

@@ -207,6 +207,7 @@ extern "C" int dwf_spectrum_bounds(dwf_handle h, int eo_form, int max_steps, dou
 {
     if (!h || (eo_form != 0 && eo_form != 1) || max_steps < 2 || !(rtol > 0) || !lambda_min || !lambda_max)
         return dwf_set_error(DWF_EINVAL, "bad argument");
+    if (h->slab) return dwf_set_error(DWF_EINVAL, "a slab handle applies its operator through dwf_slab_apply_eo");
     if (!h->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;

@@ -31,7 +31,8 @@ EXPORTED = ["dwf_create", "dwf_create_s", "dwf_destroy", "dwf_strerror", "dwf_la
             "dwf_apply", "dwf_apply_dag", "dwf_source_5d", "dwf_project_4d",
             "dwf_solve_params_default", "dwf_solve", "dwf_propagator_host", "dwf_solve_batch",
             "dwf_fifth_matrix", "dwf_fifth_matrix_host", "dwf_device_bytes", "dwf_time_hop", "dwf_time_iteration", "dwf_spectrum_bounds", "dwf_launch_count",
-            "dwf_set_hop_config", "dwf_get_hop_config", "dwf_set_sweep", "dwf_get_sweep", "dwf_autotune", "dwf_device_status",
+            "dwf_set_hop_config", "dwf_get_hop_config", "dwf_set_sweep", "dwf_get_sweep",
+            "dwf_create_slab", "dwf_slab_apply_eo", "dwf_slab_faces", "dwf_slab_exchange_ring", "dwf_autotune", "dwf_device_status",
             "dwf_set_mix_mode", "dwf_get_mix_mode", "dwf_apply_eo_noalloc",
             "dwf_train_params_default", "dwf_precond_init", "dwf_precond_set_weights", "dwf_precond_get_weights",
             "dwf_precond_apply", "dwf_precond_loss_grad", "dwf_precond_train", "dwf_precond_adam_step",
@@ -111,6 +112,13 @@ def lib():
     L.dwf_last_error.argtypes = []
     L.dwf_set_gauge.argtypes = [vp, vp, vp]
     L.dwf_apply.argtypes = [vp, i, i, vp, vp, vp]
+    L.dwf_create_slab.argtypes = [ctypes.POINTER(ctypes.c_int), i, i, i, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, i, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(vp)]
+    L.dwf_slab_apply_eo.argtypes = [vp, i, i, i, vp, vp, vp]
+    L.dwf_slab_faces.argtypes = [vp, i, i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                 ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_size_t)]
+    L.dwf_slab_exchange_ring.argtypes = [ctypes.POINTER(vp), i, i, i, vp]
     L.dwf_apply_dag.argtypes = [vp, i, i, vp, vp, vp]
     L.dwf_source_5d.argtypes = [vp, vp, vp, vp]
     L.dwf_project_4d.argtypes = [vp, vp, vp, vp]
@@ -487,3 +495,59 @@ def solve_batch(ops, b4s, x4s=None, allow_notconv=False, **kw):
     if rc != 0 and not (allow_notconv and rc == 4):
         check(rc)
     return x4s, [s.as_dict() for s in st]
+
+
+class Slab(Operator):
+    """The time slices [t0, t0 + nt) of a lattice of extents global_dims (4D
+    domain decomposition in time).  set_gauge takes the global link field; the
+    even-odd matrix is applied in three stages with a face exchange between
+    them (dwf_slab_apply_eo, dwf_slab_faces, dwf_slab_exchange_ring)."""
+
+    def __init__(self, global_dims, t0, nt, Ls, M0, mf, b, c, form="standard", alpha=1.0, bc=None):
+        self.global_dims = tuple(int(x) for x in global_dims)
+        self.t0, self.nt = int(t0), int(nt)
+        self.dims = self.global_dims[:3] + (self.nt,)
+        self.Ls = int(Ls)
+        h = ctypes.c_void_p()
+        d = (ctypes.c_int * 4)(*self.global_dims)
+        bcp = (ctypes.c_int * 4)(*bc) if bc is not None else None
+        check(lib().dwf_create_slab(d, self.t0, self.nt, self.Ls, float(M0), float(mf), float(b), float(c),
+                                    FORM[form], float(alpha), bcp, ctypes.byref(h)))
+        self._h = h
+        self.b, self.c = float(b), float(c)
+        self.M0, self.mf = float(M0), float(mf)
+        self.form, self.alpha = form, float(alpha)
+        Lx, Ly, Lz, Lt = self.dims
+        self.site_shape = (Lt, Lz, Ly, Lx)
+        self.V = Lx * Ly * Lz * Lt
+
+    def apply_eo_stage(self, stage, x=None, prec="f64", dag=False, out=None):
+        if stage == 2 and out is None:
+            out = self._new(self.shape_eo())
+        check(lib().dwf_slab_apply_eo(self._h, PREC[prec], int(stage), int(bool(dag)),
+                                      _ptr(x) if x is not None else None,
+                                      _ptr(out) if out is not None else None, _stream()))
+        return out
+
+    def faces(self, prec, stage):
+        p = [ctypes.c_void_p() for _ in range(4)]
+        n = ctypes.c_size_t()
+        check(lib().dwf_slab_faces(self._h, PREC[prec], int(stage), *[ctypes.byref(q) for q in p], ctypes.byref(n)))
+        return dict(send_lo=p[0].value, send_hi=p[1].value, recv_lo=p[2].value, recv_hi=p[3].value, bytes=n.value)
+
+
+def slab_exchange_ring(slabs, prec, stage):
+    arr = (ctypes.c_void_p * len(slabs))(*[s.handle for s in slabs])
+    check(lib().dwf_slab_exchange_ring(arr, len(slabs), PREC[prec], int(stage), _stream()))
+
+
+def slab_apply_eo(slabs, xs, prec="f64", dag=False):
+    """The even-odd matrix on a ring of slabs on one device: the three stages
+    of every slab with the face exchanges between them."""
+    for sl, x in zip(slabs, xs):
+        sl.apply_eo_stage(0, x=x, prec=prec, dag=dag)
+    slab_exchange_ring(slabs, prec, 0)
+    for sl in slabs:
+        sl.apply_eo_stage(1, prec=prec, dag=dag)
+    slab_exchange_ring(slabs, prec, 1)
+    return [sl.apply_eo_stage(2, prec=prec, dag=dag) for sl in slabs]
