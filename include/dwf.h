@@ -164,6 +164,21 @@ int dwf_slab_apply_eo(dwf_handle h, int prec, int stage, int dag, const void *in
 int dwf_slab_faces(dwf_handle h, int prec, int stage, void **send_lo, void **send_hi, void **recv_lo,
                    void **recv_hi, size_t *bytes);
 int dwf_slab_exchange_ring(dwf_handle *hs, int n, int prec, int stage, void *stream);
+
+/* CG on the normal equation of the even-odd matrix (Sec. 2.3, FP64) over a
+ * ring of n >= 2 slabs on one device, each slab's vectors its own: b[i] the
+ * slab's even right-hand side, x[i] its solution (device, complex double, the
+ * slab's even-odd layout; x is overwritten from a zero start).  Every
+ * application of D and D^dag runs the three stages of all slabs with the face
+ * exchanges between them; the inner products are per-slab sums in a fixed
+ * order added over the slabs (the all-reduce of a multi-GPU run).  Stops when
+ * the recursive residual falls below tol ||b||, then recomputes b - D x:
+ * history (host, max_iter + 1 doubles, may be NULL) gets ||r||/||b|| per
+ * iteration and the true residual last; *iters the iteration count.
+ * Errors: DWF_EINVAL, DWF_ENOGAUGE, DWF_ENOTCONV (true residual above tol),
+ * DWF_ENONFINITE, DWF_EBREAKDOWN, DWF_ECUDA. */
+int dwf_slab_cgnr_ring(dwf_handle *hs, int n, const void *const *b, void *const *x, double tol, int max_iter,
+                       int *iters, double *history, void *stream);
 int dwf_apply_dag(dwf_handle h, int op, int prec, const void *in, void *out, void *stream);
 
 /* b5 = (-D_-) P^dag (0, ..., 0, b4)^T  (Sec. 2.3, with D_- = diag_s(c D_W - 1)):

@@ -616,6 +616,99 @@ int dwf_slab_exchange_ring(dwf_handle *hs, int n, int prec, int stage, void *str
     return DWF_OK;
 }
 
+int dwf_slab_cgnr_ring(dwf_handle *hs, int n, const void *const *b, void *const *x, double tol, int max_iter,
+                       int *iters, double *history, void *stream)
+{
+    if (!hs || n < 2 || !b || !x || !(tol > 0) || max_iter < 1) return dwf_set_error(DWF_EINVAL, "bad argument");
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i] || !hs[i]->slab) return dwf_set_error(DWF_EINVAL, "not a slab handle");
+        if (!hs[i]->has_gauge) return dwf_set_error(DWF_ENOGAUGE, "dwf_set_gauge has not been called");
+        if (!b[i] || !x[i] || !aligned16(b[i]) || !aligned16(x[i]))
+            return dwf_set_error(DWF_EINVAL, "NULL or unaligned vector");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    std::vector<void *> r(n), z(n), p(n), w(n);
+    std::vector<size_t> nel(n);
+    for (int i = 0; i < n; ++i) {
+        nel[i] = (size_t)hs[i]->Vh * hs[i]->Ls * 12;   // complex numbers of one even field
+        const size_t by = nel[i] * 16;
+        r[i] = hs[i]->ws("dd_r", by, &e);
+        z[i] = hs[i]->ws("dd_z", by, &e);
+        p[i] = hs[i]->ws("dd_p", by, &e);
+        w[i] = hs[i]->ws("dd_w", by, &e);
+        if (!r[i] || !z[i] || !p[i] || !w[i]) return dwf_cuda_error(e, "workspace");
+    }
+    double *scratch = (double *)hs[0]->ws("dd_dot", (size_t)(256 + n) * sizeof(double), &e);
+    if (!scratch) return dwf_cuda_error(e, "workspace");
+    // D (dag = 0) or D^dag on the ring: the three stages of every slab, the faces exchanged between them
+    auto apply = [&](int dag, const std::vector<void *> &in, const std::vector<void *> &out) -> int {
+        int rc;
+        for (int i = 0; i < n; ++i)
+            if ((rc = dwf_slab_apply_eo(hs[i], DWF_F64, 0, dag, in[i], nullptr, stream))) return rc;
+        if ((rc = dwf_slab_exchange_ring(hs, n, DWF_F64, 0, stream))) return rc;
+        for (int i = 0; i < n; ++i)
+            if ((rc = dwf_slab_apply_eo(hs[i], DWF_F64, 1, dag, nullptr, nullptr, stream))) return rc;
+        if ((rc = dwf_slab_exchange_ring(hs, n, DWF_F64, 1, stream))) return rc;
+        for (int i = 0; i < n; ++i)
+            if ((rc = dwf_slab_apply_eo(hs[i], DWF_F64, 2, dag, nullptr, out[i], stream))) return rc;
+        return DWF_OK;
+    };
+    // Re <a, b> over the ring: per-slab sums in a fixed order, added on the host in slab order
+    std::vector<double> part(n);
+    auto dot = [&](const std::vector<void *> &a, const std::vector<void *> &bb, double &res) -> int {
+        for (int i = 0; i < n; ++i) CK(launch_cdot(a[i], bb[i], nel[i], scratch, scratch + 256 + i, st));
+        CK(cudaMemcpyAsync(part.data(), scratch + 256, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        res = 0.0;
+        for (int i = 0; i < n; ++i) res += part[i];
+        return std::isfinite(res) ? DWF_OK : dwf_set_error(DWF_ENONFINITE, "non-finite inner product");
+    };
+    std::vector<void *> bv(n), xv(x, x + n);
+    for (int i = 0; i < n; ++i) bv[i] = const_cast<void *>(b[i]);   // read only
+    int rc;
+    double bn2 = 0, gamma = 0, ww = 0, gnew = 0, rr = 0;
+    for (int i = 0; i < n; ++i) {
+        CK(cudaMemsetAsync(xv[i], 0, nel[i] * 16, st));
+        CK(cudaMemcpyAsync(r[i], bv[i], nel[i] * 16, cudaMemcpyDeviceToDevice, st));
+    }
+    if ((rc = dot(bv, bv, bn2))) return rc;
+    if (!(bn2 > 0)) return dwf_set_error(DWF_EINVAL, "zero right-hand side");
+    const double bn = std::sqrt(bn2);
+    if ((rc = apply(1, r, z))) return rc;
+    for (int i = 0; i < n; ++i) CK(cudaMemcpyAsync(p[i], z[i], nel[i] * 16, cudaMemcpyDeviceToDevice, st));
+    if ((rc = dot(z, z, gamma))) return rc;
+    int it = 0;
+    double res = 1.0;
+    if (history) history[0] = res;
+    while (res > tol && it < max_iter) {
+        if ((rc = apply(0, p, w))) return rc;
+        if ((rc = dot(w, w, ww))) return rc;
+        if (!(ww > 0)) return dwf_set_error(DWF_EBREAKDOWN, "|D p|^2 <= 0");
+        const double alpha = gamma / ww;
+        for (int i = 0; i < n; ++i) {
+            CK(launch_caxpby(alpha, p[i], 1.0, xv[i], nel[i], st));
+            CK(launch_caxpby(-alpha, w[i], 1.0, r[i], nel[i], st));
+        }
+        if ((rc = apply(1, r, z))) return rc;
+        if ((rc = dot(z, z, gnew))) return rc;
+        for (int i = 0; i < n; ++i) CK(launch_caxpby(1.0, z[i], gnew / gamma, p[i], nel[i], st));
+        gamma = gnew;
+        ++it;
+        if ((rc = dot(r, r, rr))) return rc;
+        res = std::sqrt(rr) / bn;
+        if (history) history[it] = res;
+    }
+    // the true residual b - D x
+    if ((rc = apply(0, xv, w))) return rc;
+    for (int i = 0; i < n; ++i) CK(launch_caxpby(1.0, bv[i], -1.0, w[i], nel[i], st));
+    if ((rc = dot(w, w, rr))) return rc;
+    if (iters) *iters = it;
+    const double tres = std::sqrt(rr) / bn;
+    if (history) history[it] = tres;
+    return tres <= tol ? DWF_OK : dwf_set_error(DWF_ENOTCONV, "the decomposed CGNR did not reach tol");
+}
+
 int dwf_apply(dwf_handle h, int op, int prec, const void *in, void *out, void *stream)
 {
     return apply_impl(h, op, prec, in, out, false, (cudaStream_t)stream);

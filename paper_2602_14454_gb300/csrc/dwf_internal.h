@@ -320,6 +320,9 @@ int eo_dag_apply_f32(dwf_ctx *h, FieldRef w, FieldRef out, cudaStream_t st);   /
 // time slabs (slab.cu): neighbour table with ghost rows, links from the global field
 cudaError_t launch_slab_tables(const dwf_ctx *h, cudaStream_t st);
 cudaError_t launch_slab_pack_gauge(const dwf_ctx *h, const double *U, cudaStream_t st);
+// FP64 complex vectors (n complex numbers): *out = Re <a, b> (part: 256 doubles of scratch); y = a x + b y
+cudaError_t launch_cdot(const void *a, const void *b, size_t n, double *part, double *out, cudaStream_t st);
+cudaError_t launch_caxpby(double a, const void *x, double b, void *y, size_t n, cudaStream_t st);
 }  // namespace dwf
 void dwf_precond_release(dwf_ctx *h);
 

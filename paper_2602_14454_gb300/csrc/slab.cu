@@ -131,7 +131,60 @@ SlabGeom geom_of(const dwf_ctx *h)
     return G;
 }
 
+// FP64 complex vectors of the decomposed CG (canonical layout, n complex numbers)
+constexpr int kDotBlocks = 256;
+
+// per-block partial sums of Re sum conj(a_k) b_k, the blocks' grid-stride ranges fixed
+__global__ void __launch_bounds__(kThreads) cdot_kernel(const double2 *a, const double2 *b, size_t n, double *part)
+{
+    __shared__ double red[kThreads];
+    double acc = 0.0;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const double2 u = a[k], v = b[k];
+        acc += u.x * v.x + u.y * v.y;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// the partials in a fixed order
+__global__ void csum_kernel(const double *part, int np, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < np; ++i) s += part[i];
+        *out = s;
+    }
+}
+
+// y = a x + b y
+__global__ void caxpby_kernel(double a, const double2 *x, double b, double2 *y, size_t n)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const double2 u = x[k], v = y[k];
+        y[k] = make_double2(a * u.x + b * v.x, a * u.y + b * v.y);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_cdot(const void *a, const void *b, size_t n, double *part, double *out, cudaStream_t st)
+{
+    cdot_kernel<<<kDotBlocks, kThreads, 0, st>>>((const double2 *)a, (const double2 *)b, n, part);
+    csum_kernel<<<1, 32, 0, st>>>(part, kDotBlocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_caxpby(double a, const void *x, double b, void *y, size_t n, cudaStream_t st)
+{
+    caxpby_kernel<<<grid_for(n), kThreads, 0, st>>>(a, (const double2 *)x, b, (double2 *)y, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_slab_tables(const dwf_ctx *h, cudaStream_t st)
 {

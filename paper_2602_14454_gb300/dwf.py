@@ -32,7 +32,8 @@ EXPORTED = ["dwf_create", "dwf_create_s", "dwf_destroy", "dwf_strerror", "dwf_la
             "dwf_solve_params_default", "dwf_solve", "dwf_propagator_host", "dwf_solve_batch",
             "dwf_fifth_matrix", "dwf_fifth_matrix_host", "dwf_device_bytes", "dwf_time_hop", "dwf_time_iteration", "dwf_spectrum_bounds", "dwf_launch_count",
             "dwf_set_hop_config", "dwf_get_hop_config", "dwf_set_sweep", "dwf_get_sweep",
-            "dwf_create_slab", "dwf_slab_apply_eo", "dwf_slab_faces", "dwf_slab_exchange_ring", "dwf_autotune", "dwf_device_status",
+            "dwf_create_slab", "dwf_slab_apply_eo", "dwf_slab_faces", "dwf_slab_exchange_ring",
+            "dwf_slab_cgnr_ring", "dwf_autotune", "dwf_device_status",
             "dwf_set_mix_mode", "dwf_get_mix_mode", "dwf_apply_eo_noalloc",
             "dwf_train_params_default", "dwf_precond_init", "dwf_precond_set_weights", "dwf_precond_get_weights",
             "dwf_precond_apply", "dwf_precond_loss_grad", "dwf_precond_train", "dwf_precond_adam_step",
@@ -119,6 +120,8 @@ def lib():
     L.dwf_slab_faces.argtypes = [vp, i, i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                  ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_size_t)]
     L.dwf_slab_exchange_ring.argtypes = [ctypes.POINTER(vp), i, i, i, vp]
+    L.dwf_slab_cgnr_ring.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_double,
+                                     i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double), vp]
     L.dwf_apply_dag.argtypes = [vp, i, i, vp, vp, vp]
     L.dwf_source_5d.argtypes = [vp, vp, vp, vp]
     L.dwf_project_4d.argtypes = [vp, vp, vp, vp]
@@ -551,3 +554,17 @@ def slab_apply_eo(slabs, xs, prec="f64", dag=False):
         sl.apply_eo_stage(1, prec=prec, dag=dag)
     slab_exchange_ring(slabs, prec, 1)
     return [sl.apply_eo_stage(2, prec=prec, dag=dag) for sl in slabs]
+
+
+def slab_cgnr_ring(slabs, bs, tol=1e-10, max_iter=20000):
+    """FP64 CGNR on the even-odd matrix over a ring of slabs on one device
+    (dwf_slab_cgnr_ring): returns the slabs' solutions and the residual history."""
+    n = len(slabs)
+    xs = [sl._new(sl.shape_eo()) for sl in slabs]
+    arr = (ctypes.c_void_p * n)(*[s.handle for s in slabs])
+    bp = (ctypes.c_void_p * n)(*[_ptr(b).value for b in bs])
+    xp = (ctypes.c_void_p * n)(*[_ptr(x).value for x in xs])
+    its = ctypes.c_int()
+    hist = (ctypes.c_double * (max_iter + 1))()
+    check(lib().dwf_slab_cgnr_ring(arr, n, bp, xp, float(tol), int(max_iter), ctypes.byref(its), hist, _stream()))
+    return xs, list(hist[:its.value + 1])
