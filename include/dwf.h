@@ -57,8 +57,14 @@ enum dwf_prec { DWF_F64 = 0, DWF_F32 = 1, DWF_F16 = 2 };
 
 /* DWF_OP_FULL5D: the whole 5D matrix on full-lattice 5D fields.
  * DWF_OP_EO_PREC: D = 1 - D_ee^-1 D_eo D_oo^-1 D_oe on EO fields
- *                 (eq. even-odd_linear_equation). */
-enum dwf_op { DWF_OP_FULL5D = 0, DWF_OP_EO_PREC = 1 };
+ *                 (eq. even-odd_linear_equation).
+ * DWF_OP_EO5_PREC: the same Schur complement for the 5D split of Sec. 2.3's
+ *                 alternative (sites even when x + y + z + t + s is even), on
+ *                 full-lattice 5D fields whose odd sites are ignored on input
+ *                 and zero on output; needs the standard form with every
+ *                 c_s = 0 and even Ls, where D_ee and D_oo are the on-site
+ *                 diagonal b_s (4 - M0) + 1. */
+enum dwf_op { DWF_OP_FULL5D = 0, DWF_OP_EO_PREC = 1, DWF_OP_EO5_PREC = 2 };
 
 enum dwf_status {
     DWF_OK = 0,
@@ -121,6 +127,19 @@ int dwf_set_gauge(dwf_handle h, const void *U, void *stream);
  * vector, bad prec or op), DWF_ENOGAUGE, DWF_ECUDA.
  */
 int dwf_apply(dwf_handle h, int op, int prec, const void *in, void *out, void *stream);
+
+/* D5 x5 = b5 through the 5D even-odd split (DWF_OP_EO5_PREC; Sec. 2.3's
+ * alternative to the 4D split), FP64: b'_e = D_ee^-1 (b_e - D_eo D_oo^-1 b_o),
+ * CG on the normal equation of the Schur complement from x_e = 0 until the
+ * recursive residual falls below tol ||b'_e||, x_o = D_oo^-1 (b_o - D_oe x_e).
+ * b5, x5: full 5D fields (device, complex double); history (host,
+ * max_iter + 1 doubles, may be NULL) gets ||r||/||b'_e|| per iteration and,
+ * last, the true residual ||b5 - D5 x5|| / ||b5||, which decides the status.
+ * For comparing the two splits' iteration counts; the production solver is
+ * dwf_solve.  Errors: DWF_EINVAL (as dwf_apply, split unavailable),
+ * DWF_ENOGAUGE, DWF_ENOTCONV, DWF_ENONFINITE, DWF_EBREAKDOWN, DWF_ECUDA. */
+int dwf_solve_eo5(dwf_handle h, const void *b5, void *x5, double tol, int max_iter, int *iters, double *history,
+                  void *stream);
 
 /*
  * 4D domain decomposition in time (the operator of eq. even-odd_linear_equation

@@ -388,6 +388,23 @@ static int create_impl(const int dims[4], int Ls, double M0, double mf, const do
     if ((e = cudaMalloc(&h->one, 8)) != cudaSuccess) return fail(e, "cudaMalloc");
     const double one = 1.0;
     if ((e = cudaMemcpy(h->one, &one, 8, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "cudaMemcpy");
+    {   // 5D even-odd split: standard form, c_s = 0 for every s, even Ls
+        bool ok = form == DWF_STANDARD && Ls % 2 == 0;
+        std::vector<double> ia((size_t)Ls);
+        for (int s = 0; s < Ls; ++s) {
+            ok = ok && cs[s] == 0.0;
+            const double a0 = bs[s] * (4.0 - M0) + 1.0;
+            ok = ok && a0 != 0.0;
+            ia[(size_t)s] = ok ? 1.0 / a0 : 0.0;
+        }
+        if (ok) {
+            if ((e = cudaMalloc(&h->inv_a0, (size_t)Ls * sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc");
+            if ((e = cudaMemcpy(h->inv_a0, ia.data(), (size_t)Ls * sizeof(double), cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+                return fail(e, "cudaMemcpy");
+            h->eo5 = 1;
+        }
+    }
     if ((e = launch_build_tables(h->dims, h->nbr, h->eo2lex, 0)) != cudaSuccess) return fail(e, "build_tables");
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "build_tables");
     h->bytes = md.size() * 8 + mf32.size() * 4 + (size_t)2 * h->Vh * 9 * sizeof(int) + ((size_t)h->Vh + 8192) * 8;
@@ -414,6 +431,7 @@ int dwf_destroy(dwf_handle h)
     if (h->counter) cudaFree(h->counter);
     if (h->scal) cudaFree(h->scal);
     if (h->one) cudaFree(h->one);
+    if (h->inv_a0) cudaFree(h->inv_a0);
     delete h;
     return DWF_OK;
 }
@@ -525,6 +543,29 @@ static int apply_impl(dwf_handle h, int op, int prec, const void *in, void *out,
         a2.ymode = 1;
         CK(hop(h, prec, dag, a2, st));
         CK(launch_unpack_eo(prec, y, (double *)out, h->Vh, h->Ls, st));
+        return DWF_OK;
+    }
+    if (op == DWF_OP_EO5_PREC) {   // the 5D split's Schur complement: two whole-matrix applications
+        if (!h->eo5) return dwf_set_error(DWF_EINVAL, "the 5D even-odd split needs the standard form, c = 0 and even Ls");
+        const size_t by = (size_t)h->Ls * h->V * 24 * sizeof(double);
+        void *A = h->ws("e5_a", by, &e), *B = h->ws("e5_b", by, &e), *C = h->ws("e5_c", by, &e);
+        if (!A || !B || !C) return dwf_cuda_error(e, "workspace");
+        CK(launch_eo5(0, in, nullptr, A, h->dims, h->V, h->Ls, h->inv_a0, st));   // x_e
+        h->launches += 1;
+        int rc2;
+        if (!dag) {   // x - D_ee^-1 D_eo D_oo^-1 D_oe x
+            if ((rc2 = apply_impl(h, DWF_OP_FULL5D, prec, A, B, false, st))) return rc2;
+            CK(launch_eo5(1, B, nullptr, B, h->dims, h->V, h->Ls, h->inv_a0, st));
+            if ((rc2 = apply_impl(h, DWF_OP_FULL5D, prec, B, C, false, st))) return rc2;
+            CK(launch_eo5(2, A, C, out, h->dims, h->V, h->Ls, h->inv_a0, st));
+        } else {      // x - D_oe^dag D_oo^-1 D_eo^dag D_ee^-1 x
+            CK(launch_eo5(3, A, nullptr, C, h->dims, h->V, h->Ls, h->inv_a0, st));
+            if ((rc2 = apply_impl(h, DWF_OP_FULL5D, prec, C, B, true, st))) return rc2;
+            CK(launch_eo5(1, B, nullptr, B, h->dims, h->V, h->Ls, h->inv_a0, st));
+            if ((rc2 = apply_impl(h, DWF_OP_FULL5D, prec, B, C, true, st))) return rc2;
+            CK(launch_eo5(4, A, C, out, h->dims, h->V, h->Ls, h->inv_a0, st));
+        }
+        h->launches += 2;
         return DWF_OK;
     }
     return dwf_set_error(DWF_EINVAL, "unknown operator");
@@ -712,6 +753,77 @@ int dwf_slab_cgnr_ring(dwf_handle *hs, int n, const void *const *b, void *const 
 int dwf_apply(dwf_handle h, int op, int prec, const void *in, void *out, void *stream)
 {
     return apply_impl(h, op, prec, in, out, false, (cudaStream_t)stream);
+}
+
+int dwf_solve_eo5(dwf_handle h, const void *b5, void *x5, double tol, int max_iter, int *iters, double *history,
+                  void *stream)
+{
+    int rc = check_common(h, DWF_F64, b5, x5);
+    if (rc) return rc;
+    if (!h->eo5) return dwf_set_error(DWF_EINVAL, "the 5D even-odd split needs the standard form, c = 0 and even Ls");
+    if (!(tol > 0) || max_iter < 1) return dwf_set_error(DWF_EINVAL, "bad tolerance or iteration cap");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    const size_t nel = (size_t)h->Ls * h->V * 12, by = nel * 16;
+    void *r = h->ws("e5_r", by, &e), *z = h->ws("e5_z", by, &e), *p = h->ws("e5_p", by, &e);
+    void *w = h->ws("e5_w", by, &e), *t = h->ws("e5_t", by, &e);
+    double *scr = (double *)h->ws("e5_dot", 257 * sizeof(double), &e);
+    if (!r || !z || !p || !w || !t || !scr) return dwf_cuda_error(e, "workspace");
+    auto dot = [&](const void *a, const void *b, double &res) -> int {
+        CK(launch_cdot(a, b, nel, scr, scr + 256, st));
+        CK(cudaMemcpyAsync(&res, scr + 256, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return std::isfinite(res) ? DWF_OK : dwf_set_error(DWF_ENONFINITE, "non-finite inner product");
+    };
+    auto D = [&](const void *in, void *out, bool dag) {
+        return apply_impl(h, DWF_OP_EO5_PREC, DWF_F64, in, out, dag, st);
+    };
+    // b'_e = D_ee^-1 (b_e - D_eo D_oo^-1 b_o)
+    CK(launch_eo5(1, b5, nullptr, t, h->dims, h->V, h->Ls, h->inv_a0, st));
+    if ((rc = apply_impl(h, DWF_OP_FULL5D, DWF_F64, t, w, false, st))) return rc;
+    CK(launch_eo5(5, b5, w, r, h->dims, h->V, h->Ls, h->inv_a0, st));   // r = b'_e (x_e = 0)
+    CK(cudaMemcpyAsync(t, r, by, cudaMemcpyDeviceToDevice, st));        // t = b'_e, kept
+    CK(cudaMemsetAsync(x5, 0, by, st));
+    double bn2 = 0, gamma = 0, ww = 0, gnew = 0, rr = 0;
+    if ((rc = dot(t, t, bn2))) return rc;
+    if (!(bn2 > 0)) return dwf_set_error(DWF_EINVAL, "zero right-hand side");
+    const double bn = std::sqrt(bn2);
+    if ((rc = D(r, z, true))) return rc;
+    CK(cudaMemcpyAsync(p, z, by, cudaMemcpyDeviceToDevice, st));
+    if ((rc = dot(z, z, gamma))) return rc;
+    int it = 0;
+    double res = 1.0;
+    if (history) history[0] = res;
+    while (res > tol && it < max_iter) {
+        if ((rc = D(p, w, false))) return rc;
+        if ((rc = dot(w, w, ww))) return rc;
+        if (!(ww > 0)) return dwf_set_error(DWF_EBREAKDOWN, "|D p|^2 <= 0");
+        const double alpha = gamma / ww;
+        CK(launch_caxpby(alpha, p, 1.0, x5, nel, st));
+        CK(launch_caxpby(-alpha, w, 1.0, r, nel, st));
+        if ((rc = D(r, z, true))) return rc;
+        if ((rc = dot(z, z, gnew))) return rc;
+        CK(launch_caxpby(1.0, z, gnew / gamma, p, nel, st));
+        gamma = gnew;
+        ++it;
+        if ((rc = dot(r, r, rr))) return rc;
+        res = std::sqrt(rr) / bn;
+        if (history) history[it] = res;
+    }
+    h->launches += 4;
+    // x_o = D_oo^-1 (b_o - D_oe x_e); x5 = x_e + x_o; the true residual of the whole system
+    if ((rc = apply_impl(h, DWF_OP_FULL5D, DWF_F64, x5, w, false, st))) return rc;
+    CK(launch_eo5(6, b5, w, z, h->dims, h->V, h->Ls, h->inv_a0, st));
+    CK(launch_caxpby(1.0, z, 1.0, x5, nel, st));
+    if ((rc = apply_impl(h, DWF_OP_FULL5D, DWF_F64, x5, w, false, st))) return rc;
+    CK(launch_caxpby(1.0, b5, -1.0, w, nel, st));   // w = b5 - D x5
+    double b52 = 0;
+    if ((rc = dot(w, w, rr))) return rc;
+    if ((rc = dot(b5, b5, b52))) return rc;
+    const double tres = std::sqrt(rr / b52);
+    if (iters) *iters = it;
+    if (history) history[it] = tres;
+    return tres <= tol ? DWF_OK : dwf_set_error(DWF_ENOTCONV, "the 5D even-odd CGNR did not reach tol");
 }
 
 int dwf_apply_dag(dwf_handle h, int op, int prec, const void *in, void *out, void *stream)

@@ -299,6 +299,9 @@ struct dwf_ctx {
     int gdims[4] = {0, 0, 0, 0};
     int t0 = 0;
     int ghost = 0;
+    // 5D even-odd split available (standard form, every c_s = 0, even Ls): 1 / a0_s on the device
+    int eo5 = 0;
+    double *inv_a0 = nullptr;
     dwf::NetState *net = nullptr;     // learned preconditioner (dwf_precond_*)
     int *errflag() const { return &scal[7].flags; }
 
@@ -323,6 +326,9 @@ cudaError_t launch_slab_pack_gauge(const dwf_ctx *h, const double *U, cudaStream
 // FP64 complex vectors (n complex numbers): *out = Re <a, b> (part: 256 doubles of scratch); y = a x + b y
 cudaError_t launch_cdot(const void *a, const void *b, size_t n, double *part, double *out, cudaStream_t st);
 cudaError_t launch_caxpby(double a, const void *x, double b, void *y, size_t n, cudaStream_t st);
+// 5D even-odd masks and combinations on canonical full 5D fields (eo5.cu; modes there)
+cudaError_t launch_eo5(int mode, const void *A, const void *C, void *out, const int dims[4], int V, int Ls,
+                       const double *inv_a0, cudaStream_t st);
 }  // namespace dwf
 void dwf_precond_release(dwf_ctx *h);
 

@@ -21,14 +21,15 @@ F64, F32, F16 = 0, 1, 2
 OP_FULL5D, OP_EO_PREC = 0, 1
 PREC = {"f64": F64, "f32": F32, "f16": F16, F64: F64, F32: F32, F16: F16}
 FORM = {"standard": STANDARD, "neff": NEFF, STANDARD: STANDARD, NEFF: NEFF}
-OPS = {"full": OP_FULL5D, "full5d": OP_FULL5D, "eo": OP_EO_PREC, "eo_prec": OP_EO_PREC,
-       OP_FULL5D: OP_FULL5D, OP_EO_PREC: OP_EO_PREC}
+OP_EO5_PREC = 2
+OPS = {"full": OP_FULL5D, "full5d": OP_FULL5D, "eo": OP_EO_PREC, "eo_prec": OP_EO_PREC, "eo5": OP_EO5_PREC,
+       OP_FULL5D: OP_FULL5D, OP_EO_PREC: OP_EO_PREC, OP_EO5_PREC: OP_EO5_PREC}
 
 STATUS = {0: "DWF_OK", 1: "DWF_EINVAL", 2: "DWF_ENOMEM", 3: "DWF_ECUDA", 4: "DWF_ENOTCONV",
           5: "DWF_ENONFINITE", 6: "DWF_ETIMEOUT", 7: "DWF_EBREAKDOWN", 8: "DWF_ENOGAUGE"}
 
 EXPORTED = ["dwf_create", "dwf_create_s", "dwf_destroy", "dwf_strerror", "dwf_last_error", "dwf_set_gauge",
-            "dwf_apply", "dwf_apply_dag", "dwf_source_5d", "dwf_project_4d",
+            "dwf_apply", "dwf_apply_dag", "dwf_solve_eo5", "dwf_source_5d", "dwf_project_4d",
             "dwf_solve_params_default", "dwf_solve", "dwf_propagator_host", "dwf_solve_batch",
             "dwf_fifth_matrix", "dwf_fifth_matrix_host", "dwf_device_bytes", "dwf_time_hop", "dwf_time_iteration", "dwf_spectrum_bounds", "dwf_launch_count",
             "dwf_set_hop_config", "dwf_get_hop_config", "dwf_set_sweep", "dwf_get_sweep",
@@ -123,6 +124,7 @@ def lib():
     L.dwf_slab_cgnr_ring.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_double,
                                      i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double), vp]
     L.dwf_apply_dag.argtypes = [vp, i, i, vp, vp, vp]
+    L.dwf_solve_eo5.argtypes = [vp, vp, vp, d, i, ip, ctypes.POINTER(d), vp]
     L.dwf_source_5d.argtypes = [vp, vp, vp, vp]
     L.dwf_project_4d.argtypes = [vp, vp, vp, vp]
     L.dwf_solve_params_default.argtypes = [ctypes.POINTER(SolveParams)]
@@ -272,6 +274,15 @@ class Operator:
         fn = lib().dwf_apply_dag if dag else lib().dwf_apply
         check(fn(self._h, o, PREC[prec], _ptr(x), _ptr(out), _stream()))
         return out
+
+    def solve_eo5(self, b5, tol=1e-10, max_iter=20000):
+        """FP64 CGNR through the 5D even-odd split (dwf_solve_eo5): x5 and the residual history."""
+        x5 = self._new(self.shape5())
+        its = ctypes.c_int()
+        hist = (ctypes.c_double * (max_iter + 1))()
+        check(lib().dwf_solve_eo5(self._h, _ptr(b5), _ptr(x5), float(tol), int(max_iter), ctypes.byref(its), hist,
+                                  _stream()))
+        return x5, list(hist[:its.value + 1])
 
     def source_5d(self, b4, out=None):
         if out is None:

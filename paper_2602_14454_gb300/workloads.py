@@ -6,6 +6,7 @@
     python -m paper_2602_14454_gb300.workloads alpha      # 16^3x32, Ls 16: iterations against alpha
     python -m paper_2602_14454_gb300.workloads alpha --spectrum   # ... and the condition number
     python -m paper_2602_14454_gb300.workloads delta      # 32^3x64: reliable-update threshold against time
+    python -m paper_2602_14454_gb300.workloads eo5        # 16^3x32 Shamir: the 4D against the 5D even-odd split
 
 Every run uses the seeded generators of ``inputs``; times are wall clock
 around the library call after a synchronisation (device work included).
@@ -212,9 +213,44 @@ def run_delta(args):
     print(json.dumps({"workload": name, "inner_precision": args.inner, "scan": rows}), flush=True)
 
 
+def run_eo5(args):
+    """The two even-odd splits of Sec. 2.3 on one operator where both exist
+    (standard form, c = 0: Shamir b = 1, or a scaled b): FP64 CG on the 4D
+    split's normal equation (dwf_solve) against FP64 CGNR on the 5D split's
+    (dwf_solve_eo5), iterations and time to the same true residual."""
+    import torch
+    from . import dwf, inputs
+    name = "c2_16^3x32_ls16_mobius"
+    w = inputs.WORKLOADS[name]
+    U = _links(w)
+    b4 = torch.from_numpy(inputs.gaussian_4d(w["dims"], w["src_seed"])).cuda()
+    rows = []
+    for bcoef in (1.0, 1.5):
+        op = dwf.Operator(w["dims"], w["Ls"], w["M0"], w["mf"], bcoef, 0.0, form="standard")
+        op.set_gauge(U)
+        b5 = op.source_5d(b4)
+        res = {"b": bcoef, "c": 0.0}
+        for key, fn in (("eo4_fp64_cg", lambda: op.solve(b5, inner_prec="f64", tol=1e-10)),
+                        ("eo4_fp32_mixed", lambda: op.solve(b5, inner_prec="f32", tol=1e-10)),
+                        ("eo5_fp64_cgnr", lambda: op.solve_eo5(b5, tol=1e-10))):
+            fn()
+            _sync()
+            t0 = time.perf_counter()
+            out = fn()
+            _sync()
+            secs = time.perf_counter() - t0
+            if key.startswith("eo5"):
+                res[key] = {"seconds": secs, "iterations": len(out[1]) - 1, "true_residual": out[1][-1]}
+            else:
+                res[key] = {"seconds": secs, "iterations": out[1]["iterations"], "true_residual": out[1]["true_residual"]}
+        rows.append(res)
+        op.close()
+    print(json.dumps({"workload": name + " (standard form, c = 0)", "scan": rows}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["batch", "learned", "large", "alpha", "delta"])
+    ap.add_argument("what", choices=["batch", "learned", "large", "alpha", "delta", "eo5"])
     ap.add_argument("--inner", default="f32", choices=["f16", "f32", "f64"])
     ap.add_argument("--wave", type=int, default=0)
     ap.add_argument("--small", action="store_true",
@@ -233,7 +269,7 @@ def main(argv=None):
     from . import build
     build.build()
     {"batch": run_batch, "learned": run_learned, "large": run_large, "alpha": run_alpha,
-     "delta": run_delta}[args.what](args)
+     "delta": run_delta, "eo5": run_eo5}[args.what](args)
     return 0
 
 
