@@ -141,14 +141,19 @@ def peaks():
         return None
 
 
-HOP_SOURCES = ("hop.cu", "hop_kernels.cuh", "stencil.cuh", "fields.cuh", "tcgen05.cuh", "dwf_internal.h")
+HOP_SOURCES = ("hop.cu", "hop_kernels.cuh", "stencil.cuh", "fields.cuh", "tcgen05.cuh")
 
 
 def hop_source_key():
-    """sha256 (16 hex digits) of every source file the hop kernel is compiled from."""
+    """sha256 (16 hex digits) of the source files the hop kernel is compiled
+    from and of its argument struct (HopArgs in dwf_internal.h)."""
     h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2602_14454_gb300", "csrc")
     for f in HOP_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2602_14454_gb300", "csrc", f), "rb").read())
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    txt = open(os.path.join(csrc, "dwf_internal.h"), "rb").read()
+    a = txt.index(b"struct HopArgs {")
+    h.update(txt[a:txt.index(b"};", a) + 2])
     return h.hexdigest()[:16]
 
 
