@@ -452,7 +452,7 @@ int dwf_get_mix_mode(dwf_handle h, int prec, int *mode);
  * must order each call after the others' work (events or a synchronisation).
  * Every call reads the handle's current state: its links (dwf_set_gauge), its
  * mixing mode and its hop configuration.  The first call on a device may also
- * make the driver load the library's device code that holds the array.
+ * make the CUDA driver load the library's device code that holds the array.
  * in/out: device EO fields as for dwf_apply.
  */
 int dwf_apply_eo_noalloc(dwf_handle h, int prec, int dag, const void *in, void *out, void *stream);
