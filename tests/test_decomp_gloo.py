@@ -53,12 +53,13 @@ def _worker(rank, world, port, out):
     dist.destroy_process_group()
 
 
-def test_split_operator_and_solve_equal_the_unsplit_oracle():
+@pytest.mark.parametrize("world", [2, 4])
+def test_split_operator_and_solve_equal_the_unsplit_oracle(world):
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
     for p in procs:
         p.start()
     res = sorted((q.get(timeout=300) for _ in procs), key=lambda r: r[0])
@@ -73,7 +74,7 @@ def test_split_operator_and_solve_equal_the_unsplit_oracle():
     assert np.abs(yd - wantd).max() <= 1e-14 * np.abs(wantd).max()
     # the split solve: the same iterate as the unsplit CGNR up to the order of the sums
     x = np.concatenate([r[3] for r in res], axis=1)
-    assert res[0][4]["iterations"] == res[1][4]["iterations"]
+    assert all(r[4]["iterations"] == res[0][4]["iterations"] for r in res)
     bt = ref.b_tilde(b5)
     from oracle import dwf as orc
     x_ref, info = orc.cgnr(ref.d_pc, lambda v: ref.d_pc(v, dag=True), bt, tol=1e-12)
