@@ -462,6 +462,14 @@ int dwf_apply_eo_noalloc(dwf_handle h, int prec, int dag, const void *in, void *
  * flag is cleared by this call), else DWF_OK. */
 int dwf_device_status(dwf_handle h, void *stream);
 
+/* Failure-detection probe: one device thread waits on a flag that nothing
+ * sets, bounded by %globaltimer to limit_ns nanoseconds (clamped to 1 s; 0
+ * checks once), then records the timeout in the handle's error flag as every
+ * bounded wait of the library does, and returns; the next dwf_device_status
+ * reports DWF_ETIMEOUT and the context stays usable.  Errors: DWF_EINVAL
+ * (NULL handle, negative limit), DWF_ECUDA. */
+int dwf_wait_probe(dwf_handle h, long long limit_ns, void *stream);
+
 /* Timing of one hop kernel launch in the given precision: runs the EO hop
  * (the dominant kernel of every application of D) `reps` times on stream and
  * writes the mean device time per launch in microseconds, measured with CUDA

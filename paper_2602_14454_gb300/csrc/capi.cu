@@ -826,6 +826,20 @@ int dwf_solve_eo5(dwf_handle h, const void *b5, void *x5, double tol, int max_it
     return tres <= tol ? DWF_OK : dwf_set_error(DWF_ENOTCONV, "the 5D even-odd CGNR did not reach tol");
 }
 
+int dwf_wait_probe(dwf_handle h, long long limit_ns, void *stream)
+{
+    if (!h || limit_ns < 0) return dwf_set_error(DWF_EINVAL, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    int *flag = (int *)h->ws("probe_flag", 16, &e);
+    if (!flag) return dwf_cuda_error(e, "workspace");
+    CK(cudaMemsetAsync(flag, 0, 16, st));
+    const unsigned long long lim = limit_ns > 1000000000ll ? 1000000000ull : (unsigned long long)limit_ns;
+    CK(launch_wait_probe(flag, lim, h->errflag(), st));
+    h->launches += 1;
+    return DWF_OK;
+}
+
 int dwf_apply_dag(dwf_handle h, int op, int prec, const void *in, void *out, void *stream)
 {
     return apply_impl(h, op, prec, in, out, true, (cudaStream_t)stream);

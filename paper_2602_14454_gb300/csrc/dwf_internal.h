@@ -329,6 +329,8 @@ cudaError_t launch_caxpby(double a, const void *x, double b, void *y, size_t n, 
 // 5D even-odd masks and combinations on canonical full 5D fields (eo5.cu; modes there)
 cudaError_t launch_eo5(int mode, const void *A, const void *C, void *out, const int dims[4], int V, int Ls,
                        const double *inv_a0, cudaStream_t st);
+// a bounded wait on a flag that nothing sets (eo5.cu): sets *err bit 0 after limit_ns
+cudaError_t launch_wait_probe(const int *flag, unsigned long long limit_ns, int *err, cudaStream_t st);
 }  // namespace dwf
 void dwf_precond_release(dwf_ctx *h);
 

@@ -1,4 +1,7 @@
-// 5D even-odd preconditioning (the alternative split of Sec. 2.3): sites
+// 5D even-odd preconditioning (the alternative split of Sec. 2.3) and the
+// failure-detection probe of the bounded waits.
+//
+// 5D split: sites
 // (x, s) even when x + y + z + t + s is even.  For the standard form with
 // c_s = 0 and even Ls, D_ee and D_oo are the on-site diagonal a0_s =
 // b_s (4 - M0) + 1, so the Schur complement 1 - D_ee^-1 D_eo D_oo^-1 D_oe is
@@ -61,7 +64,28 @@ __global__ void eo5_kernel(int mode, const double *A, const double *C, double *o
     }
 }
 
+// a single-thread wait on a flag nothing sets, bounded by %globaltimer
+__global__ void wait_probe_kernel(const volatile int *flag, unsigned long long limit_ns, int *err)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    while (*flag == 0) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > limit_ns) {
+            atomicOr(err, 1);
+            return;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_wait_probe(const int *flag, unsigned long long limit_ns, int *err, cudaStream_t st)
+{
+    wait_probe_kernel<<<1, 32, 0, st>>>(flag, limit_ns, err);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_eo5(int mode, const void *A, const void *C, void *out, const int dims[4], int V, int Ls,
                        const double *inv_a0, cudaStream_t st)

@@ -29,7 +29,7 @@ STATUS = {0: "DWF_OK", 1: "DWF_EINVAL", 2: "DWF_ENOMEM", 3: "DWF_ECUDA", 4: "DWF
           5: "DWF_ENONFINITE", 6: "DWF_ETIMEOUT", 7: "DWF_EBREAKDOWN", 8: "DWF_ENOGAUGE"}
 
 EXPORTED = ["dwf_create", "dwf_create_s", "dwf_destroy", "dwf_strerror", "dwf_last_error", "dwf_set_gauge",
-            "dwf_apply", "dwf_apply_dag", "dwf_solve_eo5", "dwf_source_5d", "dwf_project_4d",
+            "dwf_apply", "dwf_apply_dag", "dwf_solve_eo5", "dwf_wait_probe", "dwf_source_5d", "dwf_project_4d",
             "dwf_solve_params_default", "dwf_solve", "dwf_propagator_host", "dwf_solve_batch",
             "dwf_fifth_matrix", "dwf_fifth_matrix_host", "dwf_device_bytes", "dwf_time_hop", "dwf_time_iteration", "dwf_spectrum_bounds", "dwf_launch_count",
             "dwf_set_hop_config", "dwf_get_hop_config", "dwf_set_sweep", "dwf_get_sweep",
@@ -125,6 +125,7 @@ def lib():
                                      i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double), vp]
     L.dwf_apply_dag.argtypes = [vp, i, i, vp, vp, vp]
     L.dwf_solve_eo5.argtypes = [vp, vp, vp, d, i, ip, ctypes.POINTER(d), vp]
+    L.dwf_wait_probe.argtypes = [vp, ctypes.c_longlong, vp]
     L.dwf_source_5d.argtypes = [vp, vp, vp, vp]
     L.dwf_project_4d.argtypes = [vp, vp, vp, vp]
     L.dwf_solve_params_default.argtypes = [ctypes.POINTER(SolveParams)]
@@ -274,6 +275,10 @@ class Operator:
         fn = lib().dwf_apply_dag if dag else lib().dwf_apply
         check(fn(self._h, o, PREC[prec], _ptr(x), _ptr(out), _stream()))
         return out
+
+    def wait_probe(self, limit_ns):
+        """A bounded device wait that runs out (failure-detection probe, dwf_wait_probe)."""
+        check(lib().dwf_wait_probe(self._h, int(limit_ns), _stream()))
 
     def solve_eo5(self, b5, tol=1e-10, max_iter=20000):
         """FP64 CGNR through the 5D even-odd split (dwf_solve_eo5): x5 and the residual history."""

@@ -351,3 +351,24 @@ def test_sweep_argument_checks():
     op3.set_sweep("f32", -2)              # a z-plane pair of 32x32 at Ls 16 in FP32: 1.9 MB
     assert op3.sweep("f32") == 8
     assert op3.sweep("f16") == 0
+
+
+@pytest.mark.parametrize("limit_ns", [0, 1000, 200000])
+def test_bounded_wait_that_runs_out_is_reported(limit_ns):
+    """A bounded device wait on a flag that nothing sets (dwf_wait_probe) gives
+    up after its limit and records it like every bounded wait of the library:
+    the next status check reports DWF_ETIMEOUT once, and the context stays
+    usable (the operator still matches the oracle)."""
+    from paper_2602_14454_gb300 import dwf
+    dims, Ls = (2, 2, 2, 4), 4
+    op, ref = make_pair(dims, Ls, 1.8, 0.1, 1.0, 0.0, "standard", 1.0, seed=97)
+    op.device_status()
+    op.wait_probe(limit_ns)
+    with pytest.raises(dwf.DwfError) as e:
+        op.device_status()
+    assert e.value.status == 6
+    op.device_status()   # the report cleared the flag
+    x = inputs.gaussian_5d(dims, Ls, 98)
+    assert rel(to_np(op.apply(to_gpu(x), op="full", prec="f64")), ref.apply(x)) < 1e-12
+    with pytest.raises(dwf.DwfError):
+        op.wait_probe(-1)
