@@ -35,6 +35,7 @@ namespace dwf_detail {
 HopArgs hop_args(dwf_ctx *h, int prec, int out_par, FieldRef in, FieldRef out, int post);
 HopArgs with_programs(dwf_ctx *h, int prec, const HopArgs &a0);
 cudaError_t hop(dwf_ctx *h, int prec, bool dag, const HopArgs &a, cudaStream_t st);
+cudaError_t hop_cg_plain(dwf_ctx *h, int prec, bool dag, const HopArgs &a, cudaStream_t st);
 cudaError_t mix(dwf_ctx *h, int prec, FieldRef in, FieldRef out, int id, cudaStream_t st);
 RedArgs red(dwf_ctx *h, int op, CgScalars *scal);
 }  // namespace dwf_detail
@@ -171,7 +172,9 @@ cudaError_t inner_iteration(dwf_ctx *h, const Bufs &B, cudaStream_t st)
     h->launches += 1;
     if ((e = launch_cg_update(B.ps, I.ue, st)) != cudaSuccess) return e;
     for (int k = 0; k < 4; ++k)
-        if ((e = hop(h, B.ps, k >= 2, I.k[k], st)) != cudaSuccess) return e;
+        if ((e = (k == 0 || k == 2) ? hop_cg_plain(h, B.ps, k >= 2, I.k[k], st) : hop(h, B.ps, k >= 2, I.k[k], st)) !=
+            cudaSuccess)
+            return e;
     return cudaSuccess;
 }
 
@@ -1387,7 +1390,7 @@ int dwf_time_iteration(dwf_handle h, int prec, int reps, int flush_l2, double *u
         CK(launch_cg_update(prec, I.ue, st));
         CK(cudaEventRecord(ev[1], st));
         for (int k = 0; k < 4; ++k) {
-            CK(hop(h, prec, k >= 2, I.k[k], st));
+            CK((k == 0 || k == 2) ? hop_cg_plain(h, prec, k >= 2, I.k[k], st) : hop(h, prec, k >= 2, I.k[k], st));
             CK(cudaEventRecord(ev[k + 2], st));
         }
         CK(cudaEventSynchronize(ev[5]));
